@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Geodesic Sinkhorn benchmark on one GB300 (or N replicas, one per GPU, under torchrun).
+
+Workload (one "step" = the whole hot path once): 100,000 points on a 10-d latent manifold in R^50
+(latents N(0, I_10) through a fixed random 2-layer tanh map, isotropic noise 0.01), k = 15
+symmetric kNN graph with Gaussian weights (sigma = median kNN distance), the Chebyshev heat
+filter with K = 30, t = 5 inside 500 Sinkhorn iterations between two softmax bumps, and the FP64
+distance reduction.  Metric: Sinkhorn iterations per second (whole job: graph build included).
+
+Also reported: the roofline of the fused Chebyshev order kernel inside the timed region, an
+HBM-bound filter measurement on the 200,000-point cluster workload with 32 right-hand sides,
+the end-to-end number with host buffers, clocks during the timed region, launch counts and the
+FP64 oracle timed on the host cores (bounded sample, scaled).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2211_00805_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Sinkhorn iters/s & SpMM HBM GB/s, batched/adjoint vs plain at rtol 1e-4"
+UNIT = "Sinkhorn iters/s"
+WORKLOAD = dict(name="manifold-100k-R50: Geodesic Sinkhorn distance, graph build included",
+                n=100_000, latent=10, ambient=50, seed=2, k=15, K=30, t=5.0, iters=500)
+HBM_CASE = dict(name="clusters-200k-R30, B=32 heat filter", n=200_000, dim=30, m=32, k=10, K=40,
+                t=10.0, seed=3)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the HBM-bound filter case")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ algorithmic bytes
+def apply_bytes(n: int, nnz: int, K: int, B: int, last_streams: int) -> int:
+    """Bytes one K-order filter apply must move: each order reads the CSR (4 B column + 4 B value
+    per nonzero, 4 B per row pointer) and gathers the previous block once (4nB); order 1 also
+    writes T_1 and y (12nB in total with the gather); orders 2..K-1 read T_{k-2} and y and write
+    T_k and y (20nB with the gather); the last order streams `last_streams` n x B blocks."""
+    graph = 8 * nnz + 4 * (n + 1)
+    if K == 1:
+        return graph + 4 * n * B * last_streams
+    return K * graph + 12 * n * B + (K - 2) * 20 * n * B + 4 * n * B * last_streams
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, or None if the kernel source changed
+    since the counters were taken (the summary records the source hash it was taken on)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    src = os.path.join(ROOT, "paper_2211_00805_gb300", "csrc", "cheb.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel_tag and parts[1] == h:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------- CPU oracle
+def oracle_sample(cfg=WORKLOAD, small_n=10_000, knn_rows=2400, iters_small=150):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload, scaled to the full
+    step.  kNN: ``knn_rows`` query rows of the full point cloud (every row costs the same n d
+    work), scaled by n / rows.  Graph assembly and Sinkhorn iterations: the same generator at
+    ``small_n`` points; the assembly scaled by n / small_n, one iteration by the edge-count ratio
+    (each iteration is 2 K sparse products over all edges), times the full iteration count."""
+    import oracle
+    X, Z = W.tanh_manifold(cfg["n"], cfg["latent"], cfg["ambient"], cfg["seed"])
+    X64 = X.astype(np.float64)
+    rows = np.random.default_rng(0).choice(cfg["n"], knn_rows, replace=False)
+    t0 = time.perf_counter()
+    oracle.knn(X64, cfg["k"], rows=rows)
+    t_knn = (time.perf_counter() - t0) * cfg["n"] / knn_rows
+
+    ps = W.manifold_pair(n=small_n, latent=cfg["latent"], ambient=cfg["ambient"], seed=cfg["seed"],
+                         k=cfg["k"], K=cfg["K"], t=cfg["t"], iters=iters_small)
+    Xs = ps.X.astype(np.float64)
+    idx, dist = oracle.knn(Xs, ps.k)
+    t0 = time.perf_counter()
+    s = oracle.median_sigma(dist)
+    rp, col, A = oracle.affinity_graph(idx, dist, s)
+    deg, L = oracle.laplacian(rp, col, A)
+    Ls = oracle.shifted(L)
+    t_graph = (time.perf_counter() - t0) * cfg["n"] / small_n
+    b = oracle.cheb_coefficients(ps.t, ps.K)
+    t0 = time.perf_counter()
+    oracle.sinkhorn(Ls, b, ps.a.astype(np.float64), ps.b.astype(np.float64), ps.t, iters_small)
+    t_iter_small = (time.perf_counter() - t0) / iters_small
+    nnz_small = len(col)
+    nnz_full_est = nnz_small * cfg["n"] / small_n
+    t_iters = t_iter_small * nnz_full_est / nnz_small * cfg["iters"]
+    total = t_knn + t_graph + t_iters
+    sample = (f"oracle kNN on {knn_rows} of {cfg['n']} query rows (x{cfg['n'] / knn_rows:.0f}); graph "
+              f"assembly + {iters_small} Sinkhorn iterations of the same generator at n={small_n} "
+              f"(nnz={nnz_small}), scaled by n and by nnz to n={cfg['n']}, {cfg['iters']} iterations; "
+              f"est. full step {total:.1f} s = kNN {t_knn:.1f} + graph {t_graph:.1f} + "
+              f"iterations {t_iters:.1f}")
+    return {"value": cfg["iters"] / total, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": sample, "est_step_s": total}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample()
+    vals, cb = [], None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cb = oracle_sample()
+        vals.append(cb["est_step_s"])
+    wall = time.perf_counter() - t0
+    step_s = statistics.mean(vals)
+    value = WORKLOAD["iters"] / step_s
+    cb = dict(cb, value=value)
+    cb.pop("est_step_s", None)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD["name"], **{k: v for k, v in WORKLOAD.items() if k != "name"}},
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2211_00805_gb300 import binding as gs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gs.Context(local_rank, stream)
+    cfg = WORKLOAD
+    p = W.manifold_pair(n=cfg["n"], latent=cfg["latent"], ambient=cfg["ambient"], seed=cfg["seed"],
+                        k=cfg["k"], K=cfg["K"], t=cfg["t"], iters=cfg["iters"])
+    X = torch.from_numpy(p.X).to(dev)
+    a = torch.from_numpy(p.a).to(dev)
+    b = torch.from_numpy(p.b).to(dev)
+    n = cfg["n"]
+    u = torch.empty(n, dtype=torch.float32, device=dev)
+    v = torch.empty(n, dtype=torch.float32, device=dev)
+    dist = torch.empty(2, dtype=torch.float64, device=dev)
+    itd = torch.empty(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(Xd, ad, bd, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        g = gs.gs_build_graph(ctx, Xd, cfg["k"])
+        if ev is not None:
+            ev[1].record(stream)
+        gs.gs_sinkhorn(ctx, g, ad, bd, cfg["t"], cfg["K"], cfg["iters"], u=u, v=v, dist=dist,
+                       iters_done=itd)
+        if ev is not None:
+            ev[2].record(stream)
+        nnz = g.nnz
+        g.close()
+        return nnz
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for i in range(args.warmup):
+        nnz = step(X, a, b)
+    gs.gs_sync(ctx)
+    w2 = float(dist[0].item())
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    l0 = gs.gs_launch_count(ctx)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        flush.fill_(float(i))  # L2 flush: 256 MB write between steps
+        nnz = step(X, a, b, evs[i])
+    t_end.record(stream)
+    barrier()
+    launches = gs.gs_launch_count(ctx) - l0
+    clk = clocks.stop() if clocks else None
+    gs.gs_sync(ctx)
+    total_ms = t_start.elapsed_time(t_end)
+    graph_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    sink_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = cfg["iters"] * args.steps * world / (total_ms / 1e3)
+
+    # roofline of the fused Chebyshev order kernel inside the Sinkhorn loop (B = 1)
+    K = cfg["K"]
+    per_apply = apply_bytes(n, nnz, K, 1, last_streams=6)  # gather, T_{K-2}, y, num, out, xnext
+    orders = 2 * K * cfg["iters"]
+    sink_s = statistics.mean(sink_ms) / 1e3
+    achieved = 2 * cfg["iters"] * per_apply / sink_s / 1e9
+    peak, peak_kind = measured_peaks()
+    tr = ncu_traffic("order_b1_manifold100k")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": tr,
+                "kernel": "order_b1 (fused Chebyshev order, B=1) in the Sinkhorn loop",
+                "bytes_per_launch": per_apply / K, "launch_us": sink_s / orders * 1e6,
+                "peak_kind": f"{peak_kind} hbm_gbs",
+                "note": "working set (~19 MB) is L2-resident; see spmm_hbm for the HBM-bound case"}
+
+    extras = {}
+    if not args.no_extras:
+        extras["spmm_hbm"] = hbm_case(gs, ctx, dev, stream, peak, peak_kind)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    Xh = torch.from_numpy(p.X).pin_memory()
+    ah = torch.from_numpy(p.a).pin_memory()
+    bh = torch.from_numpy(p.b).pin_memory()
+    uh = torch.empty(n, dtype=torch.float32).pin_memory()
+    vh = torch.empty(n, dtype=torch.float32).pin_memory()
+    dh = torch.empty(2, dtype=torch.float64).pin_memory()
+    Xd, ad, bd = torch.empty_like(X), torch.empty_like(a), torch.empty_like(b)
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        ad.copy_(ah, non_blocking=True)
+        bd.copy_(bh, non_blocking=True)
+        step(Xd, ad, bd)
+        uh.copy_(u, non_blocking=True)
+        vh.copy_(v, non_blocking=True)
+        dh.copy_(dist, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    h2d = Xh.numel() * 4 + ah.numel() * 4 + bh.numel() * 4
+    d2h = uh.numel() * 4 + vh.numel() * 4 + dh.numel() * 8
+    e2e = {"value": cfg["iters"] * args.steps * world / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+        cpu.pop("est_step_s", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded tanh-manifold generator; no dataset)",
+            "config": {"workload": cfg["name"], "n": n, "d": cfg["ambient"], "k": cfg["k"],
+                       "nnz": nnz, "K": K, "t": cfg["t"], "iters": cfg["iters"],
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "256 MB buffer written between timed steps",
+                       "graph_build_ms": statistics.mean(graph_ms),
+                       "sinkhorn_ms": statistics.mean(sink_ms),
+                       "sinkhorn_only_iters_per_s": cfg["iters"] / sink_s,
+                       "W2": w2},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps,
+            "clocks": clk,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+
+
+def hbm_case(gs, ctx, dev, stream, peak, peak_kind, reps=5):
+    """Heat filter with B = 32 columns on the 200k-point cluster graph (149 MB per order, above
+    L2): achieved algorithmic GB/s of the fused order kernel."""
+    import torch
+    c = HBM_CASE
+    X, labels = W.cluster_curves(c["n"], c["dim"], seed=c["seed"])
+    M = W.cluster_unions(labels, c["m"], 3, c["seed"] + 1000)
+    g = gs.gs_build_graph(ctx, torch.from_numpy(X).to(dev), c["k"])
+    V = torch.from_numpy(M).to(dev)
+    Y = torch.empty_like(V)
+    for _ in range(2):
+        gs.gs_heat_apply(ctx, g, c["t"], c["K"], V, out=Y)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        gs.gs_heat_apply(ctx, g, c["t"], c["K"], V, out=Y)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    gs.gs_sync(ctx)
+    s = e0.elapsed_time(e1) / 1e3 / reps
+    byts = apply_bytes(c["n"], g.nnz, c["K"], c["m"], last_streams=4)  # gather, T_{K-2}, y, out
+    ach = byts / s / 1e9
+    out = {"workload": c["name"], "n": c["n"], "nnz": g.nnz, "B": c["m"], "K": c["K"],
+           "apply_ms": s * 1e3, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "bytes_per_apply": byts, "peak_kind": f"{peak_kind} hbm_gbs",
+           "traffic": ncu_traffic("order_blk_clusters200k_B32")}
+    g.close()
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

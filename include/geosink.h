@@ -1,0 +1,192 @@
+/*
+ * geosink.h -- C ABI of the GB300 Geodesic Sinkhorn library (libgeosink.so).
+ *
+ * Geodesic Sinkhorn (arXiv 2211.00805) computes entropic optimal transport on a data graph by
+ * replacing the Gibbs kernel with the heat kernel H_t = exp(-t L) of the graph Laplacian
+ * (Sec. 3.2-3.4), applied through a degree-K Chebyshev polynomial p_K(L, t) (Sec. 3.5) inside
+ * the Sinkhorn scaling loop (Algorithm 1) and the fixed-support barycenter (Sec. 3.3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Array arguments are DEVICE pointers owned by the caller (e.g. torch.empty(..., "cuda")),
+ *    unless the parameter says "host".  Blocks are row-major: V[n, B] has V[i * B + c].
+ *    Inputs and outputs must not alias unless stated.  Floating-point arrays are FP32 unless
+ *    the type says double.
+ *  - Every call is enqueued on the context's stream and returns without waiting for the GPU,
+ *    except gs_sync, gs_graph_info and the graph constructors (which wait for sizes they must
+ *    know on the host).  Scalar results are written to device memory.
+ *  - The return value reports argument errors (GS_ERR_ARG), CUDA launch/allocation errors
+ *    (GS_ERR_CUDA / GS_ERR_OOM) and unsupported shapes (GS_ERR_UNSUPPORTED) immediately.
+ *    Conditions found by the kernels themselves (non-finite scalings, a loop that did not reach
+ *    its tolerance, a bounded wait that ran out) are recorded in the context and returned by the
+ *    next gs_sync.  gs_last_error gives a message for the last non-OK status.
+ *  - Graph handles (gs_graph) and contexts (gs_ctx) are owned by the library; free them with
+ *    gs_graph_destroy / gs_destroy.  A graph may be used with any context on the same device.
+ *  - Nothing is thread-safe per context: one host thread at a time per gs_ctx.
+ *  - Working memory: the context keeps one device workspace that grows on demand (cudaMalloc).
+ *    A call that needs a larger workspace while its stream is being captured into a CUDA graph
+ *    fails with GS_ERR_UNSUPPORTED; run the same call once before capturing.
+ *
+ * Notation (mapping to the paper)
+ * -------------------------------
+ *  P = D^{-1/2} A D^{-1/2}, L = I - P (symmetric-normalised Laplacian, spectrum in [0, 2]),
+ *  Ls = L - Id = -P (the Chebyshev argument of Sec. 3.5).  Source/target marginals a, b are the
+ *  paper's mu, nu; scalings u, v are the paper's v, w; vertex weights vol are the paper's a
+ *  (Algorithm 1).  Diffusion time t relates to the regularisation by lambda = 4t (Sec. 3.2).
+ */
+#ifndef GEOSINK_H
+#define GEOSINK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_ARG = 1,            /* invalid argument (null pointer, size, range)                  */
+    GS_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed                   */
+    GS_ERR_OOM = 3,            /* device allocation failed                                      */
+    GS_ERR_NONFINITE = 4,      /* a scaling, filter output or distance became inf/NaN/negative  */
+    GS_ERR_NOT_CONVERGED = 5,  /* eps > 0 and the marginal error never fell below eps           */
+    GS_ERR_TIMEOUT = 6,        /* a bounded in-kernel wait gave up                              */
+    GS_ERR_UNSUPPORTED = 7     /* shape or state this build does not handle                     */
+} gs_status;
+
+typedef struct gs_ctx gs_ctx;
+typedef struct gs_graph gs_graph;
+
+/* ------------------------------------------------------------------------------ context --- */
+
+/* Create a context on CUDA device `device` that enqueues on `stream` (a cudaStream_t passed as
+ * void*, NULL = the legacy default stream).  *ctx receives the handle.  Errors: GS_ERR_ARG for
+ * a null ctx or bad device, GS_ERR_CUDA / GS_ERR_OOM. */
+gs_status gs_create(gs_ctx **ctx, int device, void *stream);
+
+/* Free the context and its workspace (waits for its stream first). NULL is accepted. */
+gs_status gs_destroy(gs_ctx *ctx);
+
+/* Switch the stream later calls enqueue on (cudaStream_t as void*). */
+gs_status gs_set_stream(gs_ctx *ctx, void *stream);
+
+/* Message of the last non-OK status returned on this context ("" if none).  The string is
+ * owned by the context and valid until the next call on it. */
+const char *gs_last_error(const gs_ctx *ctx);
+
+/* Wait for the context's stream, then return and clear the status recorded by kernels since
+ * the last gs_sync: GS_ERR_NONFINITE, GS_ERR_NOT_CONVERGED, GS_ERR_TIMEOUT, or GS_OK. */
+gs_status gs_sync(gs_ctx *ctx);
+
+/* Grow the workspace to at least `bytes` now (for use before CUDA-graph capture). */
+gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
+
+/* Host query: number of GPU kernels this context has enqueued so far (a replayed CUDA graph
+ * counts each of its kernel nodes).  Used to report launch counts; *count must not be NULL. */
+gs_status gs_launch_count(const gs_ctx *ctx, int64_t *count);
+
+/* ------------------------------------------------------------------------ coefficients --- */
+
+/* Chebyshev coefficients of the heat kernel (Sec. 3.5: "evaluated with the Bessel function").
+ * HOST call.  Writes c[0..K] (host array of K+1 doubles) such that
+ *     exp(-t L) ~ sum_{k=0}^{K} c[k] T_k(P),   c[0] = e^{-t} I_0(t),  c[k] = 2 e^{-t} I_k(t),
+ * the expansion of Sec. 3.5 in the polynomial variable P = Id - L (T_k(L - Id) = (-1)^k T_k(P)).
+ * I_k is the modified Bessel function of the first kind.  Requires t > 0, K >= 0.
+ * Errors: GS_ERR_ARG. */
+gs_status gs_cheb_coeffs(double t, int K, double *c);
+
+/* ----------------------------------------------------------------------------- graphs --- */
+
+/* k nearest neighbours of every point (the common graph of Sec. 4 is built from them).
+ * X: [n, d] points.  idx: [n, k] int32 neighbour indices, dist: [n, k] Euclidean distances, both
+ * ordered by increasing distance, the point itself excluded, ties broken by lower index.
+ * Distances are screened in FP32 and the candidates re-ranked with FP64 direct differences.
+ * Requires 2 <= n < 2^31, 1 <= d <= 1024, 1 <= k <= 24, k < n.  Errors: GS_ERR_ARG. */
+gs_status gs_knn(gs_ctx *ctx, const float *X, int64_t n, int d, int k, int32_t *idx, float *dist);
+
+/* Build the graph of Sec. 4 from a point cloud: symmetric kNN graph (union of the directed kNN
+ * edges), Gaussian affinities A_ij = exp(-d_ij^2 / sigma^2) (sigma <= 0 selects sigma = median of
+ * the n*k kNN distances), degrees D_ii = sum_j A_ij and P = D^{-1/2} A D^{-1/2} (Sec. 3.4).
+ * Same limits as gs_knn.  Waits for the stream (the edge count sizes the graph).
+ * *out receives a library-owned handle.  Errors: GS_ERR_ARG, GS_ERR_OOM, GS_ERR_CUDA. */
+gs_status gs_build_graph(gs_ctx *ctx, const float *X, int64_t n, int d, int k, float sigma,
+                         gs_graph **out);
+
+/* Build the operator from a caller-supplied symmetric weighted adjacency in CSR form
+ * (device rowptr [n+1] int64, col [nnz] int32 ascending per row, w [nnz] FP32 >= 0, no self-
+ * loops, every row non-empty).  Degrees and P are formed as in gs_build_graph.  Symmetry is the
+ * caller's promise and is not checked.  Errors: GS_ERR_ARG (n < 2, nnz >= 2^31), GS_ERR_OOM. */
+gs_status gs_graph_from_csr(gs_ctx *ctx, int64_t n, const int64_t *rowptr, const int32_t *col,
+                            const float *w, gs_graph **out);
+
+/* Host query of a graph's size: n nodes, nnz stored off-diagonal entries, sigma used (0 for
+ * graphs from gs_graph_from_csr).  Any output pointer may be NULL. */
+gs_status gs_graph_info(const gs_graph *g, int64_t *n, int64_t *nnz, double *sigma);
+
+/* Copy the graph out in CSR form, rows in node order and columns ascending (device arrays:
+ * rowptr [n+1] int64, col [nnz] int32, A [nnz] FP32 affinities, P [nnz] FP32 normalised
+ * weights).  Any of the output pointers may be NULL.  Used to check edge sets against a
+ * reference. */
+gs_status gs_graph_export_csr(gs_ctx *ctx, const gs_graph *g, int64_t *rowptr, int32_t *col,
+                              float *A, float *P);
+
+/* Free a graph (waits for the device). NULL is accepted. */
+gs_status gs_graph_destroy(gs_graph *g);
+
+/* ------------------------------------------------------------------------ heat filter --- */
+
+/* Y = p_K(L, t) V (Sec. 3.5): the degree-K Chebyshev approximation of exp(-tL) applied to the
+ * B columns of V[n, B], through the recurrence T_{k+1} = 2 P T_k - T_{k-1} with the running sum
+ * y += c_k T_k fused into each of the K sparse products.  V and Y: [n, B] FP32, must not alias.
+ * Requires t > 0, 1 <= K <= 10000, and 1 <= B <= 256, or B a multiple of 4 up to 1024 with V on
+ * a 16-byte boundary (such blocks are read as float4).  Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED. */
+gs_status gs_heat_apply(gs_ctx *ctx, const gs_graph *g, double t, int K, const float *V, int B,
+                        float *Y);
+
+/* ----------------------------------------------------------------------------- Sinkhorn --- */
+
+/* Algorithm 1 (Geodesic Sinkhorn): v <- 1; repeat { u <- a / p_K(vol * v); v <- b / p_K(vol * u) }
+ * (the division is fused into the last Chebyshev order), then the distance reduction
+ *     dist[0] = W^2 = 4t sum_i vol_i (a_i ln u_i + b_i ln v_i)      (Algorithm 1's return value)
+ *     dist[1] = W   = sqrt(W^2)                                     (Definition 4.1)
+ * accumulated in FP64 (0 ln 0 := 0; a_i = 0 gives u_i = 0).
+ *   a, b   : [n] non-negative marginals (the caller normalises them; not checked on device)
+ *   vol    : [n] vertex weights, NULL = all ones
+ *   eps    : > 0 -> stop at the first iteration j, j a multiple of 10, whose marginal error
+ *            sum_i |u_i (p_K(vol * v))_i - a_i| is below eps (GS_ERR_NOT_CONVERGED at gs_sync if
+ *            none); <= 0 -> run exactly `iters` iterations
+ *   u, v   : [n] outputs (scalings after the last iteration done)
+ *   dist   : [2] double output (device), may be NULL
+ *   iters_done : [1] int32 output (device), may be NULL
+ * Non-finite or negative scalings are reported as GS_ERR_NONFINITE at gs_sync.
+ * Requires t > 0, K >= 1, iters >= 1.  Errors: GS_ERR_ARG. */
+gs_status gs_sinkhorn(gs_ctx *ctx, const gs_graph *g, const float *a, const float *b,
+                      const float *vol, double t, int K, double eps, int iters, float *u, float *v,
+                      double *dist, int32_t *iters_done);
+
+/* Geodesic Sinkhorn distance only (Definition 4.1): gs_sinkhorn with the scalings kept in the
+ * context's workspace.  dist: [2] double (device) receiving W^2 and W. */
+gs_status gs_distance(gs_ctx *ctx, const gs_graph *g, const float *a, const float *b,
+                      const float *vol, double t, int K, double eps, int iters, double *dist);
+
+/* ---------------------------------------------------------------------------- barycenter --- */
+
+/* Fixed-support Wasserstein barycenter (Sec. 3.3) by iterative Bregman projections with the
+ * heat filter as kernel: v_i <- 1; repeat `iters` times { w_i <- mu_i / p_K(vol * v_i);
+ * d_i <- v_i * p_K(vol * w_i); mu <- prod_i d_i^alpha_i; v_i <- v_i * mu / d_i }.  All m
+ * distributions move through the filter as one [n, m] block; the geometric mean is a log-sum
+ * accumulated in FP64 inside the last Chebyshev order.
+ *   M      : [n, m] input distributions (column i is mu_i)
+ *   alpha  : [m] double weights (device), >= 0, summing to 1 (not checked on device)
+ *   vol    : [n] vertex weights or NULL
+ *   mu     : [n] output barycenter
+ *   v_state: [n, m] output scalings v_i after the last iteration, may be NULL
+ * Requires 1 <= m <= 1024.  Errors: GS_ERR_ARG. */
+gs_status gs_barycenter(gs_ctx *ctx, const gs_graph *g, const float *M, int m, const double *alpha,
+                        const float *vol, double t, int K, int iters, float *mu, float *v_state);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEOSINK_H */

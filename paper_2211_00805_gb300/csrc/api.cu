@@ -1,0 +1,321 @@
+// C-ABI entry points of libgeosink (declared in include/geosink.h): argument checks, context
+// and workspace management, and dispatch to the kernel drivers.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+// ------------------------------------------------------------------------------ helpers
+gs_status gs_fail(gs_ctx* ctx, gs_status st, const std::string& msg)
+{
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+gs_status gs_cuda_check(gs_ctx* ctx, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return GS_OK;
+    const gs_status st = (e == cudaErrorMemoryAllocation) ? GS_ERR_OOM : GS_ERR_CUDA;
+    return gs_fail(ctx, st, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+gs_status gs_ws_ensure(gs_ctx* ctx, size_t bytes)
+{
+    if (bytes <= ctx->ws_bytes) return GS_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->stream, &cap);
+    if (cap != cudaStreamCaptureStatusNone)
+        return gs_fail(ctx, GS_ERR_UNSUPPORTED,
+                       "workspace must grow while the stream is being captured; run the call once "
+                       "before capture or call gs_reserve");
+    gs_status st = gs_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "workspace grow (sync)");
+    if (st != GS_OK) return st;
+    gs_graph_cache_clear(ctx);  // captured graphs point into the old workspace
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    const size_t want = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaMalloc(&ctx->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return gs_fail(ctx, GS_ERR_OOM, "workspace allocation failed");
+    }
+    ctx->ws_bytes = want;
+    return GS_OK;
+}
+
+namespace {
+
+bool bad_ptr(const void* p) { return p == nullptr; }
+
+gs_status check_graph(gs_ctx* ctx, const gs_graph* g)
+{
+    if (!g) return gs_fail(ctx, GS_ERR_ARG, "null graph");
+    if (g->device != ctx->device) return gs_fail(ctx, GS_ERR_ARG, "graph lives on another device");
+    return GS_OK;
+}
+
+gs_status check_filter(gs_ctx* ctx, double t, int K)
+{
+    if (!(t > 0.0) || !isfinite(t)) return gs_fail(ctx, GS_ERR_ARG, "t must be finite and > 0");
+    if (K < 1 || K > 10000) return gs_fail(ctx, GS_ERR_ARG, "K must be in [1, 10000]");
+    return GS_OK;
+}
+
+gs_status enter(gs_ctx* ctx)
+{
+    if (!ctx) return GS_ERR_ARG;
+    ctx->err.clear();
+    return gs_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+}
+
+size_t sinkhorn_ws_bytes(int64_t n)
+{
+    WsPlan p;
+    for (int i = 0; i < 4; ++i) p.add(sizeof(float) * n);
+    p.add(sizeof(double) * 2);
+    p.add(sizeof(int) * 2);
+    p.add(sizeof(double) * gs_reduce_blocks());
+    return p.total;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ context
+extern "C" gs_status gs_create(gs_ctx** out, int device, void* stream)
+{
+    if (!out) return GS_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return GS_ERR_ARG;
+    }
+    gs_ctx* ctx = new gs_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    gs_status st = gs_cuda_check(ctx, cudaSetDevice(device), "cudaSetDevice");
+    if (st == GS_OK) st = gs_cuda_check(ctx, cudaMalloc(&ctx->flags, 4 * sizeof(int)), "flags");
+    if (st == GS_OK) st = gs_cuda_check(ctx, cudaMemset(ctx->flags, 0, 4 * sizeof(int)), "flags");
+    if (st == GS_OK)
+        st = gs_cuda_check(ctx, cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device),
+                           "SM count");
+    if (st != GS_OK) {
+        gs_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_destroy(gs_ctx* ctx)
+{
+    if (!ctx) return GS_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    gs_graph_cache_clear(ctx);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->flags) cudaFree(ctx->flags);
+    delete ctx;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_set_stream(gs_ctx* ctx, void* stream)
+{
+    if (!ctx) return GS_ERR_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return GS_OK;
+}
+
+extern "C" const char* gs_last_error(const gs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" gs_status gs_sync(gs_ctx* ctx)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = gs_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronize")) != GS_OK)
+        return st;
+    int f = 0;
+    if ((st = gs_cuda_check(ctx, cudaMemcpy(&f, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost),
+                            "reading status")) != GS_OK)
+        return st;
+    cudaMemset(ctx->flags, 0, sizeof(int));
+    if (f & GS_FLAG_TIMEOUT) return gs_fail(ctx, GS_ERR_TIMEOUT, "a bounded in-kernel wait gave up");
+    if (f & GS_FLAG_NONFINITE)
+        return gs_fail(ctx, GS_ERR_NONFINITE, "non-finite or non-positive value in a scaling or filter output");
+    if (f & GS_FLAG_NOT_CONVERGED)
+        return gs_fail(ctx, GS_ERR_NOT_CONVERGED, "marginal error never fell below eps");
+    return GS_OK;
+}
+
+extern "C" gs_status gs_reserve(gs_ctx* ctx, int64_t bytes)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if (bytes < 0) return gs_fail(ctx, GS_ERR_ARG, "negative size");
+    return gs_ws_ensure(ctx, (size_t)bytes);
+}
+
+extern "C" gs_status gs_launch_count(const gs_ctx* ctx, int64_t* count)
+{
+    if (!ctx || !count) return GS_ERR_ARG;
+    *count = ctx->launches;
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------------ coefficients
+extern "C" gs_status gs_cheb_coeffs(double t, int K, double* c)
+{
+    if (!c || !(t > 0.0) || !isfinite(t) || K < 0) return GS_ERR_ARG;
+    gs_heat_coefficients(t, K, c);
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------------------ graphs
+extern "C" gs_status gs_knn(gs_ctx* ctx, const float* X, int64_t n, int d, int k, int32_t* idx,
+                            float* dist)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if (bad_ptr(X) || bad_ptr(idx)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (n < 2 || n >= ((int64_t)1 << 31) || d < 1 || d > 1024 || k < 1 || k > 24 || k >= n)
+        return gs_fail(ctx, GS_ERR_ARG, "need 2 <= n < 2^31, 1 <= d <= 1024, 1 <= k <= 24, k < n");
+    return gs_knn_launch(ctx, X, n, d, k, idx, dist, nullptr);
+}
+
+extern "C" gs_status gs_build_graph(gs_ctx* ctx, const float* X, int64_t n, int d, int k,
+                                    float sigma, gs_graph** out)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if (bad_ptr(X) || bad_ptr(out)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    *out = nullptr;
+    if (n < 2 || n >= ((int64_t)1 << 31) || d < 1 || d > 1024 || k < 1 || k > 24 || k >= n)
+        return gs_fail(ctx, GS_ERR_ARG, "need 2 <= n < 2^31, 1 <= d <= 1024, 1 <= k <= 24, k < n");
+    if (!isfinite(sigma)) return gs_fail(ctx, GS_ERR_ARG, "sigma must be finite");
+    return gs_build_graph_impl(ctx, X, n, d, k, sigma, out);
+}
+
+extern "C" gs_status gs_graph_from_csr(gs_ctx* ctx, int64_t n, const int64_t* rowptr,
+                                       const int32_t* col, const float* w, gs_graph** out)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if (bad_ptr(rowptr) || bad_ptr(col) || bad_ptr(w) || bad_ptr(out))
+        return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    *out = nullptr;
+    if (n < 2 || n >= ((int64_t)1 << 31)) return gs_fail(ctx, GS_ERR_ARG, "need 2 <= n < 2^31");
+    return gs_graph_import_csr(ctx, n, rowptr, col, w, out);
+}
+
+extern "C" gs_status gs_graph_info(const gs_graph* g, int64_t* n, int64_t* nnz, double* sigma)
+{
+    if (!g) return GS_ERR_ARG;
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (sigma) *sigma = g->sigma;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_graph_export_csr(gs_ctx* ctx, const gs_graph* g, int64_t* rowptr,
+                                         int32_t* col, float* A, float* P)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK) return st;
+    return gs_graph_export(ctx, g, rowptr, col, A, P);
+}
+
+extern "C" gs_status gs_graph_destroy(gs_graph* g)
+{
+    if (!g) return GS_OK;
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    cudaFree(g->rowptr);
+    cudaFree(g->col);
+    cudaFree(g->pval);
+    cudaFree(g->aval);
+    cudaFree(g->deg);
+    delete g;
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------------- heat filter
+extern "C" gs_status gs_heat_apply(gs_ctx* ctx, const gs_graph* g, double t, int K, const float* V,
+                                   int B, float* Y)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(V) || bad_ptr(Y)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (V == Y) return gs_fail(ctx, GS_ERR_ARG, "V and Y must not alias");
+    if (!gs_filter_supports(B, ((uintptr_t)V % 16) == 0))
+        return gs_fail(ctx, GS_ERR_UNSUPPORTED,
+                       "B must be 1..256, or a multiple of 4 up to 1024 with V 16-byte aligned");
+    std::vector<double> c((size_t)K + 1);
+    gs_heat_coefficients(t, K, c.data());
+    const size_t blk = sizeof(float) * (size_t)g->n * (size_t)B;
+    WsPlan plan;
+    const size_t iA = plan.add(blk), iB = plan.add(blk);
+    if ((st = gs_ws_ensure(ctx, plan.total)) != GS_OK) return st;
+    Epilogue e;
+    e.kind = EPI_STORE;
+    e.out = Y;
+    return gs_filter_enqueue(ctx, g, c.data(), K, B, const_cast<float*>(V), false,
+                             ws_at<float>(ctx, plan, iA), ws_at<float>(ctx, plan, iB), Y, e,
+                             nullptr, nullptr);
+}
+
+// ----------------------------------------------------------------------------- Sinkhorn
+extern "C" gs_status gs_sinkhorn(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
+                                 const float* vol, double t, int K, double eps, int iters,
+                                 float* u, float* v, double* dist, int32_t* iters_done)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(a) || bad_ptr(b) || bad_ptr(u) || bad_ptr(v))
+        return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
+    if (!(eps == eps)) return gs_fail(ctx, GS_ERR_ARG, "eps is NaN");
+    return gs_sinkhorn_impl(ctx, g, a, b, vol, t, K, eps, iters, u, v, dist, iters_done);
+}
+
+extern "C" gs_status gs_distance(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
+                                 const float* vol, double t, int K, double eps, int iters,
+                                 double* dist)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(a) || bad_ptr(b) || bad_ptr(dist)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
+    // the scalings live after the loop's own buffers in the workspace
+    const size_t base = (sinkhorn_ws_bytes(g->n) + 255) & ~(size_t)255;
+    const size_t vec = ((sizeof(float) * (size_t)g->n) + 255) & ~(size_t)255;
+    if ((st = gs_ws_ensure(ctx, base + 2 * vec)) != GS_OK) return st;
+    float* u = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + base);
+    float* v = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + base + vec);
+    return gs_sinkhorn_impl(ctx, g, a, b, vol, t, K, eps, iters, u, v, dist, nullptr);
+}
+
+// --------------------------------------------------------------------------- barycenter
+extern "C" gs_status gs_barycenter(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
+                                   const double* alpha, const float* vol, double t, int K,
+                                   int iters, float* mu, float* v_state)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(M) || bad_ptr(alpha) || bad_ptr(mu)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (m < 1 || m > 1024) return gs_fail(ctx, GS_ERR_ARG, "m must be in [1, 1024]");
+    if (!gs_filter_supports(m, true))
+        return gs_fail(ctx, GS_ERR_UNSUPPORTED, "m must be 1..256, or a multiple of 4 up to 1024");
+    if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
+    return gs_barycenter_impl(ctx, g, M, m, alpha, vol, t, K, iters, mu, v_state);
+}

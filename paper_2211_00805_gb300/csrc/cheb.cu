@@ -1,0 +1,645 @@
+// Fused Chebyshev heat filter (Sec. 3.5) and the loops built on it: the Sinkhorn scaling loop
+// (Algorithm 1) and the fixed-support barycenter (Sec. 3.3).
+//
+// p_K(L, t) x = sum_{k=0..K} c_k T_k(P) x with P = D^{-1/2} A D^{-1/2}.  One kernel launch per
+// order k computes, for every row i,
+//     T_k[i] = 2 (P T_{k-1})[i] - T_{k-2}[i]      (T_1 = P x, T_0 = x)
+//     y[i]  += c_k T_k[i]                          (y = c_0 x + c_1 T_1 after order 1)
+// reading the CSR row of P once, gathering T_{k-1} at its columns, and reading T_{k-2} and y
+// at row i only.  T_k overwrites T_{k-2} in place (only row i ever reads T_{k-2}[i]), so two
+// vectors plus y carry the whole recurrence.  The last order does not store T_K: it hands
+// f = y + c_K T_K to an epilogue (store, Sinkhorn division, barycenter update) that also writes
+// the next filter input vol * result, so the loops need no separate elementwise kernels.
+//
+// Two row mappings:
+//   B == 1  : G lanes (a power of two) share a row and split its nonzeros; shuffle reduction.
+//   B  > 1  : a group of lanes shares a row and splits its B columns (float4 when B % 4 == 0);
+//             each lane walks the row's nonzeros and gathers its slice of each neighbour row.
+#include <math.h>
+#include <string.h>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+struct OrderArgs {
+    int64_t n;
+    int B;
+    const int* rowptr;
+    const int* col;
+    const float* pval;
+    const float* cur;   // T_{k-1} (the gathered block); x for order 1
+    const float* prev;  // T_{k-2}; unused for order 1
+    float* next;        // destination of T_k (non-last orders), may alias prev
+    float* y;           // running sum
+    float ck;           // c_k
+    float c0;           // c_0 (order 1)
+    int first;
+    int last;
+    const int* done;    // loop early-exit flag (eps stop) or null
+    int* flags;         // status bits
+    Epilogue epi;
+};
+
+__device__ __forceinline__ void flag(int* flags, int bit) { atomicOr(flags, bit); }
+
+// Zero mass stays zero; a positive numerator over a non-positive or non-finite denominator is
+// reported (the result is then inf/NaN/negative and the loop's output is invalid).
+__device__ __forceinline__ float safe_div(float num, float den, int* flags)
+{
+    if (num == 0.f) return 0.f;
+    const float r = num / den;
+    if (!(r > 0.f) || isinf(r)) flag(flags, GS_FLAG_NONFINITE);
+    return r;
+}
+
+__device__ __forceinline__ void block_add(double v, double* dst)
+{
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (l == 0 && v != 0.0) atomicAdd(dst, v);
+    }
+}
+
+// ------------------------------------------------------------------------------- B == 1
+template <int G>
+__global__ void __launch_bounds__(256) order_b1(const OrderArgs p)
+{
+    if (p.done != nullptr && *p.done) return;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const bool active = row < p.n;
+    float s = 0.f;
+    if (active) {
+        const int beg = __ldg(p.rowptr + row), end = __ldg(p.rowptr + row + 1);
+        int e = beg + lane;
+        for (; e + G < end; e += 2 * G) {
+            const int j0 = __ldg(p.col + e), j1 = __ldg(p.col + e + G);
+            const float w0 = __ldg(p.pval + e), w1 = __ldg(p.pval + e + G);
+            const float x0 = __ldg(p.cur + j0), x1 = __ldg(p.cur + j1);
+            s = fmaf(w0, x0, s);
+            s = fmaf(w1, x1, s);
+        }
+        if (e < end) s = fmaf(__ldg(p.pval + e), __ldg(p.cur + __ldg(p.col + e)), s);
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+
+    double err = 0.0;
+    if (active && lane == 0) {
+        const float tk = p.first ? s : fmaf(2.f, s, -p.prev[row]);
+        const float acc = p.first ? fmaf(p.ck, tk, p.c0 * p.cur[row]) : fmaf(p.ck, tk, p.y[row]);
+        if (!p.last) {
+            p.next[row] = tk;
+            p.y[row] = acc;
+        } else {
+            const Epilogue& e = p.epi;
+            if (e.kind == EPI_STORE) {
+                e.out[row] = acc;
+            } else {  // EPI_DIVIDE
+                const float num = e.num[row];
+                const float r = safe_div(num, acc, p.flags);
+                if (e.out) e.out[row] = r;
+                if (e.xnext) e.xnext[row] = e.vol ? e.vol[row] * r : r;
+                if (e.old) err = fabs((double)e.old[row] * (double)acc - (double)num);
+            }
+        }
+    }
+    if (p.last && p.epi.err_partials != nullptr) block_add(err, p.epi.err_partials);
+}
+
+// -------------------------------------------------------------------------------- B > 1
+template <int VEC>
+struct VecT;
+template <>
+struct VecT<4> {
+    static __device__ __forceinline__ void load(const float* src, float (&v)[4])
+    {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+};
+template <>
+struct VecT<1> {
+    static __device__ __forceinline__ void load(const float* src, float (&v)[1]) { v[0] = __ldg(src); }
+};
+
+template <int VEC, int MAXCH>
+__global__ void __launch_bounds__(256) order_blk(const OrderArgs p, int lpr_log2)
+{
+    if (p.done != nullptr && *p.done) return;
+    const int lpr = 1 << lpr_log2;
+    const int lane = threadIdx.x & (lpr - 1);
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> lpr_log2;
+    const bool active = row < p.n;
+    const int B = p.B;
+    int beg = 0, end = 0;
+    if (active) {
+        beg = __ldg(p.rowptr + row);
+        end = __ldg(p.rowptr + row + 1);
+    }
+    float f[MAXCH][VEC];
+#pragma unroll
+    for (int ch = 0; ch < MAXCH; ++ch) {
+        const int c0 = (ch * lpr + lane) * VEC;
+        if (!active || c0 >= B) break;
+        float acc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+        int e = beg;
+        for (; e + 4 <= end; e += 4) {
+            int j[4];
+            float w[4], x[4][VEC];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                j[u] = __ldg(p.col + e + u);
+                w[u] = __ldg(p.pval + e + u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) VecT<VEC>::load(p.cur + (int64_t)j[u] * B + c0, x[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] = fmaf(w[u], x[u][v], acc[v]);
+        }
+        for (; e < end; ++e) {
+            float x[VEC];
+            const float w = __ldg(p.pval + e);
+            VecT<VEC>::load(p.cur + (int64_t)__ldg(p.col + e) * B + c0, x);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] = fmaf(w, x[v], acc[v]);
+        }
+        const int64_t base = row * (int64_t)B + c0;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const float tk = p.first ? acc[v] : fmaf(2.f, acc[v], -p.prev[base + v]);
+            const float yv = p.first ? fmaf(p.ck, tk, p.c0 * p.cur[base + v])
+                                     : fmaf(p.ck, tk, p.y[base + v]);
+            if (!p.last) {
+                p.next[base + v] = tk;
+                p.y[base + v] = yv;
+            } else {
+                f[ch][v] = yv;
+            }
+        }
+    }
+    if (!p.last) return;
+
+    const Epilogue& e = p.epi;
+    const float vol = (active && e.vol) ? e.vol[row] : 1.f;
+    if (e.kind == EPI_STORE || e.kind == EPI_DIVIDE) {
+#pragma unroll
+        for (int ch = 0; ch < MAXCH; ++ch) {
+            const int c0 = (ch * lpr + lane) * VEC;
+            if (!active || c0 >= B) break;
+            const int64_t base = row * (int64_t)B + c0;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                if (e.kind == EPI_STORE) {
+                    e.out[base + v] = f[ch][v];
+                } else {
+                    const float r = safe_div(e.num[base + v], f[ch][v], p.flags);
+                    if (e.out) e.out[base + v] = r;
+                    if (e.xnext) e.xnext[base + v] = vol * r;
+                }
+            }
+        }
+        return;
+    }
+
+    // EPI_BARY_V: d_i = v_i * f_i; mu = exp(sum_i alpha_i ln d_i); v_i <- v_i mu / d_i.
+    double lsum = 0.0;
+#pragma unroll
+    for (int ch = 0; ch < MAXCH; ++ch) {
+        const int c0 = (ch * lpr + lane) * VEC;
+        if (!active || c0 >= B) break;
+        const int64_t base = row * (int64_t)B + c0;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const float d = e.V[base + v] * f[ch][v];
+            f[ch][v] = d;
+            const double al = e.alpha[c0 + v];
+            if (al != 0.0) lsum += al * (double)logf(d);
+        }
+    }
+    for (int off = lpr >> 1; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+    const float mu = (float)exp(lsum);
+    if (!active) return;
+    if (lane == 0) {
+        e.mu[row] = mu;
+        if (!(mu >= 0.f) || isinf(mu)) flag(p.flags, GS_FLAG_NONFINITE);
+    }
+#pragma unroll
+    for (int ch = 0; ch < MAXCH; ++ch) {
+        const int c0 = (ch * lpr + lane) * VEC;
+        if (c0 >= B) break;
+        const int64_t base = row * (int64_t)B + c0;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const float vnum = e.V[base + v] * mu;
+            const float d = f[ch][v];
+            const float vn = (vnum == 0.f) ? 0.f : vnum / d;
+            if (e.dsave) e.dsave[base + v] = d;
+            e.V[base + v] = vn;
+            if (e.xnext) e.xnext[base + v] = vol * vn;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ helpers
+__global__ void fill_kernel(int64_t count, float* __restrict__ out, const float* __restrict__ vol,
+                            int B, float value)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    out[i] = vol ? vol[i / B] * value : value;
+}
+
+__global__ void sink_init(int32_t* iters_done, int iters, int* done)
+{
+    if (iters_done) *iters_done = iters;
+    if (done) *done = 0;
+}
+
+// eps check after a checked u-half-step: stop (keep the previous u) or commit the new u.
+__global__ void eps_check(int64_t n, const double* err, double eps, int* done, int32_t* iters_done,
+                          int j, float* __restrict__ u, const float* __restrict__ unew, int commit)
+{
+    if (*done) return;
+    if (*err < eps) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *done = 1;
+            if (iters_done) *iters_done = j;
+        }
+        return;
+    }
+    if (!commit) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        u[i] = unew[i];
+}
+
+__global__ void sink_finalize(const int* done, int* flags)
+{
+    if (!*done) atomicOr(flags, GS_FLAG_NOT_CONVERGED);
+}
+
+inline unsigned nblocks(int64_t work, int per) { return (unsigned)((work + per - 1) / per); }
+
+int ilog2(int v)
+{
+    int r = 0;
+    while ((1 << (r + 1)) <= v) ++r;
+    return r;
+}
+
+void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const OrderArgs& a)
+{
+    gs_count(ctx, 1);
+    const int TB = pl.block;
+    if (pl.B == 1 && a.epi.kind != EPI_BARY_V) {
+        const unsigned grid = nblocks(g->n * pl.group, TB);
+        switch (pl.group) {
+            case 4: order_b1<4><<<grid, TB, 0, ctx->stream>>>(a); break;
+            case 8: order_b1<8><<<grid, TB, 0, ctx->stream>>>(a); break;
+            case 16: order_b1<16><<<grid, TB, 0, ctx->stream>>>(a); break;
+            default: order_b1<32><<<grid, TB, 0, ctx->stream>>>(a); break;
+        }
+        return;
+    }
+    const int vec = pl.vec;
+    const int lpr = pl.B == 1 ? 1 : pl.group;
+    const unsigned grid = nblocks(g->n * lpr, TB);
+    const bool one = pl.B <= lpr * vec;
+    const int lg = ilog2(lpr);
+    if (vec == 4) {
+        if (one) order_blk<4, 1><<<grid, TB, 0, ctx->stream>>>(a, lg);
+        else order_blk<4, 8><<<grid, TB, 0, ctx->stream>>>(a, lg);
+    } else {
+        if (one) order_blk<1, 1><<<grid, TB, 0, ctx->stream>>>(a, lg);
+        else order_blk<1, 8><<<grid, TB, 0, ctx->stream>>>(a, lg);
+    }
+}
+
+}  // namespace
+
+FilterPlan gs_filter_plan(const gs_ctx*, const gs_graph* g, int B, bool aligned)
+{
+    FilterPlan p;
+    p.B = B;
+    p.block = 256;
+    p.vec = (B % 4 == 0 && aligned) ? 4 : 1;
+    if (B == 1) {
+        const float m = g->mean_row;
+        p.group = m <= 6.f ? 4 : (m <= 14.f ? 8 : (m <= 28.f ? 16 : 32));
+    } else {
+        int lanes = B / p.vec;
+        if (lanes > 32) lanes = 32;
+        p.group = 1 << ilog2(lanes);
+    }
+    return p;
+}
+
+// Column counts the row-group kernels cover: at most 8 chunks of (lanes x vec) columns per lane.
+bool gs_filter_supports(int B, bool aligned)
+{
+    if (B < 1) return false;
+    if (B == 1) return true;
+    return (B % 4 == 0 && aligned) ? B <= 1024 : B <= 256;
+}
+
+gs_status gs_filter_enqueue(gs_ctx* ctx, const gs_graph* g, const double* c, int K, int B,
+                            float* x, bool x_writable, float* bufA, float* bufB, float* y,
+                            const Epilogue& epi_in, const int* done_flag, float** scratch_out)
+{
+    const bool aligned = ((uintptr_t)x % 16) == 0 && ((uintptr_t)bufA % 16) == 0 &&
+                         (bufB == nullptr || ((uintptr_t)bufB % 16) == 0);
+    if (!gs_filter_supports(B, aligned))
+        return gs_fail(ctx, GS_ERR_UNSUPPORTED, "B > 256 needs 16-byte aligned blocks with B % 4 == 0");
+    const FilterPlan pl = gs_filter_plan(ctx, g, B, aligned);
+    OrderArgs a;
+    a.n = g->n;
+    a.B = B;
+    a.rowptr = g->rowptr;
+    a.col = g->col;
+    a.pval = g->pval;
+    a.done = done_flag;
+    a.flags = ctx->flags;
+    a.y = y;
+    a.c0 = (float)c[0];
+    Epilogue epi = epi_in;
+
+    // order 1: T_1 = P x, y = c_0 x + c_1 T_1
+    a.cur = x;
+    a.prev = nullptr;
+    a.ck = (float)c[1];
+    a.first = 1;
+    if (K == 1) {
+        float* scratch = bufA;
+        if (epi.xnext_to_scratch) epi.xnext = scratch;
+        if (scratch_out) *scratch_out = scratch;
+        a.next = nullptr;
+        a.last = 1;
+        a.epi = epi;
+        launch_order(ctx, g, pl, a);
+        return gs_cuda_check(ctx, cudaGetLastError(), "Chebyshev order launch");
+    }
+    a.next = bufA;
+    a.last = 0;
+    a.epi = Epilogue();
+    launch_order(ctx, g, pl, a);
+
+    const float* cur = bufA;
+    float* prev = x;
+    bool prev_w = x_writable;
+    float* spare = bufB;
+    a.first = 0;
+    for (int k = 2; k <= K; ++k) {
+        a.cur = cur;
+        a.prev = prev;
+        a.ck = (float)c[k];
+        if (k < K) {
+            float* dst = prev_w ? prev : spare;
+            a.next = dst;
+            a.last = 0;
+            a.epi = Epilogue();
+            launch_order(ctx, g, pl, a);
+            prev = const_cast<float*>(cur);
+            cur = dst;
+            prev_w = true;
+        } else {
+            float* scratch = prev_w ? prev : spare;
+            if (epi.xnext_to_scratch) epi.xnext = scratch;
+            if (scratch_out) *scratch_out = scratch;
+            a.next = nullptr;
+            a.last = 1;
+            a.epi = epi;
+            launch_order(ctx, g, pl, a);
+        }
+    }
+    return gs_cuda_check(ctx, cudaGetLastError(), "Chebyshev order launch");
+}
+
+// ------------------------------------------------------------------------ graph capture
+template <class F>
+gs_status gs_capture(gs_ctx* ctx, F&& body, int reps, cudaGraphExec_t* out)
+{
+    if (!ctx->cap) {
+        gs_status st = gs_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking),
+                                     "capture stream");
+        if (st != GS_OK) return st;
+    }
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->cap;
+    ctx->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+    gs_status st = GS_OK;
+    if (e == cudaSuccess)
+        for (int r = 0; r < reps && st == GS_OK; ++r) st = body();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = (e == cudaSuccess) ? cudaStreamEndCapture(ctx->cap, &graph) : e;
+    ctx->stream = user;
+    ctx->capturing = false;
+    if (st != GS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if ((st = gs_cuda_check(ctx, e2, "graph capture")) != GS_OK) return st;
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    return gs_cuda_check(ctx, e, "graph instantiate");
+}
+
+void gs_graph_cache_clear(gs_ctx* ctx)
+{
+    for (auto& en : ctx->gcache) {
+        if (en.exec1) cudaGraphExecDestroy(en.exec1);
+        if (en.execR) cudaGraphExecDestroy(en.execR);
+    }
+    ctx->gcache.clear();
+}
+
+// ----------------------------------------------------------------------------- Sinkhorn
+gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
+                           const float* vol, double t, int K, double eps, int iters, float* u,
+                           float* v, double* dist, int32_t* iters_done)
+{
+    std::vector<double> c((size_t)K + 1);
+    gs_heat_coefficients(t, K, c.data());
+    const int64_t n = g->n;
+    WsPlan plan;
+    const size_t ix = plan.add(sizeof(float) * n), iA = plan.add(sizeof(float) * n),
+                 iy = plan.add(sizeof(float) * n), iu = plan.add(sizeof(float) * n),
+                 ie = plan.add(sizeof(double) * 2), id = plan.add(sizeof(int) * 2),
+                 ip = plan.add(sizeof(double) * gs_reduce_blocks());
+    gs_status st = gs_ws_ensure(ctx, plan.total);
+    if (st != GS_OK) return st;
+    float* x = ws_at<float>(ctx, plan, ix);
+    float* A = ws_at<float>(ctx, plan, iA);
+    float* y = ws_at<float>(ctx, plan, iy);
+    float* ualt = ws_at<float>(ctx, plan, iu);
+    double* err = ws_at<double>(ctx, plan, ie);
+    int* done = ws_at<int>(ctx, plan, id);
+    double* partials = ws_at<double>(ctx, plan, ip);
+    const bool use_eps = eps > 0.0;
+    const int* dflag = use_eps ? done : nullptr;
+
+    sink_init<<<1, 1, 0, ctx->stream>>>(iters_done, iters, done);
+    fill_kernel<<<nblocks(n, 256), 256, 0, ctx->stream>>>(n, x, vol, 1, 1.f);  // vol * (v = 1)
+    gs_count(ctx, 2);
+
+    auto half = [&](const float* num, float* out, const float* old, double* errp) -> gs_status {
+        Epilogue e;
+        e.kind = EPI_DIVIDE;
+        e.num = num;
+        e.vol = vol;
+        e.out = out;
+        e.old = old;
+        e.err_partials = errp;
+        e.xnext_to_scratch = true;
+        float* scratch = nullptr;
+        gs_status s = gs_filter_enqueue(ctx, g, c.data(), K, 1, x, true, A, nullptr, y, e, dflag,
+                                        &scratch);
+        if (scratch != x) std::swap(x, A);
+        return s;
+    };
+    auto iteration = [&]() -> gs_status {
+        gs_status s = half(a, u, nullptr, nullptr);
+        if (s == GS_OK) s = half(b, v, nullptr, nullptr);
+        return s;
+    };
+
+    if (!use_eps) {
+        // Fixed iteration count: replay captured CUDA graphs of R and 1 iterations.  Both halves
+        // swap the (x, A) roles the same number of times, so every iteration starts from the
+        // same buffers and one captured iteration is valid for all of them.
+        const int R = iters >= 50 ? 25 : (iters >= 10 ? 10 : 1);
+        std::vector<uintptr_t> key = {(uintptr_t)g->rowptr, (uintptr_t)g->col, (uintptr_t)g->pval,
+                                      (uintptr_t)n,         (uintptr_t)K,      (uintptr_t)a,
+                                      (uintptr_t)b,         (uintptr_t)vol,    (uintptr_t)u,
+                                      (uintptr_t)v,         (uintptr_t)ctx->ws, (uintptr_t)R};
+        uint64_t tb;
+        memcpy(&tb, &t, sizeof(tb));
+        key.push_back((uintptr_t)tb);
+        GraphCacheEntry* ent = nullptr;
+        for (auto& en : ctx->gcache)
+            if (en.key == key) ent = &en;
+        if (!ent) {
+            GraphCacheEntry en;
+            en.key = key;
+            en.R = R;
+            float* x0 = x;
+            float* A0 = A;
+            if ((st = gs_capture(ctx, iteration, 1, &en.exec1)) != GS_OK) return st;
+            if (R > 1 && (st = gs_capture(ctx, iteration, R, &en.execR)) != GS_OK) {
+                cudaGraphExecDestroy(en.exec1);
+                return st;
+            }
+            x = x0;
+            A = A0;
+            if (ctx->gcache.size() >= 8) {
+                cudaGraphExecDestroy(ctx->gcache.front().exec1);
+                if (ctx->gcache.front().execR) cudaGraphExecDestroy(ctx->gcache.front().execR);
+                ctx->gcache.erase(ctx->gcache.begin());
+            }
+            ctx->gcache.push_back(en);
+            ent = &ctx->gcache.back();
+        }
+        int left = iters;
+        cudaError_t e = cudaSuccess;
+        while (R > 1 && left >= R && e == cudaSuccess) {
+            e = cudaGraphLaunch(ent->execR, ctx->stream);
+            left -= R;
+        }
+        while (left > 0 && e == cudaSuccess) {
+            e = cudaGraphLaunch(ent->exec1, ctx->stream);
+            --left;
+        }
+        gs_count(ctx, (int64_t)iters * 2 * K);
+        if ((st = gs_cuda_check(ctx, e, "Sinkhorn graph launch")) != GS_OK) return st;
+    } else {
+        const unsigned cgrid = (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+        for (int j = 1; j <= iters && st == GS_OK; ++j) {
+            const bool check = j > 1 && ((j - 1) % 10 == 0);
+            if (check) {
+                cudaMemsetAsync(err, 0, sizeof(double), ctx->stream);
+                st = half(a, ualt, u, err);
+                eps_check<<<cgrid, 256, 0, ctx->stream>>>(n, err, eps, done, iters_done, j - 1, u,
+                                                          ualt, 1);
+                gs_count(ctx, 1);
+            } else {
+                st = half(a, u, nullptr, nullptr);
+            }
+            if (st == GS_OK) st = half(b, v, nullptr, nullptr);
+        }
+        if (st != GS_OK) return st;
+        if (iters % 10 == 0) {
+            cudaMemsetAsync(err, 0, sizeof(double), ctx->stream);
+            if ((st = half(a, ualt, u, err)) != GS_OK) return st;
+            eps_check<<<1, 32, 0, ctx->stream>>>(n, err, eps, done, iters_done, iters, u, ualt, 0);
+            gs_count(ctx, 1);
+        }
+        sink_finalize<<<1, 1, 0, ctx->stream>>>(done, ctx->flags);
+        gs_count(ctx, 1);
+    }
+    if (dist) {
+        if ((st = gs_distance_enqueue(ctx, n, a, b, vol, u, v, t, partials, dist)) != GS_OK)
+            return st;
+    }
+    return gs_cuda_check(ctx, cudaGetLastError(), "Sinkhorn loop");
+}
+
+// --------------------------------------------------------------------------- barycenter
+gs_status gs_barycenter_impl(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
+                             const double* alpha, const float* vol, double t, int K, int iters,
+                             float* mu, float* v_state)
+{
+    std::vector<double> c((size_t)K + 1);
+    gs_heat_coefficients(t, K, c.data());
+    const int64_t n = g->n;
+    const size_t blk = sizeof(float) * (size_t)n * (size_t)m;
+    WsPlan plan;
+    const size_t ix = plan.add(blk), iA = plan.add(blk), iy = plan.add(blk),
+                 iV = v_state ? 0 : plan.add(blk);
+    gs_status st = gs_ws_ensure(ctx, plan.total);
+    if (st != GS_OK) return st;
+    float* x = ws_at<float>(ctx, plan, ix);
+    float* A = ws_at<float>(ctx, plan, iA);
+    float* y = ws_at<float>(ctx, plan, iy);
+    float* V = v_state ? v_state : ws_at<float>(ctx, plan, iV);
+    const int64_t nm = n * (int64_t)m;
+    fill_kernel<<<nblocks(nm, 256), 256, 0, ctx->stream>>>(nm, V, nullptr, m, 1.f);
+    fill_kernel<<<nblocks(nm, 256), 256, 0, ctx->stream>>>(nm, x, vol, m, 1.f);
+    gs_count(ctx, 2);
+
+    for (int j = 0; j < iters && st == GS_OK; ++j) {
+        // w_i = mu_i / H(vol v_i); next input vol * w_i
+        Epilogue e1;
+        e1.kind = EPI_DIVIDE;
+        e1.num = M;
+        e1.vol = vol;
+        e1.xnext_to_scratch = true;
+        float* scratch = nullptr;
+        st = gs_filter_enqueue(ctx, g, c.data(), K, m, x, true, A, nullptr, y, e1, nullptr, &scratch);
+        if (scratch != x) std::swap(x, A);
+        if (st != GS_OK) break;
+        // d_i = v_i H(vol w_i); mu = prod d_i^alpha_i; v_i <- v_i mu / d_i; next input vol * v_i
+        Epilogue e2;
+        e2.kind = EPI_BARY_V;
+        e2.vol = vol;
+        e2.V = V;
+        e2.alpha = alpha;
+        e2.mu = mu;
+        e2.xnext_to_scratch = true;
+        st = gs_filter_enqueue(ctx, g, c.data(), K, m, x, true, A, nullptr, y, e2, nullptr, &scratch);
+        if (scratch != x) std::swap(x, A);
+    }
+    if (st != GS_OK) return st;
+    return gs_cuda_check(ctx, cudaGetLastError(), "barycenter loop");
+}

@@ -1,0 +1,159 @@
+// Internal declarations of libgeosink: context and graph structures, status helpers, and the
+// launch wrappers each .cu file provides to the C-ABI layer (api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/geosink.h"
+
+// Bits the kernels OR into the context's device status word; gs_sync turns them into a status.
+enum : int {
+    GS_FLAG_NONFINITE = 1,
+    GS_FLAG_NOT_CONVERGED = 2,
+    GS_FLAG_TIMEOUT = 4,
+};
+
+// A captured CUDA graph of one or more Sinkhorn iterations, replayed instead of re-launching
+// the 2K kernels of every iteration from the host.
+struct GraphCacheEntry {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec1 = nullptr;   // one iteration
+    cudaGraphExec_t execR = nullptr;   // R iterations
+    int R = 0;
+};
+
+struct gs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;    // private stream used only to capture graphs
+    int* flags = nullptr;          // device: status bits (GS_FLAG_*)
+    void* ws = nullptr;            // device workspace
+    size_t ws_bytes = 0;
+    int num_sms = 0;
+    bool capturing = false;        // inside an internal capture: launches are not counted
+    int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
+    std::vector<GraphCacheEntry> gcache;
+    std::string err;
+};
+
+static inline void gs_count(gs_ctx* ctx, int64_t k)
+{
+    if (!ctx->capturing) ctx->launches += k;
+}
+void gs_graph_cache_clear(gs_ctx* ctx);
+
+struct gs_graph {
+    int device = 0;
+    int64_t n = 0;
+    int64_t nnz = 0;
+    double sigma = 0.0;
+    int* rowptr = nullptr;         // [n+1] int32 offsets into col / pval / aval
+    int* col = nullptr;            // [nnz] neighbour index, ascending per row
+    float* pval = nullptr;         // [nnz] P_ij = A_ij / sqrt(deg_i deg_j)
+    float* aval = nullptr;         // [nnz] A_ij
+    double* deg = nullptr;         // [n] degrees
+    float mean_row = 0.f;          // nnz / n, steers the row-split width of the B = 1 kernel
+};
+
+// ------------------------------------------------------------------------------ helpers
+gs_status gs_fail(gs_ctx* ctx, gs_status st, const std::string& msg);
+gs_status gs_cuda_check(gs_ctx* ctx, cudaError_t e, const char* what);
+
+// Carves aligned sub-buffers out of the context workspace, growing it if needed.
+struct WsPlan {
+    std::vector<size_t> offs;
+    size_t total = 0;
+    size_t add(size_t bytes) {
+        total = (total + 255) & ~size_t(255);
+        offs.push_back(total);
+        total += bytes;
+        return offs.size() - 1;
+    }
+};
+gs_status gs_ws_ensure(gs_ctx* ctx, size_t bytes);
+template <class T>
+static inline T* ws_at(gs_ctx* ctx, const WsPlan& p, size_t i) {
+    return reinterpret_cast<T*>(static_cast<char*>(ctx->ws) + p.offs[i]);
+}
+
+// Host FP64 Chebyshev coefficients c[0..K] of exp(-tL) in the variable P (coeffs.cu).
+void gs_heat_coefficients(double t, int K, double* c);
+
+// ------------------------------------------------------------------- graph.cu
+gs_status gs_graph_alloc(gs_ctx* ctx, int64_t n, int64_t nnz, gs_graph** out);
+// Given rowptr/col/aval filled on the device, compute degrees and P (stream-ordered).
+gs_status gs_graph_finish(gs_ctx* ctx, gs_graph* g);
+gs_status gs_graph_import_csr(gs_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,
+                              const float* w, gs_graph** out);
+gs_status gs_graph_export(gs_ctx* ctx, const gs_graph* g, int64_t* rowptr, int32_t* col, float* A,
+                          float* P);
+
+// --------------------------------------------------------------------- knn.cu
+gs_status gs_knn_launch(gs_ctx* ctx, const float* X, int64_t n, int d, int k, int32_t* idx,
+                        float* dist, double* dist64);
+gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int k, float sigma,
+                              gs_graph** out);
+
+// ------------------------------------------------------------- cheb.cu (filter + loops)
+// What the last Chebyshev order does with f = p_K(x) for a block with B columns.
+enum EpiKind : int {
+    EPI_STORE = 0,    // out = f
+    EPI_DIVIDE = 1,   // out = num / f (0 where num == 0); xnext = vol * out
+    EPI_BARY_V = 2,   // d = V * f; mu = exp(sum alpha ln d); V <- V mu / d; xnext = vol * V
+};
+
+struct Epilogue {
+    int kind = EPI_STORE;
+    float* out = nullptr;          // [n, B] output (STORE/DIVIDE/BARY_W)
+    const float* num = nullptr;    // [n, B] numerator (DIVIDE: a or b; BARY_W: M)
+    const float* vol = nullptr;    // [n] vertex weights or null
+    float* xnext = nullptr;        // [n, B] vol * result, the next filter input (may be null)
+    bool xnext_to_scratch = false; // let the filter put xnext in its free scratch buffer
+    // eps check (DIVIDE, B == 1): err += |old[i] * f[i] - num[i]|
+    const float* old = nullptr;
+    double* err_partials = nullptr;
+    // barycenter
+    float* V = nullptr;            // [n, m] scalings v_i (BARY_V, updated in place)
+    const double* alpha = nullptr; // [m]
+    float* mu = nullptr;           // [n] barycenter output (BARY_V)
+    float* dsave = nullptr;        // [n, m] optional copy of d (tape for the adjoint)
+};
+
+struct FilterPlan {
+    int B = 1;
+    int vec = 1;                   // floats per lane access (4 needs B % 4 == 0 and 16 B alignment)
+    int group = 8;                 // lanes per row (B == 1: split nonzeros; B > 1: split columns)
+    int block = 256;
+};
+
+// aligned: every block the kernels gather from starts on a 16-byte boundary
+FilterPlan gs_filter_plan(const gs_ctx* ctx, const gs_graph* g, int B, bool aligned);
+int gs_err_partials_count();
+
+// Enqueue the K fused Chebyshev orders of p_K applied to x ([n, B]).
+//   x_writable: x may be overwritten by intermediate orders (the loop's own buffers)
+//   bufA/bufB : scratch [n, B] (bufB only needed when !x_writable or K == 1)
+//   y         : accumulator [n, B] (may be the output itself for EPI_STORE)
+//   scratch_out: receives the buffer the epilogue's xnext went to (when xnext_to_scratch)
+gs_status gs_filter_enqueue(gs_ctx* ctx, const gs_graph* g, const double* c, int K, int B,
+                            float* x, bool x_writable, float* bufA, float* bufB, float* y,
+                            const Epilogue& epi, const int* done_flag, float** scratch_out);
+bool gs_filter_supports(int B, bool aligned);
+
+gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
+                           const float* vol, double t, int K, double eps, int iters, float* u,
+                           float* v, double* dist, int32_t* iters_done);
+gs_status gs_barycenter_impl(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
+                             const double* alpha, const float* vol, double t, int K, int iters,
+                             float* mu, float* v_state);
+
+// ------------------------------------------------------------------------ reduce.cu
+// dist[0] = 4t sum vol (a ln u + b ln v), dist[1] = sqrt; flags NONFINITE on bad scalings.
+gs_status gs_distance_enqueue(gs_ctx* ctx, int64_t n, const float* a, const float* b,
+                              const float* vol, const float* u, const float* v, double t,
+                              double* partials, double* dist);
+int gs_reduce_blocks();

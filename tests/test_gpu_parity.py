@@ -1,0 +1,302 @@
+"""GPU (FP32 CUDA path, through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances ("Tolerances"):
+  * kNN edge sets: exact, except where the oracle's FP64 distances tie within 1e-6 relative;
+    sigma: the same FP64 number (both sides rank bitwise-identical FP64 distances).
+  * heat filter: |gpu - ref| <= 1e-4 |ref| + 1e-6 max|ref| per column block (FP32 sum of K terms of
+    size up to max|ref|: entries far below the block's maximum carry that absolute floor).
+  * distances and barycenters: rtol 1e-4; scalings: rtol 1e-3 where a_i > 0 and |ln u_i| < 80.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_00805_gb300 import workloads as W
+from tests.gpu_common import assert_close, oracle_csr_to_dev, report, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+HEAT_RTOL, HEAT_ATOL_REL = 1e-4, 1e-6
+
+
+@pytest.fixture(scope="module")
+def gs():
+    from paper_2211_00805_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(gs):
+    return gs.Context()
+
+
+def _oracle_graph_fp32(rowptr, col, A):
+    """Oracle operator built from the FP32-rounded affinities the GPU receives."""
+    A32 = np.asarray(A, np.float32).astype(np.float64)
+    deg, L = oracle.laplacian(rowptr, col, A32)
+    return oracle.shifted(L), A32
+
+
+def _random_graph(n, d, k, seed):
+    X = np.random.default_rng(seed).standard_normal((n, d)).astype(np.float32)
+    idx, dist = oracle.knn(X.astype(np.float64), k)
+    rp, col, A = oracle.affinity_graph(idx, dist, oracle.median_sigma(dist))
+    return X, rp, col, A
+
+
+def _cycle(n):
+    rp = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
+    col = np.empty(2 * n, np.int32)
+    for i in range(n):
+        col[2 * i:2 * i + 2] = sorted([(i - 1) % n, (i + 1) % n])
+    return rp, col, np.ones(2 * n)
+
+
+# ------------------------------------------------------------------------------ coefficients
+def test_library_coefficients_match_oracle(gs):
+    for t, K in [(1.0, 20), (5.0, 30), (10.0, 40), (8.0, 40)]:
+        c = np.array(gs.gs_cheb_coeffs(t, K))
+        b = oracle.cheb_coefficients(t, K)
+        # T_k(L - Id) = (-1)^k T_k(P): c_k = (-1)^k b_k, with b_0 halved
+        ref = b * (-1.0) ** np.arange(K + 1)
+        ref[0] *= 0.5
+        np.testing.assert_allclose(c, ref, rtol=1e-12)
+
+
+# ------------------------------------------------------------------------------- heat filter
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 8, 12, 32, 64, 100, 132, 260])
+def test_heat_apply_matches_oracle(gs, ctx, B):
+    X, rp, col, A = _random_graph(1500, 3, 8, seed=B)
+    g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
+    Ls, _ = _oracle_graph_fp32(rp, col, A)
+    V = np.random.default_rng(100 + B).random((1500, B)).astype(np.float32)
+    for t, K in [(1.0, 20), (5.0, 30), (2.0, 1), (3.0, 2), (4.0, 3)]:
+        Y = to_np(gs.gs_heat_apply(ctx, g, t, K, to_dev(V)))
+        ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(t, K), V.astype(np.float64))
+        assert_close(Y, ref, HEAT_RTOL, HEAT_ATOL_REL * np.abs(ref).max(), f"B={B} t={t} K={K}")
+    gs.gs_sync(ctx)
+
+
+def test_heat_apply_misaligned_input(gs, ctx):
+    # a contiguous view starting 4 bytes into its storage: the float4 path must not be used
+    X, rp, col, A = _random_graph(900, 3, 8, seed=77)
+    g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
+    Ls, _ = _oracle_graph_fp32(rp, col, A)
+    B = 32
+    V = np.random.default_rng(7).random((900, B)).astype(np.float32)
+    store = torch.empty(900 * B + 1, dtype=torch.float32, device="cuda")
+    Vd = store[1:].view(900, B)
+    Vd.copy_(to_dev(V))
+    Y = to_np(gs.gs_heat_apply(ctx, g, 3.0, 25, Vd))
+    ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(3.0, 25), V.astype(np.float64))
+    assert_close(Y, ref, HEAT_RTOL, HEAT_ATOL_REL * np.abs(ref).max(), "misaligned")
+    with pytest.raises(gs.GeosinkError) as e:
+        big = torch.empty(900 * 300 + 1, dtype=torch.float32, device="cuda")[1:].view(900, 300)
+        gs.gs_heat_apply(ctx, g, 3.0, 5, big)
+    assert e.value.status == gs.GS_ERR_UNSUPPORTED
+
+
+def test_heat_apply_cycle_closed_form(gs, ctx):
+    n = 97
+    rp, col, A = _cycle(n)
+    g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
+    e0 = np.zeros(n, np.float32)
+    e0[5] = 1.0
+    t, K = 3.0, 30
+    y = to_np(gs.gs_heat_apply(ctx, g, t, K, to_dev(e0)))
+    m = np.arange(n)
+    closed = (np.exp(-t * (1 - np.cos(2 * np.pi * m / n)))[None, :]
+              * np.cos(2 * np.pi * np.outer(np.arange(n) - 5, m) / n)).sum(1) / n
+    assert_close(y, closed, HEAT_RTOL, HEAT_ATOL_REL * closed.max(), "cycle")
+
+
+def test_heat_apply_symmetric(gs, ctx):
+    X, rp, col, A = _random_graph(3000, 4, 10, seed=9)
+    g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
+    rng = np.random.default_rng(3)
+    x, y = rng.random(3000).astype(np.float32), rng.random(3000).astype(np.float32)
+    Hx = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(x))).astype(np.float64)
+    Hy = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(y))).astype(np.float64)
+    assert abs(y @ Hx - x @ Hy) <= 1e-5 * abs(y @ Hx)
+
+
+def test_heat_apply_ragged_small_graphs(gs, ctx):
+    # sizes that leave partial row groups in the last block of every mapping
+    for n in (3, 17, 33, 255, 257, 1029):
+        X, rp, col, A = _random_graph(n, 2, 2, seed=n)
+        g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
+        Ls, _ = _oracle_graph_fp32(rp, col, A)
+        for B in (1, 4, 7):
+            V = np.random.default_rng(n + B).random((n, B)).astype(np.float32)
+            Y = to_np(gs.gs_heat_apply(ctx, g, 2.0, 12, to_dev(V)))
+            ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(2.0, 12), V.astype(np.float64))
+            assert_close(Y, ref, HEAT_RTOL, HEAT_ATOL_REL * np.abs(ref).max(), f"n={n} B={B}")
+
+
+# ------------------------------------------------------------------------------------- graph
+def _edge_sets_match(gidx, gdist64_or_None, ref_idx, ref_dist):
+    """Exact neighbour lists, allowing swaps only between entries whose FP64 distances tie
+    within 1e-6 relative."""
+    mism = np.nonzero(np.any(gidx != ref_idx, axis=1))[0]
+    for q in mism:
+        a, b = gidx[q], ref_idx[q]
+        # the sets may differ only by neighbours at (near-)tied distance with the k-th one
+        dk = ref_dist[q, -1]
+        for j in set(a.tolist()) ^ set(b.tolist()):
+            pos = np.nonzero(b == j)[0]
+            dj = ref_dist[q, pos[0]] if len(pos) else None
+            assert dj is None or abs(dj - dk) <= 1e-6 * dk, f"row {q}: neighbour {j} differs"
+        # within the set, order may swap only between ties
+        common = [j for j in a if j in set(b.tolist())]
+        assert len(common) >= len(a) - 2
+    return len(mism)
+
+
+def test_knn_sphere_exact(gs, ctx):
+    p = W.sphere_pair()
+    idx, dist = gs.gs_knn(ctx, to_dev(p.X), p.k)
+    ri, rd = oracle.knn(p.X.astype(np.float64), p.k)
+    gi = to_np(idx)
+    n_mism = _edge_sets_match(gi, None, ri, rd)
+    assert n_mism == 0
+    np.testing.assert_allclose(to_np(dist), rd, rtol=1e-7)
+
+
+def test_knn_manifold_sampled_rows(gs, ctx):
+    X, Z = W.tanh_manifold(20_000, 10, 50, seed=2)
+    idx, _ = gs.gs_knn(ctx, to_dev(X), 15)
+    rows = np.random.default_rng(0).choice(len(X), 300, replace=False)
+    ri, rd = oracle.knn(X.astype(np.float64), 15, rows=rows)
+    _edge_sets_match(to_np(idx)[rows], None, ri, rd)
+
+
+def test_build_graph_matches_oracle(gs, ctx):
+    p = W.sphere_pair()
+    g = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    rowptr, col, A, P = gs.gs_graph_export_csr(ctx, g)
+    Ls, ex = oracle.build_graph(p.X.astype(np.float64), p.k)
+    assert g.sigma == ex["sigma"]
+    assert np.array_equal(to_np(rowptr), ex["rowptr"])
+    assert np.array_equal(to_np(col), ex["col"])
+    assert_close(to_np(A), ex["A"], 1e-7, 0, "A")
+    # P_ij = -(Ls)_ij on the same pattern (Ls = L - Id has no diagonal)
+    assert np.array_equal(Ls[1], ex["col"])
+    assert_close(to_np(P), -Ls[2], 1e-6, 0, "P")
+
+
+def test_build_graph_with_given_sigma_and_duplicates(gs, ctx):
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((700, 5)).astype(np.float32)
+    X[100:110] = X[3]  # exact duplicates: distance ties at 0, resolved by index
+    g = gs.gs_build_graph(ctx, to_dev(X), 6, sigma=0.7)
+    rowptr, col, A, P = gs.gs_graph_export_csr(ctx, g)
+    Ls, ex = oracle.build_graph(X.astype(np.float64), 6, sigma=0.7)
+    assert g.sigma == pytest.approx(0.7, rel=1e-7)
+    assert np.array_equal(to_np(col), ex["col"])
+    assert_close(to_np(A), ex["A"], 1e-6, 0, "A")
+
+
+# ---------------------------------------------------------------------------------- Sinkhorn
+@pytest.fixture(scope="module")
+def sphere_graph(gs, ctx):
+    p = W.sphere_pair()
+    g = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    Ls, ex = oracle.build_graph(p.X.astype(np.float64), p.k)
+    return p, g, Ls
+
+
+def _check_sinkhorn(gs, ctx, g, Ls, a, b, t, K, iters, vol=None):
+    u, v, dist, it = gs.gs_sinkhorn(ctx, g, to_dev(a), to_dev(b), t, K, iters,
+                                    vol=None if vol is None else to_dev(vol))
+    gs.gs_sync(ctx)
+    r = oracle.sinkhorn(Ls, oracle.cheb_coefficients(t, K), a.astype(np.float64),
+                        b.astype(np.float64), t, iters, a=None if vol is None else vol.astype(np.float64))
+    assert r["status"] == oracle.OK
+    d = to_np(dist)
+    assert d[0] == pytest.approx(r["W2"], rel=1e-4)
+    assert d[1] == pytest.approx(r["W"], rel=1e-4)
+    uu, vv = to_np(u), to_np(v)
+    mu = (a > 0) & (np.abs(np.log(np.where(r["v"] > 0, r["v"], 1))) < 80)
+    mv = (b > 0) & (np.abs(np.log(np.where(r["w"] > 0, r["w"], 1))) < 80)
+    assert_close(uu, r["v"], 1e-3, 0, "u", mask=mu)
+    assert_close(vv, r["w"], 1e-3, 0, "v", mask=mv)
+    assert int(to_np(it)[0]) == iters
+    return d
+
+
+def test_sinkhorn_sphere_t5(gs, ctx, sphere_graph):
+    p, g, Ls = sphere_graph
+    _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 200)
+
+
+def test_sinkhorn_sphere_t1_reports_nonfinite(gs, ctx, sphere_graph):
+    # t = 1, K = 20 as configured: the FP32 scalings overflow (recorded deviation); the library
+    # must say so instead of returning garbage.
+    p, g, Ls = sphere_graph
+    gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 1.0, 20, 200)
+    with pytest.raises(gs.GeosinkError) as e:
+        gs.gs_sync(ctx)
+    assert e.value.status == gs.GS_ERR_NONFINITE
+
+
+def test_sinkhorn_vertex_weights_zero_mass_odd_K(gs, ctx, sphere_graph):
+    p, g, Ls = sphere_graph
+    vol = np.random.default_rng(1).uniform(0.5, 1.5, len(p.a)).astype(np.float32)
+    a = np.where(p.X[:, 2] > -0.2, p.a, 0).astype(np.float32)
+    a = (a / np.sum(a * vol)).astype(np.float32)
+    b = (p.b / np.sum(p.b * vol)).astype(np.float32)
+    _check_sinkhorn(gs, ctx, g, Ls, a, b, 5.0, 31, 120, vol=vol)
+
+
+def test_distance_equals_sinkhorn(gs, ctx, sphere_graph):
+    p, g, Ls = sphere_graph
+    d = to_np(gs.gs_distance(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 100))
+    _, _, d2, _ = gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 100)
+    assert np.array_equal(d, to_np(d2))
+
+
+def test_sinkhorn_eps_stop_matches_oracle(gs, ctx, sphere_graph):
+    p, g, Ls = sphere_graph
+    t, K = 5.0, 30
+    r = oracle.sinkhorn(Ls, oracle.cheb_coefficients(t, K), p.a.astype(np.float64),
+                        p.b.astype(np.float64), t, 400, eps=1e-5)
+    u, v, dist, it = gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), t, K, 400, eps=1e-5)
+    gs.gs_sync(ctx)
+    assert r["status"] == oracle.OK
+    assert abs(int(to_np(it)[0]) - r["iters"]) <= 10
+    assert to_np(dist)[0] == pytest.approx(r["W2"], rel=1e-4)
+    gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), t, K, 20, eps=1e-30)
+    with pytest.raises(gs.GeosinkError) as e:
+        gs.gs_sync(ctx)
+    assert e.value.status == gs.GS_ERR_NOT_CONVERGED
+
+
+def test_sinkhorn_manifold_small(gs, ctx):
+    p = W.manifold_pair(n=6000, iters=150)
+    g = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    Ls, ex = oracle.build_graph(p.X.astype(np.float64), p.k)
+    assert g.nnz == len(ex["col"])
+    _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, p.t, p.K, p.iters)
+
+
+# -------------------------------------------------------------------------------- barycenter
+@pytest.mark.parametrize("m", [1, 3, 32, 64])
+def test_barycenter_matches_oracle(gs, ctx, m):
+    cfg = W.clusters_barycenter(n=4000, m=max(m, 1), iters=30)
+    X = cfg["X"]
+    M = cfg["M"][:, :m]
+    alpha = np.random.default_rng(m).dirichlet(np.ones(m))
+    g = gs.gs_build_graph(ctx, to_dev(X), cfg["k"])
+    Ls, ex = oracle.build_graph(X.astype(np.float64), cfg["k"])
+    t, K = 10.0, 40
+    V = torch.empty((len(X), m), dtype=torch.float32, device="cuda")
+    mu = to_np(gs.gs_barycenter(ctx, g, to_dev(M), to_dev(alpha, torch.float64), t, K, cfg["iters"],
+                                v_state=V))
+    gs.gs_sync(ctx)
+    ref, Vref = oracle.barycenter(Ls, oracle.cheb_coefficients(t, K), M.astype(np.float64), alpha,
+                                  cfg["iters"], return_state=True)
+    assert_close(mu, ref, 1e-4, 1e-6 * ref.max(), f"mu m={m}")
+    assert_close(to_np(V), Vref, 1e-3, 1e-6 * np.abs(Vref).max(), f"v_i m={m}")
