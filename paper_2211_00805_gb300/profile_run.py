@@ -1,0 +1,69 @@
+"""Run one heat-filter workload a few times, for profilers (ncu) and quick timing.
+
+    python -m paper_2211_00805_gb300.profile_run --case b1   # 100k-point manifold graph, B = 1, K = 30
+    python -m paper_2211_00805_gb300.profile_run --case b32  # 200k-point cluster graph, B = 32, K = 40
+
+Builds the case's graph on the GPU, then applies the filter ``--reps`` times through the C ABI and
+prints the mean time per apply (CUDA events) and its algorithmic bandwidth.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+from paper_2211_00805_gb300 import binding as gs  # noqa: E402
+from paper_2211_00805_gb300 import workloads as W  # noqa: E402
+
+CASES = {
+    "b1": dict(kind="manifold", n=100_000, latent=10, ambient=50, seed=2, k=15, K=30, t=5.0, B=1),
+    "b32": dict(kind="clusters", n=200_000, dim=30, seed=3, k=10, K=40, t=10.0, B=32),
+    "b64": dict(kind="manifold", n=500_000, latent=6, ambient=40, seed=4, k=10, K=40, t=8.0, B=64),
+}
+
+
+def algorithmic_bytes(n, nnz, K, B):
+    graph = 8 * nnz + 4 * (n + 1)
+    return K * graph + 12 * n * B + (K - 2) * 20 * n * B + 16 * n * B
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", choices=sorted(CASES), default="b1")
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args()
+    c = CASES[args.case]
+    dev = torch.device("cuda", 0)
+    ctx = gs.Context(0)
+    if c["kind"] == "manifold":
+        X, Z = W.tanh_manifold(c["n"], c["latent"], c["ambient"], c["seed"])
+    else:
+        X, _ = W.cluster_curves(c["n"], c["dim"], seed=c["seed"])
+    g = gs.gs_build_graph(ctx, torch.from_numpy(X).to(dev), c["k"])
+    V = torch.rand((c["n"], c["B"]), generator=torch.Generator().manual_seed(0)).to(dev)
+    Y = torch.empty_like(V)
+    gs.gs_heat_apply(ctx, g, c["t"], c["K"], V, out=Y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.reps):
+        gs.gs_heat_apply(ctx, g, c["t"], c["K"], V, out=Y)
+    e1.record()
+    torch.cuda.synchronize()
+    gs.gs_sync(ctx)
+    ms = e0.elapsed_time(e1) / args.reps
+    byts = algorithmic_bytes(c["n"], g.nnz, c["K"], c["B"])
+    print(json.dumps({"case": args.case, "n": c["n"], "nnz": g.nnz, "B": c["B"], "K": c["K"],
+                      "apply_ms": ms, "order_us": ms * 1e3 / c["K"],
+                      "GBps": byts / (ms / 1e3) / 1e9, "bytes_per_order": byts / c["K"]}))
+
+
+if __name__ == "__main__":
+    main()
