@@ -81,6 +81,17 @@ gs_status gs_sync(gs_ctx *ctx);
 /* Grow the workspace to at least `bytes` now (for use before CUDA-graph capture). */
 gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
 
+/* Context options (host call).  GS_OPT_LOOP selects how gs_sinkhorn runs a fixed iteration count
+ * (eps <= 0): 0 (default) one persistent cooperative launch with bounded grid barriers between the
+ * Chebyshev orders, falling back to 1 when the device cannot co-schedule the grid; 1 CUDA-graph
+ * replay of per-order launches.  Both compute the same thing.  Errors: GS_ERR_ARG. */
+/* GS_OPT_BARRIER_SELFTEST = 1 makes the next persistent launch wait at its first grid barrier for
+ * one block more than the grid has: every block's bounded wait runs out (~10 ms), the launch ends
+ * and gs_sync reports GS_ERR_TIMEOUT, leaving the context usable.  It exercises failure handling
+ * without faulting the GPU; the option resets itself after that launch. */
+enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2 };
+gs_status gs_set_option(gs_ctx *ctx, int option, int value);
+
 /* Host query: number of GPU kernels this context has enqueued so far (a replayed CUDA graph
  * counts each of its kernel nodes).  Used to report launch counts; *count must not be NULL. */
 gs_status gs_launch_count(const gs_ctx *ctx, int64_t *count);
@@ -184,6 +195,45 @@ gs_status gs_distance(gs_ctx *ctx, const gs_graph *g, const float *a, const floa
  * Requires 1 <= m <= 1024.  Errors: GS_ERR_ARG. */
 gs_status gs_barycenter(gs_ctx *ctx, const gs_graph *g, const float *M, int m, const double *alpha,
                         const float *vol, double t, int K, int iters, float *mu, float *v_state);
+
+/* ------------------------------------------------------------------------------ adjoint --- */
+
+/* Reverse mode of Algorithm 1 unrolled over `iters` iterations (not in the paper; it serves
+ * gradient-based use of the distance).  Runs the loop forward keeping the second scaling every
+ * `checkpoint` iterations, then sweeps back segment by segment: each segment is recomputed from
+ * its checkpoint with the filter values saved, and the transposed filter applies reuse the same
+ * fused kernels because p_K(L, t) is symmetric.  Outputs
+ *     dist[0..1] (device doubles) = W^2, W            (as gs_sinkhorn)
+ *     grad_a, grad_b [n] (device)  = dW^2/da, dW^2/db  (of the unrolled map, a and b independent;
+ *                                                       entries with zero mass use 0 ln 0 := 0)
+ * Requires checkpoint >= 1.  Errors: GS_ERR_ARG. */
+gs_status gs_sinkhorn_grad(gs_ctx *ctx, const gs_graph *g, const float *a, const float *b,
+                           const float *vol, double t, int K, int iters, int checkpoint,
+                           double *dist, float *grad_a, float *grad_b);
+
+/* Reverse mode of gs_barycenter (Sec. 3.3) unrolled over `iters` iterations: given mubar [n]
+ * (device), the adjoint of the returned barycenter, writes mu [n] (the barycenter, may be NULL)
+ * and grad_alpha [m] (device doubles) = d<mubar, mu>/dalpha.  Checkpoints of the scalings every
+ * `checkpoint` iterations bound the tape to `checkpoint` iterations of [n, m] blocks.
+ * Same limits as gs_barycenter.  Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED. */
+gs_status gs_barycenter_grad(gs_ctx *ctx, const gs_graph *g, const float *M, int m,
+                             const double *alpha, const float *vol, double t, int K, int iters,
+                             int checkpoint, const float *mubar, float *mu, double *grad_alpha);
+
+/* ------------------------------------------------------------------------------ batched --- */
+
+/* Many independent Algorithm-1 problems in one persistent launch (not in the paper; it serves
+ * workloads with many small distances).  Problem i has graph graphs[i] (any size, any order),
+ * marginals a[i], b[i] (device [n_i]), diffusion time t[i] and degree K[i]; all run `iters`
+ * iterations with unit vertex weights.  Outputs u[i], v[i] (device [n_i]) and dist[2i], dist[2i+1]
+ * (device doubles: W^2, W).  `graphs`, `a`, `b`, `t`, `K`, `u`, `v` are HOST arrays of length
+ * nprob.  Each problem runs on one thread-block cluster whose Chebyshev orders are separated by
+ * hardware cluster barriers.  Requires 1 <= nprob, every K[i] >= 1, t[i] > 0.
+ * Errors: GS_ERR_ARG. */
+gs_status gs_sinkhorn_batched(gs_ctx *ctx, int nprob, const gs_graph *const *graphs,
+                              const float *const *a, const float *const *b, const double *t,
+                              const int *K, int iters, float *const *u, float *const *v,
+                              double *dist);
 
 #ifdef __cplusplus
 }

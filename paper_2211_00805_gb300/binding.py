@@ -30,6 +30,7 @@ SIGNATURES = {
     "gs_last_error": [_P],
     "gs_sync": [_P],
     "gs_reserve": [_P, _I64],
+    "gs_set_option": [_P, _I, _I],
     "gs_launch_count": [_P, _P],
     "gs_cheb_coeffs": [_D, _I, _P],
     "gs_knn": [_P, _P, _I64, _I, _I, _P, _P],
@@ -42,6 +43,9 @@ SIGNATURES = {
     "gs_sinkhorn": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P],
     "gs_distance": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P],
     "gs_barycenter": [_P, _P, _P, _I, _P, _P, _D, _I, _I, _P, _P],
+    "gs_sinkhorn_grad": [_P, _P, _P, _P, _P, _D, _I, _I, _I, _P, _P, _P],
+    "gs_barycenter_grad": [_P, _P, _P, _I, _P, _P, _D, _I, _I, _I, _P, _P, _P],
+    "gs_sinkhorn_batched": [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P],
 }
 
 
@@ -152,6 +156,14 @@ def gs_sync(ctx: Context):
 
 def gs_reserve(ctx: Context, nbytes: int):
     _raise(ctx, _lib.gs_reserve(ctx.handle, int(nbytes)))
+
+
+GS_OPT_LOOP = 1
+GS_OPT_BARRIER_SELFTEST = 2
+
+
+def gs_set_option(ctx: Context, option: int, value: int):
+    _raise(ctx, _lib.gs_set_option(ctx.handle, int(option), int(value)))
 
 
 def gs_launch_count(ctx: Context) -> int:
@@ -265,3 +277,62 @@ def gs_barycenter(ctx: Context, g: Graph, M: torch.Tensor, alpha: torch.Tensor, 
     _raise(ctx, _lib.gs_barycenter(ctx.handle, g.handle, _ptr(M), m, _ptr(alpha), _ptr(vol), float(t),
                                    int(K), int(iters), _ptr(mu), _ptr(v_state)))
     return mu
+
+
+def gs_sinkhorn_grad(ctx: Context, g: Graph, a: torch.Tensor, b: torch.Tensor, t: float, K: int,
+                     iters: int, checkpoint: int = 20, vol: torch.Tensor | None = None):
+    """Returns (dist[2] FP64 = (W^2, W), dW^2/da, dW^2/db) as device tensors."""
+    n = g.n
+    _dev(a, torch.float32, "a", (n,))
+    _dev(b, torch.float32, "b", (n,))
+    if vol is not None:
+        _dev(vol, torch.float32, "vol", (n,))
+    dist = torch.empty(2, dtype=torch.float64, device=a.device)
+    ga = torch.empty(n, dtype=torch.float32, device=a.device)
+    gb = torch.empty(n, dtype=torch.float32, device=a.device)
+    _raise(ctx, _lib.gs_sinkhorn_grad(ctx.handle, g.handle, _ptr(a), _ptr(b), _ptr(vol), float(t),
+                                      int(K), int(iters), int(checkpoint), _ptr(dist), _ptr(ga),
+                                      _ptr(gb)))
+    return dist, ga, gb
+
+
+def gs_barycenter_grad(ctx: Context, g: Graph, M: torch.Tensor, alpha: torch.Tensor, t: float,
+                       K: int, iters: int, mubar: torch.Tensor, checkpoint: int = 20,
+                       vol: torch.Tensor | None = None):
+    """Returns (mu [n], d<mubar, mu>/dalpha [m] FP64) as device tensors."""
+    n, m = M.shape
+    _dev(M, torch.float32, "M", (g.n, m))
+    _dev(alpha, torch.float64, "alpha", (m,))
+    _dev(mubar, torch.float32, "mubar", (n,))
+    if vol is not None:
+        _dev(vol, torch.float32, "vol", (n,))
+    mu = torch.empty(n, dtype=torch.float32, device=M.device)
+    galpha = torch.empty(m, dtype=torch.float64, device=M.device)
+    _raise(ctx, _lib.gs_barycenter_grad(ctx.handle, g.handle, _ptr(M), m, _ptr(alpha), _ptr(vol),
+                                        float(t), int(K), int(iters), int(checkpoint), _ptr(mubar),
+                                        _ptr(mu), _ptr(galpha)))
+    return mu, galpha
+
+
+def gs_sinkhorn_batched(ctx: Context, graphs, a_list, b_list, t_list, K_list, iters: int,
+                        u_list=None, v_list=None, dist=None):
+    """Many problems in one launch.  Returns (u_list, v_list, dist [nprob, 2] FP64)."""
+    nprob = len(graphs)
+    dev = torch.device("cuda", ctx.device)
+    for i, (g, a, b) in enumerate(zip(graphs, a_list, b_list)):
+        _dev(a, torch.float32, f"a[{i}]", (g.n,))
+        _dev(b, torch.float32, f"b[{i}]", (g.n,))
+    u_list = [torch.empty(g.n, dtype=torch.float32, device=dev) for g in graphs] if u_list is None else u_list
+    v_list = [torch.empty(g.n, dtype=torch.float32, device=dev) for g in graphs] if v_list is None else v_list
+    dist = torch.empty((nprob, 2), dtype=torch.float64, device=dev) if dist is None else dist
+    P = ctypes.c_void_p * nprob
+    hg = P(*[g.handle.value for g in graphs])
+    ha = P(*[x.data_ptr() for x in a_list])
+    hb = P(*[x.data_ptr() for x in b_list])
+    hu = P(*[x.data_ptr() for x in u_list])
+    hv = P(*[x.data_ptr() for x in v_list])
+    ht = (ctypes.c_double * nprob)(*[float(x) for x in t_list])
+    hk = (ctypes.c_int * nprob)(*[int(x) for x in K_list])
+    _raise(ctx, _lib.gs_sinkhorn_batched(ctx.handle, nprob, hg, ha, hb, ht, hk, int(iters), hu, hv,
+                                         _ptr(dist)))
+    return u_list, v_list, dist

@@ -73,15 +73,6 @@ gs_status enter(gs_ctx* ctx)
     return gs_cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
 }
 
-size_t sinkhorn_ws_bytes(int64_t n)
-{
-    WsPlan p;
-    for (int i = 0; i < 4; ++i) p.add(sizeof(float) * n);
-    p.add(sizeof(double) * 2);
-    p.add(sizeof(int) * 2);
-    p.add(sizeof(double) * gs_reduce_blocks());
-    return p.total;
-}
 
 }  // namespace
 
@@ -159,6 +150,20 @@ extern "C" gs_status gs_reserve(gs_ctx* ctx, int64_t bytes)
     if (st != GS_OK) return st;
     if (bytes < 0) return gs_fail(ctx, GS_ERR_ARG, "negative size");
     return gs_ws_ensure(ctx, (size_t)bytes);
+}
+
+extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
+{
+    if (!ctx) return GS_ERR_ARG;
+    if (option == GS_OPT_LOOP && (value == 0 || value == 1)) {
+        ctx->loop_mode = value;
+        return GS_OK;
+    }
+    if (option == GS_OPT_BARRIER_SELFTEST && (value == 0 || value == 1)) {
+        ctx->barrier_selftest = value;
+        return GS_OK;
+    }
+    return gs_fail(ctx, GS_ERR_ARG, "unknown option or value");
 }
 
 extern "C" gs_status gs_launch_count(const gs_ctx* ctx, int64_t* count)
@@ -241,6 +246,11 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g)
     cudaFree(g->pval);
     cudaFree(g->aval);
     cudaFree(g->deg);
+    cudaFree(g->perm);
+    cudaFree(g->iperm);
+    cudaFree(g->prowptr);
+    cudaFree(g->pcol);
+    cudaFree(g->ppval);
     delete g;
     return GS_OK;
 }
@@ -260,15 +270,30 @@ extern "C" gs_status gs_heat_apply(gs_ctx* ctx, const gs_graph* g, double t, int
     std::vector<double> c((size_t)K + 1);
     gs_heat_coefficients(t, K, c.data());
     const size_t blk = sizeof(float) * (size_t)g->n * (size_t)B;
-    WsPlan plan;
-    const size_t iA = plan.add(blk), iB = plan.add(blk);
-    if ((st = gs_ws_ensure(ctx, plan.total)) != GS_OK) return st;
     Epilogue e;
     e.kind = EPI_STORE;
-    e.out = Y;
-    return gs_filter_enqueue(ctx, g, c.data(), K, B, const_cast<float*>(V), false,
-                             ws_at<float>(ctx, plan, iA), ws_at<float>(ctx, plan, iB), Y, e,
-                             nullptr, nullptr);
+    if (!g->perm) {
+        WsPlan plan;
+        const size_t iA = plan.add(blk), iB = plan.add(blk);
+        if ((st = gs_ws_ensure(ctx, plan.total)) != GS_OK) return st;
+        e.out = Y;
+        return gs_filter_enqueue(ctx, g, c.data(), K, B, const_cast<float*>(V), false,
+                                 ws_at<float>(ctx, plan, iA), ws_at<float>(ctx, plan, iB), Y, e,
+                                 nullptr, nullptr);
+    }
+    // reordered graph: V into the filter's node order, apply, Y back
+    WsPlan plan;
+    const size_t iA = plan.add(blk), iV = plan.add(blk), iY = plan.add(blk);
+    if ((st = gs_ws_ensure(ctx, plan.total)) != GS_OK) return st;
+    float* Vp = ws_at<float>(ctx, plan, iV);
+    float* Yp = ws_at<float>(ctx, plan, iY);
+    gs_permute_rows(ctx, g->n, B, g->perm, V, Vp, true);
+    e.out = Yp;
+    if ((st = gs_filter_enqueue(ctx, g, c.data(), K, B, Vp, true, ws_at<float>(ctx, plan, iA), nullptr,
+                                Yp, e, nullptr, nullptr)) != GS_OK)
+        return st;
+    gs_permute_rows(ctx, g->n, B, g->perm, Yp, Y, false);
+    return gs_cuda_check(ctx, cudaGetLastError(), "heat apply");
 }
 
 // ----------------------------------------------------------------------------- Sinkhorn
@@ -295,13 +320,8 @@ extern "C" gs_status gs_distance(gs_ctx* ctx, const gs_graph* g, const float* a,
     if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
     if (bad_ptr(a) || bad_ptr(b) || bad_ptr(dist)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
-    // the scalings live after the loop's own buffers in the workspace
-    const size_t base = (sinkhorn_ws_bytes(g->n) + 255) & ~(size_t)255;
-    const size_t vec = ((sizeof(float) * (size_t)g->n) + 255) & ~(size_t)255;
-    if ((st = gs_ws_ensure(ctx, base + 2 * vec)) != GS_OK) return st;
-    float* u = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + base);
-    float* v = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + base + vec);
-    return gs_sinkhorn_impl(ctx, g, a, b, vol, t, K, eps, iters, u, v, dist, nullptr);
+    // the scalings stay in the workspace
+    return gs_sinkhorn_impl(ctx, g, a, b, vol, t, K, eps, iters, nullptr, nullptr, dist, nullptr);
 }
 
 // --------------------------------------------------------------------------- barycenter
@@ -318,4 +338,54 @@ extern "C" gs_status gs_barycenter(gs_ctx* ctx, const gs_graph* g, const float* 
         return gs_fail(ctx, GS_ERR_UNSUPPORTED, "m must be 1..256, or a multiple of 4 up to 1024");
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
     return gs_barycenter_impl(ctx, g, M, m, alpha, vol, t, K, iters, mu, v_state);
+}
+
+// ------------------------------------------------------------------------------ adjoint
+extern "C" gs_status gs_sinkhorn_grad(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
+                                      const float* vol, double t, int K, int iters, int checkpoint,
+                                      double* dist, float* grad_a, float* grad_b)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(a) || bad_ptr(b) || bad_ptr(dist) || bad_ptr(grad_a) || bad_ptr(grad_b))
+        return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (iters < 1 || checkpoint < 1) return gs_fail(ctx, GS_ERR_ARG, "iters and checkpoint must be >= 1");
+    return gs_sinkhorn_grad_impl(ctx, g, a, b, vol, t, K, iters, checkpoint, dist, grad_a, grad_b);
+}
+
+extern "C" gs_status gs_barycenter_grad(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
+                                        const double* alpha, const float* vol, double t, int K,
+                                        int iters, int checkpoint, const float* mubar, float* mu,
+                                        double* grad_alpha)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(M) || bad_ptr(alpha) || bad_ptr(mubar) || bad_ptr(grad_alpha))
+        return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (m < 1 || m > 1024) return gs_fail(ctx, GS_ERR_ARG, "m must be in [1, 1024]");
+    if (!gs_filter_supports(m, true))
+        return gs_fail(ctx, GS_ERR_UNSUPPORTED, "m must be 1..256, or a multiple of 4 up to 1024");
+    if (iters < 1 || checkpoint < 1) return gs_fail(ctx, GS_ERR_ARG, "iters and checkpoint must be >= 1");
+    return gs_barycenter_grad_impl(ctx, g, M, m, alpha, vol, t, K, iters, checkpoint, mubar, mu, grad_alpha);
+}
+
+// ------------------------------------------------------------------------------ batched
+extern "C" gs_status gs_sinkhorn_batched(gs_ctx* ctx, int nprob, const gs_graph* const* graphs,
+                                         const float* const* a, const float* const* b,
+                                         const double* t, const int* K, int iters, float* const* u,
+                                         float* const* v, double* dist)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if (nprob < 1 || !graphs || !a || !b || !t || !K || !u || !v)
+        return gs_fail(ctx, GS_ERR_ARG, "null pointer or nprob < 1");
+    if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
+    for (int i = 0; i < nprob; ++i) {
+        if ((st = check_graph(ctx, graphs[i])) != GS_OK) return st;
+        if ((st = check_filter(ctx, t[i], K[i])) != GS_OK) return st;
+        if (!a[i] || !b[i] || !u[i] || !v[i]) return gs_fail(ctx, GS_ERR_ARG, "null problem pointer");
+    }
+    return gs_sinkhorn_batched_impl(ctx, nprob, graphs, a, b, t, K, iters, u, v, dist);
 }

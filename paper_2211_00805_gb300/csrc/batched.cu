@@ -1,0 +1,271 @@
+// Many independent Geodesic Sinkhorn problems (Algorithm 1) in one persistent launch.
+//
+// Each thread-block cluster (kClusterCtas CTAs, co-scheduled by the hardware) takes problems from
+// a global work queue, largest first, and runs a problem's whole loop by itself: the problem's
+// rows are split across the cluster's CTAs, every Chebyshev order ends with a cluster barrier
+// (hardware barrier.cluster with release/acquire ordering, so no software spin-wait exists that
+// could hang), and the distance reduction finishes through distributed shared memory.  The
+// per-order work is the same fused recurrence as the single-problem kernels: gather the previous
+// block through the CSR row, update T_k in place and the running sum, and in the last order divide
+// the marginal by the filter value and write the next filter input.
+//
+// Problems with different n, K and t coexist; their state lives in one workspace arena.  The
+// problems' graphs keep their own CSR arrays; when a graph carries a locality order the kernel
+// runs in that order and reads the marginals / writes the scalings through the permutation.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int kClusterCtas = 8;
+constexpr int kThreads = 256;
+constexpr int kLanes = 8;  // lanes per row in the B = 1 mapping
+
+struct BatchProblem {
+    int n;
+    int K;
+    double t4;              // 4t
+    const int* rowptr;
+    const int* col;
+    const float* pval;
+    const int* perm;        // new -> old node id, or null
+    const float* a;         // marginals in the caller's node order
+    const float* b;
+    float* u;               // outputs in the caller's node order
+    float* v;
+    float* x;               // arena blocks [n] in the kernel's order
+    float* A;
+    float* y;
+    float* us;              // scalings in the kernel's order
+    float* vs;
+    const float* coef;      // [K + 1]
+};
+
+__device__ __forceinline__ int node_of(const BatchProblem& p, int r) { return p.perm ? p.perm[r] : r; }
+
+// One Chebyshev order over rows [r0, r1) of a problem (B = 1, kLanes lanes per row).
+// mode 0: first order, 1: middle, 2: last (epilogue: out = num / f, xnext = out).
+__device__ void order_rows(const BatchProblem& p, int r0, int r1, int mode, float ck, float c0,
+                           const float* cur, const float* prev, float* next, const float* num,
+                           float* out, float* xnext, int* flags)
+{
+    const int lane = threadIdx.x & (kLanes - 1);
+    const int rows_per_pass = blockDim.x / kLanes;
+    for (int base = r0; base < r1; base += rows_per_pass) {
+        const int row = base + threadIdx.x / kLanes;
+        const bool active = row < r1;
+        float s = 0.f;
+        if (active) {
+            const int beg = p.rowptr[row], end = p.rowptr[row + 1];
+            for (int e = beg + lane; e < end; e += kLanes) s = fmaf(p.pval[e], cur[p.col[e]], s);
+        }
+#pragma unroll
+        for (int off = kLanes / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (!active || lane != 0) continue;
+        const float tk = (mode == 0) ? s : fmaf(2.f, s, -prev[row]);
+        const float acc = (mode == 0) ? fmaf(ck, tk, c0 * cur[row]) : fmaf(ck, tk, p.y[row]);
+        if (mode != 2) {
+            next[row] = tk;
+            p.y[row] = acc;
+        } else {
+            const float m = num[node_of(p, row)];
+            float r = 0.f;
+            if (m != 0.f) {
+                r = m / acc;
+                if (!(r > 0.f) || isinf(r)) atomicOr(flags, GS_FLAG_NONFINITE);
+            }
+            out[row] = r;
+            xnext[row] = r;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) batched_sinkhorn(const BatchProblem* __restrict__ probs,
+                                                             int nprob, int iters,
+                                                             int* __restrict__ queue,
+                                                             double* __restrict__ dist, int* flags)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    __shared__ int s_prob;
+    __shared__ double s_part[kThreads / 32];
+    __shared__ double s_total;
+
+    while (true) {
+        if (rank == 0 && threadIdx.x == 0) s_prob = atomicAdd(queue, 1);
+        cluster.sync();
+        const int pid = *cluster.map_shared_rank(&s_prob, 0);
+        cluster.sync();  // everyone has read rank 0's slot before it is overwritten
+        if (pid >= nprob) break;
+        const BatchProblem p = probs[pid];
+        const int per = (p.n + kClusterCtas - 1) / kClusterCtas;
+        const int r0 = min(p.n, rank * per), r1 = min(p.n, r0 + per);
+
+        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) p.x[r] = 1.f;  // v = 1
+        cluster.sync();
+        float* X = p.x;
+        float* Ab = p.A;
+        for (int it = 0; it < iters; ++it) {
+            for (int h = 0; h < 2; ++h) {
+                const float* num = h == 0 ? p.a : p.b;
+                float* out = h == 0 ? p.us : p.vs;
+                if (p.K == 1) {
+                    order_rows(p, r0, r1, 2, p.coef[1], p.coef[0], X, nullptr, nullptr, num, out, Ab, flags);
+                    cluster.sync();
+                    float* t = X; X = Ab; Ab = t;
+                    continue;
+                }
+                order_rows(p, r0, r1, 0, p.coef[1], p.coef[0], X, nullptr, Ab, nullptr, nullptr, nullptr, flags);
+                cluster.sync();
+                float* prev = X;
+                float* cur = Ab;
+                for (int k = 2; k <= p.K; ++k) {
+                    if (k < p.K) {
+                        order_rows(p, r0, r1, 1, p.coef[k], 0.f, cur, prev, prev, nullptr, nullptr, nullptr, flags);
+                        cluster.sync();
+                        float* t = prev; prev = cur; cur = t;
+                    } else {
+                        order_rows(p, r0, r1, 2, p.coef[k], 0.f, cur, prev, nullptr, num, out, prev, flags);
+                        cluster.sync();
+                        X = prev;
+                        Ab = cur;
+                    }
+                }
+            }
+        }
+        // W^2 = 4t sum (a ln u + b ln v), FP64, rows of this CTA then the cluster through DSMEM
+        double acc = 0.0;
+        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+            const int o = node_of(p, r);
+            const float ai = p.a[o], bi = p.b[o], ui = p.us[r], vi = p.vs[r];
+            if (ai != 0.f) acc += (double)ai * log((double)ui);
+            if (bi != 0.f) acc += (double)bi * log((double)vi);
+            p.u[o] = ui;
+            p.v[o] = vi;
+        }
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) t += s_part[w];
+            s_total = t;
+        }
+        cluster.sync();
+        if (rank == 0 && threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < kClusterCtas; ++q) t += *cluster.map_shared_rank(&s_total, q);
+            const double w2 = p.t4 * t;
+            dist[2 * pid] = w2;
+            dist[2 * pid + 1] = w2 >= 0.0 ? sqrt(w2) : nan("");
+            if (!isfinite(w2)) atomicOr(flags, GS_FLAG_NONFINITE);
+        }
+        cluster.sync();  // s_total is reused by the next problem
+    }
+}
+
+}  // namespace
+
+gs_status gs_sinkhorn_batched_impl(gs_ctx* ctx, int nprob, const gs_graph* const* graphs,
+                                   const float* const* a, const float* const* b, const double* t,
+                                   const int* K, int iters, float* const* u, float* const* v,
+                                   double* dist)
+{
+    // order problems by work (nnz * K), largest first, for the dynamic queue
+    std::vector<int> order((size_t)nprob);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
+        return (double)graphs[i]->nnz * K[i] > (double)graphs[j]->nnz * K[j];
+    });
+    int64_t arena = 0, ncoef = 0;
+    for (int i = 0; i < nprob; ++i) {
+        arena += 5 * ((graphs[i]->n + 63) / 64 * 64);
+        ncoef += K[i] + 1;
+    }
+    WsPlan plan;
+    const size_t iar = plan.add(sizeof(float) * (size_t)arena), ico = plan.add(sizeof(float) * (size_t)ncoef),
+                 ipr = plan.add(sizeof(BatchProblem) * (size_t)nprob), iq = plan.add(sizeof(int) * 4),
+                 ids = plan.add(sizeof(double) * 2 * (size_t)nprob);
+    gs_status st = gs_ws_ensure(ctx, plan.total);
+    if (st != GS_OK) return st;
+    float* ar = ws_at<float>(ctx, plan, iar);
+    float* co = ws_at<float>(ctx, plan, ico);
+    BatchProblem* dprobs = ws_at<BatchProblem>(ctx, plan, ipr);
+    int* queue = ws_at<int>(ctx, plan, iq);
+    double* dsorted = ws_at<double>(ctx, plan, ids);  // distances in the sorted problem order
+
+    std::vector<BatchProblem> hp((size_t)nprob);
+    std::vector<float> hc((size_t)ncoef);
+    int64_t aoff = 0, coff = 0;
+    std::vector<double> c;
+    for (int q = 0; q < nprob; ++q) {
+        const int i = order[q];
+        const gs_graph* g = graphs[i];
+        BatchProblem& p = hp[q];
+        p.n = (int)g->n;
+        p.K = K[i];
+        p.t4 = 4.0 * t[i];
+        const bool ord = g->perm != nullptr;
+        p.rowptr = ord ? g->prowptr : g->rowptr;
+        p.col = ord ? g->pcol : g->col;
+        p.pval = ord ? g->ppval : g->pval;
+        p.perm = ord ? g->perm : nullptr;
+        p.a = a[i];
+        p.b = b[i];
+        p.u = u[i];
+        p.v = v[i];
+        const int64_t stride = (g->n + 63) / 64 * 64;
+        p.x = ar + aoff;
+        p.A = ar + aoff + stride;
+        p.y = ar + aoff + 2 * stride;
+        p.us = ar + aoff + 3 * stride;
+        p.vs = ar + aoff + 4 * stride;
+        aoff += 5 * stride;
+        c.assign((size_t)K[i] + 1, 0.0);
+        gs_heat_coefficients(t[i], K[i], c.data());
+        for (int k = 0; k <= K[i]; ++k) hc[(size_t)coff + k] = (float)c[k];
+        p.coef = co + coff;
+        coff += K[i] + 1;
+    }
+    cudaStream_t s = ctx->stream;
+    cudaMemcpyAsync(dprobs, hp.data(), sizeof(BatchProblem) * (size_t)nprob, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(co, hc.data(), sizeof(float) * (size_t)ncoef, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(queue, 0, sizeof(int), s);
+
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cfg.gridDim = dim3(kClusterCtas * 64);
+    if (cudaOccupancyMaxActiveClusters(&clusters, (void*)batched_sinkhorn, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        clusters = ctx->num_sms / kClusterCtas;
+    }
+    clusters = std::max(1, std::min(clusters, nprob));
+    cfg.gridDim = dim3(kClusterCtas * clusters);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, batched_sinkhorn, (const BatchProblem*)dprobs, nprob, iters,
+                                       queue, dsorted, ctx->flags);
+    gs_count(ctx, 1);
+    if ((st = gs_cuda_check(ctx, e, "batched Sinkhorn launch")) != GS_OK) return st;
+    if (dist) {
+        for (int q = 0; q < nprob; ++q)
+            cudaMemcpyAsync(dist + 2 * order[q], dsorted + 2 * q, 2 * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s);
+    }
+    return gs_cuda_check(ctx, cudaGetLastError(), "batched Sinkhorn");
+}

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(256) order_b1(const OrderArgs p)
             } else {  // EPI_DIVIDE
                 const float num = e.num[row];
                 const float r = safe_div(num, acc, p.flags);
+                if (e.fsave) e.fsave[row] = acc;
                 if (e.out) e.out[row] = r;
                 if (e.xnext) e.xnext[row] = e.vol ? e.vol[row] * r : r;
                 if (e.old) err = fabs((double)e.old[row] * (double)acc - (double)num);
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(256) order_blk(const OrderArgs p, int lpr_log2
                     e.out[base + v] = f[ch][v];
                 } else {
                     const float r = safe_div(e.num[base + v], f[ch][v], p.flags);
+                    if (e.fsave) e.fsave[base + v] = f[ch][v];
                     if (e.out) e.out[base + v] = r;
                     if (e.xnext) e.xnext[base + v] = vol * r;
                 }
@@ -222,6 +224,7 @@ __global__ void __launch_bounds__(256) order_blk(const OrderArgs p, int lpr_log2
         const int64_t base = row * (int64_t)B + c0;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
+            if (e.fsave) e.fsave[base + v] = f[ch][v];
             const float d = e.V[base + v] * f[ch][v];
             f[ch][v] = d;
             const double al = e.alpha[c0 + v];
@@ -364,11 +367,12 @@ gs_status gs_filter_enqueue(gs_ctx* ctx, const gs_graph* g, const double* c, int
         return gs_fail(ctx, GS_ERR_UNSUPPORTED, "B > 256 needs 16-byte aligned blocks with B % 4 == 0");
     const FilterPlan pl = gs_filter_plan(ctx, g, B, aligned);
     OrderArgs a;
+    const FilterCsr csr = gs_filter_csr(g);
     a.n = g->n;
     a.B = B;
-    a.rowptr = g->rowptr;
-    a.col = g->col;
-    a.pval = g->pval;
+    a.rowptr = csr.rowptr;
+    a.col = csr.col;
+    a.pval = csr.pval;
     a.done = done_flag;
     a.flags = ctx->flags;
     a.y = y;
@@ -467,17 +471,23 @@ void gs_graph_cache_clear(gs_ctx* ctx)
 
 // ----------------------------------------------------------------------------- Sinkhorn
 gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
-                           const float* vol, double t, int K, double eps, int iters, float* u,
-                           float* v, double* dist, int32_t* iters_done)
+                           const float* vol, double t, int K, double eps, int iters, float* u_user,
+                           float* v_user, double* dist, int32_t* iters_done)
 {
     std::vector<double> c((size_t)K + 1);
     gs_heat_coefficients(t, K, c.data());
     const int64_t n = g->n;
+    const bool perm = g->perm != nullptr;       // the loop runs in the filter's node order
+    const bool own_uv = perm || !u_user || !v_user;
+    const size_t vec = sizeof(float) * (size_t)n;
     WsPlan plan;
-    const size_t ix = plan.add(sizeof(float) * n), iA = plan.add(sizeof(float) * n),
-                 iy = plan.add(sizeof(float) * n), iu = plan.add(sizeof(float) * n),
+    const size_t ix = plan.add(vec), iA = plan.add(vec), iy = plan.add(vec), iu = plan.add(vec),
                  ie = plan.add(sizeof(double) * 2), id = plan.add(sizeof(int) * 2),
                  ip = plan.add(sizeof(double) * gs_reduce_blocks());
+    const size_t iuu = own_uv ? plan.add(vec) : 0, ivv = own_uv ? plan.add(vec) : 0;
+    const size_t icf = plan.add(sizeof(float) * ((size_t)K + 1)), ibar = plan.add(sizeof(unsigned) * 4);
+    const size_t iap = perm ? plan.add(vec) : 0, ibp = perm ? plan.add(vec) : 0,
+                 ivp = (perm && vol) ? plan.add(vec) : 0;
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
     float* x = ws_at<float>(ctx, plan, ix);
@@ -487,6 +497,21 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
     double* err = ws_at<double>(ctx, plan, ie);
     int* done = ws_at<int>(ctx, plan, id);
     double* partials = ws_at<double>(ctx, plan, ip);
+    float* u = own_uv ? ws_at<float>(ctx, plan, iuu) : u_user;
+    float* v = own_uv ? ws_at<float>(ctx, plan, ivv) : v_user;
+    if (perm) {
+        float* ap = ws_at<float>(ctx, plan, iap);
+        float* bp = ws_at<float>(ctx, plan, ibp);
+        gs_permute_rows(ctx, n, 1, g->perm, a, ap, true);
+        gs_permute_rows(ctx, n, 1, g->perm, b, bp, true);
+        a = ap;
+        b = bp;
+        if (vol) {
+            float* vp = ws_at<float>(ctx, plan, ivp);
+            gs_permute_rows(ctx, n, 1, g->perm, vol, vp, true);
+            vol = vp;
+        }
+    }
     const bool use_eps = eps > 0.0;
     const int* dflag = use_eps ? done : nullptr;
 
@@ -515,7 +540,22 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
         return s;
     };
 
-    if (!use_eps) {
+    bool looped = false;
+    if (!use_eps && ctx->loop_mode == 0) {
+        // Fixed iteration count, default: the whole loop as one persistent cooperative launch.
+        std::vector<float> cf((size_t)K + 1);
+        for (int k = 0; k <= K; ++k) cf[k] = (float)c[k];
+        float* cdev = ws_at<float>(ctx, plan, icf);
+        cudaMemcpyAsync(cdev, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice, ctx->stream);
+        st = gs_sinkhorn_persistent(ctx, g, a, b, vol, cdev, K, iters, x, A, y, u, v,
+                                    ws_at<unsigned>(ctx, plan, ibar));
+        if (st == GS_OK) looped = true;
+        else if (st != GS_ERR_UNSUPPORTED) return st;
+        st = GS_OK;
+    }
+    if (looped) {
+        // done
+    } else if (!use_eps) {
         // Fixed iteration count: replay captured CUDA graphs of R and 1 iterations.  Both halves
         // swap the (x, A) roles the same number of times, so every iteration starts from the
         // same buffers and one captured iteration is valid for all of them.
@@ -592,27 +632,51 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
         if ((st = gs_distance_enqueue(ctx, n, a, b, vol, u, v, t, partials, dist)) != GS_OK)
             return st;
     }
+    if (own_uv && u_user && v_user) {
+        if (perm) {
+            gs_permute_rows(ctx, n, 1, g->perm, u, u_user, false);
+            gs_permute_rows(ctx, n, 1, g->perm, v, v_user, false);
+        } else {
+            cudaMemcpyAsync(u_user, u, vec, cudaMemcpyDeviceToDevice, ctx->stream);
+            cudaMemcpyAsync(v_user, v, vec, cudaMemcpyDeviceToDevice, ctx->stream);
+        }
+    }
     return gs_cuda_check(ctx, cudaGetLastError(), "Sinkhorn loop");
 }
 
 // --------------------------------------------------------------------------- barycenter
 gs_status gs_barycenter_impl(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
                              const double* alpha, const float* vol, double t, int K, int iters,
-                             float* mu, float* v_state)
+                             float* mu_user, float* v_state)
 {
     std::vector<double> c((size_t)K + 1);
     gs_heat_coefficients(t, K, c.data());
     const int64_t n = g->n;
+    const bool perm = g->perm != nullptr;
     const size_t blk = sizeof(float) * (size_t)n * (size_t)m;
+    const size_t vec = sizeof(float) * (size_t)n;
     WsPlan plan;
-    const size_t ix = plan.add(blk), iA = plan.add(blk), iy = plan.add(blk),
-                 iV = v_state ? 0 : plan.add(blk);
+    const size_t ix = plan.add(blk), iA = plan.add(blk), iy = plan.add(blk), iV = plan.add(blk);
+    const size_t iM = perm ? plan.add(blk) : 0, imu = perm ? plan.add(vec) : 0,
+                 ivp = (perm && vol) ? plan.add(vec) : 0;
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
     float* x = ws_at<float>(ctx, plan, ix);
     float* A = ws_at<float>(ctx, plan, iA);
     float* y = ws_at<float>(ctx, plan, iy);
-    float* V = v_state ? v_state : ws_at<float>(ctx, plan, iV);
+    float* V = ws_at<float>(ctx, plan, iV);
+    float* mu = mu_user;
+    if (perm) {
+        float* Mp = ws_at<float>(ctx, plan, iM);
+        gs_permute_rows(ctx, n, m, g->perm, M, Mp, true);
+        M = Mp;
+        mu = ws_at<float>(ctx, plan, imu);
+        if (vol) {
+            float* vp = ws_at<float>(ctx, plan, ivp);
+            gs_permute_rows(ctx, n, 1, g->perm, vol, vp, true);
+            vol = vp;
+        }
+    }
     const int64_t nm = n * (int64_t)m;
     fill_kernel<<<nblocks(nm, 256), 256, 0, ctx->stream>>>(nm, V, nullptr, m, 1.f);
     fill_kernel<<<nblocks(nm, 256), 256, 0, ctx->stream>>>(nm, x, vol, m, 1.f);
@@ -641,5 +705,11 @@ gs_status gs_barycenter_impl(gs_ctx* ctx, const gs_graph* g, const float* M, int
         if (scratch != x) std::swap(x, A);
     }
     if (st != GS_OK) return st;
+    if (perm) {
+        gs_permute_rows(ctx, n, 1, g->perm, mu, mu_user, false);
+        if (v_state) gs_permute_rows(ctx, n, m, g->perm, V, v_state, false);
+    } else if (v_state) {
+        cudaMemcpyAsync(v_state, V, blk, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
     return gs_cuda_check(ctx, cudaGetLastError(), "barycenter loop");
 }

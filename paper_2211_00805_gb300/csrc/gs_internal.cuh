@@ -35,6 +35,8 @@ struct gs_ctx {
     size_t ws_bytes = 0;
     int num_sms = 0;
     bool capturing = false;        // inside an internal capture: launches are not counted
+    int loop_mode = 0;             // fixed-count Sinkhorn: 0 persistent launch, 1 CUDA-graph replay
+    int barrier_selftest = 0;      // next persistent launch waits for an arrival that never comes
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::string err;
@@ -57,7 +59,26 @@ struct gs_graph {
     float* aval = nullptr;         // [nnz] A_ij
     double* deg = nullptr;         // [n] degrees
     float mean_row = 0.f;          // nnz / n, steers the row-split width of the B = 1 kernel
+    // locality order used by the filter (breadth-first renumbering, order.cu); null = none
+    int* perm = nullptr;           // [n] new position -> node id
+    int* iperm = nullptr;          // [n] node id -> new position
+    int* prowptr = nullptr;        // [n+1] CSR of P in the new order
+    int* pcol = nullptr;
+    float* ppval = nullptr;
+    int levels = 0;                // breadth-first levels of the ordering sweep
 };
+
+// The CSR the filter kernels read: the reordered one when present.
+struct FilterCsr {
+    const int* rowptr;
+    const int* col;
+    const float* pval;
+};
+static inline FilterCsr gs_filter_csr(const gs_graph* g)
+{
+    if (g->prowptr) return FilterCsr{g->prowptr, g->pcol, g->ppval};
+    return FilterCsr{g->rowptr, g->col, g->pval};
+}
 
 // ------------------------------------------------------------------------------ helpers
 gs_status gs_fail(gs_ctx* ctx, gs_status st, const std::string& msg);
@@ -92,7 +113,14 @@ gs_status gs_graph_import_csr(gs_ctx* ctx, int64_t n, const int64_t* rowptr, con
 gs_status gs_graph_export(gs_ctx* ctx, const gs_graph* g, int64_t* rowptr, int32_t* col, float* A,
                           float* P);
 
+// --------------------------------------------------------------------- order.cu
+gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g);
+// dst[r, :] = src[perm[r], :] (to the filter's order) or dst[perm[r], :] = src[r, :] (back)
+void gs_permute_rows(gs_ctx* ctx, int64_t n, int B, const int* perm, const float* src, float* dst,
+                     bool to_filter_order);
+
 // --------------------------------------------------------------------- knn.cu
+void gs_exclusive_scan(cudaStream_t s, const int* cnt, int64_t n, int64_t* out, int64_t* sums);
 gs_status gs_knn_launch(gs_ctx* ctx, const float* X, int64_t n, int d, int k, int32_t* idx,
                         float* dist, double* dist64);
 gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int k, float sigma,
@@ -121,6 +149,7 @@ struct Epilogue {
     const double* alpha = nullptr; // [m]
     float* mu = nullptr;           // [n] barycenter output (BARY_V)
     float* dsave = nullptr;        // [n, m] optional copy of d (tape for the adjoint)
+    float* fsave = nullptr;        // [n, B] optional copy of the filter value f (adjoint tape)
 };
 
 struct FilterPlan {
@@ -147,6 +176,19 @@ bool gs_filter_supports(int B, bool aligned);
 gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
                            const float* vol, double t, int K, double eps, int iters, float* u,
                            float* v, double* dist, int32_t* iters_done);
+gs_status gs_sinkhorn_grad_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
+                                const float* vol, double t, int K, int iters, int ck,
+                                double* dist, float* grad_a, float* grad_b);
+gs_status gs_barycenter_grad_impl(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
+                                  const double* alpha, const float* vol, double t, int K, int iters,
+                                  int ck, const float* mubar, float* mu_out, double* grad_alpha);
+gs_status gs_sinkhorn_batched_impl(gs_ctx* ctx, int nprob, const gs_graph* const* graphs,
+                                   const float* const* a, const float* const* b, const double* t,
+                                   const int* K, int iters, float* const* u, float* const* v,
+                                   double* dist);
+gs_status gs_sinkhorn_persistent(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
+                                 const float* vol, const float* coef_dev, int K, int iters,
+                                 float* x, float* A, float* y, float* u, float* v, unsigned* bar);
 gs_status gs_barycenter_impl(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
                              const double* alpha, const float* vol, double t, int K, int iters,
                              float* mu, float* v_state);

@@ -299,13 +299,17 @@ __global__ void scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __
     if (i < n) out[i] += sums[i / SCAN_TILE];
 }
 
-void exclusive_scan(cudaStream_t s, const int* cnt, int64_t n, int64_t* out, int64_t* sums)
+}  // namespace
+
+void gs_exclusive_scan(cudaStream_t s, const int* cnt, int64_t n, int64_t* out, int64_t* sums)
 {
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     scan_tiles<<<(unsigned)nb, SCAN_T, 0, s>>>(cnt, n, out, sums);
     scan_sums<<<1, 32, 0, s>>>(sums, nb, out + n);
     scan_add<<<nblk(n, 256), 256, 0, s>>>(out, n, sums);
 }
+
+namespace {
 
 // --------------------------------------------------------------------------- symmetrise
 __global__ void in_count(const int32_t* __restrict__ idx, int64_t nk, int* __restrict__ cnt)
@@ -498,14 +502,14 @@ gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int
     cudaMemsetAsync(cnt, 0, sizeof(int) * n, s);
     cudaMemsetAsync(cur, 0, sizeof(int) * n, s);
     in_count<<<nblk(nk, 256), 256, 0, s>>>(idx, nk, cnt);
-    exclusive_scan(s, cnt, n, inptr, sums);
+    gs_exclusive_scan(s, cnt, n, inptr, sums);
     in_fill<<<nblk(nk, 256), 256, 0, s>>>(idx, d64, n, k, inptr, cur, in_src, in_d);
     sort_rows_by_col<<<nblk(n, 128), 128, 0, s>>>(n, inptr, 0, in_src, in_d);
     sort_rows_by_col<<<nblk(n, 128), 128, 0, s>>>(n, nullptr, k, idx, d64);
     union_rows<false><<<nblk(n, 128), 128, 0, s>>>(n, k, idx, d64, inptr, in_src, in_d, cnt,
                                                     nullptr, nullptr, nullptr, nullptr, nullptr,
                                                     nullptr);
-    exclusive_scan(s, cnt, n, rp64, sums);
+    gs_exclusive_scan(s, cnt, n, rp64, sums);
     gs_count(ctx, 11);
     int64_t nnz = 0;
     double hsig[1] = {0.0};
@@ -534,6 +538,10 @@ gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int
     if (hbad) {
         gs_graph_destroy(g);
         return gs_fail(ctx, GS_ERR_ARG, "graph has a node with zero degree");
+    }
+    if ((st = gs_graph_reorder(ctx, g)) != GS_OK) {
+        gs_graph_destroy(g);
+        return st;
     }
     *out = g;
     return GS_OK;

@@ -1,0 +1,244 @@
+// Locality-preserving node order for the sparse products (a Cuthill-McKee sweep without the
+// degree sort), computed on the GPU level by level, and the graph permuted into that order.
+//
+// The filter gathers neighbour rows of the previous block for every edge.  With nodes in the
+// order the points arrived (random), every gather is a fresh cache line; after a breadth-first
+// renumbering a node's neighbours sit in the previous, current or next level, and nodes placed
+// next to each other share most of their neighbours, so consecutive rows processed by one thread
+// block hit the same lines in L1.
+//
+// Deterministic parallel level construction: every unvisited neighbour w of the current level is
+// owned by the lowest-positioned parent that reaches it (atomicMin); each parent counts the
+// children it owns, an exclusive scan over the level turns counts into slots, and each parent
+// writes its children in ascending node id.  A second sweep starts from the last node of a first
+// sweep from node 0 (a pseudo-peripheral start).  Disconnected parts restart from the lowest
+// unvisited node.
+#include <vector>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+inline unsigned nblk(int64_t work, int per) { return (unsigned)((work + per - 1) / per); }
+
+__global__ void order_init(int64_t n, int* __restrict__ iperm, int* __restrict__ owner)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        iperm[i] = -1;
+        owner[i] = 0x7fffffff;
+    }
+}
+
+__global__ void order_root(int* __restrict__ perm, int* __restrict__ iperm, int pos,
+                           const int* __restrict__ root, int64_t n)
+{
+    const int r = *root;
+    if (r < 0 || r >= n) return;  // cannot happen while unvisited nodes remain; never index past n
+    perm[pos] = r;
+    iperm[r] = pos;
+}
+
+__global__ void order_first_unvisited(int64_t n, const int* __restrict__ iperm, int* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && iperm[i] < 0) atomicMin(out, (int)i);
+}
+
+__global__ void order_claim(int lo, int hi, const int* __restrict__ perm,
+                            const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const int* __restrict__ iperm, int* __restrict__ owner)
+{
+    const int p = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= hi) return;
+    const int u = perm[p];
+    for (int e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+        const int w = col[e];
+        if (iperm[w] < 0) atomicMin(&owner[w], p);
+    }
+}
+
+__global__ void order_count(int lo, int hi, const int* __restrict__ perm,
+                            const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const int* __restrict__ iperm, const int* __restrict__ owner,
+                            int* __restrict__ cnt)
+{
+    const int p = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= hi) return;
+    const int u = perm[p];
+    int c = 0;
+    for (int e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+        const int w = col[e];
+        c += (iperm[w] < 0 && owner[w] == p);
+    }
+    cnt[p - lo] = c;
+}
+
+__global__ void order_place(int lo, int hi, const int* perm_in, int* perm,
+                            const int* __restrict__ rowptr, const int* __restrict__ col,
+                            int* __restrict__ iperm, const int* __restrict__ owner,
+                            const int64_t* __restrict__ offs)
+{
+    const int p = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= hi) return;
+    const int u = perm_in[p];
+    int j = hi + (int)offs[p - lo];
+    for (int e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+        const int w = col[e];
+        if (owner[w] == p && iperm[w] < 0) {
+            perm[j] = w;
+            iperm[w] = j;
+            ++j;
+        }
+    }
+}
+
+// Permuted CSR: new row r holds old row perm[r] with columns renamed by iperm, sorted ascending.
+__global__ void permute_count(int64_t n, const int* __restrict__ perm, const int* __restrict__ rowptr,
+                              int* __restrict__ cnt)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int o = perm[r];
+    cnt[r] = rowptr[o + 1] - rowptr[o];
+}
+
+__global__ void permute_fill(int64_t n, const int* __restrict__ perm, const int* __restrict__ iperm,
+                             const int* __restrict__ rowptr, const int* __restrict__ col,
+                             const float* __restrict__ pval, const int64_t* __restrict__ prow64,
+                             int* __restrict__ pcol, float* __restrict__ ppval)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int o = perm[r];
+    const int b = (int)prow64[r];
+    const int len = rowptr[o + 1] - rowptr[o];
+    for (int i = 0; i < len; ++i) {  // insertion sort by new column id (rows are short)
+        const int c = iperm[col[rowptr[o] + i]];
+        const float v = pval[rowptr[o] + i];
+        int j = b + i - 1;
+        while (j >= b && pcol[j] > c) {
+            pcol[j + 1] = pcol[j];
+            ppval[j + 1] = ppval[j];
+            --j;
+        }
+        pcol[j + 1] = c;
+        ppval[j + 1] = v;
+    }
+}
+
+__global__ void permute_rows_kernel(int64_t count, int B, const int* __restrict__ perm,
+                                    const float* __restrict__ src, float* __restrict__ dst, int to)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t r = i / B, c = i - r * B;
+    const int64_t o = (int64_t)perm[r] * B + c;
+    if (to) dst[i] = src[o];
+    else dst[o] = src[i];
+}
+
+__global__ void rowptr_narrow(int64_t n1, const int64_t* __restrict__ in, int* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n1) out[i] = (int)in[i];
+}
+
+}  // namespace
+
+void gs_permute_rows(gs_ctx* ctx, int64_t n, int B, const int* perm, const float* src, float* dst,
+                     bool to_filter_order)
+{
+    const int64_t count = n * (int64_t)B;
+    permute_rows_kernel<<<nblk(count, 256), 256, 0, ctx->stream>>>(count, B, perm, src, dst,
+                                                                    to_filter_order ? 1 : 0);
+    gs_count(ctx, 1);
+}
+
+// One breadth-first sweep from `root` (device int), producing perm/iperm over all components.
+static gs_status bfs_sweep(gs_ctx* ctx, const gs_graph* g, const int* root, int* perm, int* iperm,
+                           int* owner, int* cnt, int64_t* offs, int64_t* sums, int* scratch_int,
+                           int* levels_out)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t n = g->n;
+    order_init<<<nblk(n, 256), 256, 0, s>>>(n, iperm, owner);
+    order_root<<<1, 1, 0, s>>>(perm, iperm, 0, root, n);
+    gs_count(ctx, 2);
+    int lo = 0, hi = 1, levels = 0;
+    while (hi < n) {
+        const int m = hi - lo;
+        order_claim<<<nblk(m, 128), 128, 0, s>>>(lo, hi, perm, g->rowptr, g->col, iperm, owner);
+        order_count<<<nblk(m, 128), 128, 0, s>>>(lo, hi, perm, g->rowptr, g->col, iperm, owner, cnt);
+        gs_exclusive_scan(s, cnt, m, offs, sums);
+        order_place<<<nblk(m, 128), 128, 0, s>>>(lo, hi, perm, perm, g->rowptr, g->col, iperm, owner, offs);
+        gs_count(ctx, 6);
+        int64_t total = 0;
+        cudaMemcpyAsync(&total, offs + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        gs_status st = gs_cuda_check(ctx, cudaStreamSynchronize(s), "node ordering");
+        if (st != GS_OK) return st;
+        ++levels;
+        if (total > 0) {
+            lo = hi;
+            hi += (int)total;
+            continue;
+        }
+        // this component is exhausted: restart from the lowest unvisited node
+        int init = 0x7fffffff;
+        cudaMemcpyAsync(scratch_int, &init, sizeof(int), cudaMemcpyHostToDevice, s);
+        order_first_unvisited<<<nblk(n, 256), 256, 0, s>>>(n, iperm, scratch_int);
+        order_root<<<1, 1, 0, s>>>(perm, iperm, hi, scratch_int, n);
+        gs_count(ctx, 2);
+        lo = hi;
+        hi += 1;
+    }
+    if (levels_out) *levels_out = levels;
+    return gs_cuda_check(ctx, cudaGetLastError(), "node ordering");
+}
+
+gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
+{
+    const int64_t n = g->n, nnz = g->nnz;
+    WsPlan plan;
+    const size_t i_owner = plan.add(sizeof(int) * n), i_cnt = plan.add(sizeof(int) * n),
+                 i_offs = plan.add(sizeof(int64_t) * (n + 1)),
+                 i_sums = plan.add(sizeof(int64_t) * (n / 4096 + 2)), i_int = plan.add(sizeof(int) * 4),
+                 i_p64 = plan.add(sizeof(int64_t) * (n + 1));
+    gs_status st = gs_ws_ensure(ctx, plan.total);
+    if (st != GS_OK) return st;
+    int* owner = ws_at<int>(ctx, plan, i_owner);
+    int* cnt = ws_at<int>(ctx, plan, i_cnt);
+    int64_t* offs = ws_at<int64_t>(ctx, plan, i_offs);
+    int64_t* sums = ws_at<int64_t>(ctx, plan, i_sums);
+    int* sint = ws_at<int>(ctx, plan, i_int);
+    int64_t* p64 = ws_at<int64_t>(ctx, plan, i_p64);
+
+    cudaError_t e = cudaMalloc(&g->perm, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->iperm, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->prowptr, sizeof(int) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->pcol, sizeof(int) * (nnz > 0 ? nnz : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->ppval, sizeof(float) * (nnz > 0 ? nnz : 1));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return gs_fail(ctx, GS_ERR_OOM, "graph ordering allocation failed");
+    }
+    cudaStream_t s = ctx->stream;
+    // sweep 1 from node 0; sweep 2 from the node it placed last
+    const int zero = 0;
+    cudaMemcpyAsync(sint + 1, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+    int levels = 0;
+    if ((st = bfs_sweep(ctx, g, sint + 1, g->perm, g->iperm, owner, cnt, offs, sums, sint, &levels)) != GS_OK)
+        return st;
+    cudaMemcpyAsync(sint + 2, g->perm + (n - 1), sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if ((st = bfs_sweep(ctx, g, sint + 2, g->perm, g->iperm, owner, cnt, offs, sums, sint, &levels)) != GS_OK)
+        return st;
+    g->levels = levels;
+    // permuted CSR
+    permute_count<<<nblk(n, 256), 256, 0, s>>>(n, g->perm, g->rowptr, cnt);
+    gs_exclusive_scan(s, cnt, n, p64, sums);
+    rowptr_narrow<<<nblk(n + 1, 256), 256, 0, s>>>(n + 1, p64, g->prowptr);
+    permute_fill<<<nblk(n, 128), 128, 0, s>>>(n, g->perm, g->iperm, g->rowptr, g->col, g->pval, p64,
+                                              g->pcol, g->ppval);
+    gs_count(ctx, 6);
+    return gs_cuda_check(ctx, cudaStreamSynchronize(s), "graph permutation");
+}

@@ -1,0 +1,140 @@
+"""GPU reverse mode (gs_sinkhorn_grad / gs_barycenter_grad, the autograd wrappers) and the batched
+persistent solver (gs_sinkhorn_batched) against the FP64 oracle and the single-problem path.
+
+Gradient tolerance: |gpu - ref| <= 2e-3 |ref| + 2e-4 max|ref|.  The reverse sweep is 2 * iters
+FP32 filter applies deep, each adding ~K eps_32 relative error to values whose sizes span the
+whole vector, so entries far below the maximum carry an absolute floor.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_00805_gb300 import workloads as W
+from tests.gpu_common import assert_close, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+GRTOL, GATOL_REL = 2e-3, 2e-4
+
+
+@pytest.fixture(scope="module")
+def gs():
+    from paper_2211_00805_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(gs):
+    return gs.Context()
+
+
+@pytest.fixture(scope="module")
+def sphere(gs, ctx):
+    p = W.sphere_pair(n=1500, kappa=8.0)
+    g = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    Ls, ex = oracle.build_graph(p.X.astype(np.float64), p.k)
+    return p, g, Ls
+
+
+@pytest.mark.parametrize("ck", [1, 7, 30])
+def test_sinkhorn_grad_matches_oracle(gs, ctx, sphere, ck):
+    p, g, Ls = sphere
+    t, K, it = 5.0, 30, 30
+    vol = np.random.default_rng(3).uniform(0.7, 1.3, len(p.a)).astype(np.float32)
+    dist, ga, gb = gs.gs_sinkhorn_grad(ctx, g, to_dev(p.a), to_dev(p.b), t, K, it, checkpoint=ck,
+                                       vol=to_dev(vol))
+    gs.gs_sync(ctx)
+    W2, rga, rgb = oracle.sinkhorn_grad(Ls, oracle.cheb_coefficients(t, K), p.a.astype(np.float64),
+                                        p.b.astype(np.float64), t, it, a=vol.astype(np.float64))
+    assert to_np(dist)[0] == pytest.approx(W2, rel=1e-4)
+    assert_close(to_np(ga), rga, GRTOL, GATOL_REL * np.abs(rga).max(), f"dW2/da ck={ck}")
+    assert_close(to_np(gb), rgb, GRTOL, GATOL_REL * np.abs(rgb).max(), f"dW2/db ck={ck}")
+
+
+def test_sinkhorn_grad_checkpoint_invariant(gs, ctx, sphere):
+    p, g, Ls = sphere
+    outs = [gs.gs_sinkhorn_grad(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 25, checkpoint=c)
+            for c in (1, 4, 25)]
+    for d, ga, gb in outs[1:]:
+        assert torch.equal(ga, outs[0][1]) and torch.equal(gb, outs[0][2])
+
+
+def test_sinkhorn_grad_vs_oracle_finite_differences(gs, ctx, sphere):
+    # GPU gradient against FP64 central differences of the oracle's forward map (relative step
+    # 1e-4 a_i, as the differentiation workload prescribes), on the largest-mass coordinates
+    p, g, Ls = sphere
+    t, K, it = 5.0, 30, 20
+    a64, b64 = p.a.astype(np.float64), p.b.astype(np.float64)
+    bk = oracle.cheb_coefficients(t, K)
+    _, ga, _ = gs.gs_sinkhorn_grad(ctx, g, to_dev(p.a), to_dev(p.b), t, K, it)
+    ga = to_np(ga)
+    for i in np.argsort(-a64)[:3]:
+        h = 1e-4 * a64[i]
+        ap, am = a64.copy(), a64.copy()
+        ap[i] += h
+        am[i] -= h
+        fd = (oracle.sinkhorn(Ls, bk, ap, b64, t, it)["W2"]
+              - oracle.sinkhorn(Ls, bk, am, b64, t, it)["W2"]) / (2 * h)
+        assert ga[i] == pytest.approx(fd, rel=2e-3, abs=GATOL_REL * np.abs(ga).max())
+
+
+def test_barycenter_grad_matches_oracle(gs, ctx):
+    cfg = W.clusters_barycenter(n=3000, m=8, iters=12)
+    X, M = cfg["X"], cfg["M"]
+    alpha = np.random.default_rng(2).dirichlet(np.ones(8))
+    g = gs.gs_build_graph(ctx, to_dev(X), cfg["k"])
+    Ls, _ = oracle.build_graph(X.astype(np.float64), cfg["k"])
+    t, K, it = 10.0, 40, 12
+    mubar = np.random.default_rng(5).standard_normal(len(X)).astype(np.float32)
+    mu, galpha = gs.gs_barycenter_grad(ctx, g, to_dev(M), to_dev(alpha, torch.float64), t, K, it,
+                                       to_dev(mubar), checkpoint=5)
+    gs.gs_sync(ctx)
+    rmu, ralpha = oracle.barycenter_grad(Ls, oracle.cheb_coefficients(t, K), M.astype(np.float64),
+                                         alpha, it, mubar.astype(np.float64))
+    assert_close(to_np(mu), rmu, 1e-4, 1e-6 * rmu.max(), "mu")
+    assert_close(to_np(galpha), ralpha, GRTOL, GATOL_REL * np.abs(ralpha).max(), "dalpha")
+
+
+def test_autograd_distance_to_barycenter(gs, ctx):
+    from paper_2211_00805_gb300.autograd import geodesic_barycenter, geodesic_sinkhorn_distance
+    cfg = W.manifold_barycenter_grad(n=2500, m=6, bary_iters=10, sink_iters=12)
+    X, M, src = cfg["X"], cfg["M"], cfg["src"]
+    g = gs.gs_build_graph(ctx, to_dev(X), cfg["k"])
+    Ls, _ = oracle.build_graph(X.astype(np.float64), cfg["k"])
+    t, K = cfg["t"], cfg["K"]
+    alpha = torch.tensor(cfg["alpha"], dtype=torch.float64, device="cuda", requires_grad=True)
+    a = to_dev(src).requires_grad_(True)
+    mu = geodesic_barycenter(ctx, g, to_dev(M), alpha, t, K, cfg["bary_iters"], checkpoint=4)
+    J = geodesic_sinkhorn_distance(ctx, g, a, mu, t, K, cfg["sink_iters"], checkpoint=5)
+    J.backward()
+    gs.gs_sync(ctx)
+    rJ, rgs, rga = oracle.barycenter_distance_grad(Ls, oracle.cheb_coefficients(t, K),
+                                                   src.astype(np.float64), M.astype(np.float64),
+                                                   cfg["alpha"], t, cfg["bary_iters"], cfg["sink_iters"])
+    assert float(J) == pytest.approx(rJ, rel=1e-4)
+    assert_close(to_np(a.grad), rgs, GRTOL, GATOL_REL * np.abs(rgs).max(), "dJ/dsrc")
+    assert_close(to_np(alpha.grad), rga, GRTOL, GATOL_REL * np.abs(rga).max(), "dJ/dalpha")
+
+
+# ----------------------------------------------------------------------------------- batched
+def test_batched_matches_single_and_oracle(gs, ctx):
+    probs = W.ragged_batch(count=10, n_min=600, n_max=6000, iters=40)
+    graphs = [gs.gs_build_graph(ctx, to_dev(p.X), p.k) for p in probs]
+    a = [to_dev(p.a) for p in probs]
+    b = [to_dev(p.b) for p in probs]
+    u, v, dist = gs.gs_sinkhorn_batched(ctx, graphs, a, b, [p.t for p in probs], [p.K for p in probs], 40)
+    gs.gs_sync(ctx)
+    d = to_np(dist)
+    for i, (p, g) in enumerate(zip(probs, graphs)):
+        us, vs, ds, _ = gs.gs_sinkhorn(ctx, g, a[i], b[i], p.t, p.K, 40)
+        gs.gs_sync(ctx)
+        assert d[i, 0] == pytest.approx(to_np(ds)[0], rel=1e-5)
+        m = p.a > 0
+        assert_close(to_np(u[i]), to_np(us), 1e-4, 0, f"u[{i}]", mask=m)
+    for i in (0, 7):
+        p = probs[i]
+        Ls, _ = oracle.build_graph(p.X.astype(np.float64), p.k)
+        r = oracle.sinkhorn(Ls, oracle.cheb_coefficients(p.t, p.K), p.a.astype(np.float64),
+                            p.b.astype(np.float64), p.t, 40)
+        assert d[i, 0] == pytest.approx(r["W2"], rel=1e-4)

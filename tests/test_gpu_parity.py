@@ -305,3 +305,30 @@ def test_barycenter_matches_oracle(gs, ctx, m):
                                   cfg["iters"], return_state=True)
     assert_close(mu, ref, 1e-4, 1e-6 * ref.max(), f"mu m={m}")
     assert_close(to_np(V), Vref, 1e-3, 1e-6 * np.abs(Vref).max(), f"v_i m={m}")
+
+
+# ------------------------------------------------------------------------- loop modes, faults
+def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph):
+    p, g, Ls = sphere_graph
+    out = {}
+    for mode in (0, 1):
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
+        u, v, d, _ = gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 120)
+        gs.gs_sync(ctx)
+        out[mode] = (to_np(u), to_np(v), to_np(d))
+    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 0)
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+
+
+def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sphere_graph):
+    # the self-test makes every block wait for an arrival that never comes; the bounded wait runs
+    # out, the launch ends, gs_sync reports the timeout, and the next call works normally
+    p, g, Ls = sphere_graph
+    gs.gs_set_option(ctx, gs.GS_OPT_BARRIER_SELFTEST, 1)
+    gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 10)
+    with pytest.raises(gs.GeosinkError) as e:
+        gs.gs_sync(ctx)
+    assert e.value.status == gs.GS_ERR_TIMEOUT
+    _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 50)
