@@ -154,6 +154,29 @@ gs_status gs_graph_destroy(gs_graph *g);
 gs_status gs_heat_apply(gs_ctx *ctx, const gs_graph *g, double t, int K, const float *V, int B,
                         float *Y);
 
+/* Allocation-free variant of gs_heat_apply for callers that cannot allocate device memory: code
+ * that runs while a CUDA graph is being captured, plug-ins whose host application owns every
+ * device allocation, loops that must never enter the allocator.  The paper has no counterpart;
+ * this is a deployment convenience.
+ * It computes the same Y = p_K(L, t) V with the same kernels, but takes the operator as plain
+ * CSR device arrays (rowptr [n+1] int32 offsets, col [nnz] int32, pval [nnz] FP32 holding
+ * P = D^{-1/2} A D^{-1/2}, as gs_graph_export_csr returns them once rowptr is narrowed to int32)
+ * and needs no gs_ctx or gs_graph.  Its two scratch blocks live in a fixed 8 MiB device array
+ * inside the library, present on every GPU that loads it until the process exits, so
+ * n * B <= 1,048,576 (2^20) is required (GS_ERR_UNSUPPORTED otherwise).  No cudaMalloc, cudaFree
+ * or other device allocation happens in this call.
+ *   - Works on the calling thread's current device; `stream` is a cudaStream_t as void*.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture.
+ *   - Every call shares the one scratch array: calls that overlap on the GPU (other streams,
+ *     other threads) race and corrupt each other; serialise them.  Nothing in the scratch must
+ *     start at zero, so stale contents from an earlier call do no harm.
+ * Same limits on t, K and B as gs_heat_apply.  Returns GS_ERR_ARG / GS_ERR_UNSUPPORTED /
+ * GS_ERR_CUDA (no message: there is no context). */
+gs_status gs_heat_apply_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
+                                const float *pval, double t, int K, const float *V, int B,
+                                float *Y, void *stream);
+
 /* ----------------------------------------------------------------------------- Sinkhorn --- */
 
 /* Algorithm 1 (Geodesic Sinkhorn): v <- 1; repeat { u <- a / p_K(vol * v); v <- b / p_K(vol * u) }

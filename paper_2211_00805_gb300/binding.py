@@ -40,6 +40,7 @@ SIGNATURES = {
     "gs_graph_export_csr": [_P, _P, _P, _P, _P, _P],
     "gs_graph_destroy": [_P],
     "gs_heat_apply": [_P, _P, _D, _I, _P, _I, _P],
+    "gs_heat_apply_noalloc": [_I64, _I64, _P, _P, _P, _D, _I, _P, _I, _P, _P],
     "gs_sinkhorn": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P],
     "gs_distance": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P],
     "gs_barycenter": [_P, _P, _P, _I, _P, _P, _D, _I, _I, _P, _P],
@@ -227,6 +228,28 @@ def gs_heat_apply(ctx: Context, g: Graph, t: float, K: int, V: torch.Tensor, out
         raise ValueError("V must have n rows")
     Y = torch.empty_like(V2) if out is None else _dev(out, torch.float32, "Y").view(V2.shape)
     _raise(ctx, _lib.gs_heat_apply(ctx.handle, g.handle, float(t), int(K), _ptr(V2), V2.shape[1], _ptr(Y)))
+    return Y.view(V.shape) if squeeze else Y
+
+
+def gs_heat_apply_noalloc(rowptr32: torch.Tensor, col: torch.Tensor, pval: torch.Tensor, t: float,
+                          K: int, V: torch.Tensor, out: torch.Tensor | None = None,
+                          stream: torch.cuda.Stream | None = None):
+    """Allocation-free heat filter on caller-held CSR arrays (int32 rowptr); the output buffer
+    is allocated here by torch only when ``out`` is None."""
+    n = rowptr32.numel() - 1
+    _dev(rowptr32, torch.int32, "rowptr32")
+    _dev(col, torch.int32, "col")
+    _dev(pval, torch.float32, "pval", col.shape)
+    squeeze = V.dim() == 1
+    V2 = V.reshape(V.shape[0], -1)
+    _dev(V2, torch.float32, "V")
+    Y = torch.empty_like(V2) if out is None else _dev(out, torch.float32, "Y").view(V2.shape)
+    stream = torch.cuda.current_stream(V.device) if stream is None else stream
+    st = _lib.gs_heat_apply_noalloc(n, col.numel(), _ptr(rowptr32), _ptr(col), _ptr(pval), float(t),
+                                    int(K), _ptr(V2), V2.shape[1], _ptr(Y),
+                                    ctypes.c_void_p(stream.cuda_stream))
+    if st != GS_OK:
+        raise GeosinkError(st, "gs_heat_apply_noalloc")
     return Y.view(V.shape) if squeeze else Y
 
 
