@@ -82,14 +82,19 @@ gs_status gs_sync(gs_ctx *ctx);
 gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
 
 /* Context options (host call).  GS_OPT_LOOP selects how gs_sinkhorn runs a fixed iteration count
- * (eps <= 0): 0 (default) one persistent cooperative launch with bounded grid barriers between the
- * Chebyshev orders, falling back to 1 when the device cannot co-schedule the grid; 1 CUDA-graph
- * replay of per-order launches.  Both compute the same thing.  Errors: GS_ERR_ARG. */
+ * (eps <= 0): 1 (default) CUDA-graph replay of per-order launches; 0 one persistent cooperative
+ * launch with bounded grid barriers between the Chebyshev orders (falls back to 1 when the device
+ * cannot co-schedule the grid).  Both compute the same thing.  Errors: GS_ERR_ARG. */
 /* GS_OPT_BARRIER_SELFTEST = 1 makes the next persistent launch wait at its first grid barrier for
  * one block more than the grid has: every block's bounded wait runs out (~10 ms), the launch ends
  * and gs_sync reports GS_ERR_TIMEOUT, leaving the context usable.  It exercises failure handling
  * without faulting the GPU; the option resets itself after that launch. */
-enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2 };
+/* GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL pick the Chebyshev order kernel for one column / several
+ * columns: 0 automatic, 1 sliced ELL (one column), 2 lane-split CSR, 3 chunked CSR with
+ * asynchronous gathers into shared memory, 4 staged neighbour lists (several columns), 5 the
+ * sliced-ELL / lane-group kernels with each block walking one contiguous row range.  All variants
+ * compute the same recurrence; they differ in summation order only. */
+enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
 
 /* Host query: number of GPU kernels this context has enqueued so far (a replayed CUDA graph

@@ -161,6 +161,8 @@ def gs_reserve(ctx: Context, nbytes: int):
 
 GS_OPT_LOOP = 1
 GS_OPT_BARRIER_SELFTEST = 2
+GS_OPT_B1_KERNEL = 3
+GS_OPT_BLK_KERNEL = 4
 
 
 def gs_set_option(ctx: Context, option: int, value: int):

@@ -163,6 +163,14 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->barrier_selftest = value;
         return GS_OK;
     }
+    if (option == GS_OPT_B1_KERNEL && (value >= 0 && value <= 3 || value == 5)) {
+        ctx->b1_kernel = value;
+        return GS_OK;
+    }
+    if (option == GS_OPT_BLK_KERNEL && (value == 0 || (value >= 2 && value <= 5))) {
+        ctx->blk_kernel = value;
+        return GS_OK;
+    }
     return gs_fail(ctx, GS_ERR_ARG, "unknown option or value");
 }
 
@@ -251,6 +259,9 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g)
     cudaFree(g->prowptr);
     cudaFree(g->pcol);
     cudaFree(g->ppval);
+    cudaFree(g->sptr);
+    cudaFree(g->scol);
+    cudaFree(g->sval);
     delete g;
     return GS_OK;
 }

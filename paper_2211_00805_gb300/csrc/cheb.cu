@@ -19,6 +19,8 @@
 #include <string.h>
 
 #include "gs_internal.cuh"
+#include "sell_row.cuh"
+#include "async_copy.cuh"
 
 namespace {
 
@@ -28,6 +30,9 @@ struct OrderArgs {
     const int* rowptr;
     const int* col;
     const float* pval;
+    const int* sptr;    // sliced ELL (B == 1 kernel), or null
+    const int* scol;
+    const float* sval;
     const float* cur;   // T_{k-1} (the gathered block); x for order 1
     const float* prev;  // T_{k-2}; unused for order 1
     float* next;        // destination of T_k (non-last orders), may alias prev
@@ -115,6 +120,62 @@ __global__ void __launch_bounds__(256) order_b1(const OrderArgs p)
     if (p.last && p.epi.err_partials != nullptr) block_add(err, p.epi.err_partials);
 }
 
+// ------------------------------------------------------------------ B == 1, sliced ELL
+// One thread per row; a warp owns one 32-row slice whose entries are stored column-major, so each
+// step j reads 32 consecutive column indices and values.  Eight gathers are issued before the
+// first is used, and the row-local loads (T_{k-2}, y) go out before the gathers.
+__device__ __forceinline__ double order_sell_row(const OrderArgs& p, int64_t row, bool active)
+{
+    double err = 0.0;
+    if (active) {
+        const float pv = p.first ? 0.f : p.prev[row];
+        const float yv = p.first ? p.c0 * p.cur[row] : p.y[row];
+        const float s = gs_sell_row<true>(p.sptr, p.scol, p.sval, p.cur, row);
+        const float tk = p.first ? s : fmaf(2.f, s, -pv);
+        const float acc = fmaf(p.ck, tk, yv);
+        if (!p.last) {
+            p.next[row] = tk;
+            p.y[row] = acc;
+        } else {
+            const Epilogue& e = p.epi;
+            if (e.kind == EPI_STORE) {
+                e.out[row] = acc;
+            } else {  // EPI_DIVIDE
+                const float num = e.num[row];
+                const float r = safe_div(num, acc, p.flags);
+                if (e.fsave) e.fsave[row] = acc;
+                if (e.out) e.out[row] = r;
+                if (e.xnext) e.xnext[row] = e.vol ? e.vol[row] * r : r;
+                if (e.old) err = fabs((double)e.old[row] * (double)acc - (double)num);
+            }
+        }
+    }
+    return err;
+}
+
+__global__ void __launch_bounds__(256) order_sell(const OrderArgs p)
+{
+    if (p.done != nullptr && *p.done) return;
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double err = order_sell_row(p, row, row < p.n);
+    if (p.last && p.epi.err_partials != nullptr) block_add(err, p.epi.err_partials);
+}
+
+// Each block walks one contiguous range of 32-row slices (8 slices per pass).
+__global__ void __launch_bounds__(256) order_sell_ranged(const OrderArgs p, int64_t rows_per_block)
+{
+    if (p.done != nullptr && *p.done) return;
+    const int64_t b0 = (int64_t)blockIdx.x * rows_per_block;
+    int64_t b1 = b0 + rows_per_block;
+    b1 = b1 < p.n ? b1 : p.n;
+    double err = 0.0;
+    for (int64_t base = b0; base < b1; base += 256) {
+        const int64_t row = base + threadIdx.x;
+        err += order_sell_row(p, row, row < b1);
+    }
+    if (p.last && p.epi.err_partials != nullptr) block_add(err, p.epi.err_partials);
+}
+
 // -------------------------------------------------------------------------------- B > 1
 template <int VEC>
 struct VecT;
@@ -132,13 +193,11 @@ struct VecT<1> {
 };
 
 template <int VEC, int MAXCH>
-__global__ void __launch_bounds__(256) order_blk(const OrderArgs p, int lpr_log2)
+__device__ __forceinline__ void order_blk_row(const OrderArgs& p, int lpr_log2, int64_t row,
+                                              bool active)
 {
-    if (p.done != nullptr && *p.done) return;
     const int lpr = 1 << lpr_log2;
     const int lane = threadIdx.x & (lpr - 1);
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> lpr_log2;
-    const bool active = row < p.n;
     const int B = p.B;
     int beg = 0, end = 0;
     if (active) {
@@ -255,6 +314,335 @@ __global__ void __launch_bounds__(256) order_blk(const OrderArgs p, int lpr_log2
     }
 }
 
+template <int VEC, int MAXCH>
+__global__ void __launch_bounds__(256) order_blk(const OrderArgs p, int lpr_log2)
+{
+    if (p.done != nullptr && *p.done) return;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> lpr_log2;
+    order_blk_row<VEC, MAXCH>(p, lpr_log2, row, row < p.n);
+}
+
+// Same rows, but each block walks one contiguous range of rows in passes, so that the rows an SM
+// works on one after another are neighbours in the locality order and share gathered lines in L1.
+template <int VEC, int MAXCH>
+__global__ void __launch_bounds__(256) order_blk_ranged(const OrderArgs p, int lpr_log2,
+                                                        int64_t rows_per_block)
+{
+    if (p.done != nullptr && *p.done) return;
+    const int rpp = 256 >> lpr_log2;  // rows per pass
+    const int64_t b0 = (int64_t)blockIdx.x * rows_per_block;
+    int64_t b1 = b0 + rows_per_block;
+    b1 = b1 < p.n ? b1 : p.n;
+    for (int64_t base = b0; base < b1; base += rpp) {
+        const int64_t row = base + (threadIdx.x >> lpr_log2);
+        order_blk_row<VEC, MAXCH>(p, lpr_log2, row, row < b1);
+    }
+}
+
+// Shared tail of the float4 row-group kernels: recurrence update and the epilogues.  Every
+// thread of the block calls it (the barycenter epilogue reduces across the row's lanes).
+template <int LPR>
+__device__ __forceinline__ void blk4_finish(const OrderArgs& p, int64_t row, bool active, int lane,
+                                            int c0, int64_t base, float (&acc)[4],
+                                            const float (&pv)[4], const float (&yv)[4])
+{
+    float f[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float tk = p.first ? acc[v] : fmaf(2.f, acc[v], -pv[v]);
+        f[v] = fmaf(p.ck, tk, yv[v]);
+        acc[v] = tk;
+    }
+    if (!p.last) {
+        if (active) {
+            *reinterpret_cast<float4*>(p.next + base) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            *reinterpret_cast<float4*>(p.y + base) = make_float4(f[0], f[1], f[2], f[3]);
+        }
+        return;
+    }
+    const Epilogue& e = p.epi;
+    const float vol = (active && e.vol) ? e.vol[row] : 1.f;
+    if (e.kind == EPI_STORE) {
+        if (active) *reinterpret_cast<float4*>(e.out + base) = make_float4(f[0], f[1], f[2], f[3]);
+        return;
+    }
+    if (e.kind == EPI_DIVIDE) {
+        if (!active) return;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float r = safe_div(e.num[base + v], f[v], p.flags);
+            if (e.fsave) e.fsave[base + v] = f[v];
+            if (e.out) e.out[base + v] = r;
+            if (e.xnext) e.xnext[base + v] = vol * r;
+        }
+        return;
+    }
+    // EPI_BARY_V
+    double lsum = 0.0;
+    float d[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        d[v] = 0.f;
+        if (!active) continue;
+        if (e.fsave) e.fsave[base + v] = f[v];
+        d[v] = e.V[base + v] * f[v];
+        const double al = e.alpha[c0 + v];
+        if (al != 0.0) lsum += al * (double)logf(d[v]);
+    }
+    for (int off = LPR >> 1; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+    const float mu = (float)exp(lsum);
+    if (!active) return;
+    if (lane == 0) {
+        e.mu[row] = mu;
+        if (!(mu >= 0.f) || isinf(mu)) flag(p.flags, GS_FLAG_NONFINITE);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float vnum = e.V[base + v] * mu;
+        const float vn = (vnum == 0.f) ? 0.f : vnum / d[v];
+        if (e.dsave) e.dsave[base + v] = d[v];
+        e.V[base + v] = vn;
+        if (e.xnext) e.xnext[base + v] = vol * vn;
+    }
+}
+
+// B = 4 * LPR columns (float4 per lane, one chunk): each row's neighbour list is staged in
+// shared memory 32 entries at a time with one coalesced load per lane, then every lane issues
+// eight float4 gathers before consuming them.  Row-local loads go out first.
+template <int LPR>
+__global__ void __launch_bounds__(256) order_blk_staged(const OrderArgs p)
+{
+    if (p.done != nullptr && *p.done) return;
+    constexpr int RPB = 256 / LPR;
+    __shared__ int s_col[RPB][33];
+    __shared__ float s_val[RPB][33];
+    const int lane = threadIdx.x & (LPR - 1);
+    const int rloc = threadIdx.x / LPR;
+    const int64_t row = (int64_t)blockIdx.x * RPB + rloc;
+    const bool active = row < p.n;
+    const int B = 4 * LPR;
+    const int c0 = lane * 4;
+    const int64_t base = row * (int64_t)B + c0;
+    int beg = 0, len = 0;
+    float pv[4] = {0.f, 0.f, 0.f, 0.f}, yv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (active) {
+        beg = __ldg(p.rowptr + row);
+        len = __ldg(p.rowptr + row + 1) - beg;
+        if (!p.first) {
+            const float4 q = *reinterpret_cast<const float4*>(p.prev + base);
+            const float4 w = *reinterpret_cast<const float4*>(p.y + base);
+            pv[0] = q.x; pv[1] = q.y; pv[2] = q.z; pv[3] = q.w;
+            yv[0] = w.x; yv[1] = w.y; yv[2] = w.z; yv[3] = w.w;
+        } else {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(p.cur + base));
+            yv[0] = p.c0 * q.x; yv[1] = p.c0 * q.y; yv[2] = p.c0 * q.z; yv[3] = p.c0 * q.w;
+        }
+    }
+    // warp-uniform chunk count
+    int nch = (len + 31) >> 5;
+    for (int off = 16; off > 0; off >>= 1) nch = max(nch, __shfl_xor_sync(0xffffffffu, nch, off));
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int ch = 0; ch < nch; ++ch) {
+        const int o = ch * 32;
+        for (int i = lane; i < 32; i += LPR) {
+            const bool ok = o + i < len;
+            s_col[rloc][i] = ok ? __ldg(p.col + beg + o + i) : 0;
+            s_val[rloc][i] = ok ? __ldg(p.pval + beg + o + i) : 0.f;
+        }
+        __syncwarp();
+        const int cnt = min(32, len - o);
+        int e = 0;
+        for (; e + 8 <= cnt; e += 8) {
+            float4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                x[u] = __ldg(reinterpret_cast<const float4*>(p.cur + (int64_t)s_col[rloc][e + u] * B + c0));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float w = s_val[rloc][e + u];
+                acc[0] = fmaf(w, x[u].x, acc[0]);
+                acc[1] = fmaf(w, x[u].y, acc[1]);
+                acc[2] = fmaf(w, x[u].z, acc[2]);
+                acc[3] = fmaf(w, x[u].w, acc[3]);
+            }
+        }
+        for (; e < cnt; ++e) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(p.cur + (int64_t)s_col[rloc][e] * B + c0));
+            const float w = s_val[rloc][e];
+            acc[0] = fmaf(w, x.x, acc[0]);
+            acc[1] = fmaf(w, x.y, acc[1]);
+            acc[2] = fmaf(w, x.z, acc[2]);
+            acc[3] = fmaf(w, x.w, acc[3]);
+        }
+        __syncwarp();
+    }
+    blk4_finish<LPR>(p, row, active, lane, c0, base, acc, pv, yv);
+}
+
+
+// B = 4 * LPR columns with the gathers issued as asynchronous copies: a block owns RPB
+// consecutive rows, whose nonzeros form one contiguous CSR range.  That range is processed in
+// chunks of CH neighbour rows (32 KB of data): the chunk's column indices and values are loaded
+// coalesced, then every thread issues cp.async copies of 16-byte slices of the neighbour rows into
+// shared memory, so hundreds of independent loads per block are in flight at once without holding
+// them in registers.  Chunks are double-buffered; each row group then accumulates its own entries
+// from shared memory.
+template <int LPR>
+__global__ void __launch_bounds__(256) order_blk_async(const OrderArgs p)
+{
+    if (p.done != nullptr && *p.done) return;
+    constexpr int B = 4 * LPR;
+    constexpr int RPB = 256 / LPR;
+    constexpr int CH = 8192 / B;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* sdata = reinterpret_cast<float4*>(smem_raw);           // [2][CH * LPR]
+    int* scol = reinterpret_cast<int*>(sdata + 2 * CH * LPR);      // [2][CH]
+    float* sval = reinterpret_cast<float*>(scol + 2 * CH);         // [2][CH]
+    const int tid = threadIdx.x;
+    const int lane = tid % LPR, rloc = tid / LPR;
+    const int64_t r0 = (int64_t)blockIdx.x * RPB;
+    const int64_t r1 = (r0 + RPB) < p.n ? (r0 + RPB) : p.n;
+    const int64_t row = r0 + rloc;
+    const bool active = row < r1;
+    const int ebeg = __ldg(p.rowptr + r0), eend = __ldg(p.rowptr + r1);
+    int myb = 0, mye = 0;
+    const int c0 = lane * 4;
+    const int64_t base = row * (int64_t)B + c0;
+    float pv[4] = {0.f, 0.f, 0.f, 0.f}, yv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (active) {
+        myb = __ldg(p.rowptr + row);
+        mye = __ldg(p.rowptr + row + 1);
+        if (!p.first) {
+            const float4 q = *reinterpret_cast<const float4*>(p.prev + base);
+            const float4 w = *reinterpret_cast<const float4*>(p.y + base);
+            pv[0] = q.x; pv[1] = q.y; pv[2] = q.z; pv[3] = q.w;
+            yv[0] = w.x; yv[1] = w.y; yv[2] = w.z; yv[3] = w.w;
+        } else {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(p.cur + base));
+            yv[0] = p.c0 * q.x; yv[1] = p.c0 * q.y; yv[2] = p.c0 * q.z; yv[3] = p.c0 * q.w;
+        }
+    }
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int nch = (eend - ebeg + CH - 1) / CH;
+    auto stage = [&](int c, int buf) {
+        const int cb = ebeg + c * CH;
+        const int cnt = (eend - cb) < CH ? (eend - cb) : CH;
+        for (int i = tid; i < cnt; i += 256) {
+            scol[buf * CH + i] = __ldg(p.col + cb + i);
+            sval[buf * CH + i] = __ldg(p.pval + cb + i);
+        }
+        __syncthreads();
+        for (int i = tid; i < cnt * LPR; i += 256) {
+            const int e = i / LPR, q = i - e * LPR;
+            gs_cp_async16(&sdata[buf * CH * LPR + i], p.cur + (int64_t)scol[buf * CH + e] * B + q * 4);
+        }
+        gs_cp_async_commit();
+    };
+    if (nch > 0) stage(0, 0);
+    for (int c = 0; c < nch; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nch) {
+            stage(c + 1, buf ^ 1);
+            gs_cp_async_wait<1>();
+        } else {
+            gs_cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int cb = ebeg + c * CH;
+        const int ce = (cb + CH) < eend ? (cb + CH) : eend;
+        const int lo = myb > cb ? myb : cb, hi = mye < ce ? mye : ce;
+        for (int e = lo; e < hi; ++e) {
+            const float w = sval[buf * CH + e - cb];
+            const float4 x = sdata[buf * CH * LPR + (e - cb) * LPR + lane];
+            acc[0] = fmaf(w, x.x, acc[0]);
+            acc[1] = fmaf(w, x.y, acc[1]);
+            acc[2] = fmaf(w, x.z, acc[2]);
+            acc[3] = fmaf(w, x.w, acc[3]);
+        }
+        __syncthreads();
+    }
+    blk4_finish<LPR>(p, row, active, lane, c0, base, acc, pv, yv);
+}
+
+template <int LPR>
+constexpr int blk_async_smem() { return 2 * (8192 / (4 * LPR)) * LPR * 16 + 2 * (8192 / (4 * LPR)) * 8; }
+
+// B = 1 with the gathers issued as 4-byte asynchronous copies: a block owns 256 consecutive rows
+// (one per thread); their contiguous CSR range is processed in double-buffered chunks of 2048
+// entries (indices and values loaded coalesced, x[col] copied asynchronously into shared memory),
+// then each thread sums its own row's entries from shared memory.
+constexpr int kB1Chunk = 2048;
+__global__ void __launch_bounds__(256) order_b1_async(const OrderArgs p)
+{
+    if (p.done != nullptr && *p.done) return;
+    __shared__ float sx[2][kB1Chunk];
+    __shared__ float sval[2][kB1Chunk];
+    const int tid = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * 256;
+    const int64_t r1 = (r0 + 256) < p.n ? (r0 + 256) : p.n;
+    const int64_t row = r0 + tid;
+    const bool active = row < r1;
+    const int ebeg = __ldg(p.rowptr + r0), eend = __ldg(p.rowptr + r1);
+    int myb = 0, mye = 0;
+    float pv = 0.f, yv = 0.f;
+    if (active) {
+        myb = __ldg(p.rowptr + row);
+        mye = __ldg(p.rowptr + row + 1);
+        pv = p.first ? 0.f : p.prev[row];
+        yv = p.first ? p.c0 * p.cur[row] : p.y[row];
+    }
+    const int nch = (eend - ebeg + kB1Chunk - 1) / kB1Chunk;
+    auto stage = [&](int c, int buf) {
+        const int cb = ebeg + c * kB1Chunk;
+        const int cnt = (eend - cb) < kB1Chunk ? (eend - cb) : kB1Chunk;
+        for (int i = tid; i < cnt; i += 256) {
+            const int j = __ldg(p.col + cb + i);
+            sval[buf][i] = __ldg(p.pval + cb + i);
+            gs_cp_async4(&sx[buf][i], p.cur + j);
+        }
+        gs_cp_async_commit();
+    };
+    float s0 = 0.f;
+    if (nch > 0) stage(0, 0);
+    for (int c = 0; c < nch; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nch) {
+            stage(c + 1, buf ^ 1);
+            gs_cp_async_wait<1>();
+        } else {
+            gs_cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int cb = ebeg + c * kB1Chunk;
+        const int ce = (cb + kB1Chunk) < eend ? (cb + kB1Chunk) : eend;
+        const int lo = myb > cb ? myb : cb, hi = mye < ce ? mye : ce;
+        for (int e = lo; e < hi; ++e) s0 = fmaf(sval[buf][e - cb], sx[buf][e - cb], s0);
+        __syncthreads();
+    }
+    double err = 0.0;
+    if (active) {
+        const float tk = p.first ? s0 : fmaf(2.f, s0, -pv);
+        const float acc = fmaf(p.ck, tk, yv);
+        if (!p.last) {
+            p.next[row] = tk;
+            p.y[row] = acc;
+        } else {
+            const Epilogue& e = p.epi;
+            if (e.kind == EPI_STORE) {
+                e.out[row] = acc;
+            } else {  // EPI_DIVIDE
+                const float num = e.num[row];
+                const float r = safe_div(num, acc, p.flags);
+                if (e.fsave) e.fsave[row] = acc;
+                if (e.out) e.out[row] = r;
+                if (e.xnext) e.xnext[row] = e.vol ? e.vol[row] * r : r;
+                if (e.old) err = fabs((double)e.old[row] * (double)acc - (double)num);
+            }
+        }
+    }
+    if (p.last && p.epi.err_partials != nullptr) block_add(err, p.epi.err_partials);
+}
+
 // ------------------------------------------------------------------------------ helpers
 __global__ void fill_kernel(int64_t count, float* __restrict__ out, const float* __restrict__ vol,
                             int B, float value)
@@ -302,10 +690,61 @@ int ilog2(int v)
     return r;
 }
 
+// Rows per block for the ranged kernels: one wave of resident blocks (occupancy of the kernel),
+// each a contiguous run of whole passes.
+template <class Kern>
+int resident_blocks_per_sm(Kern kernel)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 4;
+    }
+    return b;
+}
+
+int64_t ranged_rows(const gs_ctx* ctx, int64_t n, int rows_per_pass, int per_sm)
+{
+    const int64_t blocks = (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148) * per_sm;
+    int64_t r = (n + blocks - 1) / blocks;
+    r = (r + rows_per_pass - 1) / rows_per_pass * rows_per_pass;
+    return r > 0 ? r : rows_per_pass;
+}
+
+template <int LPR>
+void launch_blk_async(gs_ctx* ctx, const gs_graph* g, const OrderArgs& a)
+{
+    constexpr int smem = blk_async_smem<LPR>();
+    static bool attr_set = false;  // per instantiation; set outside any capture by the first call
+    if (!attr_set) {
+        cudaFuncSetAttribute(order_blk_async<LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_set = true;
+    }
+    const unsigned grid = nblocks(g->n, 256 / LPR);
+    order_blk_async<LPR><<<grid, 256, smem, ctx->stream>>>(a);
+}
+
 void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const OrderArgs& a)
 {
     gs_count(ctx, 1);
     const int TB = pl.block;
+    if (pl.B == 1 && a.epi.kind != EPI_BARY_V) {
+        const int mode = ctx->b1_kernel;
+        if (mode == GS_KERNEL_ASYNC) {
+            order_b1_async<<<nblocks(g->n, 256), 256, 0, ctx->stream>>>(a);
+            return;
+        }
+        if ((mode == GS_KERNEL_AUTO || mode == GS_KERNEL_RANGED) && a.sptr != nullptr) {
+            static const int per_sm = resident_blocks_per_sm(order_sell_ranged);
+            const int64_t rpb = ranged_rows(ctx, g->n, 256, per_sm);
+            order_sell_ranged<<<nblocks(g->n, (int)rpb), 256, 0, ctx->stream>>>(a, rpb);
+            return;
+        }
+        if (mode == GS_KERNEL_SELL && a.sptr != nullptr) {
+            order_sell<<<nblocks(g->n, 256), 256, 0, ctx->stream>>>(a);
+            return;
+        }
+    }
     if (pl.B == 1 && a.epi.kind != EPI_BARY_V) {
         const unsigned grid = nblocks(g->n * pl.group, TB);
         switch (pl.group) {
@@ -319,8 +758,48 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
     const int vec = pl.vec;
     const int lpr = pl.B == 1 ? 1 : pl.group;
     const unsigned grid = nblocks(g->n * lpr, TB);
+    if (vec == 4 && pl.B == 4 * lpr && lpr >= 2) {  // one float4 chunk per lane
+        const int mode = ctx->blk_kernel;
+        if (mode == GS_KERNEL_ASYNC) {
+            switch (lpr) {
+                case 2: launch_blk_async<2>(ctx, g, a); return;
+                case 4: launch_blk_async<4>(ctx, g, a); return;
+                case 8: launch_blk_async<8>(ctx, g, a); return;
+                case 16: launch_blk_async<16>(ctx, g, a); return;
+                case 32: launch_blk_async<32>(ctx, g, a); return;
+                default: break;
+            }
+        }
+        if (mode == GS_KERNEL_STAGED) {
+            switch (lpr) {
+                case 2: order_blk_staged<2><<<grid, TB, 0, ctx->stream>>>(a); return;
+                case 4: order_blk_staged<4><<<grid, TB, 0, ctx->stream>>>(a); return;
+                case 8: order_blk_staged<8><<<grid, TB, 0, ctx->stream>>>(a); return;
+                case 16: order_blk_staged<16><<<grid, TB, 0, ctx->stream>>>(a); return;
+                case 32: order_blk_staged<32><<<grid, TB, 0, ctx->stream>>>(a); return;
+                default: break;
+            }
+        }
+    }
     const bool one = pl.B <= lpr * vec;
     const int lg = ilog2(lpr);
+    if (pl.B > 1 && ctx->blk_kernel == GS_KERNEL_RANGED) {
+        static const int occ41 = resident_blocks_per_sm(order_blk_ranged<4, 1>);
+        static const int occ48 = resident_blocks_per_sm(order_blk_ranged<4, 8>);
+        static const int occ11 = resident_blocks_per_sm(order_blk_ranged<1, 1>);
+        static const int occ18 = resident_blocks_per_sm(order_blk_ranged<1, 8>);
+        const int occ = vec == 4 ? (one ? occ41 : occ48) : (one ? occ11 : occ18);
+        const int64_t rpb = ranged_rows(ctx, g->n, TB / lpr, occ);
+        const unsigned rgrid = nblocks(g->n, (int)rpb);
+        if (vec == 4) {
+            if (one) order_blk_ranged<4, 1><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
+            else order_blk_ranged<4, 8><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
+        } else {
+            if (one) order_blk_ranged<1, 1><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
+            else order_blk_ranged<1, 8><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
+        }
+        return;
+    }
     if (vec == 4) {
         if (one) order_blk<4, 1><<<grid, TB, 0, ctx->stream>>>(a, lg);
         else order_blk<4, 8><<<grid, TB, 0, ctx->stream>>>(a, lg);
@@ -373,6 +852,9 @@ gs_status gs_filter_enqueue(gs_ctx* ctx, const gs_graph* g, const double* c, int
     a.rowptr = csr.rowptr;
     a.col = csr.col;
     a.pval = csr.pval;
+    a.sptr = g->sptr;  // present only together with the reordered CSR
+    a.scol = g->scol;
+    a.sval = g->sval;
     a.done = done_flag;
     a.flags = ctx->flags;
     a.y = y;
@@ -542,7 +1024,7 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
 
     bool looped = false;
     if (!use_eps && ctx->loop_mode == 0) {
-        // Fixed iteration count, default: the whole loop as one persistent cooperative launch.
+        // Fixed iteration count, persistent mode: the whole loop as one cooperative launch.
         std::vector<float> cf((size_t)K + 1);
         for (int k = 0; k <= K; ++k) cf[k] = (float)c[k];
         float* cdev = ws_at<float>(ctx, plan, icf);

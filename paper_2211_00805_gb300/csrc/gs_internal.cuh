@@ -10,6 +10,16 @@
 
 #include "../../include/geosink.h"
 
+// Kernel variants of the Chebyshev order (selected per context; the autotuner picks them).
+enum : int {
+    GS_KERNEL_AUTO = 0,
+    GS_KERNEL_SELL = 1,     // B == 1: sliced ELL, thread per row
+    GS_KERNEL_VECTOR = 2,   // B == 1: CSR, lanes split the row | B > 1: lane group, direct gathers
+    GS_KERNEL_ASYNC = 3,    // chunked CSR ranges with cp.async gathers into shared memory
+    GS_KERNEL_STAGED = 4,   // B > 1: neighbour list staged in shared memory, 8-deep gathers
+    GS_KERNEL_RANGED = 5,   // each block walks a contiguous row range (sliced ELL / lane groups)
+};
+
 // Bits the kernels OR into the context's device status word; gs_sync turns them into a status.
 enum : int {
     GS_FLAG_NONFINITE = 1,
@@ -35,8 +45,10 @@ struct gs_ctx {
     size_t ws_bytes = 0;
     int num_sms = 0;
     bool capturing = false;        // inside an internal capture: launches are not counted
-    int loop_mode = 0;             // fixed-count Sinkhorn: 0 persistent launch, 1 CUDA-graph replay
+    int loop_mode = 1;             // fixed-count Sinkhorn: 1 CUDA-graph replay, 0 persistent launch
     int barrier_selftest = 0;      // next persistent launch waits for an arrival that never comes
+    int b1_kernel = 0;             // GS_KERNEL_* for one column
+    int blk_kernel = 0;            // GS_KERNEL_* for several columns
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::string err;
@@ -66,6 +78,13 @@ struct gs_graph {
     int* pcol = nullptr;
     float* ppval = nullptr;
     int levels = 0;                // breadth-first levels of the ordering sweep
+    // sliced ELL copy of the reordered P for the one-column kernels: 32-row slices, each stored
+    // column-major and padded to its longest row (padding: column = the row itself, value 0)
+    int* sptr = nullptr;           // [nslices + 1] offsets into scol / sval
+    int* scol = nullptr;
+    float* sval = nullptr;
+    int64_t nslices = 0;
+    int64_t sell_nnz = 0;          // stored entries including padding
 };
 
 // The CSR the filter kernels read: the reordered one when present.

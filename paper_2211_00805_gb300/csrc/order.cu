@@ -127,6 +127,74 @@ __global__ void permute_fill(int64_t n, const int* __restrict__ perm, const int*
     }
 }
 
+// Within each window of W consecutive positions, reorder nodes by decreasing degree (stable), so
+// that 32-row slices hold rows of similar length and sliced-ELL padding stays small.
+__global__ void window_degree_sort(int64_t n, int W, const int* __restrict__ perm_in,
+                                   const int* __restrict__ rowptr, int* __restrict__ perm_out)
+{
+    extern __shared__ int sdeg[];  // [W]
+    const int64_t w0 = (int64_t)blockIdx.x * W;
+    const int len = (int)((n - w0) < W ? (n - w0) : W);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        if (i < len) {
+            const int node = perm_in[w0 + i];
+            sdeg[i] = rowptr[node + 1] - rowptr[node];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const int di = sdeg[i];
+        int rank = 0;
+        for (int j = 0; j < len; ++j) {
+            const int dj = sdeg[j];
+            rank += (dj > di) || (dj == di && j < i);
+        }
+        perm_out[w0 + rank] = perm_in[w0 + i];
+    }
+}
+
+__global__ void invert_perm(int64_t n, const int* __restrict__ perm, int* __restrict__ iperm)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) iperm[perm[r]] = (int)r;
+}
+
+// Sliced ELL: slice width = longest row of the slice (in entries), stored width * 32.
+__global__ void sell_width(int64_t n, int64_t nslices, const int* __restrict__ prowptr,
+                           int* __restrict__ cnt)
+{
+    const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= nslices) return;
+    int w = 0;
+    for (int64_t r = sl * 32; r < sl * 32 + 32 && r < n; ++r) {
+        const int len = prowptr[r + 1] - prowptr[r];
+        w = len > w ? len : w;
+    }
+    cnt[sl] = w * 32;
+}
+
+__global__ void sell_fill(int64_t n, const int* __restrict__ prowptr, const int* __restrict__ pcol,
+                          const float* __restrict__ ppval, const int64_t* __restrict__ sptr64,
+                          int* __restrict__ scol, float* __restrict__ sval)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t sl = r >> 5, lane = r & 31;
+    const int64_t base = sptr64[sl];
+    const int width = (int)((sptr64[sl + 1] - base) >> 5);
+    const int b = prowptr[r], len = prowptr[r + 1] - b;
+    for (int j = 0; j < width; ++j) {
+        const int64_t o = base + (int64_t)j * 32 + lane;
+        if (j < len) {
+            scol[o] = pcol[b + j];
+            sval[o] = ppval[b + j];
+        } else {
+            scol[o] = (int)r;
+            sval[o] = 0.f;
+        }
+    }
+}
+
 __global__ void permute_rows_kernel(int64_t count, int B, const int* __restrict__ perm,
                                     const float* __restrict__ src, float* __restrict__ dst, int to)
 {
@@ -233,12 +301,40 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
     if ((st = bfs_sweep(ctx, g, sint + 2, g->perm, g->iperm, owner, cnt, offs, sums, sint, &levels)) != GS_OK)
         return st;
     g->levels = levels;
+    // degree sort inside windows of 256 positions, then the inverse permutation
+    {
+        const int W = 256;
+        cudaMemcpyAsync(owner, g->perm, sizeof(int) * n, cudaMemcpyDeviceToDevice, s);
+        window_degree_sort<<<nblk(n, W), 256, sizeof(int) * W, s>>>(n, W, owner, g->rowptr, g->perm);
+        invert_perm<<<nblk(n, 256), 256, 0, s>>>(n, g->perm, g->iperm);
+        gs_count(ctx, 2);
+    }
     // permuted CSR
     permute_count<<<nblk(n, 256), 256, 0, s>>>(n, g->perm, g->rowptr, cnt);
     gs_exclusive_scan(s, cnt, n, p64, sums);
     rowptr_narrow<<<nblk(n + 1, 256), 256, 0, s>>>(n + 1, p64, g->prowptr);
     permute_fill<<<nblk(n, 128), 128, 0, s>>>(n, g->perm, g->iperm, g->rowptr, g->col, g->pval, p64,
                                               g->pcol, g->ppval);
+    gs_count(ctx, 6);
+    // sliced ELL of the permuted operator
+    const int64_t ns = (n + 31) / 32;
+    sell_width<<<nblk(ns, 256), 256, 0, s>>>(n, ns, g->prowptr, cnt);
+    gs_exclusive_scan(s, cnt, ns, p64, sums);
+    int64_t tot = 0;
+    cudaMemcpyAsync(&tot, p64 + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if ((st = gs_cuda_check(ctx, cudaStreamSynchronize(s), "sliced ELL size")) != GS_OK) return st;
+    if (tot >= ((int64_t)1 << 31)) return GS_OK;  // too large for int32 offsets: CSR kernels only
+    e = cudaMalloc(&g->sptr, sizeof(int) * (ns + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->scol, sizeof(int) * (tot > 0 ? tot : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->sval, sizeof(float) * (tot > 0 ? tot : 1));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return gs_fail(ctx, GS_ERR_OOM, "sliced ELL allocation failed");
+    }
+    g->nslices = ns;
+    g->sell_nnz = tot;
+    rowptr_narrow<<<nblk(ns + 1, 256), 256, 0, s>>>(ns + 1, p64, g->sptr);
+    sell_fill<<<nblk(n, 256), 256, 0, s>>>(n, g->prowptr, g->pcol, g->ppval, p64, g->scol, g->sval);
     gs_count(ctx, 6);
     return gs_cuda_check(ctx, cudaStreamSynchronize(s), "graph permutation");
 }

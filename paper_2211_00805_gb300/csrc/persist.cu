@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "gs_internal.cuh"
+#include "sell_row.cuh"
 
 namespace {
 
@@ -30,6 +31,9 @@ struct PersistArgs {
     const int* rowptr;
     const int* col;
     const float* pval;
+    const int* sptr;     // sliced ELL, or null (then the CSR row-split mapping is used)
+    const int* scol;
+    const float* sval;
     const float* a;
     const float* b;
     const float* vol;
@@ -120,13 +124,50 @@ __device__ __forceinline__ void rows_order(const PersistArgs& p, int r0, int r1,
     }
 }
 
+// Thread-per-row variant over the sliced ELL copy (same arithmetic as the per-order kernel).
+__device__ __forceinline__ void rows_order_sell(const PersistArgs& p, int r0, int r1, int mode,
+                                                float ck, float c0, const float* cur,
+                                                const float* prev, float* next, const float* num,
+                                                float* out, float* xnext)
+{
+    for (int row = r0 + (int)threadIdx.x; row < r1; row += kThreads) {
+        const float pv = (mode == 0) ? 0.f : prev[row];
+        const float yv = (mode == 0) ? c0 * cur[row] : p.y[row];
+        const float s = gs_sell_row<false>(p.sptr, p.scol, p.sval, cur, row);
+        const float tk = (mode == 0) ? s : fmaf(2.f, s, -pv);
+        const float acc = fmaf(ck, tk, yv);
+        if (mode != 2) {
+            next[row] = tk;
+            p.y[row] = acc;
+        } else {
+            const float m = num[row];
+            float r = 0.f;
+            if (m != 0.f) {
+                r = m / acc;
+                if (!(r > 0.f) || isinf(r)) atomicOr(p.flags, GS_FLAG_NONFINITE);
+            }
+            out[row] = r;
+            xnext[row] = p.vol ? p.vol[row] * r : r;
+        }
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void rows_any(const PersistArgs& p, int r0, int r1, int mode, float ck,
+                                         float c0, const float* cur, const float* prev, float* next,
+                                         const float* num, float* out, float* xnext)
+{
+    if (p.sptr) rows_order_sell(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext);
+    else rows_order<G>(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext);
+}
+
 template <int G>
 __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArgs p)
 {
     __shared__ int s_ok;
     if (threadIdx.x == 0) s_ok = 1;
     __syncthreads();
-    const int per = (p.n + gridDim.x - 1) / gridDim.x;
+    const int per = ((p.n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;  // whole 32-row slices
     const int r0 = min(p.n, (int)blockIdx.x * per), r1 = min(p.n, r0 + per);
     for (int r = r0 + threadIdx.x; r < r1; r += kThreads) p.x[r] = p.vol ? p.vol[r] : 1.f;
     if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
@@ -138,22 +179,22 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArg
             const float* num = h == 0 ? p.a : p.b;
             float* out = h == 0 ? p.u : p.v;
             if (p.K == 1) {
-                rows_order<G>(p, r0, r1, 2, p.coef[1], c0, X, nullptr, nullptr, num, out, Ab);
+                rows_any<G>(p, r0, r1, 2, p.coef[1], c0, X, nullptr, nullptr, num, out, Ab);
                 if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                 float* t = X; X = Ab; Ab = t;
                 continue;
             }
-            rows_order<G>(p, r0, r1, 0, p.coef[1], c0, X, nullptr, Ab, nullptr, nullptr, nullptr);
+            rows_any<G>(p, r0, r1, 0, p.coef[1], c0, X, nullptr, Ab, nullptr, nullptr, nullptr);
             if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
             float* prev = X;
             float* cur = Ab;
             for (int k = 2; k <= p.K; ++k) {
                 if (k < p.K) {
-                    rows_order<G>(p, r0, r1, 1, p.coef[k], 0.f, cur, prev, prev, nullptr, nullptr, nullptr);
+                    rows_any<G>(p, r0, r1, 1, p.coef[k], 0.f, cur, prev, prev, nullptr, nullptr, nullptr);
                     if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                     float* t = prev; prev = cur; cur = t;
                 } else {
-                    rows_order<G>(p, r0, r1, 2, p.coef[k], 0.f, cur, prev, nullptr, num, out, prev);
+                    rows_any<G>(p, r0, r1, 2, p.coef[k], 0.f, cur, prev, nullptr, num, out, prev);
                     if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                     X = prev;
                     Ab = cur;
@@ -205,6 +246,9 @@ gs_status gs_sinkhorn_persistent(gs_ctx* ctx, const gs_graph* g, const float* a,
     args.rowptr = csr.rowptr;
     args.col = csr.col;
     args.pval = csr.pval;
+    args.sptr = g->sptr;
+    args.scol = g->scol;
+    args.sval = g->sval;
     args.a = a;
     args.b = b;
     args.vol = vol;

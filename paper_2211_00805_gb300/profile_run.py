@@ -34,10 +34,28 @@ def algorithmic_bytes(n, nnz, K, B):
     return K * graph + 12 * n * B + (K - 2) * 20 * n * B + 16 * n * B
 
 
+def time_apply(ctx, g, c, V, Y, reps):
+    gs.gs_heat_apply(ctx, g, c["t"], c["K"], V, out=Y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        gs.gs_heat_apply(ctx, g, c["t"], c["K"], V, out=Y)
+    e1.record()
+    torch.cuda.synchronize()
+    gs.gs_sync(ctx)
+    return e0.elapsed_time(e1) / reps
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", choices=sorted(CASES), default="b1")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="order-kernel variant (gs_set_option GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL)")
+    ap.add_argument("--sweep", action="store_true", help="time every variant of the case")
+    ap.add_argument("--sinkhorn", type=int, default=0,
+                    help="also time this many Sinkhorn iterations in both loop modes (B = 1 cases)")
     args = ap.parse_args()
     c = CASES[args.case]
     dev = torch.device("cuda", 0)
@@ -49,20 +67,32 @@ def main():
     g = gs.gs_build_graph(ctx, torch.from_numpy(X).to(dev), c["k"])
     V = torch.rand((c["n"], c["B"]), generator=torch.Generator().manual_seed(0)).to(dev)
     Y = torch.empty_like(V)
-    gs.gs_heat_apply(ctx, g, c["t"], c["K"], V, out=Y)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.reps):
-        gs.gs_heat_apply(ctx, g, c["t"], c["K"], V, out=Y)
-    e1.record()
-    torch.cuda.synchronize()
-    gs.gs_sync(ctx)
-    ms = e0.elapsed_time(e1) / args.reps
+    option = gs.GS_OPT_B1_KERNEL if c["B"] == 1 else gs.GS_OPT_BLK_KERNEL
+    variants = ([0, 1, 2, 3, 5] if c["B"] == 1 else [0, 2, 3, 4, 5]) if args.sweep else [args.variant]
     byts = algorithmic_bytes(c["n"], g.nnz, c["K"], c["B"])
-    print(json.dumps({"case": args.case, "n": c["n"], "nnz": g.nnz, "B": c["B"], "K": c["K"],
-                      "apply_ms": ms, "order_us": ms * 1e3 / c["K"],
-                      "GBps": byts / (ms / 1e3) / 1e9, "bytes_per_order": byts / c["K"]}))
+    for var in variants:
+        gs.gs_set_option(ctx, option, var)
+        ms = time_apply(ctx, g, c, V, Y, args.reps)
+        print(json.dumps({"case": args.case, "variant": var, "n": c["n"], "nnz": g.nnz, "B": c["B"],
+                          "K": c["K"], "apply_ms": ms, "order_us": ms * 1e3 / c["K"],
+                          "GBps": byts / (ms / 1e3) / 1e9, "bytes_per_order": byts / c["K"]}), flush=True)
+    gs.gs_set_option(ctx, option, args.variant)
+    if args.sinkhorn and c["B"] == 1:
+        a = torch.full((c["n"],), 1.0 / c["n"], device=dev)
+        for mode in (0, 1):
+            gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
+            gs.gs_sinkhorn(ctx, g, a, a, c["t"], c["K"], args.sinkhorn)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gs.gs_sinkhorn(ctx, g, a, a, c["t"], c["K"], args.sinkhorn)
+            e1.record()
+            torch.cuda.synchronize()
+            gs.gs_sync(ctx)
+            ms = e0.elapsed_time(e1)
+            print(json.dumps({"case": args.case, "sinkhorn_loop_mode": mode, "iters": args.sinkhorn,
+                              "ms": ms, "iters_per_s": args.sinkhorn / (ms / 1e3),
+                              "order_us": ms * 1e3 / (2 * c["K"] * args.sinkhorn)}), flush=True)
 
 
 if __name__ == "__main__":

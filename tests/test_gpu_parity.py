@@ -69,7 +69,7 @@ def test_library_coefficients_match_oracle(gs):
 
 
 # ------------------------------------------------------------------------------- heat filter
-@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 8, 12, 32, 64, 100, 132, 260])
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 8, 12, 16, 32, 64, 100, 128, 132, 260])
 def test_heat_apply_matches_oracle(gs, ctx, B):
     X, rp, col, A = _random_graph(1500, 3, 8, seed=B)
     g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
@@ -332,3 +332,23 @@ def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sp
         gs.gs_sync(ctx)
     assert e.value.status == gs.GS_ERR_TIMEOUT
     _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 50)
+
+
+@pytest.mark.parametrize("B,option,variant", [(1, 3, 1), (1, 3, 2), (1, 3, 3), (1, 3, 5), (32, 4, 2),
+                                              (32, 4, 3), (32, 4, 4), (32, 4, 5), (64, 4, 3),
+                                              (8, 4, 3), (128, 4, 3), (12, 4, 5), (3, 4, 5)])
+def test_kernel_variants_match_oracle(gs, ctx, B, option, variant):
+    # every order-kernel variant (sliced ELL, lane-split CSR, chunked async gathers, staged lists)
+    X, rp, col, A = _random_graph(2500, 4, 9, seed=31 + B)
+    g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
+    Ls, _ = _oracle_graph_fp32(rp, col, A)
+    V = np.random.default_rng(B).random((2500, B)).astype(np.float32)
+    gs.gs_set_option(ctx, option, variant)
+    try:
+        for t, K in [(5.0, 30), (2.0, 1), (3.0, 2)]:
+            Y = to_np(gs.gs_heat_apply(ctx, g, t, K, to_dev(V)))
+            ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(t, K), V.astype(np.float64))
+            assert_close(Y, ref, HEAT_RTOL, HEAT_ATOL_REL * np.abs(ref).max(), f"B={B} v={variant} K={K}")
+        gs.gs_sync(ctx)
+    finally:
+        gs.gs_set_option(ctx, option, 0)
