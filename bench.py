@@ -255,7 +255,9 @@ def run_ours(args, rank, world, local_rank):
     t_start.record(stream)
     for i in range(args.steps):
         flush.fill_(float(i))  # L2 flush: 256 MB write between steps
+        torch.cuda.nvtx.range_push("gs_timed_step")
         nnz = step(X, a, b, evs[i])
+        torch.cuda.nvtx.range_pop()
     t_end.record(stream)
     barrier()
     launches = gs.gs_launch_count(ctx) - l0

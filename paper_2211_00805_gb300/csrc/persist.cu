@@ -13,6 +13,8 @@
 //
 // Buffers written by other blocks are read with ordinary (coherent) loads after the barrier; only
 // the graph, which never changes during the kernel, goes through the read-only path.
+#include <cuda/atomic>
+
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -20,7 +22,7 @@
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 constexpr long long kBarrierBudget = 4000000000ll;  // clock cycles (~2 s) before giving up
 // Self-test: the barrier waits for one arrival more than the grid has, so every wait runs out
 // after this much shorter budget and the launch ends with GS_FLAG_TIMEOUT.
@@ -51,31 +53,32 @@ struct PersistArgs {
     long long budget;    // clock cycles a block waits at a barrier before giving up
 };
 
-// Returns false when the wait ran out (the caller leaves the loop).
+// Returns false when the wait ran out (the caller leaves the loop).  Arrival is a relaxed atomic
+// increment after a release fence; the last arriver resets the counter and bumps the generation
+// with release semantics; waiters poll the generation with acquire loads, bounded by `budget`.
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* flags, int* s_ok, unsigned expect,
                                              long long budget)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == expect - 1) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(bar[0]);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(bar[1]);
+        const unsigned g = gen.load(cuda::memory_order_relaxed);
+        cuda::atomic_thread_fence(cuda::memory_order_release, cuda::thread_scope_device);
+        if (cnt.fetch_add(1u, cuda::memory_order_relaxed) == expect - 1) {
+            cnt.store(0u, cuda::memory_order_relaxed);
+            gen.fetch_add(1u, cuda::memory_order_release);
         } else {
             const long long t0 = clock64();
-            while (*gen == g) {
+            while (gen.load(cuda::memory_order_acquire) == g) {
                 if (clock64() - t0 > budget) {
                     atomicOr(flags, GS_FLAG_TIMEOUT);
                     *s_ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
-        __threadfence();
+        cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
     }
     __syncthreads();
     return *s_ok != 0;
@@ -213,7 +216,7 @@ gs_status launch_persistent(gs_ctx* ctx, PersistArgs& args)
         cudaGetLastError();
         return GS_ERR_UNSUPPORTED;
     }
-    const int blocks = ctx->num_sms * std::min(per_sm, 2);
+    const int blocks = ctx->num_sms;  // one block of kThreads per SM
     args.expect = (unsigned)blocks + (ctx->barrier_selftest ? 1u : 0u);
     args.budget = ctx->barrier_selftest ? kSelfTestBudget : kBarrierBudget;
     ctx->barrier_selftest = 0;
