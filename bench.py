@@ -34,8 +34,13 @@ METRIC = "Sinkhorn iters/s & SpMM HBM GB/s, batched/adjoint vs plain at rtol 1e-
 UNIT = "Sinkhorn iters/s"
 WORKLOAD = dict(name="manifold-100k-R50: Geodesic Sinkhorn distance, graph build included",
                 n=100_000, latent=10, ambient=50, seed=2, k=15, K=30, t=5.0, iters=500)
-HBM_CASE = dict(name="clusters-200k-R30, B=32 heat filter", n=200_000, dim=30, m=32, k=10, K=40,
-                t=10.0, seed=3)
+HBM_CASES = {
+    "spmm_hbm": dict(name="clusters-200k-R30, B=32 heat filter", kind="clusters", n=200_000, dim=30,
+                     m=32, k=10, K=40, t=10.0, seed=3, tag="order_blk_clusters200k_B32"),
+    "spmm_hbm_b64": dict(name="manifold-500k-R40, B=64 heat filter", kind="manifold", n=500_000,
+                         latent=6, ambient=40, m=64, k=10, K=40, t=8.0, seed=4,
+                         tag="order_blk_manifold500k_B64"),
+}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -289,7 +294,8 @@ def run_ours(args, rank, world, local_rank):
 
     extras = {}
     if not args.no_extras:
-        extras["spmm_hbm"] = hbm_case(gs, ctx, dev, stream, peak, peak_kind)
+        for key, case in HBM_CASES.items():
+            extras[key] = hbm_case(gs, ctx, dev, stream, peak, peak_kind, case)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     Xh = torch.from_numpy(p.X).pin_memory()
@@ -358,13 +364,16 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
-def hbm_case(gs, ctx, dev, stream, peak, peak_kind, reps=5):
-    """Heat filter with B = 32 columns on the 200k-point cluster graph (149 MB per order, above
-    L2): achieved algorithmic GB/s of the fused order kernel."""
+def hbm_case(gs, ctx, dev, stream, peak, peak_kind, c, reps=5):
+    """Heat filter with B columns on a graph whose per-order working set exceeds L2: achieved
+    algorithmic GB/s of the fused order kernel (CUDA events around `reps` applies)."""
     import torch
-    c = HBM_CASE
-    X, labels = W.cluster_curves(c["n"], c["dim"], seed=c["seed"])
-    M = W.cluster_unions(labels, c["m"], 3, c["seed"] + 1000)
+    if c["kind"] == "clusters":
+        X, labels = W.cluster_curves(c["n"], c["dim"], seed=c["seed"])
+        M = W.cluster_unions(labels, c["m"], 3, c["seed"] + 1000)
+    else:
+        X, Z = W.tanh_manifold(c["n"], c["latent"], c["ambient"], c["seed"])
+        M = np.random.default_rng(c["seed"]).random((c["n"], c["m"])).astype(np.float32)
     g = gs.gs_build_graph(ctx, torch.from_numpy(X).to(dev), c["k"])
     V = torch.from_numpy(M).to(dev)
     Y = torch.empty_like(V)
@@ -385,7 +394,9 @@ def hbm_case(gs, ctx, dev, stream, peak, peak_kind, reps=5):
     out = {"workload": c["name"], "n": c["n"], "nnz": g.nnz, "B": c["m"], "K": c["K"],
            "apply_ms": s * 1e3, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
            "bytes_per_apply": byts, "peak_kind": f"{peak_kind} hbm_gbs",
-           "traffic": ncu_traffic("order_blk_clusters200k_B32")}
+           "bytes_per_order": byts / c["K"], "order_us": s * 1e6 / c["K"],
+           "note": "apply time includes the two [n, B] permutations into and out of the locality order",
+           "traffic": ncu_traffic(c["tag"]), "traffic_unit": "DRAM bytes per order launch (ncu)"}
     g.close()
     return out
 
