@@ -296,6 +296,8 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_extras:
         for key, case in HBM_CASES.items():
             extras[key] = hbm_case(gs, ctx, dev, stream, peak, peak_kind, case)
+        extras["batched_vs_plain"] = batched_case(gs, ctx, dev, stream)
+        extras["adjoint_vs_plain"] = adjoint_case(gs, ctx, dev, stream)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     Xh = torch.from_numpy(p.X).pin_memory()
@@ -399,6 +401,81 @@ def hbm_case(gs, ctx, dev, stream, peak, peak_kind, c, reps=5):
            "traffic": ncu_traffic(c["tag"]), "traffic_unit": "DRAM bytes per order launch (ncu)"}
     g.close()
     return out
+
+
+def _time(stream, fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def batched_case(gs, ctx, dev, stream, count=64, iters=200):
+    """Ragged batch (n log-uniform in [1e3, 5e4], d 3..20, k in {8,10,15}, K in {16,24,32}, t = 5,
+    Dirichlet marginals on 10 % supports): one persistent batched launch against `count`
+    sequential single-problem calls on the same graphs."""
+    import torch
+    probs = W.ragged_batch(count=count, iters=iters)
+    graphs = [gs.gs_build_graph(ctx, torch.from_numpy(p.X).to(dev), p.k) for p in probs]
+    a = [torch.from_numpy(p.a).to(dev) for p in probs]
+    b = [torch.from_numpy(p.b).to(dev) for p in probs]
+    ts, Ks = [p.t for p in probs], [p.K for p in probs]
+    out = {}
+    gs.gs_sinkhorn_batched(ctx, graphs, a, b, ts, Ks, iters)  # warm (workspace, queue)
+    ms_b = _time(stream, lambda: out.__setitem__("b", gs.gs_sinkhorn_batched(ctx, graphs, a, b, ts, Ks, iters)))
+    for i, g in enumerate(graphs):  # warm the per-problem graphs
+        gs.gs_sinkhorn(ctx, g, a[i], b[i], ts[i], Ks[i], iters)
+    seq = []
+    ms_s = _time(stream, lambda: seq.extend(gs.gs_sinkhorn(ctx, g, a[i], b[i], ts[i], Ks[i], iters)[2]
+                                            for i, g in enumerate(graphs)))
+    gs.gs_sync(ctx)
+    db = out["b"][2].cpu().numpy()[:, 0]
+    ds = np.array([float(d[0]) for d in seq])
+    rel = float(np.max(np.abs(db - ds) / np.maximum(np.abs(ds), 1e-30)))
+    nodes = sum(g.n for g in graphs)
+    for g in graphs:
+        g.close()
+    return {"problems": count, "iters": iters, "total_nodes": nodes, "batched_ms": ms_b,
+            "sequential_ms": ms_s, "speedup": ms_s / ms_b,
+            "batched_problem_iters_per_s": count * iters / (ms_b / 1e3),
+            "max_rel_diff_W2": rel}
+
+
+def adjoint_case(gs, ctx, dev, stream, iters=40, checkpoint=20):
+    """Gradient of W^2(src, barycenter(M, alpha)) on the 500k-point manifold with 64 inputs
+    (K = 40, t = 8): forward only vs forward + reverse sweep, `iters` iterations per loop."""
+    import torch
+    cfg = W.manifold_barycenter_grad(bary_iters=iters, sink_iters=iters, checkpoint=checkpoint)
+    g = gs.gs_build_graph(ctx, torch.from_numpy(cfg["X"]).to(dev), cfg["k"])
+    M = torch.from_numpy(cfg["M"]).to(dev)
+    alpha = torch.tensor(cfg["alpha"], dtype=torch.float64, device=dev)
+    src = torch.from_numpy(cfg["src"]).to(dev)
+    t, K = cfg["t"], cfg["K"]
+    res = {}
+
+    def forward():
+        mu = gs.gs_barycenter(ctx, g, M, alpha, t, K, iters)
+        res["d"] = gs.gs_distance(ctx, g, src, mu, t, K, iters)
+
+    def gradient():
+        mu = gs.gs_barycenter(ctx, g, M, alpha, t, K, iters)
+        d, ga, gmu = gs.gs_sinkhorn_grad(ctx, g, src, mu, t, K, iters, checkpoint=checkpoint)
+        _, galpha = gs.gs_barycenter_grad(ctx, g, M, alpha, t, K, iters, gmu, checkpoint=checkpoint)
+        res["g"] = (ga, galpha)
+
+    forward()
+    gradient()
+    ms_f = _time(stream, forward)
+    ms_g = _time(stream, gradient)
+    gs.gs_sync(ctx)
+    n = g.n
+    g.close()
+    return {"n": n, "m": int(M.shape[1]), "K": K, "iters": iters, "checkpoint": checkpoint,
+            "forward_ms": ms_f, "forward_plus_backward_ms": ms_g, "backward_over_forward": ms_g / ms_f - 1.0}
 
 
 def main():

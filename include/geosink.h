@@ -146,6 +146,14 @@ gs_status gs_graph_info(const gs_graph *g, int64_t *n, int64_t *nnz, double *sig
 gs_status gs_graph_export_csr(gs_ctx *ctx, const gs_graph *g, int64_t *rowptr, int32_t *col,
                               float *A, float *P);
 
+/* Autotuner (not in the paper; it serves throughput): times every Chebyshev-order kernel variant
+ * for B columns and degree K on this graph (heat-filter applies on a synthetic block, CUDA events,
+ * waits for the device) and records the fastest in the graph handle.  Later calls on the graph
+ * with B columns use it while the context's GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL is 0 (automatic).
+ * *choice (may be NULL) receives the chosen variant (the GS_OPT_*_KERNEL value).
+ * Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED. */
+gs_status gs_autotune(gs_ctx *ctx, gs_graph *g, int B, int K, int *choice);
+
 /* Free a graph (waits for the device). NULL is accepted. */
 gs_status gs_graph_destroy(gs_graph *g);
 

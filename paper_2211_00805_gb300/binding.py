@@ -38,6 +38,7 @@ SIGNATURES = {
     "gs_graph_from_csr": [_P, _I64, _P, _P, _P, _P],
     "gs_graph_info": [_P, _P, _P, _P],
     "gs_graph_export_csr": [_P, _P, _P, _P, _P, _P],
+    "gs_autotune": [_P, _P, _I, _I, _P],
     "gs_graph_destroy": [_P],
     "gs_heat_apply": [_P, _P, _D, _I, _P, _I, _P],
     "gs_heat_apply_noalloc": [_I64, _I64, _P, _P, _P, _D, _I, _P, _I, _P, _P],
@@ -210,6 +211,13 @@ def gs_graph_from_csr(ctx: Context, rowptr: torch.Tensor, col: torch.Tensor, w: 
     _raise(ctx, _lib.gs_graph_from_csr(ctx.handle, n, _ptr(rowptr), _ptr(col), _ptr(w),
                                        ctypes.byref(h)))
     return Graph(h)
+
+
+def gs_autotune(ctx: Context, g: Graph, B: int, K: int) -> int:
+    """Time the order-kernel variants on g for B columns and degree K; returns the chosen one."""
+    ch = ctypes.c_int()
+    _raise(ctx, _lib.gs_autotune(ctx.handle, g.handle, int(B), int(K), ctypes.byref(ch)))
+    return int(ch.value)
 
 
 def gs_graph_export_csr(ctx: Context, g: Graph):

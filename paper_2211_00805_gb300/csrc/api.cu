@@ -244,6 +244,17 @@ extern "C" gs_status gs_graph_export_csr(gs_ctx* ctx, const gs_graph* g, int64_t
     return gs_graph_export(ctx, g, rowptr, col, A, P);
 }
 
+extern "C" gs_status gs_autotune(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK) return st;
+    if (K < 1 || K > 10000) return gs_fail(ctx, GS_ERR_ARG, "K must be in [1, 10000]");
+    if (!gs_filter_supports(B, true))
+        return gs_fail(ctx, GS_ERR_UNSUPPORTED, "B must be 1..256, or a multiple of 4 up to 1024");
+    return gs_autotune_impl(ctx, g, B, K, choice);
+}
+
 extern "C" gs_status gs_graph_destroy(gs_graph* g)
 {
     if (!g) return GS_OK;

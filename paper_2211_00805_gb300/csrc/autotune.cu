@@ -1,0 +1,92 @@
+// Autotuner: picks, per graph and column count, the fastest Chebyshev-order kernel variant (and
+// for one column the Sinkhorn loop mode) by timing them on the graph itself, and stores the choice
+// in the graph handle.  Calls on that graph use the stored choice whenever the context's own
+// option is left at automatic.
+#include <vector>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+__global__ void fill_ones(int64_t count, float* __restrict__ x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) x[i] = 1.f / (1.f + (float)(i % 97));
+}
+
+}  // namespace
+
+gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_out)
+{
+    const int64_t n = g->n;
+    const size_t blk = sizeof(float) * (size_t)n * (size_t)B;
+    WsPlan plan;
+    const size_t iV = plan.add(blk), iY = plan.add(blk), iA = plan.add(blk), iBb = plan.add(blk);
+    gs_status st = gs_ws_ensure(ctx, plan.total);
+    if (st != GS_OK) return st;
+    float* V = ws_at<float>(ctx, plan, iV);
+    float* Y = ws_at<float>(ctx, plan, iY);
+    float* bufA = ws_at<float>(ctx, plan, iA);
+    float* bufB = ws_at<float>(ctx, plan, iBb);
+    const int64_t count = n * (int64_t)B;
+    fill_ones<<<(unsigned)((count + 255) / 256), 256, 0, ctx->stream>>>(count, V);
+    gs_count(ctx, 1);
+    std::vector<double> c((size_t)K + 1);
+    gs_heat_coefficients(1.0, K, c.data());
+
+    std::vector<int> cands;
+    if (B == 1) cands = {GS_KERNEL_RANGED, GS_KERNEL_SELL, GS_KERNEL_VECTOR, GS_KERNEL_ASYNC};
+    else if (B % 4 == 0 && B <= 128) cands = {GS_KERNEL_VECTOR, GS_KERNEL_STAGED, GS_KERNEL_ASYNC, GS_KERNEL_RANGED};
+    else cands = {GS_KERNEL_VECTOR, GS_KERNEL_RANGED};
+    int* knob = (B == 1) ? &ctx->b1_kernel : &ctx->blk_kernel;
+    const int saved = *knob;
+    const int saved_tb1 = g->tuned_b1, saved_tblk = g->tuned_blk, saved_tB = g->tuned_blk_B;
+    g->tuned_b1 = 0;
+    g->tuned_blk = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = cands[0];
+    float best_ms = 1e30f;
+    for (int v : cands) {
+        *knob = v;
+        Epilogue e;
+        e.kind = EPI_STORE;
+        e.out = Y;
+        // warm once, then time three applies
+        st = gs_filter_enqueue(ctx, g, c.data(), K, B, V, false, bufA, bufB, Y, e, nullptr, nullptr);
+        if (st != GS_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        for (int r = 0; r < 3 && st == GS_OK; ++r)
+            st = gs_filter_enqueue(ctx, g, c.data(), K, B, V, false, bufA, bufB, Y, e, nullptr, nullptr);
+        cudaEventRecord(e1, ctx->stream);
+        if (st != GS_OK) break;
+        if ((st = gs_cuda_check(ctx, cudaEventSynchronize(e1), "autotune timing")) != GS_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *knob = saved;
+    if (st != GS_OK) {
+        g->tuned_b1 = saved_tb1;
+        g->tuned_blk = saved_tblk;
+        g->tuned_blk_B = saved_tB;
+        return st;
+    }
+    if (B == 1) {
+        g->tuned_b1 = best;
+        g->tuned_blk = saved_tblk;
+        g->tuned_blk_B = saved_tB;
+    } else {
+        g->tuned_b1 = saved_tb1;
+        g->tuned_blk = best;
+        g->tuned_blk_B = B;
+    }
+    if (choice_out) *choice_out = best;
+    return GS_OK;
+}

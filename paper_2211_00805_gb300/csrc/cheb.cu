@@ -729,7 +729,7 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
     gs_count(ctx, 1);
     const int TB = pl.block;
     if (pl.B == 1 && a.epi.kind != EPI_BARY_V) {
-        const int mode = ctx->b1_kernel;
+        const int mode = ctx->b1_kernel != GS_KERNEL_AUTO ? ctx->b1_kernel : g->tuned_b1;
         if (mode == GS_KERNEL_ASYNC) {
             order_b1_async<<<nblocks(g->n, 256), 256, 0, ctx->stream>>>(a);
             return;
@@ -758,8 +758,11 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
     const int vec = pl.vec;
     const int lpr = pl.B == 1 ? 1 : pl.group;
     const unsigned grid = nblocks(g->n * lpr, TB);
+    const int blk_mode = ctx->blk_kernel != GS_KERNEL_AUTO
+                             ? ctx->blk_kernel
+                             : (g->tuned_blk_B == pl.B ? g->tuned_blk : GS_KERNEL_AUTO);
     if (vec == 4 && pl.B == 4 * lpr && lpr >= 2) {  // one float4 chunk per lane
-        const int mode = ctx->blk_kernel;
+        const int mode = blk_mode;
         if (mode == GS_KERNEL_ASYNC) {
             switch (lpr) {
                 case 2: launch_blk_async<2>(ctx, g, a); return;
@@ -783,7 +786,7 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
     }
     const bool one = pl.B <= lpr * vec;
     const int lg = ilog2(lpr);
-    if (pl.B > 1 && ctx->blk_kernel == GS_KERNEL_RANGED) {
+    if (pl.B > 1 && blk_mode == GS_KERNEL_RANGED) {
         static const int occ41 = resident_blocks_per_sm(order_blk_ranged<4, 1>);
         static const int occ48 = resident_blocks_per_sm(order_blk_ranged<4, 8>);
         static const int occ11 = resident_blocks_per_sm(order_blk_ranged<1, 1>);

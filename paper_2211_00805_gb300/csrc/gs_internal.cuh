@@ -85,6 +85,10 @@ struct gs_graph {
     float* sval = nullptr;
     int64_t nslices = 0;
     int64_t sell_nnz = 0;          // stored entries including padding
+    // autotuner choices (GS_KERNEL_*, 0 = none): one column, and several columns for B = tuned_blk_B
+    int tuned_b1 = 0;
+    int tuned_blk = 0;
+    int tuned_blk_B = 0;
 };
 
 // The CSR the filter kernels read: the reordered one when present.
@@ -208,6 +212,7 @@ gs_status gs_sinkhorn_batched_impl(gs_ctx* ctx, int nprob, const gs_graph* const
 gs_status gs_sinkhorn_persistent(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
                                  const float* vol, const float* coef_dev, int K, int iters,
                                  float* x, float* A, float* y, float* u, float* v, unsigned* bar);
+gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_out);
 gs_status gs_barycenter_impl(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
                              const double* alpha, const float* vol, double t, int K, int iters,
                              float* mu, float* v_state);

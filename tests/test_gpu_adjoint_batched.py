@@ -138,3 +138,15 @@ def test_batched_matches_single_and_oracle(gs, ctx):
         r = oracle.sinkhorn(Ls, oracle.cheb_coefficients(p.t, p.K), p.a.astype(np.float64),
                             p.b.astype(np.float64), p.t, 40)
         assert d[i, 0] == pytest.approx(r["W2"], rel=1e-4)
+
+
+def test_autotune_choice_is_used_and_exact(gs, ctx, sphere):
+    p, g, Ls = sphere
+    for B in (1, 32):
+        choice = gs.gs_autotune(ctx, g, B, 30)
+        assert choice in (1, 2, 3, 4, 5)
+        V = np.random.default_rng(B).random((g.n, B)).astype(np.float32)
+        Y = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
+        ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(5.0, 30), V.astype(np.float64))
+        assert_close(Y, ref, 1e-4, 1e-6 * np.abs(ref).max(), f"autotuned B={B}")
+    gs.gs_sync(ctx)
