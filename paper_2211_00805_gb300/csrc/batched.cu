@@ -20,14 +20,15 @@
 #include <vector>
 
 #include "gs_internal.cuh"
+#include "sell_row.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace {
 
 constexpr int kClusterCtas = 8;
-constexpr int kThreads = 256;
-constexpr int kLanes = 8;  // lanes per row in the B = 1 mapping
+constexpr int kThreads = 512;
+constexpr int kLanes = 8;  // lanes per row in the CSR mapping (graphs without a sliced-ELL copy)
 
 struct BatchProblem {
     int n;
@@ -37,6 +38,9 @@ struct BatchProblem {
     const int* col;
     const float* pval;
     const int* perm;        // new -> old node id, or null
+    const int* sptr;        // sliced ELL of the same operator (thread-per-row mapping), or null
+    const int* scol;
+    const float* sval;
     const float* a;         // marginals in the caller's node order
     const float* b;
     float* u;               // outputs in the caller's node order
@@ -57,6 +61,29 @@ __device__ void order_rows(const BatchProblem& p, int r0, int r1, int mode, floa
                            const float* cur, const float* prev, float* next, const float* num,
                            float* out, float* xnext, int* flags)
 {
+    if (p.sptr) {  // thread per row over the sliced ELL copy; r0 is a multiple of 32
+        for (int row = r0 + (int)threadIdx.x; row < r1; row += blockDim.x) {
+            const float pv = (mode == 0) ? 0.f : prev[row];
+            const float yv = (mode == 0) ? c0 * cur[row] : p.y[row];
+            const float s = gs_sell_row<false>(p.sptr, p.scol, p.sval, cur, row);
+            const float tk = (mode == 0) ? s : fmaf(2.f, s, -pv);
+            const float acc = fmaf(ck, tk, yv);
+            if (mode != 2) {
+                next[row] = tk;
+                p.y[row] = acc;
+            } else {
+                const float m = num[node_of(p, row)];
+                float r = 0.f;
+                if (m != 0.f) {
+                    r = m / acc;
+                    if (!(r > 0.f) || isinf(r)) atomicOr(flags, GS_FLAG_NONFINITE);
+                }
+                out[row] = r;
+                xnext[row] = r;
+            }
+        }
+        return;
+    }
     const int lane = threadIdx.x & (kLanes - 1);
     const int rows_per_pass = blockDim.x / kLanes;
     for (int base = r0; base < r1; base += rows_per_pass) {
@@ -96,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) batched_sinkhorn(const BatchProblem*
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     __shared__ int s_prob;
-    __shared__ double s_part[kThreads / 32];
+    __shared__ double s_part[kThreads / 32];  // one slot per warp
     __shared__ double s_total;
 
     while (true) {
@@ -105,8 +132,8 @@ __global__ void __launch_bounds__(kThreads) batched_sinkhorn(const BatchProblem*
         const int pid = *cluster.map_shared_rank(&s_prob, 0);
         cluster.sync();  // everyone has read rank 0's slot before it is overwritten
         if (pid >= nprob) break;
-        const BatchProblem p = probs[pid];
-        const int per = (p.n + kClusterCtas - 1) / kClusterCtas;
+        const BatchProblem& p = probs[pid];  // fields read through L1, not copied to registers
+        const int per = ((p.n + kClusterCtas - 1) / kClusterCtas + 31) / 32 * 32;  // whole slices
         const int r0 = min(p.n, rank * per), r1 = min(p.n, r0 + per);
 
         for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) p.x[r] = 1.f;  // v = 1
@@ -218,6 +245,9 @@ gs_status gs_sinkhorn_batched_impl(gs_ctx* ctx, int nprob, const gs_graph* const
         p.col = ord ? g->pcol : g->col;
         p.pval = ord ? g->ppval : g->pval;
         p.perm = ord ? g->perm : nullptr;
+        p.sptr = ord ? g->sptr : nullptr;
+        p.scol = ord ? g->scol : nullptr;
+        p.sval = ord ? g->sval : nullptr;
         p.a = a[i];
         p.b = b[i];
         p.u = u[i];
