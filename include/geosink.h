@@ -94,7 +94,10 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * asynchronous gathers into shared memory, 4 staged neighbour lists (several columns), 5 the
  * sliced-ELL / lane-group kernels with each block walking one contiguous row range.  All variants
  * compute the same recurrence; they differ in summation order only. */
-enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4 };
+/* GS_OPT_KNN_TENSOR: 1 (default) screens kNN distances with tensor-core 3xTF32 dot products when
+ * d >= 16, 0 always uses FP32 CUDA-core dot products; the FP64 rerank makes both exact. */
+enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
+       GS_OPT_KNN_TENSOR = 5 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
 
 /* Host query: number of GPU kernels this context has enqueued so far (a replayed CUDA graph

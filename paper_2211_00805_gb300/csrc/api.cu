@@ -163,6 +163,10 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->barrier_selftest = value;
         return GS_OK;
     }
+    if (option == GS_OPT_KNN_TENSOR && (value == 0 || value == 1)) {
+        ctx->knn_tensor_cores = value;
+        return GS_OK;
+    }
     if (option == GS_OPT_B1_KERNEL && (value >= 0 && value <= 3 || value == 5)) {
         ctx->b1_kernel = value;
         return GS_OK;

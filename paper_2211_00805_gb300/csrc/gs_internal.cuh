@@ -49,6 +49,7 @@ struct gs_ctx {
     int barrier_selftest = 0;      // next persistent launch waits for an arrival that never comes
     int b1_kernel = 0;             // GS_KERNEL_* for one column
     int blk_kernel = 0;            // GS_KERNEL_* for several columns
+    int knn_tensor_cores = 1;      // kNN screen on tensor cores (3xTF32) for d >= 16
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::string err;

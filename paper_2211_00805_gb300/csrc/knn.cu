@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "gs_internal.cuh"
+#include "async_copy.cuh"
 
 namespace {
 
@@ -53,6 +54,31 @@ __device__ __forceinline__ void list_insert(float& ld, int& li, float dv, int iv
     } else if (lane == pos) {
         ld = dv;
         li = iv;
+    }
+}
+
+// Fold one 64 x 64 tile of squared distances into the warp's 8 sorted top-32 lists (warp w owns
+// query rows 8w .. 8w+7 of the tile; lane l holds entry l of every list).
+__device__ __forceinline__ void select_tile(const float (*tile)[CT + 1], int c0, int warp, int lane,
+                                            float (&ld)[8], int (&li)[8])
+{
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int qrow = warp * 8 + r;
+        const float thr = __shfl_sync(FULL, ld[r], 31);
+        const float d0 = tile[qrow][lane], d1 = tile[qrow][lane + 32];
+        unsigned m0 = __ballot_sync(FULL, d0 <= thr && d0 < INFINITY);
+        unsigned m1 = __ballot_sync(FULL, d1 <= thr && d1 < INFINITY);
+        while (m0) {
+            const int src = __ffs(m0) - 1;
+            m0 &= m0 - 1;
+            list_insert(ld[r], li[r], __shfl_sync(FULL, d0, src), c0 + src, lane);
+        }
+        while (m1) {
+            const int src = __ffs(m1) - 1;
+            m1 &= m1 - 1;
+            list_insert(ld[r], li[r], __shfl_sync(FULL, d1, src), c0 + 32 + src, lane);
+        }
     }
 }
 
@@ -119,24 +145,7 @@ __global__ void __launch_bounds__(256) knn_screen(const float* __restrict__ X,
             }
         }
         __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int qrow = warp * 8 + r;
-            const float thr = __shfl_sync(FULL, ld[r], 31);
-            const float d0 = tile[qrow][lane], d1 = tile[qrow][lane + 32];
-            unsigned m0 = __ballot_sync(FULL, d0 <= thr && d0 < INFINITY);
-            unsigned m1 = __ballot_sync(FULL, d1 <= thr && d1 < INFINITY);
-            while (m0) {
-                const int src = __ffs(m0) - 1;
-                m0 &= m0 - 1;
-                list_insert(ld[r], li[r], __shfl_sync(FULL, d0, src), c0 + src, lane);
-            }
-            while (m1) {
-                const int src = __ffs(m1) - 1;
-                m1 &= m1 - 1;
-                list_insert(ld[r], li[r], __shfl_sync(FULL, d1, src), c0 + 32 + src, lane);
-            }
-        }
+        select_tile(tile, c0, warp, lane, ld, li);
         __syncthreads();
     }
 #pragma unroll
@@ -144,6 +153,266 @@ __global__ void __launch_bounds__(256) knn_screen(const float* __restrict__ X,
         const int gq = q0 + warp * 8 + r;
         if (gq < n) cand[(int64_t)gq * KK + lane] = li[r];
     }
+}
+
+
+// ------------------------------------------------------------------ tensor-core screening
+// Same tiles and selection as knn_screen, but the 64 x 64 dot-product tile runs on the tensor
+// cores (warp-level m16n8k8 TF32 MMA) with the 3xTF32 split: x = hi + lo with hi, lo TF32, and
+// q.c ~ q_hi.c_hi + q_hi.c_lo + q_lo.c_hi, which recovers FP32-grade products.  Points are split
+// once into hi / lo arrays padded to dp (a multiple of 8) features.
+constexpr int TC_DC = 32;
+constexpr int TC_LD = TC_DC + 4;  // shared row stride (floats): conflict-free fragment loads
+constexpr int TC_SMEM = 4 * 64 * TC_LD * 4 + 64 * (CT + 1) * 4;
+
+__device__ __forceinline__ float tf32_round(float x)
+{
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void split_tf32(const float* __restrict__ X, int64_t n, int d, int dp,
+                           float* __restrict__ hi, float* __restrict__ lo)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * dp) return;
+    const int64_t r = i / dp;
+    const int c = (int)(i - r * dp);
+    const float x = c < d ? X[r * d + c] : 0.f;
+    const float h = tf32_round(x);
+    hi[i] = h;
+    lo[i] = tf32_round(x - h);
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256) knn_screen_tc(const float* __restrict__ hi,
+                                                     const float* __restrict__ lo,
+                                                     const float* __restrict__ norms, int n,
+                                                     int dp, int* __restrict__ cand)
+{
+    extern __shared__ __align__(16) float tc_sm[];
+    float* qh = tc_sm;
+    float* ql = qh + 64 * TC_LD;
+    float* chh = ql + 64 * TC_LD;
+    float* cll = chh + 64 * TC_LD;
+    float (*tile)[CT + 1] = reinterpret_cast<float (*)[CT + 1]>(cll + 64 * TC_LD);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int q0 = blockIdx.x * QT;
+    const int m0 = 16 * (warp >> 1);   // this warp's 16 query rows of the tile
+    const int nb = 32 * (warp & 1);    // and its 32 candidate columns (4 n8 tiles)
+    float ld[8];
+    int li[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        ld[r] = INFINITY;
+        li[r] = 0x7fffffff;
+    }
+    const float qn0 = (q0 + m0 + gid < n) ? norms[q0 + m0 + gid] : 0.f;
+    const float qn1 = (q0 + m0 + gid + 8 < n) ? norms[q0 + m0 + gid + 8] : 0.f;
+    for (int c0 = 0; c0 < n; c0 += CT) {
+        float acc[4][4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[t][v] = 0.f;
+        for (int k0 = 0; k0 < dp; k0 += TC_DC) {
+            const int kc = (dp - k0) < TC_DC ? (dp - k0) : TC_DC;  // multiple of 8
+            for (int e = tid; e < 64 * TC_DC; e += 256) {
+                const int rr = e / TC_DC, kk = e % TC_DC;
+                const bool kin = kk < kc;
+                const int gq = q0 + rr, gc = c0 + rr;
+                const int64_t oq = (int64_t)gq * dp + k0 + kk, oc = (int64_t)gc * dp + k0 + kk;
+                qh[rr * TC_LD + kk] = (gq < n && kin) ? hi[oq] : 0.f;
+                ql[rr * TC_LD + kk] = (gq < n && kin) ? lo[oq] : 0.f;
+                chh[rr * TC_LD + kk] = (gc < n && kin) ? hi[oc] : 0.f;
+                cll[rr * TC_LD + kk] = (gc < n && kin) ? lo[oc] : 0.f;
+            }
+            __syncthreads();
+            for (int kk = 0; kk < kc; kk += 8) {
+                unsigned ah[4], al[4];
+                const int ra = (m0 + gid) * TC_LD + kk + tig, rb = (m0 + gid + 8) * TC_LD + kk + tig;
+                ah[0] = __float_as_uint(qh[ra]);
+                ah[1] = __float_as_uint(qh[rb]);
+                ah[2] = __float_as_uint(qh[ra + 4]);
+                ah[3] = __float_as_uint(qh[rb + 4]);
+                al[0] = __float_as_uint(ql[ra]);
+                al[1] = __float_as_uint(ql[rb]);
+                al[2] = __float_as_uint(ql[ra + 4]);
+                al[3] = __float_as_uint(ql[rb + 4]);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int cb = (nb + 8 * t + gid) * TC_LD + kk + tig;
+                    const unsigned bh0 = __float_as_uint(chh[cb]), bh1 = __float_as_uint(chh[cb + 4]);
+                    const unsigned bl0 = __float_as_uint(cll[cb]), bl1 = __float_as_uint(cll[cb + 4]);
+                    mma_tf32(acc[t], al, bh0, bh1);
+                    mma_tf32(acc[t], ah, bl0, bl1);
+                    mma_tf32(acc[t], ah, bh0, bh1);
+                }
+            }
+            __syncthreads();
+        }
+        // D fragment: (gid, 2tig), (gid, 2tig+1), (gid+8, 2tig), (gid+8, 2tig+1)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int rl = m0 + gid + ((v >> 1) << 3);
+                const int cl = nb + 8 * t + 2 * tig + (v & 1);
+                const int gq = q0 + rl, gc = c0 + cl;
+                const float qn = (v >> 1) ? qn1 : qn0;
+                const float cn = gc < n ? norms[gc] : 0.f;
+                tile[rl][cl] = (gc < n && gc != gq) ? fmaf(-2.f, acc[t][v], qn + cn) : INFINITY;
+            }
+        }
+        __syncthreads();
+        select_tile(tile, c0, warp, lane, ld, li);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int gq = q0 + warp * 8 + r;
+        if (gq < n) cand[(int64_t)gq * KK + lane] = li[r];
+    }
+}
+
+// Register-resident variant for dp <= 64 (KS = dp / 8 k-steps): each warp keeps the TF32 hi / lo
+// A fragments of its 16 query rows in registers for the whole kernel, and candidate tiles (hi and
+// lo, 64 rows x dp) stream through double-buffered shared memory with 16-byte cp.async copies, so
+// a candidate tile is read once per block and the query rows never again.
+template <int KS>
+__global__ void __launch_bounds__(256, 2) knn_screen_tc_reg(const float* __restrict__ hi,
+                                                             const float* __restrict__ lo,
+                                                             const float* __restrict__ norms,
+                                                             int n, int* __restrict__ cand)
+{
+    constexpr int DP = 8 * KS;
+    constexpr int LDC = DP + 4;  // (LDC / 4) odd: conflict-free B-fragment loads
+    extern __shared__ __align__(16) float tc_sm[];
+    float* cbuf = tc_sm;  // [2 buffers][2 (hi, lo)][64][LDC]
+    float (*tile)[CT + 1] = reinterpret_cast<float (*)[CT + 1]>(tc_sm + 2 * 2 * 64 * LDC);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int q0 = blockIdx.x * QT;
+    const int m0 = 16 * (warp >> 1), nb = 32 * (warp & 1);
+    float ld[8];
+    int li[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        ld[r] = INFINITY;
+        li[r] = 0x7fffffff;
+    }
+    // A fragments: rows (m0 + gid) and (m0 + gid + 8), columns 8s + tig and 8s + tig + 4
+    unsigned ah[KS][4], al[KS][4];
+    {
+        const int ra = q0 + m0 + gid, rb = ra + 8;
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            const int k = 8 * ks + tig;
+            ah[ks][0] = ra < n ? __float_as_uint(hi[(int64_t)ra * DP + k]) : 0u;
+            ah[ks][1] = rb < n ? __float_as_uint(hi[(int64_t)rb * DP + k]) : 0u;
+            ah[ks][2] = ra < n ? __float_as_uint(hi[(int64_t)ra * DP + k + 4]) : 0u;
+            ah[ks][3] = rb < n ? __float_as_uint(hi[(int64_t)rb * DP + k + 4]) : 0u;
+            al[ks][0] = ra < n ? __float_as_uint(lo[(int64_t)ra * DP + k]) : 0u;
+            al[ks][1] = rb < n ? __float_as_uint(lo[(int64_t)rb * DP + k]) : 0u;
+            al[ks][2] = ra < n ? __float_as_uint(lo[(int64_t)ra * DP + k + 4]) : 0u;
+            al[ks][3] = rb < n ? __float_as_uint(lo[(int64_t)rb * DP + k + 4]) : 0u;
+        }
+    }
+    const float qn0 = (q0 + m0 + gid < n) ? norms[q0 + m0 + gid] : 0.f;
+    const float qn1 = (q0 + m0 + gid + 8 < n) ? norms[q0 + m0 + gid + 8] : 0.f;
+
+    constexpr int CHUNKS = 2 * 64 * (DP / 4);  // 16-byte pieces of one candidate tile (hi + lo)
+    auto stage = [&](int c0, int buf) {
+        for (int i = tid; i < CHUNKS; i += 256) {
+            const int part = i / (64 * (DP / 4));          // 0 hi, 1 lo
+            const int rem = i - part * 64 * (DP / 4);
+            const int r = rem / (DP / 4), q = rem - r * (DP / 4);
+            float* dst = cbuf + ((buf * 2 + part) * 64 + r) * LDC + 4 * q;
+            const int gc = c0 + r;
+            if (gc < n) {
+                gs_cp_async16(dst, (part ? lo : hi) + (int64_t)gc * DP + 4 * q);
+            } else {
+                dst[0] = 0.f; dst[1] = 0.f; dst[2] = 0.f; dst[3] = 0.f;
+            }
+        }
+        gs_cp_async_commit();
+    };
+    const int ntiles = (n + CT - 1) / CT;
+    stage(0, 0);
+    for (int t = 0; t < ntiles; ++t) {
+        const int c0 = t * CT, buf = t & 1;
+        if (t + 1 < ntiles) {
+            stage(c0 + CT, buf ^ 1);
+            gs_cp_async_wait<1>();
+        } else {
+            gs_cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float* chh = cbuf + (buf * 2 + 0) * 64 * LDC;
+        const float* cll = cbuf + (buf * 2 + 1) * 64 * LDC;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int cb = (nb + 8 * u + gid) * LDC + 8 * ks + tig;
+                const unsigned bh0 = __float_as_uint(chh[cb]), bh1 = __float_as_uint(chh[cb + 4]);
+                const unsigned bl0 = __float_as_uint(cll[cb]), bl1 = __float_as_uint(cll[cb + 4]);
+                mma_tf32(acc[u], al[ks], bh0, bh1);
+                mma_tf32(acc[u], ah[ks], bl0, bl1);
+                mma_tf32(acc[u], ah[ks], bh0, bh1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int rl = m0 + gid + ((v >> 1) << 3);
+                const int cl = nb + 8 * u + 2 * tig + (v & 1);
+                const int gq = q0 + rl, gc = c0 + cl;
+                const float qn = (v >> 1) ? qn1 : qn0;
+                const float cn = gc < n ? norms[gc] : 0.f;
+                tile[rl][cl] = (gc < n && gc != gq) ? fmaf(-2.f, acc[u][v], qn + cn) : INFINITY;
+            }
+        }
+        __syncthreads();
+        select_tile(tile, c0, warp, lane, ld, li);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int gq = q0 + warp * 8 + r;
+        if (gq < n) cand[(int64_t)gq * KK + lane] = li[r];
+    }
+}
+
+template <int KS>
+constexpr int tc_reg_smem() { return 2 * 2 * 64 * (8 * KS + 4) * 4 + 64 * (CT + 1) * 4; }
+
+template <int KS>
+void launch_tc_reg(gs_ctx* ctx, const float* hi, const float* lo, const float* norms, int64_t n, int* cand)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(knn_screen_tc_reg<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc_reg_smem<KS>());
+        attr = true;
+    }
+    knn_screen_tc_reg<KS><<<nblk(n, QT), 256, tc_reg_smem<KS>(), ctx->stream>>>(hi, lo, norms, (int)n, cand);
 }
 
 // One warp per query: FP64 direct-difference squared distances of the 32 candidates, in the
@@ -427,16 +696,43 @@ __global__ void rowptr_to32(int64_t n1, const int64_t* __restrict__ in, int* __r
 gs_status gs_knn_launch(gs_ctx* ctx, const float* X, int64_t n, int d, int k, int32_t* idx,
                         float* dist, double* dist64)
 {
+    const bool tc = d >= 16 && ctx->knn_tensor_cores;
+    const int dp = (d + 7) / 8 * 8;
     WsPlan plan;
     const size_t inorm = plan.add(sizeof(float) * n), icand = plan.add(sizeof(int) * n * KK);
+    const size_t ihi = tc ? plan.add(sizeof(float) * n * dp) : 0, ilo = tc ? plan.add(sizeof(float) * n * dp) : 0;
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
     float* norms = ws_at<float>(ctx, plan, inorm);
     int* cand = ws_at<int>(ctx, plan, icand);
     sq_norms<<<nblk(n, 256), 256, 0, ctx->stream>>>(X, n, d, norms);
-    knn_screen<<<nblk(n, QT), 256, 0, ctx->stream>>>(X, norms, (int)n, d, cand);
+    if (tc) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(knn_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+            attr = true;
+        }
+        float* hi = ws_at<float>(ctx, plan, ihi);
+        float* lo = ws_at<float>(ctx, plan, ilo);
+        split_tf32<<<nblk(n * dp, 256), 256, 0, ctx->stream>>>(X, n, d, dp, hi, lo);
+        switch (dp / 8) {
+            case 2: launch_tc_reg<2>(ctx, hi, lo, norms, n, cand); break;
+            case 3: launch_tc_reg<3>(ctx, hi, lo, norms, n, cand); break;
+            case 4: launch_tc_reg<4>(ctx, hi, lo, norms, n, cand); break;
+            case 5: launch_tc_reg<5>(ctx, hi, lo, norms, n, cand); break;
+            case 6: launch_tc_reg<6>(ctx, hi, lo, norms, n, cand); break;
+            case 7: launch_tc_reg<7>(ctx, hi, lo, norms, n, cand); break;
+            case 8: launch_tc_reg<8>(ctx, hi, lo, norms, n, cand); break;
+            default:
+                knn_screen_tc<<<nblk(n, QT), 256, TC_SMEM, ctx->stream>>>(hi, lo, norms, (int)n, dp, cand);
+        }
+        gs_count(ctx, 2);
+    } else {
+        knn_screen<<<nblk(n, QT), 256, 0, ctx->stream>>>(X, norms, (int)n, d, cand);
+        gs_count(ctx, 1);
+    }
     knn_rerank<<<nblk(n * 32, 256), 256, 0, ctx->stream>>>(X, (int)n, d, k, cand, idx, dist, dist64);
-    gs_count(ctx, 3);
+    gs_count(ctx, 2);
     return gs_cuda_check(ctx, cudaGetLastError(), "kNN launch");
 }
 
@@ -447,7 +743,9 @@ gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE + 1;
     // one workspace plan for every stage (the knn stage reuses the front of the workspace)
     WsPlan plan;
-    const size_t i_knn = plan.add(sizeof(float) * n + 256 + sizeof(int) * n * KK);
+    const int dp = (d + 7) / 8 * 8;
+    const size_t i_knn = plan.add(sizeof(float) * n + 256 + sizeof(int) * n * KK + 512 +
+                                  2 * (sizeof(float) * n * dp + 256));
     const size_t i_idx = plan.add(sizeof(int) * nk), i_d64 = plan.add(sizeof(double) * nk),
                  i_cnt = plan.add(sizeof(int) * n), i_cur = plan.add(sizeof(int) * n),
                  i_inp = plan.add(sizeof(int64_t) * (n + 1)), i_ins = plan.add(sizeof(int) * nk),

@@ -56,10 +56,34 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="time every variant of the case")
     ap.add_argument("--sinkhorn", type=int, default=0,
                     help="also time this many Sinkhorn iterations in both loop modes (B = 1 cases)")
+    ap.add_argument("--knn", action="store_true",
+                    help="time the kNN graph builder (tensor-core and CUDA-core screens) instead")
     args = ap.parse_args()
     c = CASES[args.case]
     dev = torch.device("cuda", 0)
     ctx = gs.Context(0)
+    if args.knn:
+        X, _ = W.tanh_manifold(c["n"], c.get("latent", 10), c.get("ambient", 50), c["seed"])
+        Xd = torch.from_numpy(X).to(dev)
+        for tensor in (1, 0):
+            gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, tensor)
+            gs.gs_knn(ctx, Xd, c["k"])
+            for what, fn in (("knn", lambda: gs.gs_knn(ctx, Xd, c["k"])),
+                             ("build_graph", lambda: gs.gs_build_graph(ctx, Xd, c["k"]).close())):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(args.reps):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.reps
+                pairs = c["n"] * (c["n"] - 1)
+                print(json.dumps({"case": args.case, "what": what, "tensor_cores": tensor, "ms": ms,
+                                  "n": c["n"], "d": X.shape[1],
+                                  "dot_TFLOPs": 2.0 * pairs * X.shape[1] / (ms / 1e3) / 1e12}), flush=True)
+        gs.gs_sync(ctx)
+        return
     if c["kind"] == "manifold":
         X, Z = W.tanh_manifold(c["n"], c["latent"], c["ambient"], c["seed"])
     else:

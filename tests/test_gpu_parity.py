@@ -352,3 +352,17 @@ def test_kernel_variants_match_oracle(gs, ctx, B, option, variant):
         gs.gs_sync(ctx)
     finally:
         gs.gs_set_option(ctx, option, 0)
+
+
+@pytest.mark.parametrize("tensor", [1, 0])
+def test_knn_tensor_core_and_cuda_core_screens_exact(gs, ctx, tensor):
+    # d >= 16 screens on the tensor cores (3xTF32) unless disabled; both must give the oracle's lists
+    X, Z = W.tanh_manifold(3000, 8, 24, seed=9)
+    gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, tensor)
+    try:
+        idx, dist = gs.gs_knn(ctx, to_dev(X), 12)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, 1)
+    ri, rd = oracle.knn(X.astype(np.float64), 12)
+    assert _edge_sets_match(to_np(idx), None, ri, rd) == 0
+    np.testing.assert_allclose(to_np(dist), rd, rtol=1e-7)
