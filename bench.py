@@ -180,6 +180,17 @@ def oracle_sample(cfg=WORKLOAD, small_n=10_000, knn_rows=2400, iters_small=150):
             "kind": "oracle", "sample": sample, "est_step_s": total}
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest value across ranks (each rank times its own replica; the job takes the slowest)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -271,10 +282,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms = t_start.elapsed_time(t_end)
     graph_ms = [e[0].elapsed_time(e[1]) for e in evs]
     sink_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     value = cfg["iters"] * args.steps * world / (total_ms / 1e3)
 
     # roofline of the fused Chebyshev order kernel inside the Sinkhorn loop (B = 1)
@@ -327,10 +335,7 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     h2d = Xh.numel() * 4 + ah.numel() * 4 + bh.numel() * 4
     d2h = uh.numel() * 4 + vh.numel() * 4 + dh.numel() * 8
     e2e = {"value": cfg["iters"] * args.steps * world / (e2e_ms / 1e3), "unit": UNIT,
