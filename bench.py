@@ -261,6 +261,14 @@ def run_ours(args, rank, world, local_rank):
         nnz = step(X, a, b)
     gs.gs_sync(ctx)
     w2 = float(dist[0].item())
+    # the project's autotuner, once, on a graph of this workload: its one-column kernel and loop
+    # choices are kept by the context and used by the timed steps' freshly built graphs
+    gt = gs.gs_build_graph(ctx, X, cfg["k"])
+    tuned = {"b1_kernel": gs.gs_autotune(ctx, gt, 1, cfg["K"]),
+             "loop_mode": gs.gs_get_option(ctx, gs.GS_OPT_LOOP)}
+    gt.close()
+    for i in range(2):
+        nnz = step(X, a, b)
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     barrier()
@@ -359,7 +367,7 @@ def run_ours(args, rank, world, local_rank):
                        "graph_build_ms": statistics.mean(graph_ms),
                        "sinkhorn_ms": statistics.mean(sink_ms),
                        "sinkhorn_only_iters_per_s": cfg["iters"] / sink_s,
-                       "W2": w2},
+                       "W2": w2, "autotune": tuned},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -82,9 +82,10 @@ gs_status gs_sync(gs_ctx *ctx);
 gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
 
 /* Context options (host call).  GS_OPT_LOOP selects how gs_sinkhorn runs a fixed iteration count
- * (eps <= 0): 1 (default) CUDA-graph replay of per-order launches; 0 one persistent cooperative
- * launch with bounded grid barriers between the Chebyshev orders (falls back to 1 when the device
- * cannot co-schedule the grid).  Both compute the same thing.  Errors: GS_ERR_ARG. */
+ * (eps <= 0): 0 one persistent cooperative launch with bounded grid barriers between the Chebyshev
+ * orders (falls back to 1 when the device cannot co-schedule the grid); 1 CUDA-graph replay of
+ * per-order launches; 2 (default) the mode gs_autotune measured faster on the graph, else 0.
+ * All compute the same thing.  Errors: GS_ERR_ARG. */
 /* GS_OPT_BARRIER_SELFTEST = 1 makes the next persistent launch wait at its first grid barrier for
  * one block more than the grid has: every block's bounded wait runs out (~10 ms), the launch ends
  * and gs_sync reports GS_ERR_TIMEOUT, leaving the context usable.  It exercises failure handling
@@ -92,13 +93,20 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
 /* GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL pick the Chebyshev order kernel for one column / several
  * columns: 0 automatic, 1 sliced ELL (one column), 2 lane-split CSR, 3 chunked CSR with
  * asynchronous gathers into shared memory, 4 staged neighbour lists (several columns), 5 the
- * sliced-ELL / lane-group kernels with each block walking one contiguous row range.  All variants
- * compute the same recurrence; they differ in summation order only. */
+ * sliced-ELL / lane-group kernels with each block walking one contiguous row range, 6 sliced ELL
+ * with every row split across 4 threads (one column: the automatic choice), 7 sliced ELL with one
+ * 1024-thread block per SM over one contiguous row range.  All variants compute the same
+ * recurrence; they differ in summation order only. */
 /* GS_OPT_KNN_TENSOR: 1 (default) screens kNN distances with tensor-core 3xTF32 dot products when
  * d >= 16, 0 always uses FP32 CUDA-core dot products; the FP64 rerank makes both exact. */
 enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
        GS_OPT_KNN_TENSOR = 5 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
+
+/* Host query of an option.  For GS_OPT_LOOP and GS_OPT_B1_KERNEL left on automatic it reports what
+ * a call on a graph without its own autotune record would use (the context's last autotune
+ * result, else the built-in default: persistent loop, row-split kernel).  Errors: GS_ERR_ARG. */
+gs_status gs_get_option(const gs_ctx *ctx, int option, int *value);
 
 /* Host query: number of GPU kernels this context has enqueued so far (a replayed CUDA graph
  * counts each of its kernel nodes).  Used to report launch counts; *count must not be NULL. */
@@ -151,10 +159,13 @@ gs_status gs_graph_export_csr(gs_ctx *ctx, const gs_graph *g, int64_t *rowptr, i
 
 /* Autotuner (not in the paper; it serves throughput): times every Chebyshev-order kernel variant
  * for B columns and degree K on this graph (heat-filter applies on a synthetic block, CUDA events,
- * waits for the device) and records the fastest in the graph handle.  Later calls on the graph
- * with B columns use it while the context's GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL is 0 (automatic).
+ * waits for the device) and records the fastest in the graph handle; for B = 1 it also times a
+ * short fixed-count Sinkhorn loop in both GS_OPT_LOOP modes and records the faster.
  * *choice (may be NULL) receives the chosen variant (the GS_OPT_*_KERNEL value).
  * Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED. */
+/* Later calls on the graph use the recorded choices while the context's options are automatic
+ * (GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL 0, GS_OPT_LOOP 2); the context also keeps the last one-
+ * column choices for graphs that were never tuned (e.g. rebuilt graphs of the same workload). */
 gs_status gs_autotune(gs_ctx *ctx, gs_graph *g, int B, int K, int *choice);
 
 /* Free a graph (waits for the device). NULL is accepted. */

@@ -31,6 +31,7 @@ SIGNATURES = {
     "gs_sync": [_P],
     "gs_reserve": [_P, _I64],
     "gs_set_option": [_P, _I, _I],
+    "gs_get_option": [_P, _I, _P],
     "gs_launch_count": [_P, _P],
     "gs_cheb_coeffs": [_D, _I, _P],
     "gs_knn": [_P, _P, _I64, _I, _I, _P, _P],
@@ -169,6 +170,12 @@ GS_OPT_KNN_TENSOR = 5
 
 def gs_set_option(ctx: Context, option: int, value: int):
     _raise(ctx, _lib.gs_set_option(ctx.handle, int(option), int(value)))
+
+
+def gs_get_option(ctx: Context, option: int) -> int:
+    v = ctypes.c_int()
+    _raise(ctx, _lib.gs_get_option(ctx.handle, int(option), ctypes.byref(v)))
+    return int(v.value)
 
 
 def gs_launch_count(ctx: Context) -> int:

@@ -155,7 +155,7 @@ extern "C" gs_status gs_reserve(gs_ctx* ctx, int64_t bytes)
 extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
 {
     if (!ctx) return GS_ERR_ARG;
-    if (option == GS_OPT_LOOP && (value == 0 || value == 1)) {
+    if (option == GS_OPT_LOOP && (value >= 0 && value <= 2)) {
         ctx->loop_mode = value;
         return GS_OK;
     }
@@ -167,7 +167,7 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->knn_tensor_cores = value;
         return GS_OK;
     }
-    if (option == GS_OPT_B1_KERNEL && (value >= 0 && value <= 3 || value == 5)) {
+    if (option == GS_OPT_B1_KERNEL && (value >= 0 && value <= 3 || (value >= 5 && value <= 7))) {
         ctx->b1_kernel = value;
         return GS_OK;
     }
@@ -176,6 +176,24 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         return GS_OK;
     }
     return gs_fail(ctx, GS_ERR_ARG, "unknown option or value");
+}
+
+extern "C" gs_status gs_get_option(const gs_ctx* ctx, int option, int* value)
+{
+    if (!ctx || !value) return GS_ERR_ARG;
+    switch (option) {
+        case GS_OPT_LOOP:
+            *value = ctx->loop_mode != 2 ? ctx->loop_mode : (ctx->tuned_loop == 2 ? 1 : 0);
+            return GS_OK;
+        case GS_OPT_BARRIER_SELFTEST: *value = ctx->barrier_selftest; return GS_OK;
+        case GS_OPT_B1_KERNEL:
+            *value = ctx->b1_kernel != GS_KERNEL_AUTO ? ctx->b1_kernel
+                     : (ctx->tuned_b1 ? ctx->tuned_b1 : GS_KERNEL_SPLIT);
+            return GS_OK;
+        case GS_OPT_BLK_KERNEL: *value = ctx->blk_kernel; return GS_OK;
+        case GS_OPT_KNN_TENSOR: *value = ctx->knn_tensor_cores; return GS_OK;
+        default: return GS_ERR_ARG;
+    }
 }
 
 extern "C" gs_status gs_launch_count(const gs_ctx* ctx, int64_t* count)

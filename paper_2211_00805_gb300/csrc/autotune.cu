@@ -35,7 +35,9 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
     gs_heat_coefficients(1.0, K, c.data());
 
     std::vector<int> cands;
-    if (B == 1) cands = {GS_KERNEL_RANGED, GS_KERNEL_SELL, GS_KERNEL_VECTOR, GS_KERNEL_ASYNC};
+    if (B == 1)
+        cands = {GS_KERNEL_RANGED, GS_KERNEL_SM_RANGE, GS_KERNEL_SPLIT, GS_KERNEL_SELL,
+                 GS_KERNEL_VECTOR, GS_KERNEL_ASYNC};
     else if (B % 4 == 0 && B <= 128) cands = {GS_KERNEL_VECTOR, GS_KERNEL_STAGED, GS_KERNEL_ASYNC, GS_KERNEL_RANGED};
     else cands = {GS_KERNEL_VECTOR, GS_KERNEL_RANGED};
     int* knob = (B == 1) ? &ctx->b1_kernel : &ctx->blk_kernel;
@@ -79,6 +81,7 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
         return st;
     }
     if (B == 1) {
+        ctx->tuned_b1 = best;
         g->tuned_b1 = best;
         g->tuned_blk = saved_tblk;
         g->tuned_blk_B = saved_tB;
@@ -88,5 +91,42 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
         g->tuned_blk_B = B;
     }
     if (choice_out) *choice_out = best;
+    if (B != 1) return GS_OK;
+
+    // one column: also time the fixed-count Sinkhorn loop both ways (persistent / graph replay)
+    float* ab = nullptr;
+    if (cudaMalloc(&ab, sizeof(float) * 2 * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return GS_OK;  // keep the kernel choice; the loop stays on its default
+    }
+    fill_ones<<<(unsigned)((2 * n + 255) / 256), 256, 0, ctx->stream>>>(2 * n, ab);
+    gs_count(ctx, 1);
+    const int saved_loop = ctx->loop_mode;
+    float loop_ms[2] = {0.f, 0.f};
+    int saved_flags = 0;  // the synthetic loop's status must not reach the caller's next gs_sync
+    cudaStreamSynchronize(ctx->stream);
+    cudaMemcpy(&saved_flags, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int mode = 0; mode < 2 && st == GS_OK; ++mode) {
+        ctx->loop_mode = mode;
+        for (int rep = 0; rep < 2 && st == GS_OK; ++rep) {  // first run warms (graph capture)
+            cudaEventRecord(e0, ctx->stream);
+            st = gs_sinkhorn_impl(ctx, g, ab, ab + n, nullptr, 1.0, K, 0.0, 10, nullptr, nullptr,
+                                  nullptr, nullptr);
+            cudaEventRecord(e1, ctx->stream);
+            if (st == GS_OK) st = gs_cuda_check(ctx, cudaEventSynchronize(e1), "autotune loop timing");
+            if (st == GS_OK) cudaEventElapsedTime(&loop_ms[mode], e0, e1);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->loop_mode = saved_loop;
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ab);
+    cudaMemcpy(ctx->flags, &saved_flags, sizeof(int), cudaMemcpyHostToDevice);
+    if (st != GS_OK) return st;
+    g->tuned_loop = loop_ms[0] <= loop_ms[1] ? 1 : 2;
+    ctx->tuned_loop = g->tuned_loop;
     return GS_OK;
 }

@@ -61,7 +61,7 @@ __device__ void order_rows(const BatchProblem& p, int r0, int r1, int mode, floa
                            const float* cur, const float* prev, float* next, const float* num,
                            float* out, float* xnext, int* flags)
 {
-    if (p.sptr) {  // thread per row over the sliced ELL copy; r0 is a multiple of 32
+    if (p.sptr) {  // thread per row over the sliced ELL copy; r0 is a multiple of the slice height
         for (int row = r0 + (int)threadIdx.x; row < r1; row += blockDim.x) {
             const float pv = (mode == 0) ? 0.f : prev[row];
             const float yv = (mode == 0) ? c0 * cur[row] : p.y[row];
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) batched_sinkhorn(const BatchProblem*
         cluster.sync();  // everyone has read rank 0's slot before it is overwritten
         if (pid >= nprob) break;
         const BatchProblem& p = probs[pid];  // fields read through L1, not copied to registers
-        const int per = ((p.n + kClusterCtas - 1) / kClusterCtas + 31) / 32 * 32;  // whole slices
+        const int per = ((p.n + kClusterCtas - 1) / kClusterCtas + GS_SELL_C - 1) / GS_SELL_C * GS_SELL_C;
         const int r0 = min(p.n, rank * per), r1 = min(p.n, r0 + per);
 
         for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) p.x[r] = 1.f;  // v = 1

@@ -124,33 +124,76 @@ __global__ void __launch_bounds__(256) order_b1(const OrderArgs p)
 // One thread per row; a warp owns one 32-row slice whose entries are stored column-major, so each
 // step j reads 32 consecutive column indices and values.  Eight gathers are issued before the
 // first is used, and the row-local loads (T_{k-2}, y) go out before the gathers.
-__device__ __forceinline__ double order_sell_row(const OrderArgs& p, int64_t row, bool active)
+// Recurrence update and epilogue of one row, given the row's sum s of P T_{k-1} and its row-local
+// values (T_{k-2}, y or c_0 x).  Returns the row's share of the eps-check error.
+__device__ __forceinline__ double sell_finish(const OrderArgs& p, int64_t row, float s, float pv, float yv)
 {
     double err = 0.0;
-    if (active) {
-        const float pv = p.first ? 0.f : p.prev[row];
-        const float yv = p.first ? p.c0 * p.cur[row] : p.y[row];
-        const float s = gs_sell_row<true>(p.sptr, p.scol, p.sval, p.cur, row);
-        const float tk = p.first ? s : fmaf(2.f, s, -pv);
-        const float acc = fmaf(p.ck, tk, yv);
-        if (!p.last) {
-            p.next[row] = tk;
-            p.y[row] = acc;
-        } else {
-            const Epilogue& e = p.epi;
-            if (e.kind == EPI_STORE) {
-                e.out[row] = acc;
-            } else {  // EPI_DIVIDE
-                const float num = e.num[row];
-                const float r = safe_div(num, acc, p.flags);
-                if (e.fsave) e.fsave[row] = acc;
-                if (e.out) e.out[row] = r;
-                if (e.xnext) e.xnext[row] = e.vol ? e.vol[row] * r : r;
-                if (e.old) err = fabs((double)e.old[row] * (double)acc - (double)num);
-            }
+    const float tk = p.first ? s : fmaf(2.f, s, -pv);
+    const float acc = fmaf(p.ck, tk, yv);
+    if (!p.last) {
+        p.next[row] = tk;
+        p.y[row] = acc;
+    } else {
+        const Epilogue& e = p.epi;
+        if (e.kind == EPI_STORE) {
+            e.out[row] = acc;
+        } else {  // EPI_DIVIDE
+            const float num = e.num[row];
+            const float r = safe_div(num, acc, p.flags);
+            if (e.fsave) e.fsave[row] = acc;
+            if (e.out) e.out[row] = r;
+            if (e.xnext) e.xnext[row] = e.vol ? e.vol[row] * r : r;
+            if (e.old) err = fabs((double)e.old[row] * (double)acc - (double)num);
         }
     }
     return err;
+}
+
+__device__ __forceinline__ double order_sell_row(const OrderArgs& p, int64_t row, bool active)
+{
+    if (!active) return 0.0;
+    const float pv = p.first ? 0.f : p.prev[row];
+    const float yv = p.first ? p.c0 * p.cur[row] : p.y[row];
+    const float s = gs_sell_row<true>(p.sptr, p.scol, p.sval, p.cur, row);
+    return sell_finish(p, row, s, pv, yv);
+}
+
+// One block of 1024 threads per SM, each walking one contiguous range of rows, so that one SM's
+// gathers fall in one window of the locality order.
+__global__ void __launch_bounds__(1024) order_sell_sm_range(const OrderArgs p, int64_t rows_per_block)
+{
+    if (p.done != nullptr && *p.done) return;
+    const int64_t b0 = (int64_t)blockIdx.x * rows_per_block;
+    int64_t b1 = b0 + rows_per_block;
+    b1 = b1 < p.n ? b1 : p.n;
+    double err = 0.0;
+    for (int64_t base = b0; base < b1; base += 1024) {
+        const int64_t row = base + threadIdx.x;
+        err += order_sell_row(p, row, row < b1);
+    }
+    if (p.last && p.epi.err_partials != nullptr) block_add(err, p.epi.err_partials);
+}
+
+// T threads per row (32 / T rows per warp): phase t of a row takes entries j = t, t + T, ...
+template <int T>
+__global__ void __launch_bounds__(256) order_sell_split(const OrderArgs p)
+{
+    if (p.done != nullptr && *p.done) return;
+    constexpr int RPW = 32 / T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int phase = lane / RPW;
+    const int64_t row = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * RPW + (lane % RPW);
+    const bool active = row < p.n;
+    float pv = 0.f, yv = 0.f;
+    if (active && phase == 0) {
+        pv = p.first ? 0.f : p.prev[row];
+        yv = p.first ? p.c0 * p.cur[row] : p.y[row];
+    }
+    const float s = gs_sell_row_split<T, true>(p.sptr, p.scol, p.sval, p.cur, row, active, phase);
+    double err = 0.0;
+    if (active && phase == 0) err = sell_finish(p, row, s, pv, yv);
+    if (p.last && p.epi.err_partials != nullptr) block_add(err, p.epi.err_partials);
 }
 
 __global__ void __launch_bounds__(256) order_sell(const OrderArgs p)
@@ -729,12 +772,24 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
     gs_count(ctx, 1);
     const int TB = pl.block;
     if (pl.B == 1 && a.epi.kind != EPI_BARY_V) {
-        const int mode = ctx->b1_kernel != GS_KERNEL_AUTO ? ctx->b1_kernel : g->tuned_b1;
+        const int mode = ctx->b1_kernel != GS_KERNEL_AUTO ? ctx->b1_kernel
+                         : (g->tuned_b1 ? g->tuned_b1 : ctx->tuned_b1);
         if (mode == GS_KERNEL_ASYNC) {
             order_b1_async<<<nblocks(g->n, 256), 256, 0, ctx->stream>>>(a);
             return;
         }
-        if ((mode == GS_KERNEL_AUTO || mode == GS_KERNEL_RANGED) && a.sptr != nullptr) {
+        if ((mode == GS_KERNEL_AUTO || mode == GS_KERNEL_SPLIT) && a.sptr != nullptr) {
+            order_sell_split<GS_SPLIT_T><<<nblocks(g->n, 8 * (32 / GS_SPLIT_T)), 256, 0, ctx->stream>>>(a);
+            return;
+        }
+        if (mode == GS_KERNEL_SM_RANGE && a.sptr != nullptr) {
+            const int blocks = ctx->num_sms > 0 ? ctx->num_sms : 148;
+            int64_t rpb = (g->n + blocks - 1) / blocks;
+            rpb = (rpb + GS_SELL_C - 1) / GS_SELL_C * GS_SELL_C;
+            order_sell_sm_range<<<nblocks(g->n, (int)rpb), 1024, 0, ctx->stream>>>(a, rpb);
+            return;
+        }
+        if (mode == GS_KERNEL_RANGED && a.sptr != nullptr) {
             static const int per_sm = resident_blocks_per_sm(order_sell_ranged);
             const int64_t rpb = ranged_rows(ctx, g->n, 256, per_sm);
             order_sell_ranged<<<nblocks(g->n, (int)rpb), 256, 0, ctx->stream>>>(a, rpb);
@@ -1026,7 +1081,9 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
     };
 
     bool looped = false;
-    if (!use_eps && ctx->loop_mode == 0) {
+    const int tl = g->tuned_loop ? g->tuned_loop : ctx->tuned_loop;
+    const int loop = ctx->loop_mode != 2 ? ctx->loop_mode : (tl == 2 ? 1 : 0);
+    if (!use_eps && loop == 0) {
         // Fixed iteration count, persistent mode: the whole loop as one cooperative launch.
         std::vector<float> cf((size_t)K + 1);
         for (int k = 0; k <= K; ++k) cf[k] = (float)c[k];
@@ -1048,7 +1105,9 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
         std::vector<uintptr_t> key = {(uintptr_t)g->rowptr, (uintptr_t)g->col, (uintptr_t)g->pval,
                                       (uintptr_t)n,         (uintptr_t)K,      (uintptr_t)a,
                                       (uintptr_t)b,         (uintptr_t)vol,    (uintptr_t)u,
-                                      (uintptr_t)v,         (uintptr_t)ctx->ws, (uintptr_t)R};
+                                      (uintptr_t)v,         (uintptr_t)ctx->ws, (uintptr_t)R,
+                                      (uintptr_t)ctx->b1_kernel, (uintptr_t)g->tuned_b1,
+                                      (uintptr_t)ctx->tuned_b1};
         uint64_t tb;
         memcpy(&tb, &t, sizeof(tb));
         key.push_back((uintptr_t)tb);

@@ -10,6 +10,10 @@
 
 #include "../../include/geosink.h"
 
+// Rows per sliced-ELL slice (a slice's entries for one column index j are GS_SELL_C consecutive
+// words, one 32-byte sector).
+constexpr int GS_SELL_C = 32;
+
 // Kernel variants of the Chebyshev order (selected per context; the autotuner picks them).
 enum : int {
     GS_KERNEL_AUTO = 0,
@@ -18,7 +22,10 @@ enum : int {
     GS_KERNEL_ASYNC = 3,    // chunked CSR ranges with cp.async gathers into shared memory
     GS_KERNEL_STAGED = 4,   // B > 1: neighbour list staged in shared memory, 8-deep gathers
     GS_KERNEL_RANGED = 5,   // each block walks a contiguous row range (sliced ELL / lane groups)
+    GS_KERNEL_SPLIT = 6,    // B == 1: sliced ELL with each row split across GS_SPLIT_T threads
+    GS_KERNEL_SM_RANGE = 7, // B == 1: one 1024-thread block per SM, one contiguous row range each
 };
+constexpr int GS_SPLIT_T = 4;
 
 // Bits the kernels OR into the context's device status word; gs_sync turns them into a status.
 enum : int {
@@ -45,11 +52,13 @@ struct gs_ctx {
     size_t ws_bytes = 0;
     int num_sms = 0;
     bool capturing = false;        // inside an internal capture: launches are not counted
-    int loop_mode = 1;             // fixed-count Sinkhorn: 1 CUDA-graph replay, 0 persistent launch
+    int loop_mode = 2;             // fixed-count Sinkhorn: 0 persistent, 1 CUDA-graph replay, 2 auto
     int barrier_selftest = 0;      // next persistent launch waits for an arrival that never comes
     int b1_kernel = 0;             // GS_KERNEL_* for one column
     int blk_kernel = 0;            // GS_KERNEL_* for several columns
     int knn_tensor_cores = 1;      // kNN screen on tensor cores (3xTF32) for d >= 16
+    int tuned_b1 = 0;              // last gs_autotune result for one column (used by untuned graphs)
+    int tuned_loop = 0;            // last gs_autotune loop choice (1 persistent, 2 graph replay)
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::string err;
@@ -79,8 +88,8 @@ struct gs_graph {
     int* pcol = nullptr;
     float* ppval = nullptr;
     int levels = 0;                // breadth-first levels of the ordering sweep
-    // sliced ELL copy of the reordered P for the one-column kernels: 32-row slices, each stored
-    // column-major and padded to its longest row (padding: column = the row itself, value 0)
+    // sliced ELL copy of the reordered P for the one-column kernels: GS_SELL_C-row slices, each
+    // stored column-major and padded to its longest row (padding: column = the row itself, value 0)
     int* sptr = nullptr;           // [nslices + 1] offsets into scol / sval
     int* scol = nullptr;
     float* sval = nullptr;
@@ -90,6 +99,7 @@ struct gs_graph {
     int tuned_b1 = 0;
     int tuned_blk = 0;
     int tuned_blk_B = 0;
+    int tuned_loop = 0;            // Sinkhorn loop: 0 not tuned, 1 persistent, 2 CUDA-graph replay
 };
 
 // The CSR the filter kernels read: the reordered one when present.

@@ -128,7 +128,7 @@ __global__ void permute_fill(int64_t n, const int* __restrict__ perm, const int*
 }
 
 // Within each window of W consecutive positions, reorder nodes by decreasing degree (stable), so
-// that 32-row slices hold rows of similar length and sliced-ELL padding stays small.
+// that sliced-ELL slices hold rows of similar length and their padding stays small.
 __global__ void window_degree_sort(int64_t n, int W, const int* __restrict__ perm_in,
                                    const int* __restrict__ rowptr, int* __restrict__ perm_out)
 {
@@ -159,18 +159,18 @@ __global__ void invert_perm(int64_t n, const int* __restrict__ perm, int* __rest
     if (r < n) iperm[perm[r]] = (int)r;
 }
 
-// Sliced ELL: slice width = longest row of the slice (in entries), stored width * 32.
+// Sliced ELL: slice width = longest row of the slice (in entries), stored width * GS_SELL_C.
 __global__ void sell_width(int64_t n, int64_t nslices, const int* __restrict__ prowptr,
                            int* __restrict__ cnt)
 {
     const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (sl >= nslices) return;
     int w = 0;
-    for (int64_t r = sl * 32; r < sl * 32 + 32 && r < n; ++r) {
+    for (int64_t r = sl * GS_SELL_C; r < (sl + 1) * GS_SELL_C && r < n; ++r) {
         const int len = prowptr[r + 1] - prowptr[r];
         w = len > w ? len : w;
     }
-    cnt[sl] = w * 32;
+    cnt[sl] = w * GS_SELL_C;
 }
 
 __global__ void sell_fill(int64_t n, const int* __restrict__ prowptr, const int* __restrict__ pcol,
@@ -179,12 +179,12 @@ __global__ void sell_fill(int64_t n, const int* __restrict__ prowptr, const int*
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const int64_t sl = r >> 5, lane = r & 31;
+    const int64_t sl = r / GS_SELL_C, lane = r % GS_SELL_C;
     const int64_t base = sptr64[sl];
-    const int width = (int)((sptr64[sl + 1] - base) >> 5);
+    const int width = (int)((sptr64[sl + 1] - base) / GS_SELL_C);
     const int b = prowptr[r], len = prowptr[r + 1] - b;
     for (int j = 0; j < width; ++j) {
-        const int64_t o = base + (int64_t)j * 32 + lane;
+        const int64_t o = base + (int64_t)j * GS_SELL_C + lane;
         if (j < len) {
             scol[o] = pcol[b + j];
             sval[o] = ppval[b + j];
@@ -317,7 +317,7 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
                                               g->pcol, g->ppval);
     gs_count(ctx, 6);
     // sliced ELL of the permuted operator
-    const int64_t ns = (n + 31) / 32;
+    const int64_t ns = (n + GS_SELL_C - 1) / GS_SELL_C;
     sell_width<<<nblk(ns, 256), 256, 0, s>>>(n, ns, g->prowptr, cnt);
     gs_exclusive_scan(s, cnt, ns, p64, sums);
     int64_t tot = 0;

@@ -127,7 +127,8 @@ __device__ __forceinline__ void rows_order(const PersistArgs& p, int r0, int r1,
     }
 }
 
-// Thread-per-row variant over the sliced ELL copy (same arithmetic as the per-order kernel).
+// Thread-per-row variant over the sliced ELL copy (same arithmetic as the per-order kernel, so
+// both loop modes give identical results).
 __device__ __forceinline__ void rows_order_sell(const PersistArgs& p, int r0, int r1, int mode,
                                                 float ck, float c0, const float* cur,
                                                 const float* prev, float* next, const float* num,
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArg
     __shared__ int s_ok;
     if (threadIdx.x == 0) s_ok = 1;
     __syncthreads();
-    const int per = ((p.n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;  // whole 32-row slices
+    const int per = ((p.n + gridDim.x - 1) / gridDim.x + GS_SELL_C - 1) / GS_SELL_C * GS_SELL_C;
     const int r0 = min(p.n, (int)blockIdx.x * per), r1 = min(p.n, r0 + per);
     for (int r = r0 + threadIdx.x; r < r1; r += kThreads) p.x[r] = p.vol ? p.vol[r] : 1.f;
     if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;

@@ -1,7 +1,8 @@
-// One row of P times a block column in the sliced-ELL layout (32-row slices stored column-major,
-// padding entries have value 0), shared by the launch-per-order and the persistent kernels so both
-// sum in exactly the same order.  READONLY: the gathered vector is constant for the kernel's
-// lifetime and may use the read-only cache; otherwise ordinary coherent loads are used.
+// One row of P times a block column in the sliced-ELL layout (GS_SELL_C-row slices stored
+// column-major, padding entries have value 0), shared by the launch-per-order, persistent and
+// batched kernels so that they sum in exactly the same order.  READONLY: the gathered vector is
+// constant for the kernel's lifetime and may use the read-only cache; otherwise ordinary
+// coherent loads are used.
 #pragma once
 
 template <bool READONLY>
@@ -11,16 +12,17 @@ __device__ __forceinline__ float gs_ld(const float* p)
     return *p;
 }
 
+// Whole row by one thread.
 template <bool READONLY>
 __device__ __forceinline__ float gs_sell_row(const int* __restrict__ sptr, const int* __restrict__ scol,
                                              const float* __restrict__ sval, const float* cur,
                                              int64_t row)
 {
-    const int64_t sl = row >> 5;
+    const int64_t sl = row / GS_SELL_C;
     const int beg = __ldg(sptr + sl);
-    const int width = (__ldg(sptr + sl + 1) - beg) >> 5;
-    const int* cp = scol + beg + (row & 31);
-    const float* vp = sval + beg + (row & 31);
+    const int width = (__ldg(sptr + sl + 1) - beg) / GS_SELL_C;
+    const int* cp = scol + beg + (row % GS_SELL_C);
+    const float* vp = sval + beg + (row % GS_SELL_C);
     float s0 = 0.f, s1 = 0.f;
     int j = 0;
     for (; j + 8 <= width; j += 8) {
@@ -28,8 +30,8 @@ __device__ __forceinline__ float gs_sell_row(const int* __restrict__ sptr, const
         float w[8], x[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            c[u] = __ldg(cp + (j + u) * 32);
-            w[u] = __ldg(vp + (j + u) * 32);
+            c[u] = __ldg(cp + (j + u) * GS_SELL_C);
+            w[u] = __ldg(vp + (j + u) * GS_SELL_C);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) x[u] = gs_ld<READONLY>(cur + c[u]);
@@ -39,6 +41,48 @@ __device__ __forceinline__ float gs_sell_row(const int* __restrict__ sptr, const
             s1 = fmaf(w[u + 1], x[u + 1], s1);
         }
     }
-    for (; j < width; ++j) s0 = fmaf(__ldg(vp + j * 32), gs_ld<READONLY>(cur + __ldg(cp + j * 32)), s0);
+    for (; j < width; ++j)
+        s0 = fmaf(__ldg(vp + j * GS_SELL_C), gs_ld<READONLY>(cur + __ldg(cp + j * GS_SELL_C)), s0);
     return s0 + s1;
+}
+
+// Row split across T threads of a warp: lane = phase * (32 / T) + row-in-warp, phase t takes the
+// entries j = t, t + T, ...; the partial sums are combined with xor shuffles over the phases, so
+// every lane returns the full row sum.  All 32 lanes must call it (inactive rows pass width 0).
+template <int T, bool READONLY>
+__device__ __forceinline__ float gs_sell_row_split(const int* __restrict__ sptr,
+                                                   const int* __restrict__ scol,
+                                                   const float* __restrict__ sval, const float* cur,
+                                                   int64_t row, bool active, int phase)
+{
+    float s0 = 0.f, s1 = 0.f;
+    if (active) {
+        const int64_t sl = row / GS_SELL_C;
+        const int beg = __ldg(sptr + sl);
+        const int width = (__ldg(sptr + sl + 1) - beg) / GS_SELL_C;
+        const int* cp = scol + beg + (row % GS_SELL_C);
+        const float* vp = sval + beg + (row % GS_SELL_C);
+        int j = phase;
+        for (; j + 3 * T < width; j += 4 * T) {
+            int c[4];
+            float w[4], x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[u] = __ldg(cp + (j + u * T) * GS_SELL_C);
+                w[u] = __ldg(vp + (j + u * T) * GS_SELL_C);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = gs_ld<READONLY>(cur + c[u]);
+            s0 = fmaf(w[0], x[0], s0);
+            s1 = fmaf(w[1], x[1], s1);
+            s0 = fmaf(w[2], x[2], s0);
+            s1 = fmaf(w[3], x[3], s1);
+        }
+        for (; j < width; j += T)
+            s0 = fmaf(__ldg(vp + j * GS_SELL_C), gs_ld<READONLY>(cur + __ldg(cp + j * GS_SELL_C)), s0);
+    }
+    float s = s0 + s1;
+#pragma unroll
+    for (int off = 32 / T; off < 32; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
 }

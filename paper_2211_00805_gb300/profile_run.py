@@ -92,7 +92,7 @@ def main():
     V = torch.rand((c["n"], c["B"]), generator=torch.Generator().manual_seed(0)).to(dev)
     Y = torch.empty_like(V)
     option = gs.GS_OPT_B1_KERNEL if c["B"] == 1 else gs.GS_OPT_BLK_KERNEL
-    variants = ([0, 1, 2, 3, 5] if c["B"] == 1 else [0, 2, 3, 4, 5]) if args.sweep else [args.variant]
+    variants = ([0, 1, 2, 3, 5, 6, 7] if c["B"] == 1 else [0, 2, 3, 4, 5]) if args.sweep else [args.variant]
     byts = algorithmic_bytes(c["n"], g.nnz, c["K"], c["B"])
     for var in variants:
         gs.gs_set_option(ctx, option, var)
@@ -102,22 +102,32 @@ def main():
                           "GBps": byts / (ms / 1e3) / 1e9, "bytes_per_order": byts / c["K"]}), flush=True)
     gs.gs_set_option(ctx, option, args.variant)
     if args.sinkhorn and c["B"] == 1:
+        # loop modes x one-column kernel variants, interleaved three times, medians reported
         a = torch.full((c["n"],), 1.0 / c["n"], device=dev)
-        for mode in (0, 1):
-            gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
-            gs.gs_sinkhorn(ctx, g, a, a, c["t"], c["K"], args.sinkhorn)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            gs.gs_sinkhorn(ctx, g, a, a, c["t"], c["K"], args.sinkhorn)
-            e1.record()
-            torch.cuda.synchronize()
-            gs.gs_sync(ctx)
-            ms = e0.elapsed_time(e1)
-            print(json.dumps({"case": args.case, "sinkhorn_loop_mode": mode, "iters": args.sinkhorn,
-                              "ms": ms, "iters_per_s": args.sinkhorn / (ms / 1e3),
+        configs = [(0, 0), (1, 1), (1, 5), (1, 6), (1, 7)]
+        times = {cfg: [] for cfg in configs}
+        for rnd in range(4):
+            for mode, var in configs:
+                gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
+                gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, var)
+                gs.gs_sinkhorn(ctx, g, a, a, c["t"], c["K"], args.sinkhorn)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gs.gs_sinkhorn(ctx, g, a, a, c["t"], c["K"], args.sinkhorn)
+                e1.record()
+                torch.cuda.synchronize()
+                gs.gs_sync(ctx)
+                if rnd > 0:
+                    times[(mode, var)].append(e0.elapsed_time(e1))
+        for (mode, var), ts in times.items():
+            ms = sorted(ts)[len(ts) // 2]
+            print(json.dumps({"case": args.case, "sinkhorn_loop_mode": mode, "b1_variant": var,
+                              "iters": args.sinkhorn, "ms_median": ms,
+                              "iters_per_s": args.sinkhorn / (ms / 1e3),
                               "order_us": ms * 1e3 / (2 * c["K"] * args.sinkhorn)}), flush=True)
-
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 1)
+        gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
 
 if __name__ == "__main__":
     main()

@@ -309,14 +309,17 @@ def test_barycenter_matches_oracle(gs, ctx, m):
 
 # ------------------------------------------------------------------------- loop modes, faults
 def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph):
+    # both loop modes with the thread-per-row sliced-ELL kernel sum in the same order
     p, g, Ls = sphere_graph
     out = {}
+    gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 1)
     for mode in (0, 1):
         gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
         u, v, d, _ = gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 120)
         gs.gs_sync(ctx)
         out[mode] = (to_np(u), to_np(v), to_np(d))
-    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 0)
+    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
+    gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
     np.testing.assert_array_equal(out[0][2], out[1][2])
@@ -334,7 +337,7 @@ def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sp
     _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 50)
 
 
-@pytest.mark.parametrize("B,option,variant", [(1, 3, 1), (1, 3, 2), (1, 3, 3), (1, 3, 5), (32, 4, 2),
+@pytest.mark.parametrize("B,option,variant", [(1, 3, 1), (1, 3, 2), (1, 3, 3), (1, 3, 5), (1, 3, 6), (1, 3, 7), (32, 4, 2),
                                               (32, 4, 3), (32, 4, 4), (32, 4, 5), (64, 4, 3),
                                               (8, 4, 3), (128, 4, 3), (12, 4, 5), (3, 4, 5)])
 def test_kernel_variants_match_oracle(gs, ctx, B, option, variant):
