@@ -163,6 +163,10 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->barrier_selftest = value;
         return GS_OK;
     }
+    if (option == GS_OPT_PERSIST_SMEM_GRAPH && (value == 0 || value == 1)) {
+        ctx->persist_smem_graph = value;
+        return GS_OK;
+    }
     if (option == GS_OPT_KNN_TENSOR && (value == 0 || value == 1)) {
         ctx->knn_tensor_cores = value;
         return GS_OK;
@@ -192,6 +196,7 @@ extern "C" gs_status gs_get_option(const gs_ctx* ctx, int option, int* value)
             return GS_OK;
         case GS_OPT_BLK_KERNEL: *value = ctx->blk_kernel; return GS_OK;
         case GS_OPT_KNN_TENSOR: *value = ctx->knn_tensor_cores; return GS_OK;
+        case GS_OPT_PERSIST_SMEM_GRAPH: *value = ctx->persist_smem_graph; return GS_OK;
         default: return GS_ERR_ARG;
     }
 }

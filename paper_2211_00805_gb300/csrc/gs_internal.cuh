@@ -59,6 +59,7 @@ struct gs_ctx {
     int knn_tensor_cores = 1;      // kNN screen on tensor cores (3xTF32) for d >= 16
     int tuned_b1 = 0;              // last gs_autotune result for one column (used by untuned graphs)
     int tuned_loop = 0;            // last gs_autotune loop choice (1 persistent, 2 graph replay)
+    int persist_smem_graph = 1;    // persistent loop keeps each block's graph slice in shared memory
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::string err;
@@ -100,6 +101,8 @@ struct gs_graph {
     int tuned_blk = 0;
     int tuned_blk_B = 0;
     int tuned_loop = 0;            // Sinkhorn loop: 0 not tuned, 1 persistent, 2 CUDA-graph replay
+    std::vector<int> sptr_host;    // host copy of the slice offsets (sizes the persistent kernel's
+                                   // shared-memory graph slices)
 };
 
 // The CSR the filter kernels read: the reordered one when present.

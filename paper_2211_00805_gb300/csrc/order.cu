@@ -336,5 +336,7 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
     rowptr_narrow<<<nblk(ns + 1, 256), 256, 0, s>>>(ns + 1, p64, g->sptr);
     sell_fill<<<nblk(n, 256), 256, 0, s>>>(n, g->prowptr, g->pcol, g->ppval, p64, g->scol, g->sval);
     gs_count(ctx, 6);
+    g->sptr_host.resize((size_t)ns + 1);
+    cudaMemcpyAsync(g->sptr_host.data(), g->sptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost, s);
     return gs_cuda_check(ctx, cudaStreamSynchronize(s), "graph permutation");
 }

@@ -51,6 +51,8 @@ struct PersistArgs {
     int* flags;
     unsigned expect;     // arrivals that release a barrier (gridDim.x; one more in the self-test)
     long long budget;    // clock cycles a block waits at a barrier before giving up
+    int rows_per_block;  // whole slices
+    int smem_graph;      // 1: each block's slices of the sliced ELL are copied to shared memory once
 };
 
 // Returns false when the wait ran out (the caller leaves the loop).  Arrival is a relaxed atomic
@@ -156,23 +158,126 @@ __device__ __forceinline__ void rows_order_sell(const PersistArgs& p, int r0, in
     }
 }
 
+// Same rows and arithmetic with the block's sliced-ELL entries resident in shared memory
+// (scol_s / sval_s hold entries [e0, e0 + count) of the global arrays).
+__device__ __forceinline__ void rows_order_sell_smem(const PersistArgs& p, int r0, int r1, int mode,
+                                                     float ck, float c0, const float* cur,
+                                                     const float* prev, float* next,
+                                                     const float* num, float* out, float* xnext,
+                                                     const int* scol_s, const float* sval_s, int e0)
+{
+    for (int row = r0 + (int)threadIdx.x; row < r1; row += kThreads) {
+        const float pv = (mode == 0) ? 0.f : prev[row];
+        const float yv = (mode == 0) ? c0 * cur[row] : p.y[row];
+        const int sl = row / GS_SELL_C;
+        const int beg = __ldg(p.sptr + sl);
+        const int width = (__ldg(p.sptr + sl + 1) - beg) / GS_SELL_C;
+        const int off = beg - e0 + row % GS_SELL_C;
+        const float s = gs_sell_dot<false, false>(scol_s + off, sval_s + off, width, cur);
+        const float tk = (mode == 0) ? s : fmaf(2.f, s, -pv);
+        const float acc = fmaf(ck, tk, yv);
+        if (mode != 2) {
+            next[row] = tk;
+            p.y[row] = acc;
+        } else {
+            const float m = num[row];
+            float r = 0.f;
+            if (m != 0.f) {
+                r = m / acc;
+                if (!(r > 0.f) || isinf(r)) atomicOr(p.flags, GS_FLAG_NONFINITE);
+            }
+            out[row] = r;
+            xnext[row] = p.vol ? p.vol[row] * r : r;
+        }
+    }
+}
+
 template <int G>
 __device__ __forceinline__ void rows_any(const PersistArgs& p, int r0, int r1, int mode, float ck,
                                          float c0, const float* cur, const float* prev, float* next,
-                                         const float* num, float* out, float* xnext)
+                                         const float* num, float* out, float* xnext,
+                                         const int* scol_s = nullptr, const float* sval_s = nullptr,
+                                         int e0 = 0)
 {
-    if (p.sptr) rows_order_sell(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext);
+    if (scol_s) rows_order_sell_smem(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext, scol_s, sval_s, e0);
+    else if (p.sptr) rows_order_sell(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext);
     else rows_order<G>(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext);
+}
+
+// Bulk (TMA) copy of `bytes` from global to this CTA's shared memory, completing on `mbar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* mbar)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+        "l"(src), "r"(bytes), "r"(m)
+        : "memory");
+}
+
+// Load this block's sliced-ELL entries into shared memory with two bulk copies tracked by one
+// mbarrier transaction count.  The wait is bounded; false = it ran out (GS_FLAG_TIMEOUT set).
+__device__ bool load_graph_slices(const PersistArgs& p, int r0, int r1, int* scol_s, float* sval_s,
+                                  int* e0_out, unsigned long long* mbar)
+{
+    const int s0 = r0 / GS_SELL_C;
+    const int s1 = (r1 + GS_SELL_C - 1) / GS_SELL_C;
+    const int e0 = __ldg(p.sptr + s0);
+    const int e1 = (r1 > r0) ? __ldg(p.sptr + s1) : e0;
+    *e0_out = e0;
+    const unsigned bytes = (unsigned)(e1 - e0) * 4u;  // a multiple of 128: slices are 32 x 4 bytes wide
+    if (bytes == 0) return true;
+    const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(m) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(m), "r"(2u * bytes)
+                     : "memory");
+        bulk_g2s(scol_s, p.scol + e0, bytes, mbar);
+        bulk_g2s(sval_s, p.sval + e0, bytes, mbar);
+    }
+    const long long t0 = clock64();
+    unsigned done = 0;
+    while (!done) {
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\n"
+            " selp.u32 %0, 1, 0, P;\n}\n"
+            : "=r"(done)
+            : "r"(m)
+            : "memory");
+        if (!done && clock64() - t0 > p.budget) {
+            atomicOr(p.flags, GS_FLAG_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
 }
 
 template <int G>
 __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArgs p)
 {
     __shared__ int s_ok;
+    __shared__ __align__(8) unsigned long long s_mbar;
+    extern __shared__ __align__(128) unsigned char p_smem[];
     if (threadIdx.x == 0) s_ok = 1;
     __syncthreads();
-    const int per = ((p.n + gridDim.x - 1) / gridDim.x + GS_SELL_C - 1) / GS_SELL_C * GS_SELL_C;
+    const int per = p.rows_per_block;
     const int r0 = min(p.n, (int)blockIdx.x * per), r1 = min(p.n, r0 + per);
+    int e0 = 0;
+    int* scol_s = nullptr;
+    float* sval_s = nullptr;
+    if (p.smem_graph) {
+        const int cap = (__ldg(p.sptr + min((r0 + per + GS_SELL_C - 1) / GS_SELL_C, (p.n + GS_SELL_C - 1) / GS_SELL_C)) -
+                         __ldg(p.sptr + r0 / GS_SELL_C));
+        scol_s = reinterpret_cast<int*>(p_smem);
+        sval_s = reinterpret_cast<float*>(p_smem + (size_t)((cap + 31) / 32 * 32) * 4);
+        if (!load_graph_slices(p, r0, r1, scol_s, sval_s, &e0, &s_mbar)) s_ok = 0;
+        __syncthreads();
+        if (!s_ok) return;
+    }
     for (int r = r0 + threadIdx.x; r < r1; r += kThreads) p.x[r] = p.vol ? p.vol[r] : 1.f;
     if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
     float* X = p.x;
@@ -183,22 +288,22 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArg
             const float* num = h == 0 ? p.a : p.b;
             float* out = h == 0 ? p.u : p.v;
             if (p.K == 1) {
-                rows_any<G>(p, r0, r1, 2, p.coef[1], c0, X, nullptr, nullptr, num, out, Ab);
+                rows_any<G>(p, r0, r1, 2, p.coef[1], c0, X, nullptr, nullptr, num, out, Ab, scol_s, sval_s, e0);
                 if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                 float* t = X; X = Ab; Ab = t;
                 continue;
             }
-            rows_any<G>(p, r0, r1, 0, p.coef[1], c0, X, nullptr, Ab, nullptr, nullptr, nullptr);
+            rows_any<G>(p, r0, r1, 0, p.coef[1], c0, X, nullptr, Ab, nullptr, nullptr, nullptr, scol_s, sval_s, e0);
             if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
             float* prev = X;
             float* cur = Ab;
             for (int k = 2; k <= p.K; ++k) {
                 if (k < p.K) {
-                    rows_any<G>(p, r0, r1, 1, p.coef[k], 0.f, cur, prev, prev, nullptr, nullptr, nullptr);
+                    rows_any<G>(p, r0, r1, 1, p.coef[k], 0.f, cur, prev, prev, nullptr, nullptr, nullptr, scol_s, sval_s, e0);
                     if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                     float* t = prev; prev = cur; cur = t;
                 } else {
-                    rows_any<G>(p, r0, r1, 2, p.coef[k], 0.f, cur, prev, nullptr, num, out, prev);
+                    rows_any<G>(p, r0, r1, 2, p.coef[k], 0.f, cur, prev, nullptr, num, out, prev, scol_s, sval_s, e0);
                     if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                     X = prev;
                     Ab = cur;
@@ -208,22 +313,43 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArg
     }
 }
 
+constexpr int kSmemGraphMax = 200 * 1024;  // shared-memory budget for the resident graph slice
+
 template <int G>
-gs_status launch_persistent(gs_ctx* ctx, PersistArgs& args)
+gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
 {
+    const int blocks = ctx->num_sms;  // one block of kThreads per SM
+    args.rows_per_block = (int)(((g->n + blocks - 1) / blocks + GS_SELL_C - 1) / GS_SELL_C * GS_SELL_C);
+    // largest per-block entry range of the sliced ELL (host copy of its slice offsets)
+    size_t smem = 0;
+    args.smem_graph = 0;
+    if (g->sptr && !g->sptr_host.empty() && ctx->persist_smem_graph) {
+        const int64_t ns = g->nslices;
+        int64_t worst = 0;
+        for (int b = 0; b < blocks; ++b) {
+            const int64_t s0 = std::min<int64_t>(ns, (int64_t)b * args.rows_per_block / GS_SELL_C);
+            const int64_t s1 = std::min<int64_t>(ns, ((int64_t)(b + 1) * args.rows_per_block + GS_SELL_C - 1) / GS_SELL_C);
+            worst = std::max<int64_t>(worst, (int64_t)g->sptr_host[s1] - g->sptr_host[s0]);
+        }
+        const size_t need = 2 * (size_t)((worst + 31) / 32 * 32) * 4;
+        if (need > 0 && need <= (size_t)kSmemGraphMax) {
+            smem = need;
+            args.smem_graph = 1;
+        }
+    }
+    if (smem) cudaFuncSetAttribute(sinkhorn_persistent<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sinkhorn_persistent<G>, kThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sinkhorn_persistent<G>, kThreads, smem) !=
             cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return GS_ERR_UNSUPPORTED;
     }
-    const int blocks = ctx->num_sms;  // one block of kThreads per SM
     args.expect = (unsigned)blocks + (ctx->barrier_selftest ? 1u : 0u);
     args.budget = ctx->barrier_selftest ? kSelfTestBudget : kBarrierBudget;
     ctx->barrier_selftest = 0;
     void* params[] = {&args};
     cudaError_t e = cudaLaunchCooperativeKernel((void*)sinkhorn_persistent<G>, dim3(blocks),
-                                                dim3(kThreads), params, 0, ctx->stream);
+                                                dim3(kThreads), params, smem, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return GS_ERR_UNSUPPORTED;
@@ -268,8 +394,8 @@ gs_status gs_sinkhorn_persistent(gs_ctx* ctx, const gs_graph* g, const float* a,
     args.flags = ctx->flags;
     cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), ctx->stream);
     const float m = g->mean_row;
-    if (m <= 6.f) return launch_persistent<4>(ctx, args);
-    if (m <= 14.f) return launch_persistent<8>(ctx, args);
-    if (m <= 28.f) return launch_persistent<16>(ctx, args);
-    return launch_persistent<32>(ctx, args);
+    if (m <= 6.f) return launch_persistent<4>(ctx, g, args);
+    if (m <= 14.f) return launch_persistent<8>(ctx, g, args);
+    if (m <= 28.f) return launch_persistent<16>(ctx, g, args);
+    return launch_persistent<32>(ctx, g, args);
 }

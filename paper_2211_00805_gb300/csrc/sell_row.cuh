@@ -12,17 +12,12 @@ __device__ __forceinline__ float gs_ld(const float* p)
     return *p;
 }
 
-// Whole row by one thread.
-template <bool READONLY>
-__device__ __forceinline__ float gs_sell_row(const int* __restrict__ sptr, const int* __restrict__ scol,
-                                             const float* __restrict__ sval, const float* cur,
-                                             int64_t row)
+// Dot product of one sliced-ELL row: cp / vp point at the row's first column index / value,
+// successive entries GS_SELL_C words apart.  GLOBAL_GRAPH: cp / vp are in global memory (read-only
+// path); otherwise they are in shared memory.
+template <bool READONLY, bool GLOBAL_GRAPH>
+__device__ __forceinline__ float gs_sell_dot(const int* cp, const float* vp, int width, const float* cur)
 {
-    const int64_t sl = row / GS_SELL_C;
-    const int beg = __ldg(sptr + sl);
-    const int width = (__ldg(sptr + sl + 1) - beg) / GS_SELL_C;
-    const int* cp = scol + beg + (row % GS_SELL_C);
-    const float* vp = sval + beg + (row % GS_SELL_C);
     float s0 = 0.f, s1 = 0.f;
     int j = 0;
     for (; j + 8 <= width; j += 8) {
@@ -30,8 +25,8 @@ __device__ __forceinline__ float gs_sell_row(const int* __restrict__ sptr, const
         float w[8], x[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            c[u] = __ldg(cp + (j + u) * GS_SELL_C);
-            w[u] = __ldg(vp + (j + u) * GS_SELL_C);
+            c[u] = GLOBAL_GRAPH ? __ldg(cp + (j + u) * GS_SELL_C) : cp[(j + u) * GS_SELL_C];
+            w[u] = GLOBAL_GRAPH ? __ldg(vp + (j + u) * GS_SELL_C) : vp[(j + u) * GS_SELL_C];
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) x[u] = gs_ld<READONLY>(cur + c[u]);
@@ -41,9 +36,25 @@ __device__ __forceinline__ float gs_sell_row(const int* __restrict__ sptr, const
             s1 = fmaf(w[u + 1], x[u + 1], s1);
         }
     }
-    for (; j < width; ++j)
-        s0 = fmaf(__ldg(vp + j * GS_SELL_C), gs_ld<READONLY>(cur + __ldg(cp + j * GS_SELL_C)), s0);
+    for (; j < width; ++j) {
+        const int c = GLOBAL_GRAPH ? __ldg(cp + j * GS_SELL_C) : cp[j * GS_SELL_C];
+        const float w = GLOBAL_GRAPH ? __ldg(vp + j * GS_SELL_C) : vp[j * GS_SELL_C];
+        s0 = fmaf(w, gs_ld<READONLY>(cur + c), s0);
+    }
     return s0 + s1;
+}
+
+// Whole row by one thread, graph read from global memory.
+template <bool READONLY>
+__device__ __forceinline__ float gs_sell_row(const int* __restrict__ sptr, const int* __restrict__ scol,
+                                             const float* __restrict__ sval, const float* cur,
+                                             int64_t row)
+{
+    const int64_t sl = row / GS_SELL_C;
+    const int beg = __ldg(sptr + sl);
+    const int width = (__ldg(sptr + sl + 1) - beg) / GS_SELL_C;
+    return gs_sell_dot<READONLY, true>(scol + beg + (row % GS_SELL_C), sval + beg + (row % GS_SELL_C),
+                                       width, cur);
 }
 
 // Row split across T threads of a warp: lane = phase * (32 / T) + row-in-warp, phase t takes the

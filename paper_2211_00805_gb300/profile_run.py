@@ -104,12 +104,13 @@ def main():
     if args.sinkhorn and c["B"] == 1:
         # loop modes x one-column kernel variants, interleaved three times, medians reported
         a = torch.full((c["n"],), 1.0 / c["n"], device=dev)
-        configs = [(0, 0), (1, 1), (1, 5), (1, 6), (1, 7)]
+        configs = [(0, 0, 1), (0, 0, 0), (1, 1, 1), (1, 6, 1)]  # (loop mode, kernel, smem graph)
         times = {cfg: [] for cfg in configs}
         for rnd in range(4):
-            for mode, var in configs:
+            for mode, var, sg in configs:
                 gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
                 gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, var)
+                gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, sg)
                 gs.gs_sinkhorn(ctx, g, a, a, c["t"], c["K"], args.sinkhorn)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -119,15 +120,17 @@ def main():
                 torch.cuda.synchronize()
                 gs.gs_sync(ctx)
                 if rnd > 0:
-                    times[(mode, var)].append(e0.elapsed_time(e1))
-        for (mode, var), ts in times.items():
+                    times[(mode, var, sg)].append(e0.elapsed_time(e1))
+        for (mode, var, sg), ts in times.items():
             ms = sorted(ts)[len(ts) // 2]
             print(json.dumps({"case": args.case, "sinkhorn_loop_mode": mode, "b1_variant": var,
+                              "smem_graph": sg,
                               "iters": args.sinkhorn, "ms_median": ms,
                               "iters_per_s": args.sinkhorn / (ms / 1e3),
                               "order_us": ms * 1e3 / (2 * c["K"] * args.sinkhorn)}), flush=True)
-        gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 1)
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
         gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
+        gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 1)
 
 if __name__ == "__main__":
     main()
