@@ -99,9 +99,12 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * recurrence; they differ in summation order only. */
 /* GS_OPT_KNN_TENSOR: 1 (default) screens kNN distances with tensor-core 3xTF32 dot products when
  * d >= 16, 0 always uses FP32 CUDA-core dot products; the FP64 rerank makes both exact. */
-/* GS_OPT_PERSIST_SMEM_GRAPH: 1 (default) the persistent loop copies each block's slices of the
- * operator into shared memory once (bulk copies) when they fit in 200 KB, 0 reads them from global
- * memory every order.  Same arithmetic either way. */
+/* GS_OPT_PERSIST_SMEM_GRAPH: how the persistent loop reads the operator.  2 (default): each
+ * block's slices (values and 16-bit local column indices) are copied into shared memory once, and
+ * every order first copies the block's distinct neighbour values into a shared-memory cache;
+ * 1: slices in shared memory, neighbour values gathered from global memory; 0: everything from
+ * global memory.  Each mode falls back to the next lower one when its tables do not fit in 200 KB
+ * of shared memory.  Same arithmetic in every mode. */
 enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
        GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);

@@ -163,7 +163,7 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->barrier_selftest = value;
         return GS_OK;
     }
-    if (option == GS_OPT_PERSIST_SMEM_GRAPH && (value == 0 || value == 1)) {
+    if (option == GS_OPT_PERSIST_SMEM_GRAPH && (value >= 0 && value <= 2)) {
         ctx->persist_smem_graph = value;
         return GS_OK;
     }
@@ -300,6 +300,9 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g)
     cudaFree(g->sptr);
     cudaFree(g->scol);
     cudaFree(g->sval);
+    cudaFree(g->xc_ucol);
+    cudaFree(g->xc_ucnt);
+    cudaFree(g->xc_lidx);
     delete g;
     return GS_OK;
 }

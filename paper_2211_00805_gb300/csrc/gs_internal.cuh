@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -59,7 +60,8 @@ struct gs_ctx {
     int knn_tensor_cores = 1;      // kNN screen on tensor cores (3xTF32) for d >= 16
     int tuned_b1 = 0;              // last gs_autotune result for one column (used by untuned graphs)
     int tuned_loop = 0;            // last gs_autotune loop choice (1 persistent, 2 graph replay)
-    int persist_smem_graph = 1;    // persistent loop keeps each block's graph slice in shared memory
+    int persist_smem_graph = 2;    // persistent loop: 0 graph from global memory, 1 graph slices in
+                                   // shared memory, 2 slices plus the per-block gather cache
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::string err;
@@ -103,6 +105,15 @@ struct gs_graph {
     int tuned_loop = 0;            // Sinkhorn loop: 0 not tuned, 1 persistent, 2 CUDA-graph replay
     std::vector<int> sptr_host;    // host copy of the slice offsets (sizes the persistent kernel's
                                    // shared-memory graph slices)
+    // per-block gather cache of the persistent loop (xcache.cu): for the partition into xc_blocks
+    // blocks of xc_rpb rows, block b's distinct columns (sorted) at xc_ucol[entry offset of b],
+    // their count xc_ucnt[b], and every entry's 16-bit index into that list
+    bool xc_ok = false;
+    int xc_blocks = 0, xc_rpb = 0, xc_max_e = 0, xc_max_u = 0;
+    int* xc_ucol = nullptr;
+    int* xc_ucnt = nullptr;
+    uint16_t* xc_lidx = nullptr;
+    std::vector<int> xc_ucnt_host;
 };
 
 // The CSR the filter kernels read: the reordered one when present.
@@ -152,6 +163,13 @@ gs_status gs_graph_export(gs_ctx* ctx, const gs_graph* g, int64_t* rowptr, int32
 
 // --------------------------------------------------------------------- order.cu
 gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g);
+gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, int rpb);
+// rows per block of the persistent loop's partition (one block per SM, whole slices)
+static inline int gs_persist_rows_per_block(const gs_ctx* ctx, int64_t n)
+{
+    const int blocks = ctx->num_sms > 0 ? ctx->num_sms : 148;
+    return (int)(((n + blocks - 1) / blocks + GS_SELL_C - 1) / GS_SELL_C * GS_SELL_C);
+}
 // dst[r, :] = src[perm[r], :] (to the filter's order) or dst[perm[r], :] = src[r, :] (back)
 void gs_permute_rows(gs_ctx* ctx, int64_t n, int B, const int* perm, const float* src, float* dst,
                      bool to_filter_order);

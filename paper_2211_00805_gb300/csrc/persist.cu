@@ -53,6 +53,12 @@ struct PersistArgs {
     long long budget;    // clock cycles a block waits at a barrier before giving up
     int rows_per_block;  // whole slices
     int smem_graph;      // 1: each block's slices of the sliced ELL are copied to shared memory once
+                         // 2: values + 16-bit local column indices + the per-block gather cache
+    const int* xc_ucol;  // gather cache tables (smem_graph == 2)
+    const int* xc_ucnt;
+    const uint16_t* xc_lidx;
+    int xc_max_e;
+    int xc_max_u;
 };
 
 // Returns false when the wait ran out (the caller leaves the loop).  Arrival is a relaxed atomic
@@ -192,14 +198,54 @@ __device__ __forceinline__ void rows_order_sell_smem(const PersistArgs& p, int r
     }
 }
 
+// Rows with values and local column indices in shared memory and the neighbour values in the
+// block's gather cache xc (filled from cur at the start of the order).
+__device__ __forceinline__ void rows_order_cached(const PersistArgs& p, int r0, int r1, int mode,
+                                                  float ck, float c0, const float* cur,
+                                                  const float* prev, float* next, const float* num,
+                                                  float* out, float* xnext, const uint16_t* lidx_s,
+                                                  const float* sval_s, const float* xc, int e0)
+{
+    for (int row = r0 + (int)threadIdx.x; row < r1; row += kThreads) {
+        const float pv = (mode == 0) ? 0.f : prev[row];
+        const float yv = (mode == 0) ? c0 * cur[row] : p.y[row];
+        const int sl = row / GS_SELL_C;
+        const int beg = __ldg(p.sptr + sl);
+        const int width = (__ldg(p.sptr + sl + 1) - beg) / GS_SELL_C;
+        const int off = beg - e0 + row % GS_SELL_C;
+        const float s = gs_sell_dot_cached(lidx_s + off, sval_s + off, width, xc);
+        const float tk = (mode == 0) ? s : fmaf(2.f, s, -pv);
+        const float acc = fmaf(ck, tk, yv);
+        if (mode != 2) {
+            next[row] = tk;
+            p.y[row] = acc;
+        } else {
+            const float m = num[row];
+            float r = 0.f;
+            if (m != 0.f) {
+                r = m / acc;
+                if (!(r > 0.f) || isinf(r)) atomicOr(p.flags, GS_FLAG_NONFINITE);
+            }
+            out[row] = r;
+            xnext[row] = p.vol ? p.vol[row] * r : r;
+        }
+    }
+}
+
 template <int G>
 __device__ __forceinline__ void rows_any(const PersistArgs& p, int r0, int r1, int mode, float ck,
                                          float c0, const float* cur, const float* prev, float* next,
                                          const float* num, float* out, float* xnext,
                                          const int* scol_s = nullptr, const float* sval_s = nullptr,
-                                         int e0 = 0)
+                                         int e0 = 0, const uint16_t* lidx_s = nullptr,
+                                         const int* ucol_s = nullptr, float* xc = nullptr, int ucnt = 0)
 {
-    if (scol_s) rows_order_sell_smem(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext, scol_s, sval_s, e0);
+    if (lidx_s) {
+        // stage the block's gather cache from T_{k-1}, then the rows read it from shared memory
+        for (int i = threadIdx.x; i < ucnt; i += kThreads) xc[i] = cur[ucol_s[i]];
+        __syncthreads();
+        rows_order_cached(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext, lidx_s, sval_s, xc, e0);
+    } else if (scol_s) rows_order_sell_smem(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext, scol_s, sval_s, e0);
     else if (p.sptr) rows_order_sell(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext);
     else rows_order<G>(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext);
 }
@@ -213,6 +259,53 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
         "l"(src), "r"(bytes), "r"(m)
         : "memory");
+}
+
+// Mode 2: values, local column indices and the distinct-column list of this block into shared
+// memory with three bulk copies on one mbarrier (bounded wait).
+__device__ bool load_cached_slices(const PersistArgs& p, int r0, int r1, float* sval_s,
+                                   uint16_t* lidx_s, int* ucol_s, int* e0_out, int* ucnt_out,
+                                   unsigned long long* mbar)
+{
+    const int s0 = r0 / GS_SELL_C;
+    const int s1 = (r1 + GS_SELL_C - 1) / GS_SELL_C;
+    const int e0 = __ldg(p.sptr + s0);
+    const int e1 = (r1 > r0) ? __ldg(p.sptr + s1) : e0;
+    const int uc = (r1 > r0) ? __ldg(p.xc_ucnt + blockIdx.x) : 0;
+    *e0_out = e0;
+    *ucnt_out = uc;
+    const unsigned E = (unsigned)(e1 - e0);
+    if (E == 0) return true;
+    const unsigned bv = E * 4u, bl = E * 2u;            // E is a multiple of 32: both multiples of 16
+    const unsigned bu = ((unsigned)uc * 4u + 15u) & ~15u;  // <= E * 4 (the list lives in [e0, e1))
+    const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(m) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(m), "r"(bv + bl + bu)
+                     : "memory");
+        bulk_g2s(sval_s, p.sval + e0, bv, mbar);
+        bulk_g2s(lidx_s, p.xc_lidx + e0, bl, mbar);
+        if (bu) bulk_g2s(ucol_s, p.xc_ucol + e0, bu, mbar);
+    }
+    const long long t0 = clock64();
+    unsigned done = 0;
+    while (!done) {
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\n"
+            " selp.u32 %0, 1, 0, P;\n}\n"
+            : "=r"(done)
+            : "r"(m)
+            : "memory");
+        if (!done && clock64() - t0 > p.budget) {
+            atomicOr(p.flags, GS_FLAG_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
 }
 
 // Load this block's sliced-ELL entries into shared memory with two bulk copies tracked by one
@@ -266,10 +359,22 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArg
     __syncthreads();
     const int per = p.rows_per_block;
     const int r0 = min(p.n, (int)blockIdx.x * per), r1 = min(p.n, r0 + per);
-    int e0 = 0;
+    int e0 = 0, ucnt = 0;
     int* scol_s = nullptr;
     float* sval_s = nullptr;
-    if (p.smem_graph) {
+    uint16_t* lidx_s = nullptr;
+    int* ucol_s = nullptr;
+    float* xc = nullptr;
+    if (p.smem_graph == 2) {
+        const int emax = (p.xc_max_e + 31) / 32 * 32, umax = (p.xc_max_u + 31) / 32 * 32;
+        sval_s = reinterpret_cast<float*>(p_smem);
+        lidx_s = reinterpret_cast<uint16_t*>(p_smem + (size_t)emax * 4);
+        ucol_s = reinterpret_cast<int*>(p_smem + (size_t)emax * 6);
+        xc = reinterpret_cast<float*>(p_smem + (size_t)emax * 6 + (size_t)umax * 4);
+        if (!load_cached_slices(p, r0, r1, sval_s, lidx_s, ucol_s, &e0, &ucnt, &s_mbar)) s_ok = 0;
+        __syncthreads();
+        if (!s_ok) return;
+    } else if (p.smem_graph) {
         const int cap = (__ldg(p.sptr + min((r0 + per + GS_SELL_C - 1) / GS_SELL_C, (p.n + GS_SELL_C - 1) / GS_SELL_C)) -
                          __ldg(p.sptr + r0 / GS_SELL_C));
         scol_s = reinterpret_cast<int*>(p_smem);
@@ -288,22 +393,22 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArg
             const float* num = h == 0 ? p.a : p.b;
             float* out = h == 0 ? p.u : p.v;
             if (p.K == 1) {
-                rows_any<G>(p, r0, r1, 2, p.coef[1], c0, X, nullptr, nullptr, num, out, Ab, scol_s, sval_s, e0);
+                rows_any<G>(p, r0, r1, 2, p.coef[1], c0, X, nullptr, nullptr, num, out, Ab, scol_s, sval_s, e0, lidx_s, ucol_s, xc, ucnt);
                 if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                 float* t = X; X = Ab; Ab = t;
                 continue;
             }
-            rows_any<G>(p, r0, r1, 0, p.coef[1], c0, X, nullptr, Ab, nullptr, nullptr, nullptr, scol_s, sval_s, e0);
+            rows_any<G>(p, r0, r1, 0, p.coef[1], c0, X, nullptr, Ab, nullptr, nullptr, nullptr, scol_s, sval_s, e0, lidx_s, ucol_s, xc, ucnt);
             if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
             float* prev = X;
             float* cur = Ab;
             for (int k = 2; k <= p.K; ++k) {
                 if (k < p.K) {
-                    rows_any<G>(p, r0, r1, 1, p.coef[k], 0.f, cur, prev, prev, nullptr, nullptr, nullptr, scol_s, sval_s, e0);
+                    rows_any<G>(p, r0, r1, 1, p.coef[k], 0.f, cur, prev, prev, nullptr, nullptr, nullptr, scol_s, sval_s, e0, lidx_s, ucol_s, xc, ucnt);
                     if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                     float* t = prev; prev = cur; cur = t;
                 } else {
-                    rows_any<G>(p, r0, r1, 2, p.coef[k], 0.f, cur, prev, nullptr, num, out, prev, scol_s, sval_s, e0);
+                    rows_any<G>(p, r0, r1, 2, p.coef[k], 0.f, cur, prev, nullptr, num, out, prev, scol_s, sval_s, e0, lidx_s, ucol_s, xc, ucnt);
                     if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                     X = prev;
                     Ab = cur;
@@ -319,11 +424,25 @@ template <int G>
 gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
 {
     const int blocks = ctx->num_sms;  // one block of kThreads per SM
-    args.rows_per_block = (int)(((g->n + blocks - 1) / blocks + GS_SELL_C - 1) / GS_SELL_C * GS_SELL_C);
+    args.rows_per_block = gs_persist_rows_per_block(ctx, g->n);
     // largest per-block entry range of the sliced ELL (host copy of its slice offsets)
     size_t smem = 0;
     args.smem_graph = 0;
-    if (g->sptr && !g->sptr_host.empty() && ctx->persist_smem_graph) {
+    args.xc_ucol = g->xc_ucol;
+    args.xc_ucnt = g->xc_ucnt;
+    args.xc_lidx = g->xc_lidx;
+    args.xc_max_e = g->xc_max_e;
+    args.xc_max_u = g->xc_max_u;
+    if (ctx->persist_smem_graph == 2 && g->xc_ok && g->xc_blocks == blocks &&
+        g->xc_rpb == args.rows_per_block) {
+        const size_t emax = (size_t)(g->xc_max_e + 31) / 32 * 32, umax = (size_t)(g->xc_max_u + 31) / 32 * 32;
+        const size_t need = emax * 6 + umax * 8;
+        if (need <= (size_t)kSmemGraphMax) {
+            smem = need;
+            args.smem_graph = 2;
+        }
+    }
+    if (!args.smem_graph && g->sptr && !g->sptr_host.empty() && ctx->persist_smem_graph) {
         const int64_t ns = g->nslices;
         int64_t worst = 0;
         for (int b = 0; b < blocks; ++b) {

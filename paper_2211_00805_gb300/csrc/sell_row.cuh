@@ -4,6 +4,7 @@
 // constant for the kernel's lifetime and may use the read-only cache; otherwise ordinary
 // coherent loads are used.
 #pragma once
+#include <stdint.h>
 
 template <bool READONLY>
 __device__ __forceinline__ float gs_ld(const float* p)
@@ -41,6 +42,30 @@ __device__ __forceinline__ float gs_sell_dot(const int* cp, const float* vp, int
         const float w = GLOBAL_GRAPH ? __ldg(vp + j * GS_SELL_C) : vp[j * GS_SELL_C];
         s0 = fmaf(w, gs_ld<READONLY>(cur + c), s0);
     }
+    return s0 + s1;
+}
+
+// Same loop with the neighbour values taken from a shared-memory cache through 16-bit local
+// indices (the per-block gather cache of the persistent loop); identical summation order.
+__device__ __forceinline__ float gs_sell_dot_cached(const uint16_t* lp, const float* vp, int width,
+                                                    const float* xc)
+{
+    float s0 = 0.f, s1 = 0.f;
+    int j = 0;
+    for (; j + 8 <= width; j += 8) {
+        float w[8], x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            w[u] = vp[(j + u) * GS_SELL_C];
+            x[u] = xc[lp[(j + u) * GS_SELL_C]];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            s0 = fmaf(w[u], x[u], s0);
+            s1 = fmaf(w[u + 1], x[u + 1], s1);
+        }
+    }
+    for (; j < width; ++j) s0 = fmaf(vp[j * GS_SELL_C], xc[lp[j * GS_SELL_C]], s0);
     return s0 + s1;
 }
 

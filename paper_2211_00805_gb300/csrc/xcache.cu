@@ -1,0 +1,150 @@
+// Per-block gather cache for the persistent Sinkhorn loop.
+//
+// The persistent kernel gives block b the contiguous rows [b R, (b+1) R) (R a multiple of the
+// slice height).  In the one-column filter each nonzero gathers cur[col]; within one block many
+// nonzeros share a column.  This pass lists, once per graph, the distinct columns of every block's
+// sliced-ELL entries (sorted) and rewrites each entry's column as a 16-bit index into that list.
+// Per Chebyshev order the block then copies cur[] at its distinct columns into shared memory (one
+// load per distinct column, in increasing address order) and every nonzero reads its neighbour
+// value from shared memory.
+#include <stdint.h>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+constexpr int kXcMaxEntries = 32768;  // sort capacity per block (and the 16-bit index range)
+
+__global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ sptr,
+                                                     const int* __restrict__ scol, int64_t nslices,
+                                                     int rpb, int64_t n, int P,
+                                                     int* __restrict__ ucol, int* __restrict__ ucnt,
+                                                     uint16_t* __restrict__ lidx)
+{
+    extern __shared__ int keys[];  // [P]
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, b = blockIdx.x;
+    const int64_t r0 = (int64_t)b * rpb;
+    const int64_t r1 = (r0 + rpb) < n ? (r0 + rpb) : n;
+    if (r0 >= r1) {
+        if (tid == 0) ucnt[b] = 0;
+        return;
+    }
+    const int64_t s0 = r0 / GS_SELL_C;
+    int64_t s1 = (r1 + GS_SELL_C - 1) / GS_SELL_C;
+    s1 = s1 < nslices ? s1 : nslices;
+    const int e0 = sptr[s0], e1 = sptr[s1];
+    const int E = e1 - e0;
+    if (E > P) {  // sized from the largest block, so this cannot happen; never write past keys[]
+        if (tid == 0) ucnt[b] = -1;
+        return;
+    }
+    for (int i = tid; i < P; i += blockDim.x) keys[i] = i < E ? scol[e0 + i] : 0x7fffffff;
+    __syncthreads();
+    // bitonic sort, ascending
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const int a = keys[i], c = keys[ixj];
+                    if ((a > c) == up) {
+                        keys[i] = c;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // distinct values: exclusive scan of "first of a run" flags over contiguous chunks per thread
+    const int chunk = (P + blockDim.x - 1) / blockDim.x;
+    const int i0 = tid * chunk, i1 = (i0 + chunk) < P ? (i0 + chunk) : P;
+    int cnt = 0;
+    for (int i = i0; i < i1; ++i)
+        cnt += (keys[i] != 0x7fffffff) && (i == 0 || keys[i] != keys[i - 1]);
+    int incl = cnt;
+    const int lane = tid & 31, w = tid >> 5;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += o;
+        }
+        wsum[lane] = v;  // inclusive prefix over warps
+    }
+    __syncthreads();
+    int pos = incl - cnt + (w > 0 ? wsum[w - 1] : 0);
+    for (int i = i0; i < i1; ++i) {
+        if ((keys[i] != 0x7fffffff) && (i == 0 || keys[i] != keys[i - 1])) ucol[e0 + pos++] = keys[i];
+    }
+    const int total = wsum[(blockDim.x >> 5) - 1];
+    if (tid == 0) ucnt[b] = total;
+    __syncthreads();
+    // each entry's position in the block's distinct list (binary search; the list is sorted)
+    for (int e = e0 + tid; e < e1; e += blockDim.x) {
+        const int c = scol[e];
+        int lo = 0, hi = total - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (ucol[e0 + mid] < c) lo = mid + 1;
+            else hi = mid;
+        }
+        lidx[e] = (uint16_t)lo;
+    }
+}
+
+}  // namespace
+
+// Build the cache tables for `blocks` blocks of `rpb` rows; leaves g->xc_ok false when a block has
+// more than kXcMaxEntries entries (the persistent kernel then gathers from global memory).
+gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, int rpb)
+{
+    g->xc_ok = false;
+    if (!g->sptr || g->sptr_host.empty() || blocks < 1) return GS_OK;
+    const int64_t ns = g->nslices;
+    int64_t worst = 0;
+    for (int b = 0; b < blocks; ++b) {
+        const int64_t r0 = (int64_t)b * rpb;
+        if (r0 >= g->n) break;
+        const int64_t r1 = std::min<int64_t>(g->n, r0 + rpb);
+        const int64_t s0 = r0 / GS_SELL_C, s1 = std::min<int64_t>(ns, (r1 + GS_SELL_C - 1) / GS_SELL_C);
+        worst = std::max<int64_t>(worst, (int64_t)g->sptr_host[s1] - g->sptr_host[s0]);
+    }
+    if (worst > kXcMaxEntries || worst == 0) return GS_OK;
+    int P = 1;
+    while (P < worst) P <<= 1;
+    const size_t tot = (size_t)(g->sell_nnz > 0 ? g->sell_nnz : 1);
+    cudaError_t e = cudaMalloc(&g->xc_ucol, sizeof(int) * tot);
+    if (e == cudaSuccess) e = cudaMalloc(&g->xc_lidx, sizeof(uint16_t) * tot);
+    if (e == cudaSuccess) e = cudaMalloc(&g->xc_ucnt, sizeof(int) * blocks);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GS_OK;  // the cache is an optimisation; run without it
+    }
+    cudaMemsetAsync(g->xc_ucol, 0, sizeof(int) * tot, ctx->stream);
+    cudaFuncSetAttribute(xcache_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(P * sizeof(int)));
+    xcache_build<<<blocks, 1024, P * sizeof(int), ctx->stream>>>(g->sptr, g->scol, ns, rpb, g->n, P,
+                                                                   g->xc_ucol, g->xc_ucnt, g->xc_lidx);
+    gs_count(ctx, 1);
+    g->xc_ucnt_host.assign((size_t)blocks, 0);
+    cudaMemcpyAsync(g->xc_ucnt_host.data(), g->xc_ucnt, sizeof(int) * blocks, cudaMemcpyDeviceToHost,
+                    ctx->stream);
+    gs_status st = gs_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "gather-cache tables");
+    if (st != GS_OK) return st;
+    for (int v : g->xc_ucnt_host)
+        if (v < 0) return GS_OK;
+    g->xc_blocks = blocks;
+    g->xc_rpb = rpb;
+    g->xc_max_e = (int)worst;
+    g->xc_max_u = *std::max_element(g->xc_ucnt_host.begin(), g->xc_ucnt_host.end());
+    g->xc_ok = true;
+    return GS_OK;
+}

@@ -313,7 +313,7 @@ def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph):
     p, g, Ls = sphere_graph
     out = {}
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 1)
-    for mode, smem in ((0, 1), (0, 0), (1, 1)):
+    for mode, smem in ((0, 1), (0, 0), (0, 2), (1, 1)):
         gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
         gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, smem)
         u, v, d, _ = gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 120)
@@ -321,8 +321,8 @@ def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph):
         out[(mode, smem)] = (to_np(u), to_np(v), to_np(d))
     gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
-    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 1)
-    for key in ((0, 0), (1, 1)):
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
+    for key in ((0, 0), (0, 2), (1, 1)):
         for i in range(3):
             np.testing.assert_array_equal(out[(0, 1)][i], out[key][i])
 
