@@ -76,12 +76,12 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_tag: str):
-    """DRAM bytes per launch from the committed ncu summary, or None if the kernel source changed
-    since the counters were taken (the summary records the source hash it was taken on)."""
+def ncu_traffic(kernel_tag: str, source: str = "cheb.cu"):
+    """DRAM bytes per launch from the committed ncu summary, or None if the kernel's source file
+    changed since the counters were taken (the summary records the hash it was taken on)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    src = os.path.join(ROOT, "paper_2211_00805_gb300", "csrc", "cheb.cu")
+    src = os.path.join(ROOT, "paper_2211_00805_gb300", "csrc", source)
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         for line in open(path):
@@ -293,18 +293,25 @@ def run_ours(args, rank, world, local_rank):
     total_ms = max_over_ranks(total_ms, world, dev)
     value = cfg["iters"] * args.steps * world / (total_ms / 1e3)
 
-    # roofline of the fused Chebyshev order kernel inside the Sinkhorn loop (B = 1)
+    # roofline of the dominant kernel of the step: the Sinkhorn loop's Chebyshev orders (B = 1),
+    # either one persistent launch per loop (loop mode 0) or one launch per order (mode 1)
     K = cfg["K"]
     per_apply = apply_bytes(n, nnz, K, 1, last_streams=6)  # gather, T_{K-2}, y, num, out, xnext
     orders = 2 * K * cfg["iters"]
     sink_s = statistics.mean(sink_ms) / 1e3
     achieved = 2 * cfg["iters"] * per_apply / sink_s / 1e9
     peak, peak_kind = measured_peaks()
-    tr = ncu_traffic("order_b1_manifold100k")
+    if tuned["loop_mode"] == 0:
+        tr = ncu_traffic("sinkhorn_persistent_manifold100k_500it", "persist.cu")
+        kern = {"kernel": "sinkhorn_persistent (whole 500-iteration loop, one cooperative launch)",
+                "bytes_per_launch": 2 * cfg["iters"] * per_apply, "launch_us": sink_s * 1e6}
+    else:
+        tr = ncu_traffic("order_b1_manifold100k")
+        kern = {"kernel": "fused Chebyshev order kernel (B=1), one launch per order",
+                "bytes_per_launch": per_apply / K, "launch_us": sink_s / orders * 1e6}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": tr,
-                "kernel": "order_b1 (fused Chebyshev order, B=1) in the Sinkhorn loop",
-                "bytes_per_launch": per_apply / K, "launch_us": sink_s / orders * 1e6,
+                "frac": achieved / peak, "traffic": tr, **kern,
+                "order_us": sink_s / orders * 1e6,
                 "peak_kind": f"{peak_kind} hbm_gbs",
                 "note": "working set (~19 MB) is L2-resident; see spmm_hbm for the HBM-bound case"}
 

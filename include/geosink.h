@@ -87,7 +87,8 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * per-order launches; 2 (default) the mode gs_autotune measured faster on the graph, else 0.
  * All compute the same thing.  Errors: GS_ERR_ARG. */
 /* GS_OPT_BARRIER_SELFTEST = 1 makes the next persistent launch wait at its first grid barrier for
- * one block more than the grid has: every block's bounded wait runs out (~10 ms), the launch ends
+ * one block more than the grid has (with neighbour-flag sync: for a stage no block will publish,
+ * including its own): every block's bounded wait runs out (~10 ms), the launch ends
  * and gs_sync reports GS_ERR_TIMEOUT, leaving the context usable.  It exercises failure handling
  * without faulting the GPU; the option resets itself after that launch. */
 /* GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL pick the Chebyshev order kernel for one column / several
@@ -105,11 +106,20 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * 1: slices in shared memory, neighbour values gathered from global memory; 0: everything from
  * global memory.  Each mode falls back to the next lower one when its tables do not fit in 200 KB
  * of shared memory.  Same arithmetic in every mode. */
+/* GS_OPT_PERSIST_SYNC: how the blocks of the persistent loop wait for one another between
+ * Chebyshev orders when the gather-cache tables are in use (mode 2 above).  1 (default): each
+ * block waits only for the blocks owning rows it reads (per-block ready counters) and keeps its own
+ * rows' recurrence values in registers; 2: the same, with the readiness carried by the exchanged
+ * values themselves (64-bit value + stage words in three rotating slots, no counters or fences);
+ * 0: a barrier over the whole grid; 3 (default): the one gs_autotune measured fastest on the
+ * graph (else on the context's last tuned graph, else 2).  Same arithmetic in all of them.  All
+ * honour GS_OPT_BARRIER_SELFTEST. */
 enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
-       GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6 };
+       GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6, GS_OPT_PERSIST_SYNC = 7 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
 
-/* Host query of an option.  For GS_OPT_LOOP and GS_OPT_B1_KERNEL left on automatic it reports what
+/* Host query of an option.  For GS_OPT_LOOP, GS_OPT_B1_KERNEL and GS_OPT_PERSIST_SYNC left on
+ * automatic it reports what
  * a call on a graph without its own autotune record would use (the context's last autotune
  * result, else the built-in default: persistent loop, row-split kernel).  Errors: GS_ERR_ARG. */
 gs_status gs_get_option(const gs_ctx *ctx, int option, int *value);
@@ -166,11 +176,13 @@ gs_status gs_graph_export_csr(gs_ctx *ctx, const gs_graph *g, int64_t *rowptr, i
 /* Autotuner (not in the paper; it serves throughput): times every Chebyshev-order kernel variant
  * for B columns and degree K on this graph (heat-filter applies on a synthetic block, CUDA events,
  * waits for the device) and records the fastest in the graph handle; for B = 1 it also times a
- * short fixed-count Sinkhorn loop in both GS_OPT_LOOP modes and records the faster.
+ * short fixed-count Sinkhorn loop as graph replay and as the persistent launch with each
+ * GS_OPT_PERSIST_SYNC form, and records the fastest loop mode and synchronisation.
  * *choice (may be NULL) receives the chosen variant (the GS_OPT_*_KERNEL value).
  * Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED. */
 /* Later calls on the graph use the recorded choices while the context's options are automatic
- * (GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL 0, GS_OPT_LOOP 2); the context also keeps the last one-
+ * (GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL 0, GS_OPT_LOOP 2, GS_OPT_PERSIST_SYNC 3); the context also
+ * keeps the last one-
  * column choices for graphs that were never tuned (e.g. rebuilt graphs of the same workload). */
 gs_status gs_autotune(gs_ctx *ctx, gs_graph *g, int B, int K, int *choice);
 

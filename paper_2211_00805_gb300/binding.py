@@ -167,6 +167,7 @@ GS_OPT_B1_KERNEL = 3
 GS_OPT_BLK_KERNEL = 4
 GS_OPT_KNN_TENSOR = 5
 GS_OPT_PERSIST_SMEM_GRAPH = 6
+GS_OPT_PERSIST_SYNC = 7
 
 
 def gs_set_option(ctx: Context, option: int, value: int):

@@ -167,6 +167,10 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->persist_smem_graph = value;
         return GS_OK;
     }
+    if (option == GS_OPT_PERSIST_SYNC && (value >= 0 && value <= 3)) {
+        ctx->persist_sync = value;
+        return GS_OK;
+    }
     if (option == GS_OPT_KNN_TENSOR && (value == 0 || value == 1)) {
         ctx->knn_tensor_cores = value;
         return GS_OK;
@@ -197,6 +201,7 @@ extern "C" gs_status gs_get_option(const gs_ctx* ctx, int option, int* value)
         case GS_OPT_BLK_KERNEL: *value = ctx->blk_kernel; return GS_OK;
         case GS_OPT_KNN_TENSOR: *value = ctx->knn_tensor_cores; return GS_OK;
         case GS_OPT_PERSIST_SMEM_GRAPH: *value = ctx->persist_smem_graph; return GS_OK;
+        case GS_OPT_PERSIST_SYNC: *value = gs_persist_sync_choice(ctx, nullptr); return GS_OK;
         default: return GS_ERR_ARG;
     }
 }
@@ -303,6 +308,8 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g)
     cudaFree(g->xc_ucol);
     cudaFree(g->xc_ucnt);
     cudaFree(g->xc_lidx);
+    cudaFree(g->xc_deps);
+    cudaFree(g->xc_ndeps);
     delete g;
     return GS_OK;
 }

@@ -101,32 +101,44 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
     }
     fill_ones<<<(unsigned)((2 * n + 255) / 256), 256, 0, ctx->stream>>>(2 * n, ab);
     gs_count(ctx, 1);
-    const int saved_loop = ctx->loop_mode;
-    float loop_ms[2] = {0.f, 0.f};
+    const int saved_loop = ctx->loop_mode, saved_sync = ctx->persist_sync;
+    // candidates: the persistent loop with each block synchronisation (grid barrier, neighbour
+    // flags, tagged values), then graph replay
+    float loop_ms[4] = {0.f, 0.f, 0.f, 0.f};
     int saved_flags = 0;  // the synthetic loop's status must not reach the caller's next gs_sync
     cudaStreamSynchronize(ctx->stream);
     cudaMemcpy(&saved_flags, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int mode = 0; mode < 2 && st == GS_OK; ++mode) {
-        ctx->loop_mode = mode;
+    for (int c = 0; c < 4 && st == GS_OK; ++c) {
+        ctx->loop_mode = c < 3 ? 0 : 1;
+        ctx->persist_sync = c < 3 ? c : saved_sync;
         for (int rep = 0; rep < 2 && st == GS_OK; ++rep) {  // first run warms (graph capture)
             cudaEventRecord(e0, ctx->stream);
             st = gs_sinkhorn_impl(ctx, g, ab, ab + n, nullptr, 1.0, K, 0.0, 10, nullptr, nullptr,
                                   nullptr, nullptr);
             cudaEventRecord(e1, ctx->stream);
             if (st == GS_OK) st = gs_cuda_check(ctx, cudaEventSynchronize(e1), "autotune loop timing");
-            if (st == GS_OK) cudaEventElapsedTime(&loop_ms[mode], e0, e1);
+            if (st == GS_OK) cudaEventElapsedTime(&loop_ms[c], e0, e1);
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->loop_mode = saved_loop;
+    ctx->persist_sync = saved_sync;
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ab);
     cudaMemcpy(ctx->flags, &saved_flags, sizeof(int), cudaMemcpyHostToDevice);
     if (st != GS_OK) return st;
-    g->tuned_loop = loop_ms[0] <= loop_ms[1] ? 1 : 2;
+    int best_c = 0;
+    for (int c = 1; c < 4; ++c)
+        if (loop_ms[c] < loop_ms[best_c]) best_c = c;
+    g->tuned_loop = best_c < 3 ? 1 : 2;
     ctx->tuned_loop = g->tuned_loop;
+    int best_s = 0;
+    for (int c = 1; c < 3; ++c)
+        if (loop_ms[c] < loop_ms[best_s]) best_s = c;
+    g->tuned_sync = best_s;
+    ctx->tuned_sync = best_s;
     return GS_OK;
 }

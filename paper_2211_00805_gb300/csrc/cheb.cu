@@ -1025,9 +1025,13 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
                  ie = plan.add(sizeof(double) * 2), id = plan.add(sizeof(int) * 2),
                  ip = plan.add(sizeof(double) * gs_reduce_blocks());
     const size_t iuu = own_uv ? plan.add(vec) : 0, ivv = own_uv ? plan.add(vec) : 0;
-    const size_t icf = plan.add(sizeof(float) * ((size_t)K + 1)), ibar = plan.add(sizeof(unsigned) * 4);
+    const size_t icf = plan.add(sizeof(float) * ((size_t)K + 1)), ibar = plan.add(sizeof(unsigned) * gs_persist_bar_words(ctx));
     const size_t iap = perm ? plan.add(vec) : 0, ibp = perm ? plan.add(vec) : 0,
                  ivp = (perm && vol) ? plan.add(vec) : 0;
+    // exchange buffer of the tagged-value persistent kernel (only sizes it can run at)
+    const bool want_tag = gs_persist_sync_choice(ctx, g) == 2 &&
+                          n <= (int64_t)4 * 1024 * std::max(ctx->num_sms, 1);
+    const size_t itg = want_tag ? plan.add(sizeof(unsigned long long) * 3 * (size_t)n) : 0;
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
     float* x = ws_at<float>(ctx, plan, ix);
@@ -1090,7 +1094,8 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
         float* cdev = ws_at<float>(ctx, plan, icf);
         cudaMemcpyAsync(cdev, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice, ctx->stream);
         st = gs_sinkhorn_persistent(ctx, g, a, b, vol, cdev, K, iters, x, A, y, u, v,
-                                    ws_at<unsigned>(ctx, plan, ibar));
+                                    ws_at<unsigned>(ctx, plan, ibar),
+                                    want_tag ? ws_at<unsigned long long>(ctx, plan, itg) : nullptr);
         if (st == GS_OK) looped = true;
         else if (st != GS_ERR_UNSUPPORTED) return st;
         st = GS_OK;

@@ -62,6 +62,9 @@ struct gs_ctx {
     int tuned_loop = 0;            // last gs_autotune loop choice (1 persistent, 2 graph replay)
     int persist_smem_graph = 2;    // persistent loop: 0 graph from global memory, 1 graph slices in
                                    // shared memory, 2 slices plus the per-block gather cache
+    int persist_sync = 3;          // persistent loop with the gather cache: 2 tagged values,
+                                   // 1 neighbour flags, 0 grid barrier, 3 the autotuned choice
+    int tuned_sync = -1;           // last gs_autotune choice of the above (0..2), -1 none
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::string err;
@@ -103,6 +106,7 @@ struct gs_graph {
     int tuned_blk = 0;
     int tuned_blk_B = 0;
     int tuned_loop = 0;            // Sinkhorn loop: 0 not tuned, 1 persistent, 2 CUDA-graph replay
+    int tuned_sync = -1;           // persistent loop's block synchronisation (0..2), -1 not tuned
     std::vector<int> sptr_host;    // host copy of the slice offsets (sizes the persistent kernel's
                                    // shared-memory graph slices)
     // per-block gather cache of the persistent loop (xcache.cu): for the partition into xc_blocks
@@ -113,6 +117,8 @@ struct gs_graph {
     int* xc_ucol = nullptr;
     int* xc_ucnt = nullptr;
     uint16_t* xc_lidx = nullptr;
+    int* xc_deps = nullptr;   // [xc_blocks][xc_blocks]: block b's first xc_ndeps[b] entries are the
+    int* xc_ndeps = nullptr;  // other blocks owning one of its distinct columns
     std::vector<int> xc_ucnt_host;
 };
 
@@ -165,6 +171,21 @@ gs_status gs_graph_export(gs_ctx* ctx, const gs_graph* g, int64_t* rowptr, int32
 gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g);
 gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, int rpb);
 // rows per block of the persistent loop's partition (one block per SM, whole slices)
+// Block synchronisation of the persistent loop: the option if set, else the autotuned choice for
+// the graph, else the context's last one, else tagged values (the fastest on the graphs measured).
+static inline int gs_persist_sync_choice(const gs_ctx* ctx, const gs_graph* g)
+{
+    if (ctx->persist_sync != 3) return ctx->persist_sync;
+    if (g && g->tuned_sync >= 0) return g->tuned_sync;
+    if (ctx->tuned_sync >= 0) return ctx->tuned_sync;
+    return 2;
+}
+// Words of the persistent loop's synchronisation buffer: barrier counter and generation, then one
+// 128-byte line per block for its ready counter.
+static inline size_t gs_persist_bar_words(const gs_ctx* ctx)
+{
+    return 32 * (1 + (size_t)(ctx->num_sms > 0 ? ctx->num_sms : 148));
+}
 static inline int gs_persist_rows_per_block(const gs_ctx* ctx, int64_t n)
 {
     const int blocks = ctx->num_sms > 0 ? ctx->num_sms : 148;
@@ -243,7 +264,8 @@ gs_status gs_sinkhorn_batched_impl(gs_ctx* ctx, int nprob, const gs_graph* const
                                    double* dist);
 gs_status gs_sinkhorn_persistent(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
                                  const float* vol, const float* coef_dev, int K, int iters,
-                                 float* x, float* A, float* y, float* u, float* v, unsigned* bar);
+                                 float* x, float* A, float* y, float* u, float* v, unsigned* bar,
+                                 unsigned long long* tagged);
 gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_out);
 gs_status gs_barycenter_impl(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
                              const double* alpha, const float* vol, double t, int K, int iters,

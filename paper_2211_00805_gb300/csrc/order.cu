@@ -173,23 +173,28 @@ __global__ void sell_width(int64_t n, int64_t nslices, const int* __restrict__ p
     cnt[sl] = w * GS_SELL_C;
 }
 
-__global__ void sell_fill(int64_t n, const int* __restrict__ prowptr, const int* __restrict__ pcol,
-                          const float* __restrict__ ppval, const int64_t* __restrict__ sptr64,
-                          int* __restrict__ scol, float* __restrict__ sval)
+// One thread per row of the padded slice range [0, 32 * nslices): rows past n (the tail of the last
+// slice) get only padding entries, pointing at row n - 1 (in the same slice) with value 0, so that
+// every stored column is a valid row index.
+__global__ void sell_fill(int64_t n, int64_t nslices, const int* __restrict__ prowptr,
+                          const int* __restrict__ pcol, const float* __restrict__ ppval,
+                          const int64_t* __restrict__ sptr64, int* __restrict__ scol,
+                          float* __restrict__ sval)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
+    if (r >= nslices * GS_SELL_C) return;
     const int64_t sl = r / GS_SELL_C, lane = r % GS_SELL_C;
     const int64_t base = sptr64[sl];
     const int width = (int)((sptr64[sl + 1] - base) / GS_SELL_C);
-    const int b = prowptr[r], len = prowptr[r + 1] - b;
+    const bool real = r < n;
+    const int b = real ? prowptr[r] : 0, len = real ? prowptr[r + 1] - b : 0;
     for (int j = 0; j < width; ++j) {
         const int64_t o = base + (int64_t)j * GS_SELL_C + lane;
         if (j < len) {
             scol[o] = pcol[b + j];
             sval[o] = ppval[b + j];
         } else {
-            scol[o] = (int)r;
+            scol[o] = (int)(real ? r : n - 1);
             sval[o] = 0.f;
         }
     }
@@ -334,7 +339,8 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
     g->nslices = ns;
     g->sell_nnz = tot;
     rowptr_narrow<<<nblk(ns + 1, 256), 256, 0, s>>>(ns + 1, p64, g->sptr);
-    sell_fill<<<nblk(n, 256), 256, 0, s>>>(n, g->prowptr, g->pcol, g->ppval, p64, g->scol, g->sval);
+    sell_fill<<<nblk(ns * GS_SELL_C, 256), 256, 0, s>>>(n, ns, g->prowptr, g->pcol, g->ppval, p64,
+                                                          g->scol, g->sval);
     gs_count(ctx, 6);
     g->sptr_host.resize((size_t)ns + 1);
     cudaMemcpyAsync(g->sptr_host.data(), g->sptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost, s);

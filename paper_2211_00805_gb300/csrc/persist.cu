@@ -23,6 +23,7 @@
 namespace {
 
 constexpr int kThreads = 1024;
+constexpr int kReadyStride = 32;  // one 128-byte line per block's ready counter
 constexpr long long kBarrierBudget = 4000000000ll;  // clock cycles (~2 s) before giving up
 // Self-test: the barrier waits for one arrival more than the grid has, so every wait runs out
 // after this much shorter budget and the launch ends with GS_FLAG_TIMEOUT.
@@ -59,6 +60,11 @@ struct PersistArgs {
     const uint16_t* xc_lidx;
     int xc_max_e;
     int xc_max_u;
+    const int* xc_deps;  // [gridDim.x][gridDim.x] blocks each block reads from (neighbour-flag sync)
+    const int* xc_ndeps;
+    unsigned* ready;     // [gridDim.x * kReadyStride] per-block count of published stages
+    int selftest;        // neighbour-flag sync: wait for one stage more than will ever be published
+    unsigned long long* tagged;  // [3][n] (value, stage + 1) words, zeroed (tagged-value sync)
 };
 
 // Returns false when the wait ran out (the caller leaves the loop).  Arrival is a relaxed atomic
@@ -92,6 +98,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* flags, int* s_o
     return *s_ok != 0;
 }
 
+// Row functions: mode 0 is the first order (T_1 = P x, y = c_0 x + c_1 T_1), 1 a middle order, 2
+// the last order (divide the marginal by the filter value, write the next input vol * u), 3 the
+// only order when K = 1 (first and last at once).
 template <int G>
 __device__ __forceinline__ void rows_order(const PersistArgs& p, int r0, int r1, int mode, float ck,
                                            float c0, const float* cur, const float* prev,
@@ -117,9 +126,10 @@ __device__ __forceinline__ void rows_order(const PersistArgs& p, int r0, int r1,
 #pragma unroll
         for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (!active || lane != 0) continue;
-        const float tk = (mode == 0) ? s : fmaf(2.f, s, -prev[row]);
-        const float acc = (mode == 0) ? fmaf(ck, tk, c0 * cur[row]) : fmaf(ck, tk, p.y[row]);
-        if (mode != 2) {
+        const bool first = mode == 0 || mode == 3;
+        const float tk = first ? s : fmaf(2.f, s, -prev[row]);
+        const float acc = first ? fmaf(ck, tk, c0 * cur[row]) : fmaf(ck, tk, p.y[row]);
+        if (mode < 2) {
             next[row] = tk;
             p.y[row] = acc;
         } else {
@@ -143,12 +153,13 @@ __device__ __forceinline__ void rows_order_sell(const PersistArgs& p, int r0, in
                                                 float* out, float* xnext)
 {
     for (int row = r0 + (int)threadIdx.x; row < r1; row += kThreads) {
-        const float pv = (mode == 0) ? 0.f : prev[row];
-        const float yv = (mode == 0) ? c0 * cur[row] : p.y[row];
+        const bool first = mode == 0 || mode == 3;
+        const float pv = first ? 0.f : prev[row];
+        const float yv = first ? c0 * cur[row] : p.y[row];
         const float s = gs_sell_row<false>(p.sptr, p.scol, p.sval, cur, row);
-        const float tk = (mode == 0) ? s : fmaf(2.f, s, -pv);
+        const float tk = first ? s : fmaf(2.f, s, -pv);
         const float acc = fmaf(ck, tk, yv);
-        if (mode != 2) {
+        if (mode < 2) {
             next[row] = tk;
             p.y[row] = acc;
         } else {
@@ -173,16 +184,17 @@ __device__ __forceinline__ void rows_order_sell_smem(const PersistArgs& p, int r
                                                      const int* scol_s, const float* sval_s, int e0)
 {
     for (int row = r0 + (int)threadIdx.x; row < r1; row += kThreads) {
-        const float pv = (mode == 0) ? 0.f : prev[row];
-        const float yv = (mode == 0) ? c0 * cur[row] : p.y[row];
+        const bool first = mode == 0 || mode == 3;
+        const float pv = first ? 0.f : prev[row];
+        const float yv = first ? c0 * cur[row] : p.y[row];
         const int sl = row / GS_SELL_C;
         const int beg = __ldg(p.sptr + sl);
         const int width = (__ldg(p.sptr + sl + 1) - beg) / GS_SELL_C;
         const int off = beg - e0 + row % GS_SELL_C;
         const float s = gs_sell_dot<false, false>(scol_s + off, sval_s + off, width, cur);
-        const float tk = (mode == 0) ? s : fmaf(2.f, s, -pv);
+        const float tk = first ? s : fmaf(2.f, s, -pv);
         const float acc = fmaf(ck, tk, yv);
-        if (mode != 2) {
+        if (mode < 2) {
             next[row] = tk;
             p.y[row] = acc;
         } else {
@@ -207,16 +219,17 @@ __device__ __forceinline__ void rows_order_cached(const PersistArgs& p, int r0, 
                                                   const float* sval_s, const float* xc, int e0)
 {
     for (int row = r0 + (int)threadIdx.x; row < r1; row += kThreads) {
-        const float pv = (mode == 0) ? 0.f : prev[row];
-        const float yv = (mode == 0) ? c0 * cur[row] : p.y[row];
+        const bool first = mode == 0 || mode == 3;
+        const float pv = first ? 0.f : prev[row];
+        const float yv = first ? c0 * cur[row] : p.y[row];
         const int sl = row / GS_SELL_C;
         const int beg = __ldg(p.sptr + sl);
         const int width = (__ldg(p.sptr + sl + 1) - beg) / GS_SELL_C;
         const int off = beg - e0 + row % GS_SELL_C;
         const float s = gs_sell_dot_cached(lidx_s + off, sval_s + off, width, xc);
-        const float tk = (mode == 0) ? s : fmaf(2.f, s, -pv);
+        const float tk = first ? s : fmaf(2.f, s, -pv);
         const float acc = fmaf(ck, tk, yv);
-        if (mode != 2) {
+        if (mode < 2) {
             next[row] = tk;
             p.y[row] = acc;
         } else {
@@ -393,7 +406,7 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArg
             const float* num = h == 0 ? p.a : p.b;
             float* out = h == 0 ? p.u : p.v;
             if (p.K == 1) {
-                rows_any<G>(p, r0, r1, 2, p.coef[1], c0, X, nullptr, nullptr, num, out, Ab, scol_s, sval_s, e0, lidx_s, ucol_s, xc, ucnt);
+                rows_any<G>(p, r0, r1, 3, p.coef[1], c0, X, nullptr, nullptr, num, out, Ab, scol_s, sval_s, e0, lidx_s, ucol_s, xc, ucnt);
                 if (!grid_barrier(p.bar, p.flags, &s_ok, p.expect, p.budget)) return;
                 float* t = X; X = Ab; Ab = t;
                 continue;
@@ -413,6 +426,312 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArg
                     X = prev;
                     Ab = cur;
                 }
+            }
+        }
+    }
+}
+
+
+// ------------------------------------------------------------------ neighbour-flag variant
+// Same loop, same arithmetic as mode 2 above, with two changes.  (1) Each block keeps the
+// recurrence values of its own rows (T_{k-1}, T_{k-2}, the running sum, the input x and the
+// marginals) in registers, since no other block reads them; only T_k (or, after the last order,
+// the next input vol * u) is published, alternately into one of two global slots.  (2) Instead of
+// a barrier over the grid, block b waits before each order only for the blocks that own a column
+// of its rows: "stage s published" is a per-block counter ready[b] = s + 1 written with release
+// semantics after the stage's stores.  Order s reads stage s-1 from slot (s-1) & 1 and writes stage
+// s into slot s & 1, which held stage s-2; waiting for ready[d] >= s on every block d it reads
+// covers both the read of stage s-1 and, the operator being symmetric, the end of every read of
+// stage s-2 from this block's rows (block d read it in order s-1, before publishing stage s-1).
+// Every wait is bounded by the clock budget.
+
+// Wait until every block this one reads from has published stage `need - 1`.  Bounded; false =
+// the wait ran out (GS_FLAG_TIMEOUT set).
+__device__ __forceinline__ bool wait_neighbours(const PersistArgs& p, int dep, unsigned need,
+                                                int* s_ok)
+{
+    if (dep >= 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> f(p.ready[dep * kReadyStride]);
+        if (f.load(cuda::memory_order_relaxed) < need) {
+            const long long t0 = clock64();
+            while (f.load(cuda::memory_order_relaxed) < need) {
+                if (clock64() - t0 > p.budget) {
+                    atomicOr(p.flags, GS_FLAG_TIMEOUT);
+                    *s_ok = 0;
+                    break;
+                }
+            }
+        }
+        cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// All of this block's stores of stage s are done: publish ready[b] = s + 1.
+__device__ __forceinline__ void publish(const PersistArgs& p, unsigned stage)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_thread_fence(cuda::memory_order_release, cuda::thread_scope_device);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> f(p.ready[blockIdx.x * kReadyStride]);
+        f.store(stage + 1u, cuda::memory_order_relaxed);
+    }
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(kThreads) sinkhorn_neighbour_sync(const PersistArgs p)
+{
+    __shared__ int s_ok;
+    __shared__ __align__(8) unsigned long long s_mbar;
+    extern __shared__ __align__(128) unsigned char p_smem[];
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    const int per = p.rows_per_block;
+    const int r0 = min(p.n, (int)blockIdx.x * per), r1 = min(p.n, r0 + per);
+    const int emax = (p.xc_max_e + 31) / 32 * 32, umax = (p.xc_max_u + 31) / 32 * 32;
+    float* sval_s = reinterpret_cast<float*>(p_smem);
+    uint16_t* lidx_s = reinterpret_cast<uint16_t*>(p_smem + (size_t)emax * 4);
+    int* ucol_s = reinterpret_cast<int*>(p_smem + (size_t)emax * 6);
+    float* xc = reinterpret_cast<float*>(p_smem + (size_t)emax * 6 + (size_t)umax * 4);
+    int e0 = 0, ucnt = 0;
+    if (!load_cached_slices(p, r0, r1, sval_s, lidx_s, ucol_s, &e0, &ucnt, &s_mbar)) s_ok = 0;
+    __syncthreads();
+    if (!s_ok) return;
+    if (r0 >= r1 && !p.selftest) return;  // no rows: no block reads from this one
+
+    // the block this thread waits on (one per thread; a self-test waits for its own block too)
+    const int nd = __ldg(p.xc_ndeps + blockIdx.x);
+    int dep = (int)threadIdx.x < nd ? __ldg(p.xc_deps + (int64_t)blockIdx.x * gridDim.x + threadIdx.x) : -1;
+    if (p.selftest && (int)threadIdx.x == nd) dep = (int)blockIdx.x;
+    const unsigned extra = p.selftest ? 1u : 0u;
+
+    // own rows: sliced-ELL position, marginals, volume, recurrence state
+    int off[RPT], width[RPT];
+    float av[RPT], bv[RPT], vv[RPT], xo[RPT], t1[RPT], t2[RPT], yo[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int row = r0 + (int)threadIdx.x + j * kThreads;
+        off[j] = 0;
+        width[j] = 0;
+        av[j] = bv[j] = 0.f;
+        vv[j] = 1.f;
+        if (row < r1) {
+            const int sl = row / GS_SELL_C;
+            const int beg = __ldg(p.sptr + sl);
+            width[j] = (__ldg(p.sptr + sl + 1) - beg) / GS_SELL_C;
+            off[j] = beg - e0 + row % GS_SELL_C;
+            av[j] = __ldg(p.a + row);
+            bv[j] = __ldg(p.b + row);
+            if (p.vol) vv[j] = __ldg(p.vol + row);
+        }
+        xo[j] = vv[j];  // vol * (v = 1)
+        t1[j] = t2[j] = yo[j] = 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int row = r0 + (int)threadIdx.x + j * kThreads;
+        if (row < r1) p.x[row] = xo[j];
+    }
+    unsigned stage = 0;
+    publish(p, stage);
+    const float c0 = p.coef[0];
+    const int K = p.K;
+    for (int it = 0; it < p.iters; ++it) {
+        for (int h = 0; h < 2; ++h) {
+            for (int k = 1; k <= K; ++k) {
+                ++stage;
+                if (!wait_neighbours(p, dep, stage + extra, &s_ok)) return;
+                const float* src = (stage & 1) ? p.x : p.A;  // stage s - 1 lives in slot (s - 1) & 1
+                float* dst = (stage & 1) ? p.A : p.x;
+                for (int i = threadIdx.x; i < ucnt; i += kThreads) xc[i] = __ldcg(src + ucol_s[i]);
+                __syncthreads();
+                const float ck = p.coef[k];
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const int row = r0 + (int)threadIdx.x + j * kThreads;
+                    if (row >= r1) continue;
+                    const float s = gs_sell_dot_cached(lidx_s + off[j], sval_s + off[j], width[j], xc);
+                    float tk, acc;
+                    if (k == 1) {
+                        tk = s;
+                        acc = fmaf(ck, tk, c0 * xo[j]);
+                    } else {
+                        tk = fmaf(2.f, s, -t2[j]);
+                        acc = fmaf(ck, tk, yo[j]);
+                    }
+                    if (k < K) {
+                        t2[j] = k == 1 ? xo[j] : t1[j];
+                        t1[j] = tk;
+                        yo[j] = acc;
+                        dst[row] = tk;
+                    } else {
+                        const float m = h == 0 ? av[j] : bv[j];
+                        float r = 0.f;
+                        if (m != 0.f) {
+                            r = m / acc;
+                            if (!(r > 0.f) || isinf(r)) atomicOr(p.flags, GS_FLAG_NONFINITE);
+                        }
+                        (h == 0 ? p.u : p.v)[row] = r;
+                        xo[j] = p.vol ? vv[j] * r : r;
+                        dst[row] = xo[j];
+                    }
+                }
+                publish(p, stage);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ tagged-value variant
+// Same loop and arithmetic again, with the readiness carried by the data itself: every published
+// value is one 64-bit word (FP32 bits low, stage + 1 high), written and read as a single-copy-
+// atomic 64-bit access, into one of three slots (stage s in slot s mod 3; the slots are zeroed
+// before the launch, so a tag of 0 is never a stage).  A block reading stage s - 1 simply re-reads
+// any word whose tag is not yet s: no counters, no fences, and no barrier of any kind between
+// blocks.  Three slots make the overwrite safe: the block writing stage s into a slot (which held
+// stage s - 3) has read stage s - 1 from every block it reads from, and each of those blocks had
+// finished reading stage s - 3 (in order s - 2) before it computed stage s - 1.  Should a value
+// ever be overwritten early anyway, its reader would find a tag other than the one it waits for
+// and its bounded wait would run out (GS_FLAG_TIMEOUT), never a silently wrong value.
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* a)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* a, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;\n" ::"l"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long pack_tagged(float x, unsigned tag)
+{
+    return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(x);
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(kThreads) sinkhorn_tagged(const PersistArgs p)
+{
+    __shared__ int s_ok;
+    __shared__ __align__(8) unsigned long long s_mbar;
+    extern __shared__ __align__(128) unsigned char p_smem[];
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    const int per = p.rows_per_block;
+    const int r0 = min(p.n, (int)blockIdx.x * per), r1 = min(p.n, r0 + per);
+    const int emax = (p.xc_max_e + 31) / 32 * 32, umax = (p.xc_max_u + 31) / 32 * 32;
+    float* sval_s = reinterpret_cast<float*>(p_smem);
+    uint16_t* lidx_s = reinterpret_cast<uint16_t*>(p_smem + (size_t)emax * 4);
+    int* ucol_s = reinterpret_cast<int*>(p_smem + (size_t)emax * 6);
+    float* xc = reinterpret_cast<float*>(p_smem + (size_t)emax * 6 + (size_t)umax * 4);
+    int e0 = 0, ucnt = 0;
+    if (!load_cached_slices(p, r0, r1, sval_s, lidx_s, ucol_s, &e0, &ucnt, &s_mbar)) s_ok = 0;
+    __syncthreads();
+    if (!s_ok) return;
+    if (r0 >= r1) return;  // no rows: nothing to publish, nothing to read
+    const unsigned extra = p.selftest ? 1u : 0u;
+    const size_t n = (size_t)p.n;
+
+    int off[RPT], width[RPT];
+    float av[RPT], bv[RPT], vv[RPT], xo[RPT], t1[RPT], t2[RPT], yo[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int row = r0 + (int)threadIdx.x + j * kThreads;
+        off[j] = 0;
+        width[j] = 0;
+        av[j] = bv[j] = 0.f;
+        vv[j] = 1.f;
+        if (row < r1) {
+            const int sl = row / GS_SELL_C;
+            const int beg = __ldg(p.sptr + sl);
+            width[j] = (__ldg(p.sptr + sl + 1) - beg) / GS_SELL_C;
+            off[j] = beg - e0 + row % GS_SELL_C;
+            av[j] = __ldg(p.a + row);
+            bv[j] = __ldg(p.b + row);
+            if (p.vol) vv[j] = __ldg(p.vol + row);
+        }
+        xo[j] = vv[j];  // vol * (v = 1)
+        t1[j] = t2[j] = yo[j] = 0.f;
+        if (row < r1) st_relaxed_u64(p.tagged + row, pack_tagged(xo[j], 1u));  // stage 0, slot 0
+    }
+    unsigned stage = 0;
+    int rslot = 0, wslot = 1;  // slots of stage - 1 and stage (mod 3) inside the order loop
+    const float c0 = p.coef[0];
+    const int K = p.K;
+    for (int it = 0; it < p.iters; ++it) {
+        for (int h = 0; h < 2; ++h) {
+            for (int k = 1; k <= K; ++k) {
+                ++stage;
+                const unsigned long long* src = p.tagged + (size_t)rslot * n;
+                unsigned long long* dst = p.tagged + (size_t)wslot * n;
+                const unsigned want = stage + extra;  // stage - 1 carries tag stage
+                // issue up to 8 loads per thread before checking any tag
+                for (int i0 = threadIdx.x; i0 < ucnt; i0 += 8 * kThreads) {
+                    unsigned long long w[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + u * kThreads;
+                        w[u] = i < ucnt ? ld_relaxed_u64(src + ucol_s[i]) : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + u * kThreads;
+                        if (i >= ucnt) break;
+                        if ((unsigned)(w[u] >> 32) != want) {
+                            const long long t0 = clock64();
+                            do {
+                                w[u] = ld_relaxed_u64(src + ucol_s[i]);
+                                if (clock64() - t0 > p.budget) {
+                                    atomicOr(p.flags, GS_FLAG_TIMEOUT);
+                                    s_ok = 0;
+                                    break;
+                                }
+                            } while ((unsigned)(w[u] >> 32) != want);
+                        }
+                        xc[i] = __uint_as_float((unsigned)w[u]);
+                    }
+                }
+                __syncthreads();
+                if (!s_ok) return;
+                const float ck = p.coef[k];
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const int row = r0 + (int)threadIdx.x + j * kThreads;
+                    if (row >= r1) continue;
+                    const float s = gs_sell_dot_cached(lidx_s + off[j], sval_s + off[j], width[j], xc);
+                    float tk, acc;
+                    if (k == 1) {
+                        tk = s;
+                        acc = fmaf(ck, tk, c0 * xo[j]);
+                    } else {
+                        tk = fmaf(2.f, s, -t2[j]);
+                        acc = fmaf(ck, tk, yo[j]);
+                    }
+                    float pub;
+                    if (k < K) {
+                        t2[j] = k == 1 ? xo[j] : t1[j];
+                        t1[j] = tk;
+                        yo[j] = acc;
+                        pub = tk;
+                    } else {
+                        const float m = h == 0 ? av[j] : bv[j];
+                        float r = 0.f;
+                        if (m != 0.f) {
+                            r = m / acc;
+                            if (!(r > 0.f) || isinf(r)) atomicOr(p.flags, GS_FLAG_NONFINITE);
+                        }
+                        (h == 0 ? p.u : p.v)[row] = r;
+                        xo[j] = p.vol ? vv[j] * r : r;
+                        pub = xo[j];
+                    }
+                    st_relaxed_u64(dst + row, pack_tagged(pub, stage + 1u));
+                }
+                __syncthreads();  // xc is refilled by the next order
+                rslot = wslot;
+                wslot = wslot == 2 ? 0 : wslot + 1;
             }
         }
     }
@@ -456,6 +775,40 @@ gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
             args.smem_graph = 1;
         }
     }
+    args.expect = (unsigned)blocks + (ctx->barrier_selftest ? 1u : 0u);
+    args.budget = ctx->barrier_selftest ? kSelfTestBudget : kBarrierBudget;
+    args.selftest = ctx->barrier_selftest;
+    args.xc_deps = g->xc_deps;
+    args.xc_ndeps = g->xc_ndeps;
+    args.ready = args.bar + kReadyStride;
+    const int rpt = (args.rows_per_block + kThreads - 1) / kThreads;
+    const int sync = gs_persist_sync_choice(ctx, g);
+    const bool tagged_ok = sync == 2 && args.tagged &&
+                           2.0 * args.K * (double)args.iters + 2.0 < 4294967295.0;
+    if (args.smem_graph == 2 && rpt <= 4 && (tagged_ok || (sync == 1 && g->xc_deps))) {
+        void (*kern)(PersistArgs) = tagged_ok ? (rpt == 1   ? sinkhorn_tagged<1>
+                                                 : rpt == 2 ? sinkhorn_tagged<2>
+                                                            : sinkhorn_tagged<4>)
+                                              : (rpt == 1   ? sinkhorn_neighbour_sync<1>
+                                                 : rpt == 2 ? sinkhorn_neighbour_sync<2>
+                                                            : sinkhorn_neighbour_sync<4>);
+        if (tagged_ok)
+            cudaMemsetAsync(args.tagged, 0, sizeof(unsigned long long) * 3 * (size_t)args.n, ctx->stream);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) == cudaSuccess &&
+            per_sm >= 1) {
+            ctx->barrier_selftest = 0;
+            void* params[] = {&args};
+            const cudaError_t e = cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(kThreads),
+                                                              params, smem, ctx->stream);
+            if (e == cudaSuccess) {
+                gs_count(ctx, 1);
+                return GS_OK;
+            }
+        }
+        cudaGetLastError();
+    }
     if (smem) cudaFuncSetAttribute(sinkhorn_persistent<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sinkhorn_persistent<G>, kThreads, smem) !=
@@ -463,8 +816,6 @@ gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
         cudaGetLastError();
         return GS_ERR_UNSUPPORTED;
     }
-    args.expect = (unsigned)blocks + (ctx->barrier_selftest ? 1u : 0u);
-    args.budget = ctx->barrier_selftest ? kSelfTestBudget : kBarrierBudget;
     ctx->barrier_selftest = 0;
     void* params[] = {&args};
     cudaError_t e = cudaLaunchCooperativeKernel((void*)sinkhorn_persistent<G>, dim3(blocks),
@@ -480,11 +831,13 @@ gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
 }  // namespace
 
 // Enqueue the fixed-count loop as one persistent launch.  All vectors are in the filter's node
-// order; `coef_dev` holds K+1 FP32 coefficients; `bar` is two zeroed unsigned words.
+// order; `coef_dev` holds K+1 FP32 coefficients; `bar` has room for gs_persist_bar_words(ctx)
+// unsigned words (zeroed here); `tagged` (3 n words, or null) is the tagged-value kernel's exchange buffer.
 // Returns GS_ERR_UNSUPPORTED (nothing enqueued) when a cooperative launch is not possible.
 gs_status gs_sinkhorn_persistent(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
                                  const float* vol, const float* coef_dev, int K, int iters,
-                                 float* x, float* A, float* y, float* u, float* v, unsigned* bar)
+                                 float* x, float* A, float* y, float* u, float* v, unsigned* bar,
+                                 unsigned long long* tagged)
 {
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
@@ -511,7 +864,8 @@ gs_status gs_sinkhorn_persistent(gs_ctx* ctx, const gs_graph* g, const float* a,
     args.iters = iters;
     args.bar = bar;
     args.flags = ctx->flags;
-    cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), ctx->stream);
+    args.tagged = tagged;
+    cudaMemsetAsync(bar, 0, gs_persist_bar_words(ctx) * sizeof(unsigned), ctx->stream);
     const float m = g->mean_row;
     if (m <= 6.f) return launch_persistent<4>(ctx, g, args);
     if (m <= 14.f) return launch_persistent<8>(ctx, g, args);

@@ -6,7 +6,10 @@
 // sliced-ELL entries (sorted) and rewrites each entry's column as a 16-bit index into that list.
 // Per Chebyshev order the block then copies cur[] at its distinct columns into shared memory (one
 // load per distinct column, in increasing address order) and every nonzero reads its neighbour
-// value from shared memory.
+// value from shared memory.  The same pass lists, per block, the other blocks that own one of those
+// columns: the blocks whose results this block reads in every order (and, the pattern being
+// symmetric, the blocks that read this block's results), which is what the persistent loop waits
+// for between orders instead of a barrier over the whole grid.
 #include <stdint.h>
 
 #include "gs_internal.cuh"
@@ -14,20 +17,25 @@
 namespace {
 
 constexpr int kXcMaxEntries = 32768;  // sort capacity per block (and the 16-bit index range)
+constexpr int kXcMaxBlocks = 1024;    // partition blocks (one per SM)
 
 __global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ sptr,
                                                      const int* __restrict__ scol, int64_t nslices,
                                                      int rpb, int64_t n, int P,
                                                      int* __restrict__ ucol, int* __restrict__ ucnt,
-                                                     uint16_t* __restrict__ lidx)
+                                                     uint16_t* __restrict__ lidx,
+                                                     int* __restrict__ deps, int* __restrict__ ndeps)
 {
     extern __shared__ int keys[];  // [P]
     __shared__ int wsum[32];
+    __shared__ int mark[kXcMaxBlocks];
+    __shared__ int s_nd;
     const int tid = threadIdx.x, b = blockIdx.x;
     const int64_t r0 = (int64_t)b * rpb;
     const int64_t r1 = (r0 + rpb) < n ? (r0 + rpb) : n;
     if (r0 >= r1) {
         if (tid == 0) ucnt[b] = 0;
+        if (tid == 0) ndeps[b] = 0;
         return;
     }
     const int64_t s0 = r0 / GS_SELL_C;
@@ -37,10 +45,23 @@ __global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ spt
     const int E = e1 - e0;
     if (E > P) {  // sized from the largest block, so this cannot happen; never write past keys[]
         if (tid == 0) ucnt[b] = -1;
+        if (tid == 0) ndeps[b] = 0;
         return;
     }
-    for (int i = tid; i < P; i += blockDim.x) keys[i] = i < E ? scol[e0 + i] : 0x7fffffff;
+    __shared__ int s_bad;
+    if (tid == 0) s_bad = 0;
     __syncthreads();
+    for (int i = tid; i < P; i += blockDim.x) {
+        const int c = i < E ? scol[e0 + i] : 0x7fffffff;
+        if (i < E && (c < 0 || c >= n)) s_bad = 1;
+        keys[i] = c;
+    }
+    __syncthreads();
+    if (s_bad) {  // a column outside [0, n): no cache for this graph
+        if (tid == 0) ucnt[b] = -1;
+        if (tid == 0) ndeps[b] = 0;
+        return;
+    }
     // bitonic sort, ascending
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -99,6 +120,28 @@ __global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ spt
         }
         lidx[e] = (uint16_t)lo;
     }
+    // blocks owning one of the distinct columns (other than this one), in increasing order
+    const int nb = (int)gridDim.x;
+    for (int i = tid; i < nb; i += blockDim.x) mark[i] = 0;
+    if (tid == 0) s_nd = 0;
+    __syncthreads();
+    for (int i = tid; i < total; i += blockDim.x) {
+        const int o = ucol[e0 + i] / rpb;
+        if (o != b && o < nb) mark[o] = 1;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        for (int base = 0; base < nb; base += 32) {
+            const int i = base + tid;
+            const bool m = i < nb && mark[i];
+            const unsigned bal = __ballot_sync(0xffffffffu, m);
+            if (m) deps[(int64_t)b * nb + s_nd + __popc(bal & ((1u << tid) - 1u))] = i;
+            __syncwarp();
+            if (tid == 0) s_nd += __popc(bal);
+            __syncwarp();
+        }
+        if (tid == 0) ndeps[b] = s_nd;
+    }
 }
 
 }  // namespace
@@ -108,7 +151,7 @@ __global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ spt
 gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, int rpb)
 {
     g->xc_ok = false;
-    if (!g->sptr || g->sptr_host.empty() || blocks < 1) return GS_OK;
+    if (!g->sptr || g->sptr_host.empty() || blocks < 1 || blocks > kXcMaxBlocks) return GS_OK;
     const int64_t ns = g->nslices;
     int64_t worst = 0;
     for (int b = 0; b < blocks; ++b) {
@@ -125,6 +168,8 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, int rpb)
     cudaError_t e = cudaMalloc(&g->xc_ucol, sizeof(int) * tot);
     if (e == cudaSuccess) e = cudaMalloc(&g->xc_lidx, sizeof(uint16_t) * tot);
     if (e == cudaSuccess) e = cudaMalloc(&g->xc_ucnt, sizeof(int) * blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&g->xc_deps, sizeof(int) * (size_t)blocks * blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&g->xc_ndeps, sizeof(int) * blocks);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return GS_OK;  // the cache is an optimisation; run without it
@@ -132,7 +177,8 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, int rpb)
     cudaMemsetAsync(g->xc_ucol, 0, sizeof(int) * tot, ctx->stream);
     cudaFuncSetAttribute(xcache_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(P * sizeof(int)));
     xcache_build<<<blocks, 1024, P * sizeof(int), ctx->stream>>>(g->sptr, g->scol, ns, rpb, g->n, P,
-                                                                   g->xc_ucol, g->xc_ucnt, g->xc_lidx);
+                                                                   g->xc_ucol, g->xc_ucnt, g->xc_lidx,
+                                                                   g->xc_deps, g->xc_ndeps);
     gs_count(ctx, 1);
     g->xc_ucnt_host.assign((size_t)blocks, 0);
     cudaMemcpyAsync(g->xc_ucnt_host.data(), g->xc_ucnt, sizeof(int) * blocks, cudaMemcpyDeviceToHost,

@@ -54,6 +54,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0,
                     help="order-kernel variant (gs_set_option GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL)")
     ap.add_argument("--sweep", action="store_true", help="time every variant of the case")
+    ap.add_argument("--configs", default="0,0,2,2;0,0,2,1;0,0,2,0;0,0,1,0;1,6,1,0",
+                    help="with --sinkhorn: ';'-separated loop mode,kernel,smem graph,sync tuples")
     ap.add_argument("--sinkhorn", type=int, default=0,
                     help="also time this many Sinkhorn iterations in both loop modes (B = 1 cases)")
     ap.add_argument("--knn", action="store_true",
@@ -104,10 +106,11 @@ def main():
     if args.sinkhorn and c["B"] == 1:
         # loop modes x one-column kernel variants, interleaved three times, medians reported
         a = torch.full((c["n"],), 1.0 / c["n"], device=dev)
-        configs = [(0, 0, 2), (0, 0, 1), (0, 0, 0), (1, 6, 1)]  # (loop mode, kernel, smem graph)
+        configs = [tuple(int(x) for x in c.split(",")) for c in args.configs.split(";")]
         times = {cfg: [] for cfg in configs}
         for rnd in range(4):
-            for mode, var, sg in configs:
+            for mode, var, sg, sy in configs:
+                gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, sy)
                 gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
                 gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, var)
                 gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, sg)
@@ -120,17 +123,18 @@ def main():
                 torch.cuda.synchronize()
                 gs.gs_sync(ctx)
                 if rnd > 0:
-                    times[(mode, var, sg)].append(e0.elapsed_time(e1))
-        for (mode, var, sg), ts in times.items():
+                    times[(mode, var, sg, sy)].append(e0.elapsed_time(e1))
+        for (mode, var, sg, sy), ts in times.items():
             ms = sorted(ts)[len(ts) // 2]
             print(json.dumps({"case": args.case, "sinkhorn_loop_mode": mode, "b1_variant": var,
-                              "smem_graph": sg,
+                              "smem_graph": sg, "sync": sy,
                               "iters": args.sinkhorn, "ms_median": ms,
                               "iters_per_s": args.sinkhorn / (ms / 1e3),
                               "order_us": ms * 1e3 / (2 * c["K"] * args.sinkhorn)}), flush=True)
         gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
         gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
         gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
+        gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 1)
 
 if __name__ == "__main__":
     main()

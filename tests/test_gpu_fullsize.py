@@ -1,0 +1,102 @@
+"""Parity at the configured full sizes, in the launch configuration bench.py times, on what the
+oracle can compute row by row (kNN of sampled points) and on properties that hold at any size.
+
+  * 100k-point manifold in R^50, k = 15 (the Sinkhorn workload): kNN lists of 200 sampled rows equal
+    the oracle's brute-force lists; sigma is the median of the GPU's own kNN distances; the heat
+    filter (K = 30, t = 5) is symmetric; 500 Sinkhorn iterations reach the b-marginal exactly and
+    the a-marginal to the FP32 floor; loop modes agree bitwise.
+  * 200k-point cluster graph in R^30, k = 10, B = 32 (the barycenter workload): sampled kNN rows
+    exact; the barycenter is positive with the invariant sum_i alpha_i ln v_i = 0.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_00805_gb300 import workloads as W
+from tests.gpu_common import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    from paper_2211_00805_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(gs):
+    return gs.Context()
+
+
+def _sampled_knn_exact(gs, ctx, X, k, rows):
+    idx, dist = gs.gs_knn(ctx, to_dev(X), k)
+    ri, rd = oracle.knn(X.astype(np.float64), k, rows=rows)
+    gi = to_np(idx)[rows]
+    mism = np.nonzero(np.any(gi != ri, axis=1))[0]
+    for q in mism:  # only exact FP64 ties may swap places
+        dk = rd[q, -1]
+        for j in set(gi[q].tolist()) ^ set(ri[q].tolist()):
+            pos = np.nonzero(ri[q] == j)[0]
+            assert not len(pos) or abs(rd[q, pos[0]] - dk) <= 1e-6 * dk
+    np.testing.assert_allclose(to_np(dist)[rows][np.all(gi == ri, axis=1)],
+                               rd[np.all(gi == ri, axis=1)], rtol=1e-7)
+    return idx, dist
+
+
+def test_manifold_100k_full_size(gs, ctx):
+    p = W.manifold_pair()
+    rows = np.random.default_rng(1).choice(len(p.X), 200, replace=False)
+    idx, dist = _sampled_knn_exact(gs, ctx, p.X, p.k, rows)
+    g = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    assert g.sigma == pytest.approx(float(np.median(to_np(dist).astype(np.float64))), rel=1e-6)
+    # symmetry of p_K(L, t) at full size
+    rng = np.random.default_rng(2)
+    x, y = rng.random(g.n).astype(np.float32), rng.random(g.n).astype(np.float32)
+    Hx = to_np(gs.gs_heat_apply(ctx, g, p.t, p.K, to_dev(x))).astype(np.float64)
+    Hy = to_np(gs.gs_heat_apply(ctx, g, p.t, p.K, to_dev(y))).astype(np.float64)
+    assert abs(y @ Hx - x @ Hy) <= 1e-5 * abs(y @ Hx)
+    # Algorithm 1 at full size: exact nu-marginal after the w half-step, mu-marginal converged
+    a, b = to_dev(p.a), to_dev(p.b)
+    u, v, d, it = gs.gs_sinkhorn(ctx, g, a, b, p.t, p.K, p.iters)
+    gs.gs_sync(ctx)
+    Hu = gs.gs_heat_apply(ctx, g, p.t, p.K, u)
+    Hv = gs.gs_heat_apply(ctx, g, p.t, p.K, v)
+    marg_b = to_np(v * Hu).astype(np.float64)
+    marg_a = to_np(u * Hv).astype(np.float64)
+    assert np.abs(marg_b - p.b).sum() < 1e-5
+    assert np.abs(marg_a - p.a).sum() < 1e-5  # this pair converges well inside 500 iterations
+    assert np.isfinite(to_np(d)[0])
+    # both loop modes, in bench's configuration, give identical results
+    gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 1)
+    outs = []
+    for mode in (0, 1):
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
+        r = gs.gs_sinkhorn(ctx, g, a, b, p.t, p.K, 50)
+        outs.append(np.concatenate([to_np(r[0]), to_np(r[1]), to_np(r[2])]))
+    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
+    gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
+    gs.gs_sync(ctx)
+    assert np.array_equal(outs[0], outs[1], equal_nan=True)  # W is NaN where W^2 < 0
+
+
+def test_clusters_200k_full_size(gs, ctx):
+    cfg = W.clusters_barycenter()
+    X, M = cfg["X"], cfg["M"]
+    rows = np.random.default_rng(3).choice(len(X), 100, replace=False)
+    _sampled_knn_exact(gs, ctx, X, cfg["k"], rows)
+    g = gs.gs_build_graph(ctx, to_dev(X), cfg["k"])
+    V = torch.empty((g.n, M.shape[1]), dtype=torch.float32, device="cuda")
+    alpha = to_dev(cfg["alpha"], torch.float64)
+    mu = to_np(gs.gs_barycenter(ctx, g, to_dev(M), alpha, cfg["t"], cfg["K"], 20, v_state=V))
+    gs.gs_sync(ctx)
+    assert np.all(mu >= 0) and np.isfinite(mu).all() and mu.sum() > 0
+    # v_i <- v_i mu / d_i with mu = prod_i d_i^alpha_i and sum alpha = 1 keeps sum_i alpha_i ln v_i
+    # at its initial value 0 on every row where all scalings stay positive
+    Vn = to_np(V).astype(np.float64)
+    ok = np.all((Vn > 0) & np.isfinite(Vn), axis=1)
+    assert ok.mean() > 0.5
+    L = np.log(Vn[ok])
+    inv = L @ cfg["alpha"]
+    assert np.all(np.abs(inv) <= 1e-4 * (1 + np.abs(L).max(axis=1)))

@@ -308,35 +308,61 @@ def test_barycenter_matches_oracle(gs, ctx, m):
 
 
 # ------------------------------------------------------------------------- loop modes, faults
-def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph):
-    # both loop modes with the thread-per-row sliced-ELL kernel sum in the same order
+def _broad_pair(p):
+    # a broad bump (vMF, kappa = 1) and a mild tilt of it: with the one- and two-hop kernels of
+    # K = 1, 2 (zero between farther nodes) the scalings stay within e^{+-40}, inside FP32's range
+    ez = np.array([0.0, 0.0, 1.0])
+    a = W.vmf_bump(p.X, ez, 1.0)
+    b = a * (1.0 + 0.3 * p.X[:, 0])
+    return a, (b / b.sum()).astype(np.float32)
+
+
+@pytest.mark.parametrize("t,K", [(5.0, 30), (0.5, 1), (1.0, 2)])
+def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph, t, K):
+    # every persistent form (graph from global memory, slices in shared memory, gather cache with a
+    # grid barrier, neighbour flags or tagged values) and graph replay of the thread-per-row sliced-ELL kernel
+    # sum in the same order; K = 1 (the only order is first and last) and K = 2 are the edge cases
     p, g, Ls = sphere_graph
+    a, b = (p.a, p.b) if K > 2 else _broad_pair(p)
     out = {}
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 1)
-    for mode, smem in ((0, 1), (0, 0), (0, 2), (1, 1)):
+    for cfg in ((0, 1, 1), (0, 0, 1), (0, 2, 0), (0, 2, 1), (0, 2, 2), (1, 1, 1)):
+        mode, smem, sync = cfg
         gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
         gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, smem)
-        u, v, d, _ = gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 120)
+        gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, sync)
+        u, v, d, _ = gs.gs_sinkhorn(ctx, g, to_dev(a), to_dev(b), t, K, 120)
         gs.gs_sync(ctx)
-        out[(mode, smem)] = (to_np(u), to_np(v), to_np(d))
+        out[cfg] = (to_np(u), to_np(v), to_np(d))
     gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
     gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
-    for key in ((0, 0), (0, 2), (1, 1)):
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 1)
+    for key in out:
         for i in range(3):
-            np.testing.assert_array_equal(out[(0, 1)][i], out[key][i])
+            np.testing.assert_array_equal(out[(0, 1, 1)][i], out[key][i], err_msg=str(key))
 
 
-def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sphere_graph):
-    # the self-test makes every block wait for an arrival that never comes; the bounded wait runs
-    # out, the launch ends, gs_sync reports the timeout, and the next call works normally
+def test_sinkhorn_single_order_filter_matches_oracle(gs, ctx, sphere_graph):
+    # K = 1: H = c_0 I + c_1 P, positive for t = 0.5 (I_0(t) > 2 I_1(t)); persistent default path
     p, g, Ls = sphere_graph
+    a, b = _broad_pair(p)
+    _check_sinkhorn(gs, ctx, g, Ls, a, b, 0.5, 1, 60)
+
+
+@pytest.mark.parametrize("sync", [0, 1, 2])
+def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sphere_graph, sync):
+    # the self-test makes every block wait for an arrival (or a stage) that never comes; the
+    # bounded wait runs out, the launch ends, gs_sync reports the timeout, and the next call works
+    p, g, Ls = sphere_graph
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, sync)
     gs.gs_set_option(ctx, gs.GS_OPT_BARRIER_SELFTEST, 1)
     gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 10)
     with pytest.raises(gs.GeosinkError) as e:
         gs.gs_sync(ctx)
     assert e.value.status == gs.GS_ERR_TIMEOUT
     _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 50)
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 1)
 
 
 @pytest.mark.parametrize("B,option,variant", [(1, 3, 1), (1, 3, 2), (1, 3, 3), (1, 3, 5), (1, 3, 6), (1, 3, 7), (32, 4, 2),
