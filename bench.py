@@ -265,7 +265,8 @@ def run_ours(args, rank, world, local_rank):
     # choices are kept by the context and used by the timed steps' freshly built graphs
     gt = gs.gs_build_graph(ctx, X, cfg["k"])
     tuned = {"b1_kernel": gs.gs_autotune(ctx, gt, 1, cfg["K"]),
-             "loop_mode": gs.gs_get_option(ctx, gs.GS_OPT_LOOP)}
+             "loop_mode": gs.gs_get_option(ctx, gs.GS_OPT_LOOP),
+             "persist_sync": gs.gs_get_option(ctx, gs.GS_OPT_PERSIST_SYNC)}
     gt.close()
     for i in range(2):
         nnz = step(X, a, b)
@@ -303,7 +304,8 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peaks()
     if tuned["loop_mode"] == 0:
         tr = ncu_traffic("sinkhorn_persistent_manifold100k_500it", "persist.cu")
-        kern = {"kernel": "sinkhorn_persistent (whole 500-iteration loop, one cooperative launch)",
+        name = {0: "sinkhorn_persistent", 1: "sinkhorn_neighbour_sync", 2: "sinkhorn_tagged"}[tuned["persist_sync"]]
+        kern = {"kernel": f"{name} (whole 500-iteration loop, one cooperative launch)",
                 "bytes_per_launch": 2 * cfg["iters"] * per_apply, "launch_us": sink_s * 1e6}
     else:
         tr = ncu_traffic("order_b1_manifold100k")

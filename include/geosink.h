@@ -98,8 +98,12 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * with every row split across 4 threads (one column: the automatic choice), 7 sliced ELL with one
  * 1024-thread block per SM over one contiguous row range.  All variants compute the same
  * recurrence; they differ in summation order only. */
-/* GS_OPT_KNN_TENSOR: 1 (default) screens kNN distances with tensor-core 3xTF32 dot products when
- * d >= 16, 0 always uses FP32 CUDA-core dot products; the FP64 rerank makes both exact. */
+/* GS_OPT_KNN_TENSOR: how kNN distances are screened before the exact FP64 rerank.  2 (default):
+ * squared distances as one augmented 3xTF32 contraction on the fifth-generation tensor cores
+ * (tcgen05, operands by TMA multicast within CTA pairs, accumulators in tensor memory) when
+ * d <= 62; 1: warp-level TF32 MMA (3xTF32) when d >= 16; 0: FP32 CUDA-core dot products.  A
+ * choice the shape or device does not allow falls back to the next lower one; the rerank makes
+ * every choice exact. */
 /* GS_OPT_PERSIST_SMEM_GRAPH: how the persistent loop reads the operator.  2 (default): each
  * block's slices (values and 16-bit local column indices) are copied into shared memory once, and
  * every order first copies the block's distinct neighbour values into a shared-memory cache;
@@ -114,8 +118,12 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * 0: a barrier over the whole grid; 3 (default): the one gs_autotune measured fastest on the
  * graph (else on the context's last tuned graph, else 2).  Same arithmetic in all of them.  All
  * honour GS_OPT_BARRIER_SELFTEST. */
+/* GS_OPT_PERSIST_BLOCKS: blocks per SM of the gather-cache partition (1 = one 1024-thread block,
+ * default; 2 = two 512-thread blocks, so one block's exchange overlaps the other's sums), for the
+ * tagged-value and neighbour-flag forms.  Applies to graphs built after the call. */
 enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
-       GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6, GS_OPT_PERSIST_SYNC = 7 };
+       GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6, GS_OPT_PERSIST_SYNC = 7,
+       GS_OPT_PERSIST_BLOCKS = 8 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
 
 /* Host query of an option.  For GS_OPT_LOOP, GS_OPT_B1_KERNEL and GS_OPT_PERSIST_SYNC left on
@@ -165,6 +173,13 @@ gs_status gs_graph_from_csr(gs_ctx *ctx, int64_t n, const int64_t *rowptr, const
 /* Host query of a graph's size: n nodes, nnz stored off-diagonal entries, sigma used (0 for
  * graphs from gs_graph_from_csr).  Any output pointer may be NULL. */
 gs_status gs_graph_info(const gs_graph *g, int64_t *n, int64_t *nnz, double *sigma);
+
+/* Host query of the graph's execution layout (diagnostics; not in the paper).  Writes up to
+ * `count` values into `out`, in this order: 0 sliced-ELL slices, 1 sliced-ELL entries (with
+ * padding), 2 gather-cache tables built (0/1), 3 partition blocks, 4 rows of the largest block, 5 largest
+ * entry count of a block, 6 largest distinct-column count of a block, 7 sum of the blocks'
+ * distinct-column counts, 8 largest dependency-list length.  Errors: GS_ERR_ARG. */
+gs_status gs_graph_layout(const gs_graph *g, int64_t *out, int count);
 
 /* Copy the graph out in CSR form, rows in node order and columns ascending (device arrays:
  * rowptr [n+1] int64, col [nnz] int32, A [nnz] FP32 affinities, P [nnz] FP32 normalised

@@ -38,6 +38,7 @@ SIGNATURES = {
     "gs_build_graph": [_P, _P, _I64, _I, _I, _F, _P],
     "gs_graph_from_csr": [_P, _I64, _P, _P, _P, _P],
     "gs_graph_info": [_P, _P, _P, _P],
+    "gs_graph_layout": [_P, _P, ctypes.c_int],
     "gs_graph_export_csr": [_P, _P, _P, _P, _P, _P],
     "gs_autotune": [_P, _P, _I, _I, _P],
     "gs_graph_destroy": [_P],
@@ -168,6 +169,7 @@ GS_OPT_BLK_KERNEL = 4
 GS_OPT_KNN_TENSOR = 5
 GS_OPT_PERSIST_SMEM_GRAPH = 6
 GS_OPT_PERSIST_SYNC = 7
+GS_OPT_PERSIST_BLOCKS = 8
 
 
 def gs_set_option(ctx: Context, option: int, value: int):
@@ -228,6 +230,16 @@ def gs_autotune(ctx: Context, g: Graph, B: int, K: int) -> int:
     ch = ctypes.c_int()
     _raise(ctx, _lib.gs_autotune(ctx.handle, g.handle, int(B), int(K), ctypes.byref(ch)))
     return int(ch.value)
+
+
+GRAPH_LAYOUT_FIELDS = ("slices", "sell_entries", "cache_tables", "blocks", "rows_per_block",
+                       "max_block_entries", "max_block_distinct", "sum_block_distinct", "max_deps")
+
+
+def gs_graph_layout(g: Graph) -> dict:
+    out = (ctypes.c_int64 * len(GRAPH_LAYOUT_FIELDS))()
+    _raise(None, _lib.gs_graph_layout(g.handle, out, len(GRAPH_LAYOUT_FIELDS)))
+    return dict(zip(GRAPH_LAYOUT_FIELDS, list(out)))
 
 
 def gs_graph_export_csr(ctx: Context, g: Graph):

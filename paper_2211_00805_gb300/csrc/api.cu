@@ -167,11 +167,15 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->persist_smem_graph = value;
         return GS_OK;
     }
+    if (option == GS_OPT_PERSIST_BLOCKS && (value == 1 || value == 2)) {
+        ctx->persist_bps = value;
+        return GS_OK;
+    }
     if (option == GS_OPT_PERSIST_SYNC && (value >= 0 && value <= 3)) {
         ctx->persist_sync = value;
         return GS_OK;
     }
-    if (option == GS_OPT_KNN_TENSOR && (value == 0 || value == 1)) {
+    if (option == GS_OPT_KNN_TENSOR && (value >= 0 && value <= 2)) {
         ctx->knn_tensor_cores = value;
         return GS_OK;
     }
@@ -202,6 +206,7 @@ extern "C" gs_status gs_get_option(const gs_ctx* ctx, int option, int* value)
         case GS_OPT_KNN_TENSOR: *value = ctx->knn_tensor_cores; return GS_OK;
         case GS_OPT_PERSIST_SMEM_GRAPH: *value = ctx->persist_smem_graph; return GS_OK;
         case GS_OPT_PERSIST_SYNC: *value = gs_persist_sync_choice(ctx, nullptr); return GS_OK;
+        case GS_OPT_PERSIST_BLOCKS: *value = ctx->persist_bps; return GS_OK;
         default: return GS_ERR_ARG;
     }
 }
@@ -267,6 +272,17 @@ extern "C" gs_status gs_graph_info(const gs_graph* g, int64_t* n, int64_t* nnz, 
     return GS_OK;
 }
 
+extern "C" gs_status gs_graph_layout(const gs_graph* g, int64_t* out, int count)
+{
+    if (!g || !out || count < 0) return GS_ERR_ARG;
+    int64_t sum_u = 0;
+    for (int v : g->xc_ucnt_host) sum_u += v > 0 ? v : 0;
+    const int64_t v[9] = {g->nslices, g->sell_nnz, g->xc_ok ? 1 : 0, g->xc_blocks, g->xc_rpb,
+                          g->xc_max_e, g->xc_max_u, sum_u, g->xc_max_deps};
+    for (int i = 0; i < count && i < 9; ++i) out[i] = v[i];
+    return GS_OK;
+}
+
 extern "C" gs_status gs_graph_export_csr(gs_ctx* ctx, const gs_graph* g, int64_t* rowptr,
                                          int32_t* col, float* A, float* P)
 {
@@ -310,6 +326,7 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g)
     cudaFree(g->xc_lidx);
     cudaFree(g->xc_deps);
     cudaFree(g->xc_ndeps);
+    cudaFree(g->xc_rows);
     delete g;
     return GS_OK;
 }

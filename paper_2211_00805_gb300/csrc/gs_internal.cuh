@@ -57,7 +57,8 @@ struct gs_ctx {
     int barrier_selftest = 0;      // next persistent launch waits for an arrival that never comes
     int b1_kernel = 0;             // GS_KERNEL_* for one column
     int blk_kernel = 0;            // GS_KERNEL_* for several columns
-    int knn_tensor_cores = 1;      // kNN screen on tensor cores (3xTF32) for d >= 16
+    int knn_tensor_cores = 2;      // kNN screen: 2 tcgen05 (d <= 62), 1 warp-level MMA (d >= 16),
+                                   // 0 CUDA cores; each falls back to the next one it can use
     int tuned_b1 = 0;              // last gs_autotune result for one column (used by untuned graphs)
     int tuned_loop = 0;            // last gs_autotune loop choice (1 persistent, 2 graph replay)
     int persist_smem_graph = 2;    // persistent loop: 0 graph from global memory, 1 graph slices in
@@ -65,6 +66,8 @@ struct gs_ctx {
     int persist_sync = 3;          // persistent loop with the gather cache: 2 tagged values,
                                    // 1 neighbour flags, 0 grid barrier, 3 the autotuned choice
     int tuned_sync = -1;           // last gs_autotune choice of the above (0..2), -1 none
+    int persist_bps = 1;           // gather-cache partition of graphs built from now on: blocks per
+                                   // SM (1: 1024 threads each, 2: 512 threads each)
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::string err;
@@ -113,12 +116,15 @@ struct gs_graph {
     // blocks of xc_rpb rows, block b's distinct columns (sorted) at xc_ucol[entry offset of b],
     // their count xc_ucnt[b], and every entry's 16-bit index into that list
     bool xc_ok = false;
-    int xc_blocks = 0, xc_rpb = 0, xc_max_e = 0, xc_max_u = 0;
+    int xc_blocks = 0, xc_rpb = 0, xc_max_e = 0, xc_max_u = 0;  // xc_rpb: rows of the largest block
+    int* xc_rows = nullptr;              // [xc_blocks + 1] block b owns rows [xc_rows[b], xc_rows[b+1])
+    std::vector<int> xc_rows_host;
     int* xc_ucol = nullptr;
     int* xc_ucnt = nullptr;
     uint16_t* xc_lidx = nullptr;
     int* xc_deps = nullptr;   // [xc_blocks][xc_blocks]: block b's first xc_ndeps[b] entries are the
     int* xc_ndeps = nullptr;  // other blocks owning one of its distinct columns
+    int xc_max_deps = 0;
     std::vector<int> xc_ucnt_host;
 };
 
@@ -169,7 +175,7 @@ gs_status gs_graph_export(gs_ctx* ctx, const gs_graph* g, int64_t* rowptr, int32
 
 // --------------------------------------------------------------------- order.cu
 gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g);
-gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, int rpb);
+gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks);
 // rows per block of the persistent loop's partition (one block per SM, whole slices)
 // Block synchronisation of the persistent loop: the option if set, else the autotuned choice for
 // the graph, else the context's last one, else tagged values (the fastest on the graphs measured).
@@ -181,14 +187,19 @@ static inline int gs_persist_sync_choice(const gs_ctx* ctx, const gs_graph* g)
     return 2;
 }
 // Words of the persistent loop's synchronisation buffer: barrier counter and generation, then one
-// 128-byte line per block for its ready counter.
+// 128-byte line per block (up to two blocks per SM) for its ready counter.
 static inline size_t gs_persist_bar_words(const gs_ctx* ctx)
 {
-    return 32 * (1 + (size_t)(ctx->num_sms > 0 ? ctx->num_sms : 148));
+    return 32 * (1 + 2 * (size_t)(ctx->num_sms > 0 ? ctx->num_sms : 148));
 }
-static inline int gs_persist_rows_per_block(const gs_ctx* ctx, int64_t n)
+// Blocks of the gather-cache partition (one or two per SM) and rows per block (whole slices) when
+// n rows are split over `blocks` blocks.
+static inline int gs_persist_cache_blocks(const gs_ctx* ctx)
 {
-    const int blocks = ctx->num_sms > 0 ? ctx->num_sms : 148;
+    return (ctx->num_sms > 0 ? ctx->num_sms : 148) * ctx->persist_bps;
+}
+static inline int gs_persist_rows_per_block(const gs_ctx*, int64_t n, int blocks)
+{
     return (int)(((n + blocks - 1) / blocks + GS_SELL_C - 1) / GS_SELL_C * GS_SELL_C);
 }
 // dst[r, :] = src[perm[r], :] (to the filter's order) or dst[perm[r], :] = src[r, :] (back)
@@ -199,6 +210,12 @@ void gs_permute_rows(gs_ctx* ctx, int64_t n, int B, const int* perm, const float
 void gs_exclusive_scan(cudaStream_t s, const int* cnt, int64_t n, int64_t* out, int64_t* sums);
 gs_status gs_knn_launch(gs_ctx* ctx, const float* X, int64_t n, int d, int k, int32_t* idx,
                         float* dist, double* dist64);
+size_t gs_knn_ws_bytes(const gs_ctx* ctx, int64_t n, int d);
+// --------------------------------------------------------------------- knn_umma.cu
+size_t gs_knn_umma_bytes(int64_t n, int d);
+bool gs_knn_umma_available();
+gs_status gs_knn_screen_umma(gs_ctx* ctx, const float* X, const float* norms, int64_t n, int d,
+                             unsigned char* ws, int* cand);
 gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int k, float sigma,
                               gs_graph** out);
 

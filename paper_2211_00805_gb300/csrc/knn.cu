@@ -693,27 +693,57 @@ __global__ void rowptr_to32(int64_t n1, const int64_t* __restrict__ in, int* __r
 
 }  // namespace
 
+// Screen selection and the workspace the kNN stage takes from the front of the context's buffer:
+// 2 tensor-memory kernel (tcgen05; d + 2 <= 64), 1 warp-level TF32 MMA (d >= 16), 0 CUDA cores.
+struct KnnPlan {
+    WsPlan p;
+    size_t inorm = 0, icand = 0, ihi = 0, ilo = 0, iumma = 0;
+    int mode = 0;
+};
+
+static KnnPlan knn_plan(const gs_ctx* ctx, int64_t n, int d)
+{
+    KnnPlan k;
+    if (ctx->knn_tensor_cores == 2 && gs_knn_umma_bytes(n, d) > 0 && gs_knn_umma_available()) k.mode = 2;
+    else if (ctx->knn_tensor_cores >= 1 && d >= 16) k.mode = 1;
+    const int dp = (d + 7) / 8 * 8;
+    k.inorm = k.p.add(sizeof(float) * n);
+    k.icand = k.p.add(sizeof(int) * n * KK);
+    if (k.mode == 1) {
+        k.ihi = k.p.add(sizeof(float) * n * dp);
+        k.ilo = k.p.add(sizeof(float) * n * dp);
+    }
+    if (k.mode == 2) k.iumma = k.p.add(gs_knn_umma_bytes(n, d));
+    return k;
+}
+
+size_t gs_knn_ws_bytes(const gs_ctx* ctx, int64_t n, int d) { return knn_plan(ctx, n, d).p.total; }
+
 gs_status gs_knn_launch(gs_ctx* ctx, const float* X, int64_t n, int d, int k, int32_t* idx,
                         float* dist, double* dist64)
 {
-    const bool tc = d >= 16 && ctx->knn_tensor_cores;
+    const KnnPlan kp = knn_plan(ctx, n, d);
     const int dp = (d + 7) / 8 * 8;
-    WsPlan plan;
-    const size_t inorm = plan.add(sizeof(float) * n), icand = plan.add(sizeof(int) * n * KK);
-    const size_t ihi = tc ? plan.add(sizeof(float) * n * dp) : 0, ilo = tc ? plan.add(sizeof(float) * n * dp) : 0;
-    gs_status st = gs_ws_ensure(ctx, plan.total);
+    gs_status st = gs_ws_ensure(ctx, kp.p.total);
     if (st != GS_OK) return st;
-    float* norms = ws_at<float>(ctx, plan, inorm);
-    int* cand = ws_at<int>(ctx, plan, icand);
+    float* norms = ws_at<float>(ctx, kp.p, kp.inorm);
+    int* cand = ws_at<int>(ctx, kp.p, kp.icand);
     sq_norms<<<nblk(n, 256), 256, 0, ctx->stream>>>(X, n, d, norms);
-    if (tc) {
+    gs_count(ctx, 1);
+    bool screened = false;
+    if (kp.mode == 2) {
+        st = gs_knn_screen_umma(ctx, X, norms, n, d, ws_at<unsigned char>(ctx, kp.p, kp.iumma), cand);
+        if (st == GS_OK) screened = true;
+        else if (st != GS_ERR_UNSUPPORTED) return st;
+    }
+    if (!screened && kp.mode == 1) {
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(knn_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
             attr = true;
         }
-        float* hi = ws_at<float>(ctx, plan, ihi);
-        float* lo = ws_at<float>(ctx, plan, ilo);
+        float* hi = ws_at<float>(ctx, kp.p, kp.ihi);
+        float* lo = ws_at<float>(ctx, kp.p, kp.ilo);
         split_tf32<<<nblk(n * dp, 256), 256, 0, ctx->stream>>>(X, n, d, dp, hi, lo);
         switch (dp / 8) {
             case 2: launch_tc_reg<2>(ctx, hi, lo, norms, n, cand); break;
@@ -727,12 +757,14 @@ gs_status gs_knn_launch(gs_ctx* ctx, const float* X, int64_t n, int d, int k, in
                 knn_screen_tc<<<nblk(n, QT), 256, TC_SMEM, ctx->stream>>>(hi, lo, norms, (int)n, dp, cand);
         }
         gs_count(ctx, 2);
-    } else {
+        screened = true;
+    }
+    if (!screened) {
         knn_screen<<<nblk(n, QT), 256, 0, ctx->stream>>>(X, norms, (int)n, d, cand);
         gs_count(ctx, 1);
     }
     knn_rerank<<<nblk(n * 32, 256), 256, 0, ctx->stream>>>(X, (int)n, d, k, cand, idx, dist, dist64);
-    gs_count(ctx, 2);
+    gs_count(ctx, 1);
     return gs_cuda_check(ctx, cudaGetLastError(), "kNN launch");
 }
 
@@ -743,9 +775,7 @@ gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE + 1;
     // one workspace plan for every stage (the knn stage reuses the front of the workspace)
     WsPlan plan;
-    const int dp = (d + 7) / 8 * 8;
-    const size_t i_knn = plan.add(sizeof(float) * n + 256 + sizeof(int) * n * KK + 512 +
-                                  2 * (sizeof(float) * n * dp + 256));
+    const size_t i_knn = plan.add(gs_knn_ws_bytes(ctx, n, d));
     const size_t i_idx = plan.add(sizeof(int) * nk), i_d64 = plan.add(sizeof(double) * nk),
                  i_cnt = plan.add(sizeof(int) * n), i_cur = plan.add(sizeof(int) * n),
                  i_inp = plan.add(sizeof(int64_t) * (n + 1)), i_ins = plan.add(sizeof(int) * nk),

@@ -345,6 +345,6 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
     g->sptr_host.resize((size_t)ns + 1);
     cudaMemcpyAsync(g->sptr_host.data(), g->sptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost, s);
     if ((st = gs_cuda_check(ctx, cudaStreamSynchronize(s), "graph permutation")) != GS_OK) return st;
-    const int blocks = ctx->num_sms > 0 ? ctx->num_sms : 148;
-    return gs_graph_build_xcache(ctx, g, blocks, gs_persist_rows_per_block(ctx, n));
+    const int blocks = gs_persist_cache_blocks(ctx);
+    return gs_graph_build_xcache(ctx, g, blocks);
 }

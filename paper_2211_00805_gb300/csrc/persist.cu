@@ -55,6 +55,7 @@ struct PersistArgs {
     int rows_per_block;  // whole slices
     int smem_graph;      // 1: each block's slices of the sliced ELL are copied to shared memory once
                          // 2: values + 16-bit local column indices + the per-block gather cache
+    const int* xc_rows;  // smem_graph == 2: block b owns rows [xc_rows[b], xc_rows[b+1])
     const int* xc_ucol;  // gather cache tables (smem_graph == 2)
     const int* xc_ucnt;
     const uint16_t* xc_lidx;
@@ -371,7 +372,8 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_persistent(const PersistArg
     if (threadIdx.x == 0) s_ok = 1;
     __syncthreads();
     const int per = p.rows_per_block;
-    const int r0 = min(p.n, (int)blockIdx.x * per), r1 = min(p.n, r0 + per);
+    const int r0 = p.smem_graph == 2 ? __ldg(p.xc_rows + blockIdx.x) : min(p.n, (int)blockIdx.x * per);
+    const int r1 = p.smem_graph == 2 ? __ldg(p.xc_rows + blockIdx.x + 1) : min(p.n, r0 + per);
     int e0 = 0, ucnt = 0;
     int* scol_s = nullptr;
     float* sval_s = nullptr;
@@ -479,16 +481,15 @@ __device__ __forceinline__ void publish(const PersistArgs& p, unsigned stage)
     }
 }
 
-template <int RPT>
-__global__ void __launch_bounds__(kThreads) sinkhorn_neighbour_sync(const PersistArgs p)
+template <int RPT, int NT>
+__global__ void __launch_bounds__(NT) sinkhorn_neighbour_sync(const PersistArgs p)
 {
     __shared__ int s_ok;
     __shared__ __align__(8) unsigned long long s_mbar;
     extern __shared__ __align__(128) unsigned char p_smem[];
     if (threadIdx.x == 0) s_ok = 1;
     __syncthreads();
-    const int per = p.rows_per_block;
-    const int r0 = min(p.n, (int)blockIdx.x * per), r1 = min(p.n, r0 + per);
+    const int r0 = __ldg(p.xc_rows + blockIdx.x), r1 = __ldg(p.xc_rows + blockIdx.x + 1);
     const int emax = (p.xc_max_e + 31) / 32 * 32, umax = (p.xc_max_u + 31) / 32 * 32;
     float* sval_s = reinterpret_cast<float*>(p_smem);
     uint16_t* lidx_s = reinterpret_cast<uint16_t*>(p_smem + (size_t)emax * 4);
@@ -511,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_neighbour_sync(const Persis
     float av[RPT], bv[RPT], vv[RPT], xo[RPT], t1[RPT], t2[RPT], yo[RPT];
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
-        const int row = r0 + (int)threadIdx.x + j * kThreads;
+        const int row = r0 + (int)threadIdx.x + j * NT;
         off[j] = 0;
         width[j] = 0;
         av[j] = bv[j] = 0.f;
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_neighbour_sync(const Persis
     }
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
-        const int row = r0 + (int)threadIdx.x + j * kThreads;
+        const int row = r0 + (int)threadIdx.x + j * NT;
         if (row < r1) p.x[row] = xo[j];
     }
     unsigned stage = 0;
@@ -544,12 +545,12 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_neighbour_sync(const Persis
                 if (!wait_neighbours(p, dep, stage + extra, &s_ok)) return;
                 const float* src = (stage & 1) ? p.x : p.A;  // stage s - 1 lives in slot (s - 1) & 1
                 float* dst = (stage & 1) ? p.A : p.x;
-                for (int i = threadIdx.x; i < ucnt; i += kThreads) xc[i] = __ldcg(src + ucol_s[i]);
+                for (int i = threadIdx.x; i < ucnt; i += NT) xc[i] = __ldcg(src + ucol_s[i]);
                 __syncthreads();
                 const float ck = p.coef[k];
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) {
-                    const int row = r0 + (int)threadIdx.x + j * kThreads;
+                    const int row = r0 + (int)threadIdx.x + j * NT;
                     if (row >= r1) continue;
                     const float s = gs_sell_dot_cached(lidx_s + off[j], sval_s + off[j], width[j], xc);
                     float tk, acc;
@@ -612,16 +613,15 @@ __device__ __forceinline__ unsigned long long pack_tagged(float x, unsigned tag)
     return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(x);
 }
 
-template <int RPT>
-__global__ void __launch_bounds__(kThreads) sinkhorn_tagged(const PersistArgs p)
+template <int RPT, int NT>
+__global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
 {
     __shared__ int s_ok;
     __shared__ __align__(8) unsigned long long s_mbar;
     extern __shared__ __align__(128) unsigned char p_smem[];
     if (threadIdx.x == 0) s_ok = 1;
     __syncthreads();
-    const int per = p.rows_per_block;
-    const int r0 = min(p.n, (int)blockIdx.x * per), r1 = min(p.n, r0 + per);
+    const int r0 = __ldg(p.xc_rows + blockIdx.x), r1 = __ldg(p.xc_rows + blockIdx.x + 1);
     const int emax = (p.xc_max_e + 31) / 32 * 32, umax = (p.xc_max_u + 31) / 32 * 32;
     float* sval_s = reinterpret_cast<float*>(p_smem);
     uint16_t* lidx_s = reinterpret_cast<uint16_t*>(p_smem + (size_t)emax * 4);
@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_tagged(const PersistArgs p)
     float av[RPT], bv[RPT], vv[RPT], xo[RPT], t1[RPT], t2[RPT], yo[RPT];
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
-        const int row = r0 + (int)threadIdx.x + j * kThreads;
+        const int row = r0 + (int)threadIdx.x + j * NT;
         off[j] = 0;
         width[j] = 0;
         av[j] = bv[j] = 0.f;
@@ -669,16 +669,16 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_tagged(const PersistArgs p)
                 unsigned long long* dst = p.tagged + (size_t)wslot * n;
                 const unsigned want = stage + extra;  // stage - 1 carries tag stage
                 // issue up to 8 loads per thread before checking any tag
-                for (int i0 = threadIdx.x; i0 < ucnt; i0 += 8 * kThreads) {
+                for (int i0 = threadIdx.x; i0 < ucnt; i0 += 8 * NT) {
                     unsigned long long w[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const int i = i0 + u * kThreads;
+                        const int i = i0 + u * NT;
                         w[u] = i < ucnt ? ld_relaxed_u64(src + ucol_s[i]) : 0ull;
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const int i = i0 + u * kThreads;
+                        const int i = i0 + u * NT;
                         if (i >= ucnt) break;
                         if ((unsigned)(w[u] >> 32) != want) {
                             const long long t0 = clock64();
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_tagged(const PersistArgs p)
                 const float ck = p.coef[k];
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) {
-                    const int row = r0 + (int)threadIdx.x + j * kThreads;
+                    const int row = r0 + (int)threadIdx.x + j * NT;
                     if (row >= r1) continue;
                     const float s = gs_sell_dot_cached(lidx_s + off[j], sval_s + off[j], width[j], xc);
                     float tk, acc;
@@ -739,29 +739,76 @@ __global__ void __launch_bounds__(kThreads) sinkhorn_tagged(const PersistArgs p)
 
 constexpr int kSmemGraphMax = 200 * 1024;  // shared-memory budget for the resident graph slice
 
+template <int NT>
+void (*gather_cache_kernel(bool tagged, int rpt))(PersistArgs)
+{
+    if (tagged) return rpt == 1 ? sinkhorn_tagged<1, NT> : (rpt == 2 ? sinkhorn_tagged<2, NT> : sinkhorn_tagged<4, NT>);
+    return rpt == 1 ? sinkhorn_neighbour_sync<1, NT>
+                    : (rpt == 2 ? sinkhorn_neighbour_sync<2, NT> : sinkhorn_neighbour_sync<4, NT>);
+}
+
 template <int G>
 gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
 {
-    const int blocks = ctx->num_sms;  // one block of kThreads per SM
-    args.rows_per_block = gs_persist_rows_per_block(ctx, g->n);
-    // largest per-block entry range of the sliced ELL (host copy of its slice offsets)
-    size_t smem = 0;
-    args.smem_graph = 0;
+    args.xc_rows = g->xc_rows;
     args.xc_ucol = g->xc_ucol;
     args.xc_ucnt = g->xc_ucnt;
     args.xc_lidx = g->xc_lidx;
     args.xc_max_e = g->xc_max_e;
     args.xc_max_u = g->xc_max_u;
-    if (ctx->persist_smem_graph == 2 && g->xc_ok && g->xc_blocks == blocks &&
-        g->xc_rpb == args.rows_per_block) {
-        const size_t emax = (size_t)(g->xc_max_e + 31) / 32 * 32, umax = (size_t)(g->xc_max_u + 31) / 32 * 32;
-        const size_t need = emax * 6 + umax * 8;
-        if (need <= (size_t)kSmemGraphMax) {
-            smem = need;
+    args.budget = ctx->barrier_selftest ? kSelfTestBudget : kBarrierBudget;
+    args.selftest = ctx->barrier_selftest;
+    args.xc_deps = g->xc_deps;
+    args.xc_ndeps = g->xc_ndeps;
+    args.ready = args.bar + kReadyStride;
+    const size_t emax = (size_t)(g->xc_max_e + 31) / 32 * 32, umax = (size_t)(g->xc_max_u + 31) / 32 * 32;
+    const size_t cache_smem = emax * 6 + umax * 8;
+
+    // Gather-cache kernels with tagged-value or neighbour-flag synchronisation run on the cache
+    // tables' own partition: one block of 1024 threads per SM, or two of 512.
+    const int sync = gs_persist_sync_choice(ctx, g);
+    const bool tagged = sync == 2 && args.tagged && 2.0 * args.K * (double)args.iters + 2.0 < 4294967295.0;
+    const int bps = (g->xc_ok && ctx->num_sms > 0 && g->xc_blocks % ctx->num_sms == 0)
+                        ? g->xc_blocks / ctx->num_sms : 0;
+    if (ctx->persist_smem_graph == 2 && (bps == 1 || bps == 2) && (tagged || (sync == 1 && g->xc_deps))) {
+        const int nt = kThreads / bps;
+        const int rpt = (g->xc_rpb + nt - 1) / nt;
+        if (rpt <= 4 && cache_smem <= (size_t)kSmemGraphMax / bps) {
+            args.rows_per_block = g->xc_rpb;
             args.smem_graph = 2;
+            void (*kern)(PersistArgs) = bps == 1 ? gather_cache_kernel<kThreads>(tagged, rpt)
+                                                 : gather_cache_kernel<kThreads / 2>(tagged, rpt);
+            if (tagged)
+                cudaMemsetAsync(args.tagged, 0, sizeof(unsigned long long) * 3 * (size_t)args.n, ctx->stream);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cache_smem);
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, cache_smem) == cudaSuccess &&
+                per_sm >= bps) {
+                ctx->barrier_selftest = 0;
+                void* params[] = {&args};
+                const cudaError_t e = cudaLaunchCooperativeKernel((void*)kern, dim3(g->xc_blocks), dim3(nt),
+                                                                  params, cache_smem, ctx->stream);
+                if (e == cudaSuccess) {
+                    gs_count(ctx, 1);
+                    return GS_OK;
+                }
+            }
+            cudaGetLastError();
         }
     }
+
+    // Grid-barrier kernel: one 1024-thread block per SM over its own partition.
+    const int blocks = ctx->num_sms;
+    args.rows_per_block = gs_persist_rows_per_block(ctx, g->n, blocks);
+    args.expect = (unsigned)blocks + (ctx->barrier_selftest ? 1u : 0u);
+    size_t smem = 0;
+    args.smem_graph = 0;
+    if (ctx->persist_smem_graph == 2 && g->xc_ok && g->xc_blocks == blocks && cache_smem <= (size_t)kSmemGraphMax) {
+        smem = cache_smem;
+        args.smem_graph = 2;
+    }
     if (!args.smem_graph && g->sptr && !g->sptr_host.empty() && ctx->persist_smem_graph) {
+        // largest per-block entry range of the sliced ELL (host copy of its slice offsets)
         const int64_t ns = g->nslices;
         int64_t worst = 0;
         for (int b = 0; b < blocks; ++b) {
@@ -774,40 +821,6 @@ gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
             smem = need;
             args.smem_graph = 1;
         }
-    }
-    args.expect = (unsigned)blocks + (ctx->barrier_selftest ? 1u : 0u);
-    args.budget = ctx->barrier_selftest ? kSelfTestBudget : kBarrierBudget;
-    args.selftest = ctx->barrier_selftest;
-    args.xc_deps = g->xc_deps;
-    args.xc_ndeps = g->xc_ndeps;
-    args.ready = args.bar + kReadyStride;
-    const int rpt = (args.rows_per_block + kThreads - 1) / kThreads;
-    const int sync = gs_persist_sync_choice(ctx, g);
-    const bool tagged_ok = sync == 2 && args.tagged &&
-                           2.0 * args.K * (double)args.iters + 2.0 < 4294967295.0;
-    if (args.smem_graph == 2 && rpt <= 4 && (tagged_ok || (sync == 1 && g->xc_deps))) {
-        void (*kern)(PersistArgs) = tagged_ok ? (rpt == 1   ? sinkhorn_tagged<1>
-                                                 : rpt == 2 ? sinkhorn_tagged<2>
-                                                            : sinkhorn_tagged<4>)
-                                              : (rpt == 1   ? sinkhorn_neighbour_sync<1>
-                                                 : rpt == 2 ? sinkhorn_neighbour_sync<2>
-                                                            : sinkhorn_neighbour_sync<4>);
-        if (tagged_ok)
-            cudaMemsetAsync(args.tagged, 0, sizeof(unsigned long long) * 3 * (size_t)args.n, ctx->stream);
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) == cudaSuccess &&
-            per_sm >= 1) {
-            ctx->barrier_selftest = 0;
-            void* params[] = {&args};
-            const cudaError_t e = cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(kThreads),
-                                                              params, smem, ctx->stream);
-            if (e == cudaSuccess) {
-                gs_count(ctx, 1);
-                return GS_OK;
-            }
-        }
-        cudaGetLastError();
     }
     if (smem) cudaFuncSetAttribute(sinkhorn_persistent<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;

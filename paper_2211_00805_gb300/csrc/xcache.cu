@@ -1,7 +1,7 @@
 // Per-block gather cache for the persistent Sinkhorn loop.
 //
-// The persistent kernel gives block b the contiguous rows [b R, (b+1) R) (R a multiple of the
-// slice height).  In the one-column filter each nonzero gathers cur[col]; within one block many
+// The persistent kernel gives block b a contiguous range of whole slices of rows, [rows[b],
+// rows[b+1]), the ranges holding about equal numbers of sliced-ELL entries.  In the one-column filter each nonzero gathers cur[col]; within one block many
 // nonzeros share a column.  This pass lists, once per graph, the distinct columns of every block's
 // sliced-ELL entries (sorted) and rewrites each entry's column as a 16-bit index into that list.
 // Per Chebyshev order the block then copies cur[] at its distinct columns into shared memory (one
@@ -21,7 +21,7 @@ constexpr int kXcMaxBlocks = 1024;    // partition blocks (one per SM)
 
 __global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ sptr,
                                                      const int* __restrict__ scol, int64_t nslices,
-                                                     int rpb, int64_t n, int P,
+                                                     const int* __restrict__ rows, int64_t n, int P,
                                                      int* __restrict__ ucol, int* __restrict__ ucnt,
                                                      uint16_t* __restrict__ lidx,
                                                      int* __restrict__ deps, int* __restrict__ ndeps)
@@ -29,10 +29,14 @@ __global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ spt
     extern __shared__ int keys[];  // [P]
     __shared__ int wsum[32];
     __shared__ int mark[kXcMaxBlocks];
+    __shared__ int s_rows[kXcMaxBlocks + 1];
     __shared__ int s_nd;
     const int tid = threadIdx.x, b = blockIdx.x;
-    const int64_t r0 = (int64_t)b * rpb;
-    const int64_t r1 = (r0 + rpb) < n ? (r0 + rpb) : n;
+    const int nb = (int)gridDim.x;
+    for (int i = tid; i <= nb; i += blockDim.x) s_rows[i] = rows[i];
+    __syncthreads();
+    const int64_t r0 = s_rows[b];
+    const int64_t r1 = s_rows[b + 1];
     if (r0 >= r1) {
         if (tid == 0) ucnt[b] = 0;
         if (tid == 0) ndeps[b] = 0;
@@ -121,13 +125,18 @@ __global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ spt
         lidx[e] = (uint16_t)lo;
     }
     // blocks owning one of the distinct columns (other than this one), in increasing order
-    const int nb = (int)gridDim.x;
     for (int i = tid; i < nb; i += blockDim.x) mark[i] = 0;
     if (tid == 0) s_nd = 0;
     __syncthreads();
     for (int i = tid; i < total; i += blockDim.x) {
-        const int o = ucol[e0 + i] / rpb;
-        if (o != b && o < nb) mark[o] = 1;
+        const int c = ucol[e0 + i];
+        int lo = 0, hi = nb - 1;  // the block o with rows[o] <= c < rows[o + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_rows[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != b) mark[lo] = 1;
     }
     __syncthreads();
     if (tid < 32) {
@@ -146,20 +155,32 @@ __global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ spt
 
 }  // namespace
 
-// Build the cache tables for `blocks` blocks of `rpb` rows; leaves g->xc_ok false when a block has
-// more than kXcMaxEntries entries (the persistent kernel then gathers from global memory).
-gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, int rpb)
+// Build the cache tables for a partition of the rows into `blocks` contiguous ranges of whole
+// slices with about equal sliced-ELL entry counts (the per-order work of a block), so that no
+// block of the persistent loop lags its neighbours.  Leaves g->xc_ok false when a block has more
+// than kXcMaxEntries entries (the persistent loop then uses its other forms).
+gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
 {
     g->xc_ok = false;
     if (!g->sptr || g->sptr_host.empty() || blocks < 1 || blocks > kXcMaxBlocks) return GS_OK;
     const int64_t ns = g->nslices;
-    int64_t worst = 0;
+    const std::vector<int>& sp = g->sptr_host;
+    std::vector<int> rows((size_t)blocks + 1, 0);
+    const double total = (double)sp[(size_t)ns];
+    int64_t s = 0;
+    for (int b = 1; b < blocks; ++b) {
+        const double target = total * b / blocks;
+        while (s < ns && (double)sp[(size_t)s] < target) ++s;
+        rows[(size_t)b] = (int)std::min<int64_t>(g->n, s * GS_SELL_C);
+    }
+    rows[(size_t)blocks] = (int)g->n;
+    int64_t worst = 0, most_rows = 0;
     for (int b = 0; b < blocks; ++b) {
-        const int64_t r0 = (int64_t)b * rpb;
-        if (r0 >= g->n) break;
-        const int64_t r1 = std::min<int64_t>(g->n, r0 + rpb);
+        const int64_t r0 = rows[(size_t)b], r1 = rows[(size_t)b + 1];
+        if (r1 <= r0) continue;
         const int64_t s0 = r0 / GS_SELL_C, s1 = std::min<int64_t>(ns, (r1 + GS_SELL_C - 1) / GS_SELL_C);
-        worst = std::max<int64_t>(worst, (int64_t)g->sptr_host[s1] - g->sptr_host[s0]);
+        worst = std::max<int64_t>(worst, (int64_t)sp[(size_t)s1] - sp[(size_t)s0]);
+        most_rows = std::max<int64_t>(most_rows, r1 - r0);
     }
     if (worst > kXcMaxEntries || worst == 0) return GS_OK;
     int P = 1;
@@ -170,27 +191,34 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, int rpb)
     if (e == cudaSuccess) e = cudaMalloc(&g->xc_ucnt, sizeof(int) * blocks);
     if (e == cudaSuccess) e = cudaMalloc(&g->xc_deps, sizeof(int) * (size_t)blocks * blocks);
     if (e == cudaSuccess) e = cudaMalloc(&g->xc_ndeps, sizeof(int) * blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&g->xc_rows, sizeof(int) * ((size_t)blocks + 1));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return GS_OK;  // the cache is an optimisation; run without it
     }
+    g->xc_rows_host = rows;
+    cudaMemcpyAsync(g->xc_rows, g->xc_rows_host.data(), sizeof(int) * ((size_t)blocks + 1), cudaMemcpyHostToDevice,
+                    ctx->stream);
     cudaMemsetAsync(g->xc_ucol, 0, sizeof(int) * tot, ctx->stream);
     cudaFuncSetAttribute(xcache_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(P * sizeof(int)));
-    xcache_build<<<blocks, 1024, P * sizeof(int), ctx->stream>>>(g->sptr, g->scol, ns, rpb, g->n, P,
+    xcache_build<<<blocks, 1024, P * sizeof(int), ctx->stream>>>(g->sptr, g->scol, ns, g->xc_rows, g->n, P,
                                                                    g->xc_ucol, g->xc_ucnt, g->xc_lidx,
                                                                    g->xc_deps, g->xc_ndeps);
     gs_count(ctx, 1);
     g->xc_ucnt_host.assign((size_t)blocks, 0);
+    std::vector<int> nd((size_t)blocks, 0);
     cudaMemcpyAsync(g->xc_ucnt_host.data(), g->xc_ucnt, sizeof(int) * blocks, cudaMemcpyDeviceToHost,
                     ctx->stream);
+    cudaMemcpyAsync(nd.data(), g->xc_ndeps, sizeof(int) * blocks, cudaMemcpyDeviceToHost, ctx->stream);
     gs_status st = gs_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "gather-cache tables");
     if (st != GS_OK) return st;
     for (int v : g->xc_ucnt_host)
         if (v < 0) return GS_OK;
     g->xc_blocks = blocks;
-    g->xc_rpb = rpb;
+    g->xc_rpb = (int)most_rows;
     g->xc_max_e = (int)worst;
     g->xc_max_u = *std::max_element(g->xc_ucnt_host.begin(), g->xc_ucnt_host.end());
+    g->xc_max_deps = *std::max_element(nd.begin(), nd.end());
     g->xc_ok = true;
     return GS_OK;
 }

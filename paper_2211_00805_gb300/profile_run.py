@@ -58,16 +58,22 @@ def main():
                     help="with --sinkhorn: ';'-separated loop mode,kernel,smem graph,sync tuples")
     ap.add_argument("--sinkhorn", type=int, default=0,
                     help="also time this many Sinkhorn iterations in both loop modes (B = 1 cases)")
+    ap.add_argument("--n", type=int, default=0, help="override the case's point count")
+    ap.add_argument("--bps", default="1", help="with --sinkhorn: ','-separated GS_OPT_PERSIST_BLOCKS values "
+                    "(one graph built per value; timings interleaved)")
+    ap.add_argument("--knn-modes", default="2,1,0", help="with --knn: GS_OPT_KNN_TENSOR values to time")
     ap.add_argument("--knn", action="store_true",
                     help="time the kNN graph builder (tensor-core and CUDA-core screens) instead")
     args = ap.parse_args()
-    c = CASES[args.case]
+    c = dict(CASES[args.case])
+    if args.n:
+        c["n"] = args.n
     dev = torch.device("cuda", 0)
     ctx = gs.Context(0)
     if args.knn:
         X, _ = W.tanh_manifold(c["n"], c.get("latent", 10), c.get("ambient", 50), c["seed"])
         Xd = torch.from_numpy(X).to(dev)
-        for tensor in (1, 0):
+        for tensor in [int(m) for m in args.knn_modes.split(",")]:
             gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, tensor)
             gs.gs_knn(ctx, Xd, c["k"])
             for what, fn in (("knn", lambda: gs.gs_knn(ctx, Xd, c["k"])),
@@ -90,7 +96,13 @@ def main():
         X, Z = W.tanh_manifold(c["n"], c["latent"], c["ambient"], c["seed"])
     else:
         X, _ = W.cluster_curves(c["n"], c["dim"], seed=c["seed"])
-    g = gs.gs_build_graph(ctx, torch.from_numpy(X).to(dev), c["k"])
+    graphs = {}
+    for bps in [int(b) for b in args.bps.split(",")]:
+        gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_BLOCKS, bps)
+        graphs[bps] = gs.gs_build_graph(ctx, torch.from_numpy(X).to(dev), c["k"])
+        print(json.dumps({"case": args.case, "bps": bps, "layout": gs.gs_graph_layout(graphs[bps])}), flush=True)
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_BLOCKS, 1)
+    g = next(iter(graphs.values()))
     V = torch.rand((c["n"], c["B"]), generator=torch.Generator().manual_seed(0)).to(dev)
     Y = torch.empty_like(V)
     option = gs.GS_OPT_B1_KERNEL if c["B"] == 1 else gs.GS_OPT_BLK_KERNEL
@@ -106,10 +118,12 @@ def main():
     if args.sinkhorn and c["B"] == 1:
         # loop modes x one-column kernel variants, interleaved three times, medians reported
         a = torch.full((c["n"],), 1.0 / c["n"], device=dev)
-        configs = [tuple(int(x) for x in c.split(",")) for c in args.configs.split(";")]
+        configs = [(bps,) + tuple(int(x) for x in c.split(",")) for c in args.configs.split(";")
+                   for bps in graphs]
         times = {cfg: [] for cfg in configs}
         for rnd in range(4):
-            for mode, var, sg, sy in configs:
+            for bps, mode, var, sg, sy in configs:
+                g = graphs[bps]
                 gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, sy)
                 gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
                 gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, var)
@@ -123,11 +137,11 @@ def main():
                 torch.cuda.synchronize()
                 gs.gs_sync(ctx)
                 if rnd > 0:
-                    times[(mode, var, sg, sy)].append(e0.elapsed_time(e1))
-        for (mode, var, sg, sy), ts in times.items():
+                    times[(bps, mode, var, sg, sy)].append(e0.elapsed_time(e1))
+        for (bps, mode, var, sg, sy), ts in times.items():
             ms = sorted(ts)[len(ts) // 2]
             print(json.dumps({"case": args.case, "sinkhorn_loop_mode": mode, "b1_variant": var,
-                              "smem_graph": sg, "sync": sy,
+                              "smem_graph": sg, "sync": sy, "bps": bps,
                               "iters": args.sinkhorn, "ms_median": ms,
                               "iters_per_s": args.sinkhorn / (ms / 1e3),
                               "order_us": ms * 1e3 / (2 * c["K"] * args.sinkhorn)}), flush=True)

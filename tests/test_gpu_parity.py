@@ -334,10 +334,24 @@ def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph, t, K):
         u, v, d, _ = gs.gs_sinkhorn(ctx, g, to_dev(a), to_dev(b), t, K, 120)
         gs.gs_sync(ctx)
         out[cfg] = (to_np(u), to_np(v), to_np(d))
+    # the same graph partitioned into two 512-thread blocks per SM (tagged values, neighbour flags)
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_BLOCKS, 2)
+    try:
+        g2 = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_BLOCKS, 1)
+    assert gs.gs_graph_layout(g2)["blocks"] == 2 * gs.gs_graph_layout(g)["blocks"]
+    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 0)
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
+    for sync in (2, 1):
+        gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, sync)
+        u, v, d, _ = gs.gs_sinkhorn(ctx, g2, to_dev(a), to_dev(b), t, K, 120)
+        gs.gs_sync(ctx)
+        out[("bps2", sync)] = (to_np(u), to_np(v), to_np(d))
     gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
     gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
-    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 1)
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 3)
     for key in out:
         for i in range(3):
             np.testing.assert_array_equal(out[(0, 1, 1)][i], out[key][i], err_msg=str(key))
@@ -362,7 +376,7 @@ def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sp
         gs.gs_sync(ctx)
     assert e.value.status == gs.GS_ERR_TIMEOUT
     _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 50)
-    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 1)
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 3)
 
 
 @pytest.mark.parametrize("B,option,variant", [(1, 3, 1), (1, 3, 2), (1, 3, 3), (1, 3, 5), (1, 3, 6), (1, 3, 7), (32, 4, 2),
@@ -385,15 +399,52 @@ def test_kernel_variants_match_oracle(gs, ctx, B, option, variant):
         gs.gs_set_option(ctx, option, 0)
 
 
-@pytest.mark.parametrize("tensor", [1, 0])
+@pytest.mark.parametrize("tensor", [2, 1, 0])
 def test_knn_tensor_core_and_cuda_core_screens_exact(gs, ctx, tensor):
-    # d >= 16 screens on the tensor cores (3xTF32) unless disabled; both must give the oracle's lists
+    # 2: tcgen05 screen, 1: warp-level TF32 MMA, 0: CUDA cores; all must give the oracle's lists
     X, Z = W.tanh_manifold(3000, 8, 24, seed=9)
+    saved = gs.gs_get_option(ctx, gs.GS_OPT_KNN_TENSOR)
     gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, tensor)
     try:
         idx, dist = gs.gs_knn(ctx, to_dev(X), 12)
+        gs.gs_sync(ctx)
     finally:
-        gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, 1)
+        gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, saved)
     ri, rd = oracle.knn(X.astype(np.float64), 12)
     assert _edge_sets_match(to_np(idx), None, ri, rd) == 0
     np.testing.assert_allclose(to_np(dist), rd, rtol=1e-7)
+
+
+@pytest.mark.parametrize("n,d,k", [(2999, 50, 15), (1000, 62, 10), (777, 3, 10), (40, 30, 24), (30, 12, 20),
+                                   (130, 5, 8), (600, 70, 10)])
+def test_knn_tcgen05_screen_shapes_exact(gs, ctx, n, d, k):
+    # augmented width d + 2 in one or two 32-feature blocks, ragged last query / candidate tiles,
+    # fewer points than screened candidates, and d = 70 (beyond the kernel: falls back)
+    X = np.random.default_rng(n + d).standard_normal((n, d)).astype(np.float32)
+    saved = gs.gs_get_option(ctx, gs.GS_OPT_KNN_TENSOR)
+    gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, 2)
+    try:
+        idx, dist = gs.gs_knn(ctx, to_dev(X), k)
+        gs.gs_sync(ctx)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, saved)
+    ri, rd = oracle.knn(X.astype(np.float64), k)
+    assert _edge_sets_match(to_np(idx), None, ri, rd) == 0
+    np.testing.assert_allclose(to_np(dist), rd, rtol=1e-7)
+
+
+
+def test_knn_tcgen05_screen_exact_ties(gs, ctx):
+    # duplicated points give exactly tied distances, broken by index on both sides
+    base = np.random.default_rng(11).standard_normal((400, 20)).astype(np.float32)
+    X = np.concatenate([base, base, base[:150]])
+    saved = gs.gs_get_option(ctx, gs.GS_OPT_KNN_TENSOR)
+    gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, 2)
+    try:
+        idx, dist = gs.gs_knn(ctx, to_dev(X), 10)
+        gs.gs_sync(ctx)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, saved)
+    ri, rd = oracle.knn(X.astype(np.float64), 10)
+    assert np.array_equal(to_np(idx), ri)
+    np.testing.assert_allclose(to_np(dist), rd, rtol=1e-7, atol=1e-30)
