@@ -58,7 +58,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(b)) : "memory");
 }
-// Wait for the phase of parity `par` to complete; false when the budget runs out.
+// Wait for the phase of parity `par` to complete; false when the budget runs out.  Each try_wait
+// may suspend the thread in hardware until the phase completes (or a 20 us hint passes), so the
+// waiting producer and MMA threads take fewer issue slots from the epilogue warps.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned par)
 {
     const uint32_t a = su32(b);
@@ -66,10 +68,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned par)
     for (;;) {
         unsigned done;
         asm volatile(
-            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n"
             " selp.u32 %0, 1, 0, P;\n}\n"
             : "=r"(done)
-            : "r"(a), "r"(par)
+            : "r"(a), "r"(par), "r"(20000u)
             : "memory");
         if (done) return true;
         const long long t = clock64();
