@@ -121,9 +121,14 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
 /* GS_OPT_PERSIST_BLOCKS: blocks per SM of the gather-cache partition (1 = one 1024-thread block,
  * default; 2 = two 512-thread blocks, so one block's exchange overlaps the other's sums), for the
  * tagged-value and neighbour-flag forms.  Applies to graphs built after the call. */
+/* GS_OPT_TAG_WORD: the word of the tagged-value exchange (GS_OPT_PERSIST_SYNC 2).  4 (default):
+ * the FP32 value with its last mantissa bit carrying the stage parity, so the values one block
+ * reads from another may differ from the exact FP32 ones by one unit in the last place (results
+ * agree with the exact form to ~1e-8 relative, not bitwise); 8: exact FP32 value plus a 32-bit
+ * stage tag (results bitwise equal to the other loop forms), with twice the exchanged bytes. */
 enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
        GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6, GS_OPT_PERSIST_SYNC = 7,
-       GS_OPT_PERSIST_BLOCKS = 8 };
+       GS_OPT_PERSIST_BLOCKS = 8, GS_OPT_TAG_WORD = 9 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
 
 /* Host query of an option.  For GS_OPT_LOOP, GS_OPT_B1_KERNEL and GS_OPT_PERSIST_SYNC left on

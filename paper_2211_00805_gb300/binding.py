@@ -170,6 +170,7 @@ GS_OPT_KNN_TENSOR = 5
 GS_OPT_PERSIST_SMEM_GRAPH = 6
 GS_OPT_PERSIST_SYNC = 7
 GS_OPT_PERSIST_BLOCKS = 8
+GS_OPT_TAG_WORD = 9
 
 
 def gs_set_option(ctx: Context, option: int, value: int):

@@ -167,6 +167,10 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->persist_smem_graph = value;
         return GS_OK;
     }
+    if (option == GS_OPT_TAG_WORD && (value == 4 || value == 8)) {
+        ctx->tag_word = value;
+        return GS_OK;
+    }
     if (option == GS_OPT_PERSIST_BLOCKS && (value == 1 || value == 2)) {
         ctx->persist_bps = value;
         return GS_OK;
@@ -207,6 +211,7 @@ extern "C" gs_status gs_get_option(const gs_ctx* ctx, int option, int* value)
         case GS_OPT_PERSIST_SMEM_GRAPH: *value = ctx->persist_smem_graph; return GS_OK;
         case GS_OPT_PERSIST_SYNC: *value = gs_persist_sync_choice(ctx, nullptr); return GS_OK;
         case GS_OPT_PERSIST_BLOCKS: *value = ctx->persist_bps; return GS_OK;
+        case GS_OPT_TAG_WORD: *value = ctx->tag_word; return GS_OK;
         default: return GS_ERR_ARG;
     }
 }

@@ -66,6 +66,7 @@ struct gs_ctx {
     int persist_sync = 3;          // persistent loop with the gather cache: 2 tagged values,
                                    // 1 neighbour flags, 0 grid barrier, 3 the autotuned choice
     int tuned_sync = -1;           // last gs_autotune choice of the above (0..2), -1 none
+    int tag_word = 4;              // tagged-value exchange word: 4 (value with a parity bit) or 8 (exact)
     int persist_bps = 1;           // gather-cache partition of graphs built from now on: blocks per
                                    // SM (1: 1024 threads each, 2: 512 threads each)
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)

@@ -588,7 +588,9 @@ __global__ void __launch_bounds__(NT) sinkhorn_neighbour_sync(const PersistArgs 
 // Same loop and arithmetic again, with the readiness carried by the data itself: every published
 // value is one 64-bit word (FP32 bits low, stage + 1 high), written and read as a single-copy-
 // atomic 64-bit access, into one of three slots (stage s in slot s mod 3; the slots are zeroed
-// before the launch, so a tag of 0 is never a stage).  A block reading stage s - 1 simply re-reads
+// before the launch, so a tag of 0 is never a stage).  The default 4-byte form (W4) halves the
+// exchanged bytes, which is what the staging is bound by (scattered loads, one cache line per
+// few values): the tag is the stage parity in the value's last mantissa bit.  A block reading stage s - 1 simply re-reads
 // any word whose tag is not yet s: no counters, no fences, and no barrier of any kind between
 // blocks.  Three slots make the overwrite safe: the block writing stage s into a slot (which held
 // stage s - 3) has read stage s - 1 from every block it reads from, and each of those blocks had
@@ -613,7 +615,32 @@ __device__ __forceinline__ unsigned long long pack_tagged(float x, unsigned tag)
     return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(x);
 }
 
-template <int RPT, int NT>
+
+// 4-byte exchange words: the FP32 value with its last mantissa bit replaced by the stage parity
+// (at most one unit in the last place on the values other blocks read; the owner keeps the exact
+// value in registers).  Three slots still tell a stale word (stage s - 4) from the wanted one
+// (s - 1): their parities differ, and so does an early overwrite (s + 2).
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* a)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned* a, unsigned v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;\n" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned pack_tag32(float x, unsigned parity)
+{
+    return (__float_as_uint(x) & ~1u) | parity;
+}
+template <bool W4>
+__device__ __forceinline__ unsigned tag_of(unsigned long long w)
+{
+    return W4 ? (unsigned)(w & 1ull) : (unsigned)(w >> 32);
+}
+
+template <int RPT, int NT, bool W4>
 __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
 {
     __shared__ int s_ok;
@@ -634,6 +661,7 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
     if (r0 >= r1) return;  // no rows: nothing to publish, nothing to read
     const unsigned extra = p.selftest ? 1u : 0u;
     const size_t n = (size_t)p.n;
+    unsigned* tw = reinterpret_cast<unsigned*>(p.tagged);
 
     int off[RPT], width[RPT];
     float av[RPT], bv[RPT], vv[RPT], xo[RPT], t1[RPT], t2[RPT], yo[RPT];
@@ -655,7 +683,10 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
         }
         xo[j] = vv[j];  // vol * (v = 1)
         t1[j] = t2[j] = yo[j] = 0.f;
-        if (row < r1) st_relaxed_u64(p.tagged + row, pack_tagged(xo[j], 1u));  // stage 0, slot 0
+        if (row < r1) {  // stage 0, slot 0
+            if (W4) st_relaxed_u32(tw + row, pack_tag32(xo[j], 0u));
+            else st_relaxed_u64(p.tagged + row, pack_tagged(xo[j], 1u));
+        }
     }
     unsigned stage = 0;
     int rslot = 0, wslot = 1;  // slots of stage - 1 and stage (mod 3) inside the order loop
@@ -667,29 +698,35 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
                 ++stage;
                 const unsigned long long* src = p.tagged + (size_t)rslot * n;
                 unsigned long long* dst = p.tagged + (size_t)wslot * n;
-                const unsigned want = stage + extra;  // stage - 1 carries tag stage
+                const unsigned* src4 = tw + (size_t)rslot * n;
+                unsigned* dst4 = tw + (size_t)wslot * n;
+                // stage s - 1 carries tag s (8-byte words) or parity (s - 1) & 1 (4-byte words);
+                // the self-test waits for a tag no word will carry
+                const unsigned want = W4 ? (p.selftest ? 2u : ((stage - 1u) & 1u)) : stage + extra;
                 // issue up to 8 loads per thread before checking any tag
                 for (int i0 = threadIdx.x; i0 < ucnt; i0 += 8 * NT) {
                     unsigned long long w[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int i = i0 + u * NT;
-                        w[u] = i < ucnt ? ld_relaxed_u64(src + ucol_s[i]) : 0ull;
+                        w[u] = i >= ucnt ? 0ull : (W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i])
+                                                       : ld_relaxed_u64(src + ucol_s[i]));
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int i = i0 + u * NT;
                         if (i >= ucnt) break;
-                        if ((unsigned)(w[u] >> 32) != want) {
+                        if (tag_of<W4>(w[u]) != want) {
                             const long long t0 = clock64();
                             do {
-                                w[u] = ld_relaxed_u64(src + ucol_s[i]);
+                                w[u] = W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i])
+                                          : ld_relaxed_u64(src + ucol_s[i]);
                                 if (clock64() - t0 > p.budget) {
                                     atomicOr(p.flags, GS_FLAG_TIMEOUT);
                                     s_ok = 0;
                                     break;
                                 }
-                            } while ((unsigned)(w[u] >> 32) != want);
+                            } while (tag_of<W4>(w[u]) != want);
                         }
                         xc[i] = __uint_as_float((unsigned)w[u]);
                     }
@@ -727,7 +764,8 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
                         xo[j] = p.vol ? vv[j] * r : r;
                         pub = xo[j];
                     }
-                    st_relaxed_u64(dst + row, pack_tagged(pub, stage + 1u));
+                    if (W4) st_relaxed_u32(dst4 + row, pack_tag32(pub, stage & 1u));
+                    else st_relaxed_u64(dst + row, pack_tagged(pub, stage + 1u));
                 }
                 __syncthreads();  // xc is refilled by the next order
                 rslot = wslot;
@@ -739,10 +777,16 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
 
 constexpr int kSmemGraphMax = 200 * 1024;  // shared-memory budget for the resident graph slice
 
-template <int NT>
-void (*gather_cache_kernel(bool tagged, int rpt))(PersistArgs)
+template <int NT, bool W4>
+void (*tagged_kernel(int rpt))(PersistArgs)
 {
-    if (tagged) return rpt == 1 ? sinkhorn_tagged<1, NT> : (rpt == 2 ? sinkhorn_tagged<2, NT> : sinkhorn_tagged<4, NT>);
+    return rpt == 1 ? sinkhorn_tagged<1, NT, W4> : (rpt == 2 ? sinkhorn_tagged<2, NT, W4> : sinkhorn_tagged<4, NT, W4>);
+}
+
+template <int NT>
+void (*gather_cache_kernel(bool tagged, bool w4, int rpt))(PersistArgs)
+{
+    if (tagged) return w4 ? tagged_kernel<NT, true>(rpt) : tagged_kernel<NT, false>(rpt);
     return rpt == 1 ? sinkhorn_neighbour_sync<1, NT>
                     : (rpt == 2 ? sinkhorn_neighbour_sync<2, NT> : sinkhorn_neighbour_sync<4, NT>);
 }
@@ -776,10 +820,18 @@ gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
         if (rpt <= 4 && cache_smem <= (size_t)kSmemGraphMax / bps) {
             args.rows_per_block = g->xc_rpb;
             args.smem_graph = 2;
-            void (*kern)(PersistArgs) = bps == 1 ? gather_cache_kernel<kThreads>(tagged, rpt)
-                                                 : gather_cache_kernel<kThreads / 2>(tagged, rpt);
-            if (tagged)
+            const bool w4 = ctx->tag_word == 4;
+            void (*kern)(PersistArgs) = bps == 1 ? gather_cache_kernel<kThreads>(tagged, w4, rpt)
+                                                 : gather_cache_kernel<kThreads / 2>(tagged, w4, rpt);
+            if (tagged && !w4)  // 8-byte words: tag 0 is no stage
                 cudaMemsetAsync(args.tagged, 0, sizeof(unsigned long long) * 3 * (size_t)args.n, ctx->stream);
+            if (tagged && w4) {  // 4-byte words: slot k must not start with stage k's parity
+                unsigned* tw = reinterpret_cast<unsigned*>(args.tagged);
+                const size_t bytes = sizeof(unsigned) * (size_t)args.n;
+                cudaMemsetAsync(tw, 0x01, bytes, ctx->stream);
+                cudaMemsetAsync(tw + args.n, 0x00, bytes, ctx->stream);
+                cudaMemsetAsync(tw + 2 * (size_t)args.n, 0x01, bytes, ctx->stream);
+            }
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cache_smem);
             int per_sm = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, cache_smem) == cudaSuccess &&

@@ -68,17 +68,23 @@ def test_manifold_100k_full_size(gs, ctx):
     assert np.abs(marg_b - p.b).sum() < 1e-5
     assert np.abs(marg_a - p.a).sum() < 1e-5  # this pair converges well inside 500 iterations
     assert np.isfinite(to_np(d)[0])
-    # both loop modes, in bench's configuration, give identical results
+    # both loop modes, in bench's configuration, give identical results with exact exchange
+    # words; the default 4-byte words stay within one unit in the last place per exchanged value
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 1)
     outs = []
-    for mode in (0, 1):
+    for mode, word in ((0, 8), (1, 8), (0, 4)):
         gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
+        gs.gs_set_option(ctx, gs.GS_OPT_TAG_WORD, word)
         r = gs.gs_sinkhorn(ctx, g, a, b, p.t, p.K, 50)
         outs.append(np.concatenate([to_np(r[0]), to_np(r[1]), to_np(r[2])]))
     gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
+    gs.gs_set_option(ctx, gs.GS_OPT_TAG_WORD, 4)
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
     gs.gs_sync(ctx)
     assert np.array_equal(outs[0], outs[1], equal_nan=True)  # W is NaN where W^2 < 0
+    n2 = 2 * g.n
+    np.testing.assert_allclose(outs[2][:n2], outs[0][:n2], rtol=1e-4, atol=1e-6 * np.abs(outs[0][:n2]).max())
+    assert outs[2][n2] == pytest.approx(outs[0][n2], rel=1e-6)
 
 
 def test_clusters_200k_full_size(gs, ctx):

@@ -326,6 +326,7 @@ def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph, t, K):
     a, b = (p.a, p.b) if K > 2 else _broad_pair(p)
     out = {}
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 1)
+    gs.gs_set_option(ctx, gs.GS_OPT_TAG_WORD, 8)  # exact exchange words: bitwise comparable
     for cfg in ((0, 1, 1), (0, 0, 1), (0, 2, 0), (0, 2, 1), (0, 2, 2), (1, 1, 1)):
         mode, smem, sync = cfg
         gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
@@ -348,6 +349,11 @@ def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph, t, K):
         u, v, d, _ = gs.gs_sinkhorn(ctx, g2, to_dev(a), to_dev(b), t, K, 120)
         gs.gs_sync(ctx)
         out[("bps2", sync)] = (to_np(u), to_np(v), to_np(d))
+    # default 4-byte exchange words (values read across blocks within one unit in the last place)
+    gs.gs_set_option(ctx, gs.GS_OPT_TAG_WORD, 4)
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 2)
+    u4, v4, d4, _ = gs.gs_sinkhorn(ctx, g, to_dev(a), to_dev(b), t, K, 120)
+    gs.gs_sync(ctx)
     gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
     gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
@@ -355,6 +361,11 @@ def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph, t, K):
     for key in out:
         for i in range(3):
             np.testing.assert_array_equal(out[(0, 1, 1)][i], out[key][i], err_msg=str(key))
+    ref = out[(0, 1, 1)]
+    assert to_np(d4)[0] == pytest.approx(ref[2][0], rel=1e-6)
+    for got, want in ((to_np(u4), ref[0]), (to_np(v4), ref[1])):
+        m = want > 0
+        np.testing.assert_allclose(got[m], want[m], rtol=1e-4)
 
 
 def test_sinkhorn_single_order_filter_matches_oracle(gs, ctx, sphere_graph):
@@ -364,12 +375,13 @@ def test_sinkhorn_single_order_filter_matches_oracle(gs, ctx, sphere_graph):
     _check_sinkhorn(gs, ctx, g, Ls, a, b, 0.5, 1, 60)
 
 
-@pytest.mark.parametrize("sync", [0, 1, 2])
-def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sphere_graph, sync):
+@pytest.mark.parametrize("sync,word", [(0, 4), (1, 4), (2, 4), (2, 8)])
+def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sphere_graph, sync, word):
     # the self-test makes every block wait for an arrival (or a stage) that never comes; the
     # bounded wait runs out, the launch ends, gs_sync reports the timeout, and the next call works
     p, g, Ls = sphere_graph
     gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, sync)
+    gs.gs_set_option(ctx, gs.GS_OPT_TAG_WORD, word)
     gs.gs_set_option(ctx, gs.GS_OPT_BARRIER_SELFTEST, 1)
     gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 10)
     with pytest.raises(gs.GeosinkError) as e:
@@ -377,6 +389,7 @@ def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sp
     assert e.value.status == gs.GS_ERR_TIMEOUT
     _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 50)
     gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 3)
+    gs.gs_set_option(ctx, gs.GS_OPT_TAG_WORD, 4)
 
 
 @pytest.mark.parametrize("B,option,variant", [(1, 3, 1), (1, 3, 2), (1, 3, 3), (1, 3, 5), (1, 3, 6), (1, 3, 7), (32, 4, 2),
