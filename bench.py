@@ -100,7 +100,10 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
+        import threading
         self.proc = None
+        self.lines = []
+        self.first = threading.Event()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
@@ -108,16 +111,30 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            self.first.set()
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        # the sampler's start-up (NVML initialisation) must not overlap the timed region
+        self.first.wait(timeout=5.0)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line)
+            self.first.set()
+        self.first.set()
 
     def stop(self):
         if self.proc is None:
             return None
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        self.reader.join(timeout=5)
+        out = "".join(self.lines)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
@@ -272,8 +289,8 @@ def run_ours(args, rank, world, local_rank):
         nnz = step(X, a, b)
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank) if rank == 0 else None  # up and sampling before the barrier
     barrier()
-    clocks = ClockSampler(local_rank) if rank == 0 else None
     l0 = gs.gs_launch_count(ctx)
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
@@ -291,6 +308,9 @@ def run_ours(args, rank, world, local_rank):
     total_ms = t_start.elapsed_time(t_end)
     graph_ms = [e[0].elapsed_time(e[1]) for e in evs]
     sink_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    # span of every step, from its start to the next step's start (the last to the end event)
+    step_ms = [evs[i][0].elapsed_time(evs[i + 1][0]) for i in range(len(evs) - 1)]
+    step_ms.append(evs[-1][0].elapsed_time(t_end))
     total_ms = max_over_ranks(total_ms, world, dev)
     value = cfg["iters"] * args.steps * world / (total_ms / 1e3)
 
@@ -376,6 +396,7 @@ def run_ours(args, rank, world, local_rank):
                        "graph_build_ms": statistics.mean(graph_ms),
                        "sinkhorn_ms": statistics.mean(sink_ms),
                        "sinkhorn_only_iters_per_s": cfg["iters"] / sink_s,
+                       "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],
                        "W2": w2, "autotune": tuned},
             "roofline": roofline,
             "cpu_baseline": cpu,
