@@ -222,25 +222,13 @@ __global__ void __launch_bounds__(32 * kSchedWarps) sell_bank_schedule(const int
 
 }  // namespace
 
-// Build the cache tables for a partition of the rows into `blocks` contiguous ranges of whole
-// slices with about equal sliced-ELL entry counts (the per-order work of a block), so that no
-// block of the persistent loop lags its neighbours.  Leaves g->xc_ok false when a block has more
-// than kXcMaxEntries entries (the persistent loop then uses its other forms).
-gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
+// Build the cache tables for the partition `rows` (whole slices per block).  Leaves g->xc_ok false
+// when a block has more than kXcMaxEntries entries (the loop then uses its other forms).
+static gs_status build_tables(gs_ctx* ctx, gs_graph* g, const std::vector<int>& rows)
 {
-    g->xc_ok = false;
-    if (!g->sptr || g->sptr_host.empty() || blocks < 1 || blocks > kXcMaxBlocks) return GS_OK;
+    const int blocks = (int)rows.size() - 1;
     const int64_t ns = g->nslices;
     const std::vector<int>& sp = g->sptr_host;
-    std::vector<int> rows((size_t)blocks + 1, 0);
-    const double total = (double)sp[(size_t)ns];
-    int64_t s = 0;
-    for (int b = 1; b < blocks; ++b) {
-        const double target = total * b / blocks;
-        while (s < ns && (double)sp[(size_t)s] < target) ++s;
-        rows[(size_t)b] = (int)std::min<int64_t>(g->n, s * GS_SELL_C);
-    }
-    rows[(size_t)blocks] = (int)g->n;
     int64_t worst = 0, most_rows = 0;
     for (int b = 0; b < blocks; ++b) {
         const int64_t r0 = rows[(size_t)b], r1 = rows[(size_t)b + 1];
@@ -253,12 +241,13 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
     int P = 1;
     while (P < worst) P <<= 1;
     const size_t tot = (size_t)(g->sell_nnz > 0 ? g->sell_nnz : 1);
-    cudaError_t e = cudaMalloc(&g->xc_ucol, sizeof(int) * tot);
-    if (e == cudaSuccess) e = cudaMalloc(&g->xc_lidx, sizeof(uint16_t) * tot);
-    if (e == cudaSuccess) e = cudaMalloc(&g->xc_ucnt, sizeof(int) * blocks);
-    if (e == cudaSuccess) e = cudaMalloc(&g->xc_deps, sizeof(int) * (size_t)blocks * blocks);
-    if (e == cudaSuccess) e = cudaMalloc(&g->xc_ndeps, sizeof(int) * blocks);
-    if (e == cudaSuccess) e = cudaMalloc(&g->xc_rows, sizeof(int) * ((size_t)blocks + 1));
+    cudaError_t e = cudaSuccess;
+    if (!g->xc_ucol) e = cudaMalloc(&g->xc_ucol, sizeof(int) * tot);
+    if (e == cudaSuccess && !g->xc_lidx) e = cudaMalloc(&g->xc_lidx, sizeof(uint16_t) * tot);
+    if (e == cudaSuccess && !g->xc_ucnt) e = cudaMalloc(&g->xc_ucnt, sizeof(int) * blocks);
+    if (e == cudaSuccess && !g->xc_deps) e = cudaMalloc(&g->xc_deps, sizeof(int) * (size_t)blocks * blocks);
+    if (e == cudaSuccess && !g->xc_ndeps) e = cudaMalloc(&g->xc_ndeps, sizeof(int) * blocks);
+    if (e == cudaSuccess && !g->xc_rows) e = cudaMalloc(&g->xc_rows, sizeof(int) * ((size_t)blocks + 1));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return GS_OK;  // the cache is an optimisation; run without it
@@ -281,10 +270,6 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
     if (st != GS_OK) return st;
     for (int v : g->xc_ucnt_host)
         if (v < 0) return GS_OK;
-    // entries of each slice in bank-aware order (all readers of the sliced ELL follow it)
-    sell_bank_schedule<<<(unsigned)((ns + kSchedWarps - 1) / kSchedWarps), 32 * kSchedWarps, 0, ctx->stream>>>(
-        g->sptr, ns, g->scol, g->sval, g->xc_lidx);
-    gs_count(ctx, 1);
     g->xc_blocks = blocks;
     g->xc_rpb = (int)most_rows;
     g->xc_max_e = (int)worst;
@@ -292,4 +277,59 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
     g->xc_max_deps = *std::max_element(nd.begin(), nd.end());
     g->xc_ok = true;
     return GS_OK;
+}
+
+// Split whole slices into `blocks` contiguous ranges of about equal total weight.
+static std::vector<int> balanced_rows(const std::vector<double>& w, int64_t n, int blocks)
+{
+    const size_t ns = w.size();
+    std::vector<double> cum(ns + 1, 0.0);
+    for (size_t s = 0; s < ns; ++s) cum[s + 1] = cum[s] + w[s];
+    std::vector<int> rows((size_t)blocks + 1, 0);
+    size_t s = 0;
+    for (int b = 1; b < blocks; ++b) {
+        const double target = cum[ns] * b / blocks;
+        while (s < ns && cum[s] < target) ++s;
+        rows[(size_t)b] = (int)std::min<int64_t>(n, (int64_t)s * GS_SELL_C);
+    }
+    rows[(size_t)blocks] = (int)n;
+    return rows;
+}
+
+// Build the cache tables for a partition of the rows into `blocks` contiguous ranges of whole
+// slices with about equal per-order work, so that no block of the persistent loop lags its
+// neighbours.  A block's work is its sums (proportional to its sliced-ELL entries) plus its
+// staging (proportional to its distinct columns, about four times as costly per item, measured);
+// the distinct counts are known only once the tables exist, so the ranges are first balanced on
+// entries, then re-balanced on entries plus four times the block's distinct count spread over
+// its slices, and the tables rebuilt.  Then the entries of every slice are put in bank-aware order.
+gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
+{
+    g->xc_ok = false;
+    if (!g->sptr || g->sptr_host.empty() || blocks < 1 || blocks > kXcMaxBlocks) return GS_OK;
+    const int64_t ns = g->nslices;
+    const std::vector<int>& sp = g->sptr_host;
+    std::vector<double> w((size_t)ns);
+    for (int64_t i = 0; i < ns; ++i) w[(size_t)i] = (double)(sp[(size_t)i + 1] - sp[(size_t)i]);
+    gs_status st = build_tables(ctx, g, balanced_rows(w, g->n, blocks));
+    if (st != GS_OK || !g->xc_ok) return st;
+    constexpr double kStageWeight = 4.0;
+    for (int b = 0; b < blocks; ++b) {
+        const int64_t s0 = g->xc_rows_host[(size_t)b] / GS_SELL_C;
+        const int64_t s1 = std::min<int64_t>(ns, (g->xc_rows_host[(size_t)b + 1] + GS_SELL_C - 1) / GS_SELL_C);
+        const double eb = (double)(sp[(size_t)s1] - sp[(size_t)s0]);
+        if (eb <= 0.0) continue;
+        const double per_entry = kStageWeight * g->xc_ucnt_host[(size_t)b] / eb;
+        for (int64_t i = s0; i < s1; ++i) w[(size_t)i] *= 1.0 + per_entry;
+    }
+    const std::vector<int> rows = balanced_rows(w, g->n, blocks);
+    if (rows != g->xc_rows_host) {
+        g->xc_ok = false;
+        if ((st = build_tables(ctx, g, rows)) != GS_OK || !g->xc_ok) return st;
+    }
+    // entries of each slice in bank-aware order (all readers of the sliced ELL follow it)
+    sell_bank_schedule<<<(unsigned)((ns + kSchedWarps - 1) / kSchedWarps), 32 * kSchedWarps, 0, ctx->stream>>>(
+        g->sptr, ns, g->scol, g->sval, g->xc_lidx);
+    gs_count(ctx, 1);
+    return gs_cuda_check(ctx, cudaGetLastError(), "gather-cache tables");
 }
