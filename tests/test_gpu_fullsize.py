@@ -93,6 +93,12 @@ def test_clusters_200k_full_size(gs, ctx):
     rows = np.random.default_rng(3).choice(len(X), 100, replace=False)
     _sampled_knn_exact(gs, ctx, X, cfg["k"], rows)
     g = gs.gs_build_graph(ctx, to_dev(X), cfg["k"])
+    # the full-size cluster graph is connected (one component)
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    rowptr, col, A, P = gs.gs_graph_export_csr(ctx, g)
+    Ah = csr_matrix((to_np(A), to_np(col), to_np(rowptr)), shape=(g.n, g.n))
+    assert connected_components(Ah, directed=False)[0] == 1
     V = torch.empty((g.n, M.shape[1]), dtype=torch.float32, device="cuda")
     alpha = to_dev(cfg["alpha"], torch.float64)
     mu = to_np(gs.gs_barycenter(ctx, g, to_dev(M), alpha, cfg["t"], cfg["K"], 20, v_state=V))

@@ -15,6 +15,7 @@ import scipy.special as ss
 from scipy.spatial import cKDTree
 
 import oracle
+from paper_2211_00805_gb300 import workloads as W
 from tests.oracle_helpers import (bessel_tail_bound, csr_to_dense, dense_knn_laplacian, heat_eigh,
                                   heat_expm)
 
@@ -192,3 +193,16 @@ def test_laplacian_null_vector_and_spectrum():
     lam = np.linalg.eigvalsh(L)
     assert lam.min() > -1e-12 and lam.max() < 2 + 1e-12
     assert np.all(np.diag(L) == 1.0)
+
+
+def test_benchmark_graphs_are_connected():
+    # the cluster-curve workload is built so that consecutive clusters overlap: its kNN graph (and
+    # the manifold workload's) must have one connected component, or Sinkhorn has no transport
+    # between components and the barycenter is ill-posed
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    for X in (W.cluster_curves(4000, 30, seed=3)[0], W.tanh_manifold(4000, 10, 50, 2)[0]):
+        Ls, ex = oracle.build_graph(X.astype(np.float64), 10)
+        n = len(X)
+        A = csr_matrix((ex["A"], ex["col"], ex["rowptr"]), shape=(n, n))
+        assert connected_components(A, directed=False)[0] == 1
