@@ -55,20 +55,87 @@ struct BatchProblem {
 
 __device__ __forceinline__ int node_of(const BatchProblem& p, int r) { return p.perm ? p.perm[r] : r; }
 
+
+// Two sliced-ELL rows summed together: their column / value loads and gathers are issued side by
+// side, so one round trip to L2 serves both.  Each row's terms are added in exactly the order of
+// gs_sell_dot (full 8-entry blocks alternating between two partial sums, the rest sequentially
+// into the first), so the result equals gs_sell_row's bit for bit.
+__device__ __forceinline__ void sell_rows2(const BatchProblem& p, int row0, bool act0, int row1, bool act1,
+                                           const float* cur, float& out0, float& out1)
+{
+    const int rows[2] = {row0, row1};
+    const bool act[2] = {act0, act1};
+    const int* cp[2];
+    const float* vp[2];
+    int w[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int sl = act[r] ? rows[r] / GS_SELL_C : 0;
+        const int beg = act[r] ? __ldg(p.sptr + sl) : 0;
+        w[r] = act[r] ? (__ldg(p.sptr + sl + 1) - beg) / GS_SELL_C : 0;
+        cp[r] = p.scol + beg + (act[r] ? rows[r] % GS_SELL_C : 0);
+        vp[r] = p.sval + beg + (act[r] ? rows[r] % GS_SELL_C : 0);
+    }
+    float s0[2] = {0.f, 0.f}, s1[2] = {0.f, 0.f};
+    const int full0 = w[0] & ~7, full1 = w[1] & ~7;
+    const int fmax = full0 > full1 ? full0 : full1;
+    for (int j = 0; j < fmax; j += 4) {
+        int c[2][4];
+        float wv[2][4], x[2][4];
+        const bool go[2] = {j < full0, j < full1};
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[r][u] = go[r] ? __ldg(cp[r] + (j + u) * GS_SELL_C) : 0;
+                wv[r][u] = go[r] ? __ldg(vp[r] + (j + u) * GS_SELL_C) : 0.f;
+            }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[r][u] = go[r] ? cur[c[r][u]] : 0.f;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (!go[r]) continue;
+            s0[r] = fmaf(wv[r][0], x[r][0], s0[r]);
+            s1[r] = fmaf(wv[r][1], x[r][1], s1[r]);
+            s0[r] = fmaf(wv[r][2], x[r][2], s0[r]);
+            s1[r] = fmaf(wv[r][3], x[r][3], s1[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int full = r == 0 ? full0 : full1;
+        for (int j = full; j < w[r]; ++j) s0[r] = fmaf(__ldg(vp[r] + j * GS_SELL_C), cur[__ldg(cp[r] + j * GS_SELL_C)], s0[r]);
+    }
+    out0 = s0[0] + s1[0];
+    out1 = s0[1] + s1[1];
+}
+
 // One Chebyshev order over rows [r0, r1) of a problem (B = 1, kLanes lanes per row).
-// mode 0: first order, 1: middle, 2: last (epilogue: out = num / f, xnext = out).
+// mode 0: first order, 1: middle, 2: last (epilogue: out = num / f, xnext = out), 3: the only
+// order when K = 1 (first and last at once).
 __device__ void order_rows(const BatchProblem& p, int r0, int r1, int mode, float ck, float c0,
                            const float* cur, const float* prev, float* next, const float* num,
                            float* out, float* xnext, int* flags)
 {
     if (p.sptr) {  // thread per row over the sliced ELL copy; r0 is a multiple of the slice height
-        for (int row = r0 + (int)threadIdx.x; row < r1; row += blockDim.x) {
-            const float pv = (mode == 0) ? 0.f : prev[row];
-            const float yv = (mode == 0) ? c0 * cur[row] : p.y[row];
-            const float s = gs_sell_row<false>(p.sptr, p.scol, p.sval, cur, row);
-            const float tk = (mode == 0) ? s : fmaf(2.f, s, -pv);
+        // two rows per pass (row and row + blockDim.x), their gathers in flight together
+        for (int rowa = r0 + (int)threadIdx.x; rowa < r1; rowa += 2 * blockDim.x) {
+          const int rowb = rowa + (int)blockDim.x;
+          float sp[2];
+          sell_rows2(p, rowa, true, rowb, rowb < r1, cur, sp[0], sp[1]);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int row = q == 0 ? rowa : rowb;
+            if (row >= r1) continue;
+            const bool first = mode == 0 || mode == 3;
+            const float pv = first ? 0.f : prev[row];
+            const float yv = first ? c0 * cur[row] : p.y[row];
+            const float s = sp[q];
+            const float tk = first ? s : fmaf(2.f, s, -pv);
             const float acc = fmaf(ck, tk, yv);
-            if (mode != 2) {
+            if (mode < 2) {
                 next[row] = tk;
                 p.y[row] = acc;
             } else {
@@ -81,6 +148,7 @@ __device__ void order_rows(const BatchProblem& p, int r0, int r1, int mode, floa
                 out[row] = r;
                 xnext[row] = r;
             }
+          }
         }
         return;
     }
@@ -97,9 +165,10 @@ __device__ void order_rows(const BatchProblem& p, int r0, int r1, int mode, floa
 #pragma unroll
         for (int off = kLanes / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (!active || lane != 0) continue;
-        const float tk = (mode == 0) ? s : fmaf(2.f, s, -prev[row]);
-        const float acc = (mode == 0) ? fmaf(ck, tk, c0 * cur[row]) : fmaf(ck, tk, p.y[row]);
-        if (mode != 2) {
+        const bool first = mode == 0 || mode == 3;
+        const float tk = first ? s : fmaf(2.f, s, -prev[row]);
+        const float acc = first ? fmaf(ck, tk, c0 * cur[row]) : fmaf(ck, tk, p.y[row]);
+        if (mode < 2) {
             next[row] = tk;
             p.y[row] = acc;
         } else {
@@ -115,7 +184,7 @@ __device__ void order_rows(const BatchProblem& p, int r0, int r1, int mode, floa
     }
 }
 
-__global__ void __launch_bounds__(kThreads) batched_sinkhorn(const BatchProblem* __restrict__ probs,
+__global__ void __launch_bounds__(kThreads, 1) batched_sinkhorn(const BatchProblem* __restrict__ probs,
                                                              int nprob, int iters,
                                                              int* __restrict__ queue,
                                                              double* __restrict__ dist, int* flags)
@@ -145,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) batched_sinkhorn(const BatchProblem*
                 const float* num = h == 0 ? p.a : p.b;
                 float* out = h == 0 ? p.us : p.vs;
                 if (p.K == 1) {
-                    order_rows(p, r0, r1, 2, p.coef[1], p.coef[0], X, nullptr, nullptr, num, out, Ab, flags);
+                    order_rows(p, r0, r1, 3, p.coef[1], p.coef[0], X, nullptr, nullptr, num, out, Ab, flags);
                     cluster.sync();
                     float* t = X; X = Ab; Ab = t;
                     continue;

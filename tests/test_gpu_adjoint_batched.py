@@ -140,6 +140,30 @@ def test_batched_matches_single_and_oracle(gs, ctx):
         assert d[i, 0] == pytest.approx(r["W2"], rel=1e-4)
 
 
+def test_batched_single_order_filter(gs, ctx):
+    # K = 1 (the only order is first and last) and mixed K across the batch
+    probs = W.ragged_batch(count=3, n_min=500, n_max=1500, iters=20)
+    graphs = [gs.gs_build_graph(ctx, to_dev(p.X), p.k) for p in probs]
+    Ks = [1, 2, 5]
+    ts = [0.5, 1.0, 2.0]
+    # broad full-support marginals (one- and two-hop kernels keep the scalings in FP32 range)
+    ab = []
+    for p in probs:
+        a = np.full(len(p.X), 1.0 / len(p.X), np.float32)
+        b = (a * (1.0 + 0.3 * np.tanh(p.X[:, 0]))).astype(np.float32)
+        ab.append((a, b / b.sum()))
+    u, v, dist = gs.gs_sinkhorn_batched(ctx, graphs, [to_dev(a) for a, _ in ab], [to_dev(b) for _, b in ab],
+                                         ts, Ks, 20)
+    gs.gs_sync(ctx)
+    d = to_np(dist)
+    for i, (p, g) in enumerate(zip(probs, graphs)):
+        Ls, _ = oracle.build_graph(p.X.astype(np.float64), p.k)
+        r = oracle.sinkhorn(Ls, oracle.cheb_coefficients(ts[i], Ks[i]), ab[i][0].astype(np.float64),
+                            ab[i][1].astype(np.float64), ts[i], 20)
+        assert r["status"] == oracle.OK
+        assert d[i, 0] == pytest.approx(r["W2"], rel=1e-4)
+
+
 def test_autotune_choice_is_used_and_exact(gs, ctx, sphere):
     p, g, Ls = sphere
     for B in (1, 32):
