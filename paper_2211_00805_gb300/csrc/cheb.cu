@@ -235,6 +235,35 @@ struct VecT<1> {
     static __device__ __forceinline__ void load(const float* src, float (&v)[1]) { v[0] = __ldg(src); }
 };
 
+template <int VEC>
+__device__ __forceinline__ void stream_load(const float* src, float (&v)[VEC])
+{
+    if constexpr (VEC == 4) {
+        const float4 q = __ldcs(reinterpret_cast<const float4*>(src));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) v[i] = __ldcs(src + i);
+    }
+}
+
+template <int VEC, bool STREAM>
+__device__ __forceinline__ void store_vec(float* dst, const float (&v)[VEC])
+{
+    if constexpr (VEC == 4) {
+        const float4 q = make_float4(v[0], v[1], v[2], v[3]);
+        if (STREAM) __stcs(reinterpret_cast<float4*>(dst), q);
+        else *reinterpret_cast<float4*>(dst) = q;
+    } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+            if (STREAM) __stcs(dst + i, v[i]);
+            else dst[i] = v[i];
+        }
+    }
+}
+
+
 template <int VEC, int MAXCH>
 __device__ __forceinline__ void order_blk_row(const OrderArgs& p, int lpr_log2, int64_t row,
                                               bool active)
@@ -279,17 +308,25 @@ __device__ __forceinline__ void order_blk_row(const OrderArgs& p, int lpr_log2, 
             for (int v = 0; v < VEC; ++v) acc[v] = fmaf(w, x[v], acc[v]);
         }
         const int64_t base = row * (int64_t)B + c0;
+        // row-local streams (T_{k-2} and y read, T_k and y written, once per order) are marked
+        // evict-first, so they do not push the gathered neighbour rows out of L1 and L2
+        float pv[VEC], yv0[VEC];
+        if (p.first) {
+            stream_load<VEC>(p.cur + base, yv0);
+        } else {
+            stream_load<VEC>(p.prev + base, pv);
+            stream_load<VEC>(p.y + base, yv0);
+        }
+        float tk[VEC], yv[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-            const float tk = p.first ? acc[v] : fmaf(2.f, acc[v], -p.prev[base + v]);
-            const float yv = p.first ? fmaf(p.ck, tk, p.c0 * p.cur[base + v])
-                                     : fmaf(p.ck, tk, p.y[base + v]);
-            if (!p.last) {
-                p.next[base + v] = tk;
-                p.y[base + v] = yv;
-            } else {
-                f[ch][v] = yv;
-            }
+            tk[v] = p.first ? acc[v] : fmaf(2.f, acc[v], -pv[v]);
+            yv[v] = p.first ? fmaf(p.ck, tk[v], p.c0 * yv0[v]) : fmaf(p.ck, tk[v], yv0[v]);
+            f[ch][v] = yv[v];
+        }
+        if (!p.last) {
+            store_vec<VEC, true>(p.next + base, tk);
+            store_vec<VEC, true>(p.y + base, yv);
         }
     }
     if (!p.last) return;
