@@ -319,6 +319,7 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g)
     cudaFree(g->aval);
     cudaFree(g->deg);
     cudaFree(g->perm);
+    cudaFree(g->heavy);
     cudaFree(g->iperm);
     cudaFree(g->prowptr);
     cudaFree(g->pcol);

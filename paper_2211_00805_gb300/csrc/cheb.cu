@@ -43,6 +43,9 @@ struct OrderArgs {
     int last;
     const int* done;    // loop early-exit flag (eps stop) or null
     int* flags;         // status bits
+    const int* heavy = nullptr;  // B > 1 row-group kernel: rows longer than heavy_len, summed by
+    int64_t nheavy = 0;          // split warps
+    int heavy_len = 0;           // 0: no split, every row summed by its own lane group
     Epilogue epi;
 };
 
@@ -264,9 +267,14 @@ __device__ __forceinline__ void store_vec(float* dst, const float (&v)[VEC])
 }
 
 
+// One row of the row-group kernels: the row's lpr lanes each own VEC columns of every chunk of
+// lpr * VEC columns.  split = false: the lane group sums the whole row and skips rows longer than
+// p.heavy_len (the split warps take those).  split = true: every lane group of the warp is given
+// the same row and sums one contiguous segment of its entries; the segments' partial sums are then
+// added in segment order and the first group finishes the row.
 template <int VEC, int MAXCH>
 __device__ __forceinline__ void order_blk_row(const OrderArgs& p, int lpr_log2, int64_t row,
-                                              bool active)
+                                              bool active, bool split)
 {
     const int lpr = 1 << lpr_log2;
     const int lane = threadIdx.x & (lpr - 1);
@@ -275,15 +283,24 @@ __device__ __forceinline__ void order_blk_row(const OrderArgs& p, int lpr_log2, 
     if (active) {
         beg = __ldg(p.rowptr + row);
         end = __ldg(p.rowptr + row + 1);
+        if (!split && p.heavy_len > 0 && end - beg > p.heavy_len) active = false;
+    }
+    const int groups_log2 = split ? 5 - lpr_log2 : 0;
+    if (split && groups_log2 > 0) {
+        const int gi = (threadIdx.x & 31) >> lpr_log2;
+        const int seg = (end - beg + (1 << groups_log2) - 1) >> groups_log2;
+        const int sb = min(beg + gi * seg, end);
+        end = min(sb + seg, end);
+        beg = sb;
     }
     float f[MAXCH][VEC];
 #pragma unroll
     for (int ch = 0; ch < MAXCH; ++ch) {
-        const int c0 = (ch * lpr + lane) * VEC;
-        if (!active || c0 >= B) break;
-        float acc[VEC];
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+        for (int v = 0; v < VEC; ++v) f[ch][v] = 0.f;
+        const int c0 = (ch * lpr + lane) * VEC;
+        if (!active || c0 >= B) continue;
+        float* acc = f[ch];
         int e = beg;
         for (; e + 4 <= end; e += 4) {
             int j[4];
@@ -307,6 +324,26 @@ __device__ __forceinline__ void order_blk_row(const OrderArgs& p, int lpr_log2, 
 #pragma unroll
             for (int v = 0; v < VEC; ++v) acc[v] = fmaf(w, x[v], acc[v]);
         }
+    }
+    if (split && groups_log2 > 0) {
+        // the segments' partial sums, added in segment order (every lane gets its column's total)
+        const int li = (threadIdx.x & 31) & (lpr - 1);
+#pragma unroll
+        for (int ch = 0; ch < MAXCH; ++ch)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                float t = __shfl_sync(0xffffffffu, f[ch][v], li);
+                for (int gsrc = 1; gsrc < (1 << groups_log2); ++gsrc)
+                    t += __shfl_sync(0xffffffffu, f[ch][v], li + (gsrc << lpr_log2));
+                f[ch][v] = t;
+            }
+        if ((threadIdx.x & 31) >> lpr_log2) active = false;
+    }
+#pragma unroll
+    for (int ch = 0; ch < MAXCH; ++ch) {
+        const int c0 = (ch * lpr + lane) * VEC;
+        if (!active || c0 >= B) break;
+        const float* acc = f[ch];
         const int64_t base = row * (int64_t)B + c0;
         // row-local streams (T_{k-2} and y read, T_k and y written, once per order) are marked
         // evict-first, so they do not push the gathered neighbour rows out of L1 and L2
@@ -322,8 +359,9 @@ __device__ __forceinline__ void order_blk_row(const OrderArgs& p, int lpr_log2, 
         for (int v = 0; v < VEC; ++v) {
             tk[v] = p.first ? acc[v] : fmaf(2.f, acc[v], -pv[v]);
             yv[v] = p.first ? fmaf(p.ck, tk[v], p.c0 * yv0[v]) : fmaf(p.ck, tk[v], yv0[v]);
-            f[ch][v] = yv[v];
         }
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) f[ch][v] = yv[v];
         if (!p.last) {
             store_vec<VEC, true>(p.next + base, tk);
             store_vec<VEC, true>(p.y + base, yv);
@@ -394,12 +432,21 @@ __device__ __forceinline__ void order_blk_row(const OrderArgs& p, int lpr_log2, 
     }
 }
 
+// The first split_blocks blocks take the long rows (one warp each, dispatched first so that the
+// longest chains start first); the rest take every other row, 256 / lpr consecutive rows a block.
 template <int VEC, int MAXCH>
-__global__ void __launch_bounds__(256) order_blk(const OrderArgs p, int lpr_log2)
+__global__ void __launch_bounds__(256) order_blk(const OrderArgs p, int lpr_log2, int split_blocks)
 {
     if (p.done != nullptr && *p.done) return;
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> lpr_log2;
-    order_blk_row<VEC, MAXCH>(p, lpr_log2, row, row < p.n);
+    if ((int)blockIdx.x < split_blocks) {
+        const int64_t h = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+        const bool act = h < p.nheavy;
+        const int64_t row = act ? __ldg(p.heavy + h) : 0;
+        order_blk_row<VEC, MAXCH>(p, lpr_log2, row, act, true);
+        return;
+    }
+    const int64_t row = ((int64_t)(blockIdx.x - split_blocks) * blockDim.x + threadIdx.x) >> lpr_log2;
+    order_blk_row<VEC, MAXCH>(p, lpr_log2, row, row < p.n, false);
 }
 
 // Same rows, but each block walks one contiguous range of rows in passes, so that the rows an SM
@@ -415,7 +462,7 @@ __global__ void __launch_bounds__(256) order_blk_ranged(const OrderArgs p, int l
     b1 = b1 < p.n ? b1 : p.n;
     for (int64_t base = b0; base < b1; base += rpp) {
         const int64_t row = base + (threadIdx.x >> lpr_log2);
-        order_blk_row<VEC, MAXCH>(p, lpr_log2, row, row < b1);
+        order_blk_row<VEC, MAXCH>(p, lpr_log2, row, row < b1, false);
     }
 }
 
@@ -895,12 +942,22 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
         }
         return;
     }
+    // long rows go to split warps (8 to a block) in front of the regular blocks
+    OrderArgs sa = a;
+    int split_blocks = 0;
+    if (g->heavy != nullptr && g->nheavy > 0) {
+        sa.heavy = g->heavy;
+        sa.nheavy = g->nheavy;
+        sa.heavy_len = GS_HEAVY_ROW;
+        split_blocks = (int)((g->nheavy + 7) / 8);
+    }
+    const unsigned sgrid = grid + (unsigned)split_blocks;
     if (vec == 4) {
-        if (one) order_blk<4, 1><<<grid, TB, 0, ctx->stream>>>(a, lg);
-        else order_blk<4, 8><<<grid, TB, 0, ctx->stream>>>(a, lg);
+        if (one) order_blk<4, 1><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
+        else order_blk<4, 8><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
     } else {
-        if (one) order_blk<1, 1><<<grid, TB, 0, ctx->stream>>>(a, lg);
-        else order_blk<1, 8><<<grid, TB, 0, ctx->stream>>>(a, lg);
+        if (one) order_blk<1, 1><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
+        else order_blk<1, 8><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
     }
 }
 

@@ -15,6 +15,11 @@
 // words, one 32-byte sector).
 constexpr int GS_SELL_C = 32;
 
+// Rows with more than this many entries are summed by a whole warp (its lane groups splitting the
+// entry list) in the B > 1 filter, so that hub rows of high-dimensional kNN graphs do not set the
+// critical path of a launch.
+constexpr int GS_HEAVY_ROW = 32;
+
 // Kernel variants of the Chebyshev order (selected per context; the autotuner picks them).
 enum : int {
     GS_KERNEL_AUTO = 0,
@@ -98,6 +103,8 @@ struct gs_graph {
     int* pcol = nullptr;
     float* ppval = nullptr;
     int levels = 0;                // breadth-first levels of the ordering sweep
+    int* heavy = nullptr;          // [nheavy] rows (new order) with more than GS_HEAVY_ROW entries,
+    int64_t nheavy = 0;            // ascending; the B > 1 filter splits each across a warp
     // sliced ELL copy of the reordered P for the one-column kernels: GS_SELL_C-row slices, each
     // stored column-major and padded to its longest row (padding: column = the row itself, value 0)
     int* sptr = nullptr;           // [nslices + 1] offsets into scol / sval

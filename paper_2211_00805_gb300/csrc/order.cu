@@ -211,6 +211,19 @@ __global__ void permute_rows_kernel(int64_t count, int B, const int* __restrict_
     else dst[o] = src[i];
 }
 
+__global__ void heavy_flag(int64_t n, const int* __restrict__ prowptr, int len, int* __restrict__ flag)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = (prowptr[i + 1] - prowptr[i]) > len ? 1 : 0;
+}
+
+__global__ void heavy_place(int64_t n, const int* __restrict__ flag, const int64_t* __restrict__ pos,
+                            int* __restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[pos[i]] = (int)i;
+}
+
 __global__ void rowptr_narrow(int64_t n1, const int64_t* __restrict__ in, int* __restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -276,7 +289,8 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
     const size_t i_owner = plan.add(sizeof(int) * n), i_cnt = plan.add(sizeof(int) * n),
                  i_offs = plan.add(sizeof(int64_t) * (n + 1)),
                  i_sums = plan.add(sizeof(int64_t) * (n / 4096 + 2)), i_int = plan.add(sizeof(int) * 4),
-                 i_p64 = plan.add(sizeof(int64_t) * (n + 1));
+                 i_p64 = plan.add(sizeof(int64_t) * (n + 1)), i_hflag = plan.add(sizeof(int) * n),
+                 i_h64 = plan.add(sizeof(int64_t) * (n + 1));
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
     int* owner = ws_at<int>(ctx, plan, i_owner);
@@ -285,6 +299,8 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
     int64_t* sums = ws_at<int64_t>(ctx, plan, i_sums);
     int* sint = ws_at<int>(ctx, plan, i_int);
     int64_t* p64 = ws_at<int64_t>(ctx, plan, i_p64);
+    int* hflag = ws_at<int>(ctx, plan, i_hflag);
+    int64_t* h64 = ws_at<int64_t>(ctx, plan, i_h64);
 
     cudaError_t e = cudaMalloc(&g->perm, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMalloc(&g->iperm, sizeof(int) * n);
@@ -321,6 +337,12 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
     permute_fill<<<nblk(n, 128), 128, 0, s>>>(n, g->perm, g->iperm, g->rowptr, g->col, g->pval, p64,
                                               g->pcol, g->ppval);
     gs_count(ctx, 6);
+    // the long rows, ascending
+    heavy_flag<<<nblk(n, 256), 256, 0, s>>>(n, g->prowptr, GS_HEAVY_ROW, hflag);
+    gs_exclusive_scan(s, hflag, n, h64, sums);
+    gs_count(ctx, 4);
+    int64_t nheavy = 0;
+    cudaMemcpyAsync(&nheavy, h64 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     // sliced ELL of the permuted operator
     const int64_t ns = (n + GS_SELL_C - 1) / GS_SELL_C;
     sell_width<<<nblk(ns, 256), 256, 0, s>>>(n, ns, g->prowptr, cnt);
@@ -328,6 +350,15 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
     int64_t tot = 0;
     cudaMemcpyAsync(&tot, p64 + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if ((st = gs_cuda_check(ctx, cudaStreamSynchronize(s), "sliced ELL size")) != GS_OK) return st;
+    if (nheavy > 0) {
+        if (cudaMalloc(&g->heavy, sizeof(int) * nheavy) != cudaSuccess) {
+            cudaGetLastError();
+            return gs_fail(ctx, GS_ERR_OOM, "long-row list allocation failed");
+        }
+        heavy_place<<<nblk(n, 256), 256, 0, s>>>(n, hflag, h64, g->heavy);
+        gs_count(ctx, 1);
+        g->nheavy = nheavy;
+    }
     if (tot >= ((int64_t)1 << 31)) return GS_OK;  // too large for int32 offsets: CSR kernels only
     e = cudaMalloc(&g->sptr, sizeof(int) * (ns + 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->scol, sizeof(int) * (tot > 0 ? tot : 1));

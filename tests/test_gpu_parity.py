@@ -412,6 +412,61 @@ def test_kernel_variants_match_oracle(gs, ctx, B, option, variant):
         gs.gs_set_option(ctx, option, 0)
 
 
+def _hub_graph(n, seed):
+    """A kNN graph with hub rows added (degrees 40 to 400, far above the split threshold of the
+    B > 1 kernel), as high-dimensional kNN graphs have; symmetric, weights in (0, 1]."""
+    import scipy.sparse as sp
+    X, rp, col, A = _random_graph(n, 4, 9, seed)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    Msp = sp.csr_matrix((A, (rows, col)), shape=(n, n))
+    rng = np.random.default_rng(seed)
+    hubs = rng.choice(n, 8, replace=False)
+    hr, hc = [], []
+    for h, deg in zip(hubs, [40, 60, 97, 150, 233, 300, 333, 400]):
+        nb = rng.choice(np.setdiff1d(np.arange(n), [h]), deg, replace=False)
+        hr += [h] * deg
+        hc += list(nb)
+    H = sp.csr_matrix((rng.uniform(0.05, 1.0, len(hr)), (hr, hc)), shape=(n, n))
+    G = Msp.maximum(Msp.T).maximum(H).maximum(H.T).tocsr()
+    G.sort_indices()
+    return G.indptr.astype(np.int64), G.indices.astype(np.int32), G.data.astype(np.float64)
+
+
+@pytest.mark.parametrize("B", [2, 3, 8, 12, 32, 64, 128, 200])
+def test_long_rows_split_across_a_warp_match_oracle(gs, ctx, B):
+    # rows longer than the split threshold are summed by a whole warp in segments
+    rp, col, A = _hub_graph(3000, 71)
+    assert np.diff(rp).max() >= 400
+    g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
+    Ls, _ = _oracle_graph_fp32(rp, col, A)
+    V = np.random.default_rng(B).random((3000, B)).astype(np.float32)
+    for t, K in [(5.0, 30), (2.0, 1), (3.0, 2)]:
+        Y = to_np(gs.gs_heat_apply(ctx, g, t, K, to_dev(V)))
+        ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(t, K), V.astype(np.float64))
+        assert_close(Y, ref, HEAT_RTOL, HEAT_ATOL_REL * np.abs(ref).max(), f"B={B} K={K}")
+    Y1 = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
+    Y2 = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
+    assert np.array_equal(Y1, Y2)  # the segment order is fixed: repeatable bit for bit
+    gs.gs_sync(ctx)
+
+
+@pytest.mark.parametrize("m", [1, 32])
+def test_barycenter_on_hub_graph_matches_oracle(gs, ctx, m):
+    # the barycenter epilogue (geometric mean across the row's lanes) on split rows
+    rp, col, A = _hub_graph(3000, 72)
+    g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
+    Ls, _ = _oracle_graph_fp32(rp, col, A)
+    rng = np.random.default_rng(m)
+    M = rng.random((3000, m)) + 0.1
+    M = (M / M.sum(0)).astype(np.float32)
+    alpha = rng.dirichlet(np.ones(m))
+    t, K, iters = 5.0, 20, 10
+    mu = to_np(gs.gs_barycenter(ctx, g, to_dev(M), to_dev(alpha, torch.float64), t, K, iters))
+    gs.gs_sync(ctx)
+    ref = oracle.barycenter(Ls, oracle.cheb_coefficients(t, K), M.astype(np.float64), alpha, iters)
+    assert_close(mu, ref, 1e-4, 1e-6 * ref.max(), f"mu m={m}")
+
+
 @pytest.mark.parametrize("tensor", [2, 1, 0])
 def test_knn_tensor_core_and_cuda_core_screens_exact(gs, ctx, tensor):
     # 2: tcgen05 screen, 1: warp-level TF32 MMA, 0: CUDA cores; all must give the oracle's lists
