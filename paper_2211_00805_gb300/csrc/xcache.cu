@@ -154,6 +154,117 @@ __global__ void __launch_bounds__(1024) xcache_build(const int* __restrict__ spt
 }
 
 
+// Bank assignment of the gather-cache slots.  Slot i of a block's cache sits in shared-memory bank
+// i mod 32, and a slice's step conflicts where two lanes read different slots of one bank; no
+// order of the entries within the rows can do better than the slice's most-used bank.  The slots
+// of every aligned group of 32 distinct columns may be permuted freely: a warp's staging loads
+// still cover the same 32 columns (the same cache lines) and its staging stores still hit 32
+// distinct banks.  Within each group the columns with the most entries choose first, each taking
+// the free bank least used so far by the slices it occurs in, which evens out every slice's bank
+// counts.  Four warps take four consecutive groups per round against the counts of the rounds
+// before (so the result does not depend on timing), then add their choices to the counts.
+constexpr int kAssignMaxSlices = 64;  // blocks with more slices keep the sorted slots
+constexpr int kAssignWarps = 4;
+
+__global__ void __launch_bounds__(32 * kAssignWarps) xcache_bank_assign(const int* __restrict__ sptr, int64_t nslices,
+                                                                        const int* __restrict__ rows,
+                                                                        const int* __restrict__ ucnt,
+                                                                        int* __restrict__ ucol,
+                                                                        uint16_t* __restrict__ lidx)
+{
+    extern __shared__ int a_smem[];
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t r0 = rows[b], r1 = rows[b + 1];
+    const int U = ucnt[b];
+    if (r0 >= r1 || U <= 1) return;
+    const int64_t s0 = r0 / GS_SELL_C;
+    int64_t s1 = (r1 + GS_SELL_C - 1) / GS_SELL_C;
+    s1 = s1 < nslices ? s1 : nslices;
+    const int nsl = (int)(s1 - s0);
+    if (nsl > kAssignMaxSlices) return;
+    const int e0 = sptr[s0], E = sptr[s1] - e0;
+    int* off = a_smem;                                       // [U + 1] column -> its entries
+    int* cur = off + (U + 1);                                // [U] fill cursors, then new slots
+    unsigned* bank_use = reinterpret_cast<unsigned*>(cur + U);         // [nsl][32]
+    int* cost_s = reinterpret_cast<int*>(bank_use + nsl * 32);         // [kAssignWarps][32][32]
+    unsigned char* ent_slice = reinterpret_cast<unsigned char*>(cost_s + kAssignWarps * 1024);  // [E]
+    const int nt = 32 * kAssignWarps;
+    // the slices each column occurs in (with multiplicity), grouped by column
+    for (int i = tid; i <= U; i += nt) off[i] = 0;
+    for (int i = tid; i < nsl * 32; i += nt) bank_use[i] = 0;
+    __syncthreads();
+    for (int e = tid; e < E; e += nt) atomicAdd(&off[lidx[e0 + e] + 1], 1);
+    __syncthreads();
+    if (w == 0) {  // inclusive scan of off[1..U]
+        int carry = 0;
+        for (int base = 1; base <= U; base += 32) {
+            const int i = base + lane;
+            int v = i <= U ? off[i] : 0;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int o = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d) v += o;
+            }
+            if (i <= U) off[i] = v + carry;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < U; i += nt) cur[i] = off[i];
+    __syncthreads();
+    for (int sl = w; sl < nsl; sl += kAssignWarps) {
+        const int e1 = sptr[s0 + sl + 1] - e0;
+        for (int e = sptr[s0 + sl] - e0 + lane; e < e1; e += 32)
+            ent_slice[atomicAdd(&cur[lidx[e0 + e]], 1)] = (unsigned char)sl;
+    }
+    __syncthreads();
+    int* cost = cost_s + w * 1024;  // [column in group][bank]
+    for (int r0g = 0; r0g < U; r0g += 32 * kAssignWarps) {
+        const int g0 = r0g + 32 * w;
+        const int k = g0 < U ? min(32, U - g0) : 0;
+        const int my = g0 + lane;
+        int bank = lane;
+        if (k > 0) {
+            // every column's cost per bank against the counts of the earlier rounds
+            for (int c = 0; c < k; ++c) {
+                int sum = 0;
+                for (int q = off[g0 + c]; q < off[g0 + c + 1]; ++q) sum += (int)bank_use[ent_slice[q] * 32 + lane];
+                cost[c * 32 + lane] = sum;
+            }
+            // rank of this lane's column: more entries first, ties to the lower column
+            const int weight = lane < k ? off[my + 1] - off[my] : -1;
+            int rank = 0;
+            for (int j = 0; j < 32; ++j) {
+                const int wj = __shfl_sync(0xffffffffu, weight, j);
+                rank += (wj > weight) || (wj == weight && j < lane);
+            }
+            __syncwarp();
+            unsigned freeb = k == 32 ? 0xffffffffu : ((1u << k) - 1u);
+            for (int it = 0; it < k; ++it) {
+                const int col = __ffs(__ballot_sync(0xffffffffu, rank == it)) - 1;
+                int key = ((freeb >> lane) & 1u) ? (cost[col * 32 + lane] << 5) | lane : 0x7fffffff;
+                for (int d = 16; d > 0; d >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, d));
+                const int bk = key & 31;
+                if (lane == col) bank = bk;
+                freeb &= ~(1u << bk);
+            }
+        }
+        __syncthreads();
+        if (lane < k) {
+            for (int q = off[my]; q < off[my + 1]; ++q) atomicAdd(&bank_use[ent_slice[q] * 32 + bank], 1u);
+        }
+        // move the group's columns to their slots; cur[] maps old slot -> new slot
+        const int c = lane < k ? ucol[e0 + my] : 0;
+        __syncwarp();
+        if (lane < k) {
+            ucol[e0 + g0 + bank] = c;
+            cur[my] = g0 + bank;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < E; e += nt) lidx[e0 + e] = (uint16_t)cur[lidx[e0 + e]];
+}
+
 // Bank-aware order of the entries of every 32-row slice.  In the persistent loop a warp sums one
 // slice, lane = row, step j = the j-th stored entry of every row, reading the neighbour value from
 // the block's gather cache at its 16-bit local index; lanes whose indices share a shared-memory
@@ -327,7 +438,25 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
         g->xc_ok = false;
         if ((st = build_tables(ctx, g, rows)) != GS_OK || !g->xc_ok) return st;
     }
-    // entries of each slice in bank-aware order (all readers of the sliced ELL follow it)
+    // cache slots spread over the banks, then the entries of each slice in bank-aware order (all
+    // readers of the sliced ELL follow it)
+    {
+        int max_sl = 0;
+        for (int b = 0; b < blocks; ++b) {
+            const int64_t s0 = g->xc_rows_host[(size_t)b] / GS_SELL_C;
+            const int64_t s1 = std::min<int64_t>(ns, (g->xc_rows_host[(size_t)b + 1] + GS_SELL_C - 1) / GS_SELL_C);
+            max_sl = std::max<int>(max_sl, (int)(s1 - s0));
+        }
+        const size_t smem = sizeof(int) * (2 * (size_t)g->xc_max_u + 1) +
+                            sizeof(unsigned) * 32 * (size_t)std::min(max_sl, kAssignMaxSlices) +
+                            sizeof(int) * kAssignWarps * 1024 + (size_t)g->xc_max_e + 16;
+        if (smem <= 200 * 1024) {
+            cudaFuncSetAttribute(xcache_bank_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            xcache_bank_assign<<<blocks, 32 * kAssignWarps, smem, ctx->stream>>>(g->sptr, ns, g->xc_rows, g->xc_ucnt,
+                                                                 g->xc_ucol, g->xc_lidx);
+            gs_count(ctx, 1);
+        }
+    }
     sell_bank_schedule<<<(unsigned)((ns + kSchedWarps - 1) / kSchedWarps), 32 * kSchedWarps, 0, ctx->stream>>>(
         g->sptr, ns, g->scol, g->sval, g->xc_lidx);
     gs_count(ctx, 1);
