@@ -268,66 +268,212 @@ __global__ void __launch_bounds__(32 * kAssignWarps) xcache_bank_assign(const in
 // Bank-aware order of the entries of every 32-row slice.  In the persistent loop a warp sums one
 // slice, lane = row, step j = the j-th stored entry of every row, reading the neighbour value from
 // the block's gather cache at its 16-bit local index; lanes whose indices share a shared-memory
-// bank (index mod 32) serialise.  The entries of a row may be summed in any order, so each row's
-// entries are permuted across the steps: step by step, lane by lane, every lane takes the
-// remaining entry whose bank is least used at that step so far (ties: the earlier entry).  For
-// random banks this lowers the expected bank multiplicity per step from ~3.5 to ~2.1.  Column,
-// value and local index move together, so every kernel reading the sliced ELL sums each row in
-// the same (new) order.
+// bank (index mod 32) serialise.  The entries of a row may be summed in any order, so the steps
+// are a free choice: an assignment of steps to the entries in which every row uses each step once
+// and, ideally, every bank at most once per step.  That is an edge colouring of the bipartite
+// multigraph rows x banks with as many colours as the slice is wide, which exists whenever no
+// bank has more entries than that (Koenig's edge-colouring theorem); the construction adds the
+// edges one at a time, and where no colour is free at both ends it swaps the two colours along
+// the alternating path from the bank end (Kempe chain), which in a bipartite graph never reaches
+// the row end.  Entries beyond a full bank take any colour left free at their row (a conflict).
+// One thread per slice; the steps go to `step`, and a second pass moves column, value and local
+// index together, so every kernel reading the sliced ELL sums each row in the same (new) order.
 constexpr int kSchedMaxWidth = 64;
-constexpr int kSchedWarps = 2;  // 45 KB of static shared memory per block
+constexpr unsigned char kNone = 0xff;
 
-__global__ void __launch_bounds__(32 * kSchedWarps) sell_bank_schedule(const int* __restrict__ sptr,
-                                                                       int64_t nslices, int* __restrict__ scol,
-                                                                       float* __restrict__ sval,
-                                                                       uint16_t* __restrict__ lidx)
+__host__ __device__ inline int lowest_bit(unsigned long long m)
 {
-    __shared__ int c_s[kSchedWarps][kSchedMaxWidth][32];
-    __shared__ float v_s[kSchedWarps][kSchedMaxWidth][32];
-    __shared__ uint16_t l_s[kSchedWarps][kSchedMaxWidth][32];
-    __shared__ unsigned char taken[kSchedWarps][kSchedMaxWidth][32];
-    __shared__ int used[kSchedWarps][32];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t sl = (int64_t)blockIdx.x * kSchedWarps + w;
+#ifdef __CUDA_ARCH__
+    return __ffsll((long long)m) - 1;
+#else
+    return __builtin_ctzll(m);
+#endif
+}
+
+// Steps for one slice of width W (1..64): lx = the slice's local indices ([W][32], entry j of row
+// l at j * 32 + l), st = the step of every entry (same layout).  Always a permutation of the steps
+// within every row: should the construction ever leave a row incomplete, the slice keeps its order.
+struct ColourWork {
+    unsigned char lane_at[32][kSchedMaxWidth];  // row l, colour c -> entry j (or none)
+    unsigned char bank_at[32][kSchedMaxWidth];  // bank b, colour c -> row (or none); then counts
+    unsigned long long lane_free[32], bank_free[32], over[32];
+    int deg[32];
+    unsigned char worst[kSchedMaxWidth];
+    unsigned char pl[64], pj[64], pb[64], pc[64];  // an alternating path
+};
+
+__host__ __device__ inline void colour_slice(const uint16_t* lx, int W, unsigned char* st, ColourWork& wk)
+{
+    auto& lane_at = wk.lane_at;
+    auto& bank_at = wk.bank_at;
+    auto& lane_free = wk.lane_free;
+    auto& bank_free = wk.bank_free;
+    auto& over = wk.over;
+    auto& deg = wk.deg;
+    const unsigned long long full = W == 64 ? ~0ull : ((1ull << W) - 1ull);
+    for (int i = 0; i < 32; ++i) {
+        lane_free[i] = full;
+        bank_free[i] = full;
+        over[i] = 0ull;
+        deg[i] = 0;
+        for (int c = 0; c < W; ++c) {
+            lane_at[i][c] = kNone;
+            bank_at[i][c] = kNone;
+        }
+    }
+    for (int j = 0; j < W; ++j)
+        for (int l = 0; l < 32; ++l) {
+            const int bk = lx[j * 32 + l] & 31;
+            if (++deg[bk] > W) over[l] |= 1ull << j;  // entries beyond a full bank: left for the end
+        }
+    for (int j = 0; j < W; ++j) {
+        for (int l = 0; l < 32; ++l) {
+            if ((over[l] >> j) & 1ull) continue;
+            const int bk = lx[j * 32 + l] & 31;
+            const unsigned long long both = lane_free[l] & bank_free[bk];
+            int c;
+            if (both) {
+                c = lowest_bit(both);
+            } else {
+                const int a = lowest_bit(lane_free[l]);    // free at the row, used at the bank
+                const int bb = lowest_bit(bank_free[bk]);  // free at the bank, used at the row
+                // the a/bb path from the bank: bank -a-> row -bb-> bank -a-> ...; swap a and bb on it
+                auto& pl = wk.pl;
+                auto& pj = wk.pj;
+                auto& pb = wk.pb;
+                auto& pc = wk.pc;
+                int len = 0;
+                int vb = bk;
+                while (len < 63) {
+                    const int x = bank_at[vb][a];
+                    if (x == kNone) break;
+                    pl[len] = (unsigned char)x; pj[len] = lane_at[x][a]; pb[len] = (unsigned char)vb; pc[len] = (unsigned char)a;
+                    ++len;
+                    const int jy = lane_at[x][bb];
+                    if (jy == kNone) break;
+                    const int y = lx[jy * 32 + x] & 31;
+                    pl[len] = (unsigned char)x; pj[len] = (unsigned char)jy; pb[len] = (unsigned char)y; pc[len] = (unsigned char)bb;
+                    ++len;
+                    vb = y;
+                }
+                for (int q = 0; q < len; ++q) {
+                    lane_at[pl[q]][pc[q]] = kNone;
+                    bank_at[pb[q]][pc[q]] = kNone;
+                }
+                for (int q = 0; q < len; ++q) {
+                    const int nc = pc[q] == a ? bb : a;
+                    lane_at[pl[q]][nc] = pj[q];
+                    bank_at[pb[q]][nc] = pl[q];
+                }
+                const unsigned long long m = (1ull << a) | (1ull << bb);
+                for (int q = 0; q < len; ++q) {
+                    unsigned long long lf = lane_free[pl[q]] | m, bf = bank_free[pb[q]] | m;
+                    if (lane_at[pl[q]][a] != kNone) lf &= ~(1ull << a);
+                    if (lane_at[pl[q]][bb] != kNone) lf &= ~(1ull << bb);
+                    if (bank_at[pb[q]][a] != kNone) bf &= ~(1ull << a);
+                    if (bank_at[pb[q]][bb] != kNone) bf &= ~(1ull << bb);
+                    lane_free[pl[q]] = lf;
+                    bank_free[pb[q]] = bf;
+                }
+                if (!((lane_free[l] & bank_free[bk]) >> a & 1ull)) {  // not in a bipartite graph
+                    over[l] |= 1ull << j;
+                    continue;
+                }
+                c = a;
+            }
+            lane_at[l][c] = (unsigned char)j;
+            bank_at[bk][c] = (unsigned char)l;
+            lane_free[l] &= ~(1ull << c);
+            bank_free[bk] &= ~(1ull << c);
+        }
+    }
+    // the rest: the colour free at the row that raises the step's worst bank multiplicity least
+    // (ties: the lower colour), so that the unavoidable conflicts share steps
+    auto& mult = wk.bank_at;  // bank b, colour c -> entries (the rows are no longer needed)
+    auto& worst = wk.worst;
+    for (int c = 0; c < W; ++c) {
+        worst[c] = 0;
+        for (int b = 0; b < 32; ++b) {
+            mult[b][c] = bank_at[b][c] != kNone ? 1 : 0;
+            worst[c] = mult[b][c] > worst[c] ? mult[b][c] : worst[c];
+        }
+    }
+    for (int l = 0; l < 32; ++l) {
+        unsigned long long o = over[l];
+        while (o) {
+            const int j = lowest_bit(o);
+            o &= o - 1ull;
+            if (!lane_free[l]) break;
+            const int bk = lx[j * 32 + l] & 31;
+            int best = -1, best_inc = 1 << 30;
+            for (unsigned long long f = lane_free[l]; f; f &= f - 1ull) {
+                const int c = lowest_bit(f);
+                const int inc = mult[bk][c] + 1 > worst[c] ? mult[bk][c] + 1 - worst[c] : 0;
+                if (inc < best_inc) {
+                    best_inc = inc;
+                    best = c;
+                }
+            }
+            lane_at[l][best] = (unsigned char)j;
+            lane_free[l] &= ~(1ull << best);
+            if (mult[bk][best] < 255) mult[bk][best] += 1;
+            if (mult[bk][best] > worst[best]) worst[best] = mult[bk][best];
+        }
+    }
+    bool ok = true;
+    for (int l = 0; l < 32 && ok; ++l) {
+        unsigned long long seen = 0ull;
+        for (int c = 0; c < W; ++c) {
+            const int j = lane_at[l][c];
+            if (j == kNone || j >= W || ((seen >> j) & 1ull)) {
+                ok = false;
+                break;
+            }
+            seen |= 1ull << j;
+        }
+    }
+    for (int l = 0; l < 32; ++l)
+        for (int c = 0; c < W; ++c) {
+            if (ok) st[lane_at[l][c] * 32 + l] = (unsigned char)c;
+            else st[c * 32 + l] = (unsigned char)c;
+        }
+}
+
+// One thread per slice, its working arrays in shared memory (a few KB: in local memory they
+// would not stay in L1).
+constexpr int kColourThreads = 8;
+
+__global__ void __launch_bounds__(kColourThreads) sell_bank_colour(const int* __restrict__ sptr, int64_t nslices,
+                                                                   const uint16_t* __restrict__ lidx,
+                                                                   unsigned char* __restrict__ step)
+{
+    __shared__ ColourWork wk[kColourThreads];
+    const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (sl >= nslices) return;
     const int base = sptr[sl];
     const int W = (sptr[sl + 1] - base) / 32;
-    if (W <= 1 || W > kSchedMaxWidth) return;
+    if (W < 1 || W > kSchedMaxWidth) return;
+    colour_slice(lidx + base, W, step + base, wk[threadIdx.x]);
+}
+
+// Moves every entry of a slice to its step (from copies of the three arrays).
+__global__ void sell_apply_steps(const int* __restrict__ sptr, int64_t nslices, const unsigned char* __restrict__ step,
+                                 const int* __restrict__ c_in, const float* __restrict__ v_in,
+                                 const uint16_t* __restrict__ l_in, int* __restrict__ scol,
+                                 float* __restrict__ sval, uint16_t* __restrict__ lidx)
+{
+    const int64_t sl = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (sl >= nslices) return;
+    const int l = threadIdx.x & 31;
+    const int base = sptr[sl];
+    const int W = (sptr[sl + 1] - base) / 32;
+    if (W < 1 || W > kSchedMaxWidth) return;
     for (int j = 0; j < W; ++j) {
-        const int e = base + j * 32 + lane;
-        c_s[w][j][lane] = scol[e];
-        v_s[w][j][lane] = sval[e];
-        l_s[w][j][lane] = lidx[e];
-        taken[w][j][lane] = 0;
-    }
-    __syncwarp();
-    for (int j = 0; j < W; ++j) {
-        used[w][lane] = 0;
-        __syncwarp();
-        int mine = 0;  // this lane's entry for step j
-        for (int l = 0; l < 32; ++l) {
-            // lanes scan lane l's remaining entries (two each): key = uses of the bank, then index
-            int best = 0x7fffffff;
-            for (int e = lane; e < W; e += 32) {
-                if (!taken[w][e][l]) {
-                    const int key = used[w][l_s[w][e][l] & 31] * 1024 + e;
-                    best = key < best ? key : best;
-                }
-            }
-            for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
-            const int pick = best & 1023;
-            if (lane == l) {
-                mine = pick;
-                taken[w][pick][l] = 1;
-                used[w][l_s[w][pick][l] & 31] += 1;
-            }
-            __syncwarp();
-        }
-        const int e = base + j * 32 + lane;
-        scol[e] = c_s[w][mine][lane];
-        sval[e] = v_s[w][mine][lane];
-        lidx[e] = l_s[w][mine][lane];
-        __syncwarp();
+        const int e = base + j * 32 + l;
+        const int d = base + step[e] * 32 + l;
+        scol[d] = c_in[e];
+        sval[d] = v_in[e];
+        lidx[d] = l_in[e];
     }
 }
 
@@ -457,8 +603,25 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
             gs_count(ctx, 1);
         }
     }
-    sell_bank_schedule<<<(unsigned)((ns + kSchedWarps - 1) / kSchedWarps), 32 * kSchedWarps, 0, ctx->stream>>>(
-        g->sptr, ns, g->scol, g->sval, g->xc_lidx);
-    gs_count(ctx, 1);
+    {
+        const size_t ne = (size_t)g->sell_nnz;
+        WsPlan plan;
+        const size_t i_step = plan.add(ne), i_c = plan.add(sizeof(int) * ne), i_v = plan.add(sizeof(float) * ne),
+                     i_l = plan.add(sizeof(uint16_t) * ne);
+        if ((st = gs_ws_ensure(ctx, plan.total)) != GS_OK) return st;
+        unsigned char* stp = ws_at<unsigned char>(ctx, plan, i_step);
+        int* c_in = ws_at<int>(ctx, plan, i_c);
+        float* v_in = ws_at<float>(ctx, plan, i_v);
+        uint16_t* l_in = ws_at<uint16_t>(ctx, plan, i_l);
+        cudaStream_t s = ctx->stream;
+        cudaMemcpyAsync(c_in, g->scol, sizeof(int) * ne, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(v_in, g->sval, sizeof(float) * ne, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(l_in, g->xc_lidx, sizeof(uint16_t) * ne, cudaMemcpyDeviceToDevice, s);
+        sell_bank_colour<<<(unsigned)((ns + kColourThreads - 1) / kColourThreads), kColourThreads, 0, s>>>(
+            g->sptr, ns, l_in, stp);
+        sell_apply_steps<<<(unsigned)((ns + 7) / 8), 256, 0, s>>>(g->sptr, ns, stp, c_in, v_in, l_in, g->scol,
+                                                                   g->sval, g->xc_lidx);
+        gs_count(ctx, 2);
+    }
     return gs_cuda_check(ctx, cudaGetLastError(), "gather-cache tables");
 }
