@@ -143,6 +143,7 @@ gs_status gs_launch_count(const gs_ctx *ctx, int64_t *count);
 
 /* ------------------------------------------------------------------------ coefficients --- */
 
+
 /* Chebyshev coefficients of the heat kernel (Sec. 3.5: "evaluated with the Bessel function").
  * HOST call.  Writes c[0..K] (host array of K+1 doubles) such that
  *     exp(-t L) ~ sum_{k=0}^{K} c[k] T_k(P),   c[0] = e^{-t} I_0(t),  c[k] = 2 e^{-t} I_k(t),
@@ -150,6 +151,16 @@ gs_status gs_launch_count(const gs_ctx *ctx, int64_t *count);
  * I_k is the modified Bessel function of the first kind.  Requires t > 0, K >= 0.
  * Errors: GS_ERR_ARG. */
 gs_status gs_cheb_coeffs(double t, int K, double *c);
+
+/* Step order of one 32-row slice of the sliced-ELL operator (the graph builder's bank-aware
+ * entry order for the one-column Sinkhorn loop, exposed for inspection).  HOST call.
+ * idx: W * 32 local cache indices of the slice, entry j of row l at idx[j * 32 + l] (the index's
+ * shared-memory bank is idx mod 32).  steps (out, same layout): the step at which each entry is
+ * summed.  Every row gets each step 0..W-1 exactly once; where no bank holds more than W of the
+ * slice's entries, no step has two entries in one bank (a bipartite edge colouring of
+ * rows x banks), and entries beyond a full bank are grouped into shared steps.  Requires
+ * 1 <= W <= 64.  Errors: GS_ERR_ARG. */
+gs_status gs_sell_step_order(const uint16_t *idx, int W, unsigned char *steps);
 
 /* ----------------------------------------------------------------------------- graphs --- */
 

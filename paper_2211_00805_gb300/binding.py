@@ -34,6 +34,7 @@ SIGNATURES = {
     "gs_get_option": [_P, _I, _P],
     "gs_launch_count": [_P, _P],
     "gs_cheb_coeffs": [_D, _I, _P],
+    "gs_sell_step_order": [_P, _I, _P],
     "gs_knn": [_P, _P, _I64, _I, _I, _P, _P],
     "gs_build_graph": [_P, _P, _I64, _I, _I, _F, _P],
     "gs_graph_from_csr": [_P, _I64, _P, _P, _P, _P],
@@ -196,6 +197,21 @@ def gs_cheb_coeffs(t: float, K: int):
     if st != GS_OK:
         raise GeosinkError(st, "gs_cheb_coeffs")
     return list(buf)
+
+
+def gs_sell_step_order(idx):
+    """Host call: step of every entry of one 32-row slice, given its [W, 32] local cache indices
+    (numpy uint16, entry j of row l at [j, l]); returns a [W, 32] uint8 array."""
+    import numpy as np
+    a = np.ascontiguousarray(idx, dtype=np.uint16)
+    if a.ndim != 2 or a.shape[1] != 32:
+        raise ValueError("idx must be [W, 32]")
+    out = np.empty(a.shape, dtype=np.uint8)
+    st = _lib.gs_sell_step_order(a.ctypes.data_as(ctypes.c_void_p), int(a.shape[0]),
+                                 out.ctypes.data_as(ctypes.c_void_p))
+    if st != GS_OK:
+        raise GeosinkError(st, "gs_sell_step_order")
+    return out
 
 
 def gs_knn(ctx: Context, X: torch.Tensor, k: int):

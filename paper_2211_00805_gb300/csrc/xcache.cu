@@ -12,6 +12,8 @@
 // for between orders instead of a barrier over the whole grid.
 #include <stdint.h>
 
+#include <new>
+
 #include "gs_internal.cuh"
 
 namespace {
@@ -624,4 +626,14 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
         gs_count(ctx, 2);
     }
     return gs_cuda_check(ctx, cudaGetLastError(), "gather-cache tables");
+}
+
+extern "C" gs_status gs_sell_step_order(const uint16_t* idx, int W, unsigned char* steps)
+{
+    if (idx == nullptr || steps == nullptr || W < 1 || W > kSchedMaxWidth) return GS_ERR_ARG;
+    ColourWork* wk = new (std::nothrow) ColourWork;
+    if (wk == nullptr) return GS_ERR_OOM;
+    colour_slice(idx, W, steps, *wk);
+    delete wk;
+    return GS_OK;
 }

@@ -81,3 +81,55 @@ def test_product_never_imports_oracle_and_oracle_never_imports_product():
             assert "paper_2211_00805_gb300" not in _imports(os.path.join(ROOT, "oracle", f)), f
     src = " ".join(open(os.path.join(pkg, "csrc", f)).read() for f in os.listdir(os.path.join(pkg, "csrc")))
     assert "oracle" not in src.lower()
+
+
+def _wavefronts(idx, steps):
+    """Shared-memory wavefronts of a slice summed in the given step order: per step, the largest
+    number of distinct indices that share a bank (at least 1)."""
+    W = idx.shape[0]
+    order = np.empty_like(idx)
+    for l in range(32):
+        order[steps[:, l], l] = idx[:, l]
+    tot = 0
+    for j in range(W):
+        per_bank = {}
+        for v in set(order[j].tolist()):
+            per_bank[v % 32] = per_bank.get(v % 32, 0) + 1
+        tot += max(per_bank.values())
+    return tot
+
+
+def test_sell_step_order_is_a_per_row_permutation_without_conflicts_when_banks_balance(built):
+    # every bank holds exactly W of the slice's entries: a proper edge colouring exists (Koenig),
+    # so no step may put two different indices in one bank
+    from paper_2211_00805_gb300 import binding
+    rng = np.random.default_rng(5)
+    for W in (1, 2, 7, 16, 20, 33, 64):
+        banks = rng.permutation(np.repeat(np.arange(32), W))
+        idx = (rng.integers(0, 250, W * 32) * 32 + banks).astype(np.uint16).reshape(W, 32)
+        steps = binding.gs_sell_step_order(idx)
+        for l in range(32):
+            assert sorted(steps[:, l].tolist()) == list(range(W))
+        assert _wavefronts(idx, steps) == W
+
+
+def test_sell_step_order_on_unbalanced_banks_stays_a_permutation_and_beats_the_stored_order(built):
+    from paper_2211_00805_gb300 import binding
+    rng = np.random.default_rng(6)
+    for W in (5, 20, 48):
+        idx = rng.integers(0, 9000, (W, 32)).astype(np.uint16)
+        idx[W // 2:, 3] = idx[0, 3]  # a row whose padding repeats one index
+        steps = binding.gs_sell_step_order(idx)
+        for l in range(32):
+            assert sorted(steps[:, l].tolist()) == list(range(W))
+        ident = np.repeat(np.arange(W, dtype=np.uint8)[:, None], 32, axis=1)
+        deg = np.bincount((idx % 32).ravel(), minlength=32).max()
+        assert max(W, deg) <= _wavefronts(idx, steps) < _wavefronts(idx, ident)
+
+
+def test_sell_step_order_rejects_bad_widths(built):
+    from paper_2211_00805_gb300 import binding
+    with pytest.raises(binding.GeosinkError):
+        binding.gs_sell_step_order(np.zeros((65, 32), np.uint16))
+    with pytest.raises(binding.GeosinkError):
+        binding.gs_sell_step_order(np.zeros((0, 32), np.uint16))
