@@ -182,8 +182,15 @@ gs_status gs_graph_export(gs_ctx* ctx, const gs_graph* g, int64_t* rowptr, int32
                           float* P);
 
 // --------------------------------------------------------------------- order.cu
-gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g);
-gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks);
+// Node order of the filter: recursive coordinate bisection of the points X [n, d] (device FP32,
+// or null) into the persistent loop's partition, else breadth-first; then the sliced ELL and the
+// gather-cache tables.
+gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d);
+// Gather-cache tables for `blocks` partition blocks: on the given row ranges (parts, blocks + 1
+// boundaries), else on cost-balanced ranges.
+gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, const std::vector<int>* parts);
+// Boundaries of `blocks` ranges of whole 32-row slices with equal slice counts (+-1).
+std::vector<int> gs_equal_slice_rows(int64_t n, int blocks);
 // rows per block of the persistent loop's partition (one block per SM, whole slices)
 // Block synchronisation of the persistent loop: the option if set, else the autotuned choice for
 // the graph, else the context's last one, else tagged values (the fastest on the graphs measured).

@@ -867,7 +867,7 @@ gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int
         gs_graph_destroy(g);
         return gs_fail(ctx, GS_ERR_ARG, "graph has a node with zero degree");
     }
-    if ((st = gs_graph_reorder(ctx, g)) != GS_OK) {
+    if ((st = gs_graph_reorder(ctx, g, X, d)) != GS_OK) {
         gs_graph_destroy(g);
         return st;
     }

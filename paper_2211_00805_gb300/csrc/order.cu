@@ -230,6 +230,255 @@ __global__ void rowptr_narrow(int64_t n1, const int64_t* __restrict__ in, int* _
     if (i < n1) out[i] = (int)in[i];
 }
 
+// ------------------------------------------------------------------ coordinate bisection
+// For a graph built from points, the nodes are ordered by recursive bisection of the point set:
+// every segment of the order is split at a prescribed rank along its principal direction, so the
+// final segments, one per block of the persistent loop, are compact regions of the point cloud
+// (far fewer neighbours outside a block than the slabs of a breadth-first order).  The direction
+// is estimated from an evenly spaced sample of the segment (mean, then power iteration), every
+// point is projected and binned, and the split takes the bins below the rank's bin, and inside
+// that bin the points in their current order, so it is exact and deterministic.
+constexpr int kRcbBins = 4096;
+constexpr int kRcbChunk = 1024;
+constexpr int kRcbMaxDim = 128;   // larger dimensions keep the breadth-first order
+constexpr int kRcbSampleFloats = 24576;  // sample size x dimension held in shared memory
+constexpr int kRcbPower = 8;
+constexpr int kRcbMaxPart = 4096;  // rows of a part for the in-part degree sort
+
+struct RcbSeg {
+    int beg, len, left;  // positions [beg, beg + len); the first `left` go to the left child
+    int chunk0, nchunk;  // its chunks of kRcbChunk positions
+};
+struct RcbChunk {
+    int seg, beg, count;
+};
+
+__global__ void __launch_bounds__(256) rcb_stats(const float* __restrict__ X, int d, const int* __restrict__ ord,
+                                                 const RcbSeg* __restrict__ segs, float* __restrict__ mean,
+                                                 float* __restrict__ dir, float* __restrict__ range)
+{
+    extern __shared__ float r_smem[];
+    const RcbSeg sg = segs[blockIdx.x];
+    const int S = min(sg.len, kRcbSampleFloats / d);
+    float* Y = r_smem;            // [S][d]
+    float* mu = Y + S * d;        // [d]
+    float* v = mu + d;            // [d]
+    float* w = v + d;             // [d]
+    float* pr = w + d;            // [S]
+    __shared__ float s_norm;
+    for (int e = threadIdx.x; e < S * d; e += blockDim.x) {
+        const int i = e / d, j = e - i * d;
+        const int pos = sg.beg + (int)(((long long)i * sg.len) / S);
+        Y[e] = X[(int64_t)ord[pos] * d + j];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        float acc = 0.f;
+        for (int i = 0; i < S; ++i) acc += Y[i * d + j];
+        mu[j] = acc / (float)S;
+        v[j] = 1.f + 0.01f * (float)(j % 7);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < S * d; e += blockDim.x) Y[e] -= mu[e % d];
+    __syncthreads();
+    for (int it = 0; it <= kRcbPower; ++it) {
+        for (int i = threadIdx.x; i < S; i += blockDim.x) {
+            float acc = 0.f;
+            for (int j = 0; j < d; ++j) acc = fmaf(Y[i * d + j], v[j], acc);
+            pr[i] = acc;
+        }
+        __syncthreads();
+        if (it == kRcbPower) break;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            float acc = 0.f;
+            for (int i = 0; i < S; ++i) acc = fmaf(pr[i], Y[i * d + j], acc);
+            w[j] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float nn = 0.f;
+            for (int j = 0; j < d; ++j) nn = fmaf(w[j], w[j], nn);
+            s_norm = sqrtf(nn);
+        }
+        __syncthreads();
+        if (s_norm > 0.f)
+            for (int j = threadIdx.x; j < d; j += blockDim.x) v[j] = w[j] / s_norm;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        float lo = pr[0], hi = pr[0];
+        for (int i = 1; i < S; ++i) {
+            lo = fminf(lo, pr[i]);
+            hi = fmaxf(hi, pr[i]);
+        }
+        range[2 * blockIdx.x] = lo;
+        range[2 * blockIdx.x + 1] = hi;
+    }
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        mean[(int64_t)blockIdx.x * d + j] = mu[j];
+        dir[(int64_t)blockIdx.x * d + j] = v[j];
+    }
+}
+
+__global__ void __launch_bounds__(kRcbChunk) rcb_bin(const float* __restrict__ X, int d, const int* __restrict__ ord,
+                                                     const RcbChunk* __restrict__ chunks, const float* __restrict__ mean,
+                                                     const float* __restrict__ dir, const float* __restrict__ range,
+                                                     uint16_t* __restrict__ bin, int* __restrict__ hist)
+{
+    extern __shared__ float b_smem[];  // [d] mean, [d] direction
+    const RcbChunk ch = chunks[blockIdx.x];
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        b_smem[j] = mean[(int64_t)ch.seg * d + j];
+        b_smem[d + j] = dir[(int64_t)ch.seg * d + j];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= ch.count) return;
+    const int pos = ch.beg + threadIdx.x;
+    const float* x = X + (int64_t)ord[pos] * d;
+    float acc = 0.f;
+    for (int j = 0; j < d; ++j) acc = fmaf(x[j] - b_smem[j], b_smem[d + j], acc);
+    const float lo = range[2 * ch.seg], hi = range[2 * ch.seg + 1];
+    int b = 0;
+    if (hi > lo) {
+        const float f = (acc - lo) / (hi - lo) * (float)kRcbBins;
+        b = f > 0.f ? (f < (float)(kRcbBins - 1) ? (int)f : kRcbBins - 1) : 0;  // NaN -> bin 0
+    }
+    bin[pos] = (uint16_t)b;
+    atomicAdd(&hist[(int64_t)ch.seg * kRcbBins + b], 1);
+}
+
+// per segment: the bin holding rank `left` (sel[0]) and how many of that bin go left (sel[1])
+__global__ void __launch_bounds__(256) rcb_select(const RcbSeg* __restrict__ segs, const int* __restrict__ hist,
+                                                  int* __restrict__ sel)
+{
+    __shared__ int part[256];
+    const int* h = hist + (int64_t)blockIdx.x * kRcbBins;
+    constexpr int per = kRcbBins / 256;
+    int c = 0;
+    for (int q = 0; q < per; ++q) c += h[threadIdx.x * per + q];
+    part[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int left = segs[blockIdx.x].left;
+        int below = 0, t = 0;
+        while (t < 255 && below + part[t] < left) below += part[t++];
+        int b = t * per;
+        while (b < kRcbBins - 1 && below + h[b] < left) below += h[b++];
+        sel[2 * blockIdx.x] = b;
+        sel[2 * blockIdx.x + 1] = left - below;
+    }
+}
+
+__device__ __forceinline__ int rcb_block_excl(int flag, int* warp_tot, int* total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) warp_tot[w] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            const int t = warp_tot[i];
+            warp_tot[i] = run;
+            run += t;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    const int r = warp_tot[w] + __popc(m & ((1u << lane) - 1u));
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kRcbChunk) rcb_count(const RcbChunk* __restrict__ chunks, const uint16_t* __restrict__ bin,
+                                                       const int* __restrict__ sel, int* __restrict__ cnt)
+{
+    __shared__ int wt[kRcbChunk / 32];
+    __shared__ int tot;
+    const RcbChunk ch = chunks[blockIdx.x];
+    const bool act = (int)threadIdx.x < ch.count;
+    const int b = act ? bin[ch.beg + threadIdx.x] : 0;
+    const int bs = sel[2 * ch.seg];
+    rcb_block_excl(act && b < bs, wt, &tot);
+    const int lt = tot;
+    rcb_block_excl(act && b == bs, wt, &tot);
+    if (threadIdx.x == 0) {
+        cnt[2 * blockIdx.x] = lt;
+        cnt[2 * blockIdx.x + 1] = tot;
+    }
+}
+
+// per chunk: equal-bin elements before it in its segment, and its left / right output bases
+__global__ void rcb_bases(const RcbSeg* __restrict__ segs, const RcbChunk* __restrict__ chunks, int nseg,
+                          const int* __restrict__ sel, const int* __restrict__ cnt, int* __restrict__ base)
+{
+    const int sgi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sgi >= nseg) return;
+    const RcbSeg sg = segs[sgi];
+    const int need = sel[2 * sgi + 1];
+    int eq = 0, lb = 0, rb = 0;
+    for (int c = sg.chunk0; c < sg.chunk0 + sg.nchunk; ++c) {
+        const int lt = cnt[2 * c], e = cnt[2 * c + 1];
+        const int eq_left = need - eq <= 0 ? 0 : (need - eq >= e ? e : need - eq);
+        base[3 * c] = eq;
+        base[3 * c + 1] = lb;
+        base[3 * c + 2] = rb;
+        eq += e;
+        lb += lt + eq_left;
+        rb += chunks[c].count - lt - eq_left;
+    }
+}
+
+__global__ void __launch_bounds__(kRcbChunk) rcb_scatter(const RcbChunk* __restrict__ chunks,
+                                                         const RcbSeg* __restrict__ segs, const int* __restrict__ ord,
+                                                         const uint16_t* __restrict__ bin, const int* __restrict__ sel,
+                                                         const int* __restrict__ base, int* __restrict__ ord_new)
+{
+    __shared__ int wt[kRcbChunk / 32];
+    __shared__ int tot;
+    const RcbChunk ch = chunks[blockIdx.x];
+    const RcbSeg sg = segs[ch.seg];
+    const bool act = (int)threadIdx.x < ch.count;
+    const int pos = ch.beg + threadIdx.x;
+    const int b = act ? bin[pos] : 0;
+    const int bs = sel[2 * ch.seg], need = sel[2 * ch.seg + 1];
+    const int eq_rank = rcb_block_excl(act && b == bs, wt, &tot);
+    const bool L = act && (b < bs || (b == bs && base[3 * blockIdx.x] + eq_rank < need));
+    const int l_rank = rcb_block_excl(L, wt, &tot);
+    if (!act) return;
+    const int r_rank = (int)threadIdx.x - l_rank;
+    const int dst = L ? sg.beg + base[3 * blockIdx.x + 1] + l_rank : sg.beg + sg.left + base[3 * blockIdx.x + 2] + r_rank;
+    ord_new[dst] = ord[pos];
+}
+
+__global__ void rcb_iota(int64_t n, int* __restrict__ ord)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) ord[i] = (int)i;
+}
+
+// Inside each part, nodes by decreasing degree (stable): sliced-ELL slices of similar rows.
+__global__ void __launch_bounds__(256) part_degree_sort(const int* __restrict__ parts, const int* __restrict__ perm_in,
+                                                        const int* __restrict__ rowptr, int* __restrict__ perm_out)
+{
+    extern __shared__ int pdeg[];  // [len]
+    const int beg = parts[blockIdx.x], len = parts[blockIdx.x + 1] - beg;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const int node = perm_in[beg + i];
+        pdeg[i] = rowptr[node + 1] - rowptr[node];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const int di = pdeg[i];
+        int rank = 0;
+        for (int j = 0; j < len; ++j) {
+            const int dj = pdeg[j];
+            rank += (dj > di) || (dj == di && j < i);
+        }
+        perm_out[beg + rank] = perm_in[beg + i];
+    }
+}
+
 }  // namespace
 
 void gs_permute_rows(gs_ctx* ctx, int64_t n, int B, const int* perm, const float* src, float* dst,
@@ -239,6 +488,91 @@ void gs_permute_rows(gs_ctx* ctx, int64_t n, int B, const int* perm, const float
     permute_rows_kernel<<<nblk(count, 256), 256, 0, ctx->stream>>>(count, B, perm, src, dst,
                                                                     to_filter_order ? 1 : 0);
     gs_count(ctx, 1);
+}
+
+// Recursive coordinate bisection of the points X [n, d] into the parts [parts[b], parts[b+1]) of
+// the order, then decreasing degree inside each part; writes g->perm.  ord / ord2: n ints of
+// scratch.  Every level is a handful of launches with no host synchronisation.
+static gs_status rcb_order(gs_ctx* ctx, gs_graph* g, const float* X, int d, const std::vector<int>& parts,
+                           int* ord, int* ord2, void* scratch, size_t scratch_bytes)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t n = g->n;
+    const int P = (int)parts.size() - 1;
+    const int max_chunks = (int)((n + kRcbChunk - 1) / kRcbChunk) + P;
+    // scratch layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        void* q = static_cast<char*>(scratch) + off;
+        off = (off + bytes + 255) & ~size_t(255);
+        return q;
+    };
+    uint16_t* bin = static_cast<uint16_t*>(take(sizeof(uint16_t) * (size_t)n));
+    int* hist = static_cast<int*>(take(sizeof(int) * (size_t)P * kRcbBins));
+    float* mean = static_cast<float*>(take(sizeof(float) * (size_t)P * d));
+    float* dir = static_cast<float*>(take(sizeof(float) * (size_t)P * d));
+    float* range = static_cast<float*>(take(sizeof(float) * 2 * (size_t)P));
+    int* sel = static_cast<int*>(take(sizeof(int) * 2 * (size_t)P));
+    int* cnt = static_cast<int*>(take(sizeof(int) * 2 * (size_t)max_chunks));
+    int* base = static_cast<int*>(take(sizeof(int) * 3 * (size_t)max_chunks));
+    RcbSeg* segs_d = static_cast<RcbSeg*>(take(sizeof(RcbSeg) * (size_t)P));
+    RcbChunk* chunks_d = static_cast<RcbChunk*>(take(sizeof(RcbChunk) * (size_t)max_chunks));
+    int* parts_d = static_cast<int*>(take(sizeof(int) * ((size_t)P + 1)));
+    if (off > scratch_bytes) return gs_fail(ctx, GS_ERR_OOM, "bisection scratch");
+
+    const int S_max = kRcbSampleFloats / d;
+    const size_t stats_smem = sizeof(float) * ((size_t)S_max * d + 3 * (size_t)d + (size_t)S_max);
+    cudaFuncSetAttribute(rcb_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stats_smem);
+    rcb_iota<<<nblk(n, 256), 256, 0, s>>>(n, ord);
+    gs_count(ctx, 1);
+    struct Node {
+        int beg, len, pa, pb;
+    };
+    std::vector<Node> cur{{0, (int)n, 0, P}};
+    std::vector<RcbSeg> segs;
+    std::vector<RcbChunk> chunks;
+    while (true) {
+        std::vector<Node> next;
+        segs.clear();
+        chunks.clear();
+        for (const Node& nd : cur) {
+            if (nd.pb - nd.pa <= 1) continue;
+            const int mid = (nd.pa + nd.pb) / 2;
+            const int left = parts[(size_t)mid] - parts[(size_t)nd.pa];
+            next.push_back({nd.beg, left, nd.pa, mid});
+            next.push_back({nd.beg + left, nd.len - left, mid, nd.pb});
+            if (left <= 0 || left >= nd.len) continue;  // nothing moves
+            const int nc = (nd.len + kRcbChunk - 1) / kRcbChunk;
+            segs.push_back({nd.beg, nd.len, left, (int)chunks.size(), nc});
+            for (int c = 0; c < nc; ++c)
+                chunks.push_back({(int)segs.size() - 1, nd.beg + c * kRcbChunk, std::min(kRcbChunk, nd.len - c * kRcbChunk)});
+        }
+        if (next.empty()) break;
+        const int ns = (int)segs.size(), nc = (int)chunks.size();
+        if (ns > 0) {
+            // pageable copies: staged before the calls return, so the vectors may change afterwards
+            cudaMemcpyAsync(segs_d, segs.data(), sizeof(RcbSeg) * ns, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(chunks_d, chunks.data(), sizeof(RcbChunk) * nc, cudaMemcpyHostToDevice, s);
+            cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)ns * kRcbBins, s);
+            rcb_stats<<<ns, 256, stats_smem, s>>>(X, d, ord, segs_d, mean, dir, range);
+            rcb_bin<<<nc, kRcbChunk, sizeof(float) * 2 * d, s>>>(X, d, ord, chunks_d, mean, dir, range, bin, hist);
+            rcb_select<<<ns, 256, 0, s>>>(segs_d, hist, sel);
+            rcb_count<<<nc, kRcbChunk, 0, s>>>(chunks_d, bin, sel, cnt);
+            rcb_bases<<<(ns + 127) / 128, 128, 0, s>>>(segs_d, chunks_d, ns, sel, cnt, base);
+            cudaMemcpyAsync(ord2, ord, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+            rcb_scatter<<<nc, kRcbChunk, 0, s>>>(chunks_d, segs_d, ord, bin, sel, base, ord2);
+            gs_count(ctx, 6);
+            std::swap(ord, ord2);
+        }
+        cur.swap(next);
+    }
+    int maxpart = 0;
+    for (int b = 0; b < P; ++b) maxpart = std::max(maxpart, parts[(size_t)b + 1] - parts[(size_t)b]);
+    cudaMemcpyAsync(parts_d, parts.data(), sizeof(int) * ((size_t)P + 1), cudaMemcpyHostToDevice, s);
+    cudaFuncSetAttribute(part_degree_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * maxpart));
+    part_degree_sort<<<P, 256, sizeof(int) * std::max(maxpart, 1), s>>>(parts_d, ord, g->rowptr, g->perm);
+    gs_count(ctx, 1);
+    return gs_cuda_check(ctx, cudaGetLastError(), "coordinate bisection");
 }
 
 // One breadth-first sweep from `root` (device int), producing perm/iperm over all components.
@@ -282,7 +616,7 @@ static gs_status bfs_sweep(gs_ctx* ctx, const gs_graph* g, const int* root, int*
     return gs_cuda_check(ctx, cudaGetLastError(), "node ordering");
 }
 
-gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
+gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d)
 {
     const int64_t n = g->n, nnz = g->nnz;
     WsPlan plan;
@@ -291,6 +625,12 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
                  i_sums = plan.add(sizeof(int64_t) * (n / 4096 + 2)), i_int = plan.add(sizeof(int) * 4),
                  i_p64 = plan.add(sizeof(int64_t) * (n + 1)), i_hflag = plan.add(sizeof(int) * n),
                  i_h64 = plan.add(sizeof(int64_t) * (n + 1));
+    // coordinate bisection scratch (bins, histograms, per-segment statistics, chunk tables)
+    const int64_t P_ = gs_persist_cache_blocks(ctx), chunks_ = (n + kRcbChunk - 1) / kRcbChunk + P_;
+    const size_t rcb_bytes = (X != nullptr) ? (size_t)(2 * n + 4 * P_ * kRcbBins + 8 * P_ * (d > 0 ? d : 1) + 16 * P_ +
+                                                       20 * chunks_ + 12 * chunks_ + 24 * P_ + 4 * (P_ + 1) + 16 * 256)
+                                            : 0;
+    const size_t i_rcb = plan.add(rcb_bytes > 0 ? rcb_bytes : 1);
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
     int* owner = ws_at<int>(ctx, plan, i_owner);
@@ -312,18 +652,33 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
         return gs_fail(ctx, GS_ERR_OOM, "graph ordering allocation failed");
     }
     cudaStream_t s = ctx->stream;
-    // sweep 1 from node 0; sweep 2 from the node it placed last
-    const int zero = 0;
-    cudaMemcpyAsync(sint + 1, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
-    int levels = 0;
-    if ((st = bfs_sweep(ctx, g, sint + 1, g->perm, g->iperm, owner, cnt, offs, sums, sint, &levels)) != GS_OK)
-        return st;
-    cudaMemcpyAsync(sint + 2, g->perm + (n - 1), sizeof(int), cudaMemcpyDeviceToDevice, s);
-    if ((st = bfs_sweep(ctx, g, sint + 2, g->perm, g->iperm, owner, cnt, offs, sums, sint, &levels)) != GS_OK)
-        return st;
-    g->levels = levels;
-    // degree sort inside windows of 256 positions, then the inverse permutation
-    {
+    // points given: recursive coordinate bisection into the persistent loop's partition (when the
+    // parts fit the in-part sort); otherwise the breadth-first order
+    const int blocks = gs_persist_cache_blocks(ctx);
+    std::vector<int> parts;
+    bool rcb = X != nullptr && d >= 1 && d <= kRcbMaxDim && blocks >= 2 && n >= 2;
+    if (rcb) {
+        parts = gs_equal_slice_rows(n, blocks);
+        for (int b = 0; b < blocks && rcb; ++b) rcb = parts[(size_t)b + 1] - parts[(size_t)b] <= kRcbMaxPart;
+    }
+    if (rcb) {
+        if ((st = rcb_order(ctx, g, X, d, parts, owner, cnt, ws_at<void>(ctx, plan, i_rcb), rcb_bytes)) != GS_OK)
+            return st;
+        g->levels = 0;
+        invert_perm<<<nblk(n, 256), 256, 0, s>>>(n, g->perm, g->iperm);
+        gs_count(ctx, 1);
+    } else {
+        // sweep 1 from node 0; sweep 2 from the node it placed last
+        const int zero = 0;
+        cudaMemcpyAsync(sint + 1, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+        int levels = 0;
+        if ((st = bfs_sweep(ctx, g, sint + 1, g->perm, g->iperm, owner, cnt, offs, sums, sint, &levels)) != GS_OK)
+            return st;
+        cudaMemcpyAsync(sint + 2, g->perm + (n - 1), sizeof(int), cudaMemcpyDeviceToDevice, s);
+        if ((st = bfs_sweep(ctx, g, sint + 2, g->perm, g->iperm, owner, cnt, offs, sums, sint, &levels)) != GS_OK)
+            return st;
+        g->levels = levels;
+        // degree sort inside windows of 256 positions, then the inverse permutation
         const int W = 256;
         cudaMemcpyAsync(owner, g->perm, sizeof(int) * n, cudaMemcpyDeviceToDevice, s);
         window_degree_sort<<<nblk(n, W), 256, sizeof(int) * W, s>>>(n, W, owner, g->rowptr, g->perm);
@@ -376,6 +731,5 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g)
     g->sptr_host.resize((size_t)ns + 1);
     cudaMemcpyAsync(g->sptr_host.data(), g->sptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost, s);
     if ((st = gs_cuda_check(ctx, cudaStreamSynchronize(s), "graph permutation")) != GS_OK) return st;
-    const int blocks = gs_persist_cache_blocks(ctx);
-    return gs_graph_build_xcache(ctx, g, blocks);
+    return gs_graph_build_xcache(ctx, g, blocks, rcb ? &parts : nullptr);
 }

@@ -562,7 +562,13 @@ static std::vector<int> balanced_rows(const std::vector<double>& w, int64_t n, i
 // the distinct counts are known only once the tables exist, so the ranges are first balanced on
 // entries, then re-balanced on entries plus four times the block's distinct count spread over
 // its slices, and the tables rebuilt.  Then the entries of every slice are put in bank-aware order.
-gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
+std::vector<int> gs_equal_slice_rows(int64_t n, int blocks)
+{
+    const int64_t ns = (n + GS_SELL_C - 1) / GS_SELL_C;
+    return balanced_rows(std::vector<double>((size_t)ns, 1.0), n, blocks);
+}
+
+gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, const std::vector<int>* parts)
 {
     g->xc_ok = false;
     if (!g->sptr || g->sptr_host.empty() || blocks < 1 || blocks > kXcMaxBlocks) return GS_OK;
@@ -570,7 +576,8 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
     const std::vector<int>& sp = g->sptr_host;
     std::vector<double> w((size_t)ns);
     for (int64_t i = 0; i < ns; ++i) w[(size_t)i] = (double)(sp[(size_t)i + 1] - sp[(size_t)i]);
-    gs_status st = build_tables(ctx, g, balanced_rows(w, g->n, blocks));
+    const bool fixed = parts != nullptr && (int)parts->size() == blocks + 1;
+    gs_status st = build_tables(ctx, g, fixed ? *parts : balanced_rows(w, g->n, blocks));
     if (st != GS_OK || !g->xc_ok) return st;
     constexpr double kStageWeight = 4.0;
     for (int b = 0; b < blocks; ++b) {
@@ -581,7 +588,7 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks)
         const double per_entry = kStageWeight * g->xc_ucnt_host[(size_t)b] / eb;
         for (int64_t i = s0; i < s1; ++i) w[(size_t)i] *= 1.0 + per_entry;
     }
-    const std::vector<int> rows = balanced_rows(w, g->n, blocks);
+    const std::vector<int> rows = fixed ? *parts : balanced_rows(w, g->n, blocks);
     if (rows != g->xc_rows_host) {
         g->xc_ok = false;
         if ((st = build_tables(ctx, g, rows)) != GS_OK || !g->xc_ok) return st;
