@@ -253,7 +253,9 @@ struct RcbChunk {
     int seg, beg, count;
 };
 
-__global__ void __launch_bounds__(256) rcb_stats(const float* __restrict__ X, int d, const int* __restrict__ ord,
+constexpr int kRcbStatThreads = 1024;
+
+__global__ void __launch_bounds__(kRcbStatThreads) rcb_stats(const float* __restrict__ X, int d, const int* __restrict__ ord,
                                                  const RcbSeg* __restrict__ segs, float* __restrict__ mean,
                                                  float* __restrict__ dir, float* __restrict__ range)
 {
@@ -265,17 +267,41 @@ __global__ void __launch_bounds__(256) rcb_stats(const float* __restrict__ X, in
     float* v = mu + d;            // [d]
     float* w = v + d;             // [d]
     float* pr = w + d;            // [S]
+    int* node = reinterpret_cast<int*>(pr + S);  // [S]
     __shared__ float s_norm;
+    __shared__ float part[kRcbStatThreads];  // per (dimension, sample phase) partial sums
+    const int R = d < kRcbStatThreads ? kRcbStatThreads / d : 1;  // sample phases per dimension
+    for (int i = threadIdx.x; i < S; i += blockDim.x) node[i] = ord[sg.beg + (int)(((long long)i * sg.len) / S)];
+    __syncthreads();
+#pragma unroll 4
     for (int e = threadIdx.x; e < S * d; e += blockDim.x) {
         const int i = e / d, j = e - i * d;
-        const int pos = sg.beg + (int)(((long long)i * sg.len) / S);
-        Y[e] = X[(int64_t)ord[pos] * d + j];
+        Y[e] = X[(int64_t)node[i] * d + j];
     }
     __syncthreads();
+    // column sums over the samples: thread (j, r) adds samples r, r + R, ..., then the R partials
+    // of each column are added in phase order
+    auto column_sums = [&](const float* wt, float* out) {
+        for (int t = threadIdx.x; t < d * R; t += blockDim.x) {
+            const int j = t % d, r = t / d;
+            float acc = 0.f;
+            for (int i = r; i < S; i += R) acc = wt ? fmaf(wt[i], Y[i * d + j], acc) : acc + Y[i * d + j];
+            if (R > 1) part[t] = acc;
+            else out[j] = acc;
+        }
+        __syncthreads();
+        if (R > 1) {
+            for (int j = threadIdx.x; j < d; j += blockDim.x) {
+                float acc = 0.f;
+                for (int r = 0; r < R; ++r) acc += part[r * d + j];
+                out[j] = acc;
+            }
+            __syncthreads();
+        }
+    };
+    column_sums(nullptr, mu);
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        float acc = 0.f;
-        for (int i = 0; i < S; ++i) acc += Y[i * d + j];
-        mu[j] = acc / (float)S;
+        mu[j] /= (float)S;
         v[j] = 1.f + 0.01f * (float)(j % 7);
     }
     __syncthreads();
@@ -289,12 +315,7 @@ __global__ void __launch_bounds__(256) rcb_stats(const float* __restrict__ X, in
         }
         __syncthreads();
         if (it == kRcbPower) break;
-        for (int j = threadIdx.x; j < d; j += blockDim.x) {
-            float acc = 0.f;
-            for (int i = 0; i < S; ++i) acc = fmaf(pr[i], Y[i * d + j], acc);
-            w[j] = acc;
-        }
-        __syncthreads();
+        column_sums(pr, w);
         if (threadIdx.x == 0) {
             float nn = 0.f;
             for (int j = 0; j < d; ++j) nn = fmaf(w[j], w[j], nn);
@@ -521,7 +542,7 @@ static gs_status rcb_order(gs_ctx* ctx, gs_graph* g, const float* X, int d, cons
     if (off > scratch_bytes) return gs_fail(ctx, GS_ERR_OOM, "bisection scratch");
 
     const int S_max = kRcbSampleFloats / d;
-    const size_t stats_smem = sizeof(float) * ((size_t)S_max * d + 3 * (size_t)d + (size_t)S_max);
+    const size_t stats_smem = sizeof(float) * ((size_t)S_max * d + 3 * (size_t)d + 2 * (size_t)S_max);
     cudaFuncSetAttribute(rcb_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stats_smem);
     rcb_iota<<<nblk(n, 256), 256, 0, s>>>(n, ord);
     gs_count(ctx, 1);
@@ -554,7 +575,7 @@ static gs_status rcb_order(gs_ctx* ctx, gs_graph* g, const float* X, int d, cons
             cudaMemcpyAsync(segs_d, segs.data(), sizeof(RcbSeg) * ns, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(chunks_d, chunks.data(), sizeof(RcbChunk) * nc, cudaMemcpyHostToDevice, s);
             cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)ns * kRcbBins, s);
-            rcb_stats<<<ns, 256, stats_smem, s>>>(X, d, ord, segs_d, mean, dir, range);
+            rcb_stats<<<ns, kRcbStatThreads, stats_smem, s>>>(X, d, ord, segs_d, mean, dir, range);
             rcb_bin<<<nc, kRcbChunk, sizeof(float) * 2 * d, s>>>(X, d, ord, chunks_d, mean, dir, range, bin, hist);
             rcb_select<<<ns, 256, 0, s>>>(segs_d, hist, sel);
             rcb_count<<<nc, kRcbChunk, 0, s>>>(chunks_d, bin, sel, cnt);

@@ -302,6 +302,7 @@ struct ColourWork {
     int deg[32];
     unsigned char worst[kSchedMaxWidth];
     unsigned char pl[64], pj[64], pb[64], pc[64];  // an alternating path
+    unsigned char bank_of[kSchedMaxWidth][32];     // bank of entry j of row l
 };
 
 __host__ __device__ inline void colour_slice(const uint16_t* lx, int W, unsigned char* st, ColourWork& wk)
@@ -323,15 +324,17 @@ __host__ __device__ inline void colour_slice(const uint16_t* lx, int W, unsigned
             bank_at[i][c] = kNone;
         }
     }
+    auto& bank_of = wk.bank_of;
+    for (int e = 0; e < W * 32; ++e) bank_of[e >> 5][e & 31] = (unsigned char)(lx[e] & 31);
     for (int j = 0; j < W; ++j)
         for (int l = 0; l < 32; ++l) {
-            const int bk = lx[j * 32 + l] & 31;
+            const int bk = bank_of[j][l];
             if (++deg[bk] > W) over[l] |= 1ull << j;  // entries beyond a full bank: left for the end
         }
     for (int j = 0; j < W; ++j) {
         for (int l = 0; l < 32; ++l) {
             if ((over[l] >> j) & 1ull) continue;
-            const int bk = lx[j * 32 + l] & 31;
+            const int bk = bank_of[j][l];
             const unsigned long long both = lane_free[l] & bank_free[bk];
             int c;
             if (both) {
@@ -353,7 +356,7 @@ __host__ __device__ inline void colour_slice(const uint16_t* lx, int W, unsigned
                     ++len;
                     const int jy = lane_at[x][bb];
                     if (jy == kNone) break;
-                    const int y = lx[jy * 32 + x] & 31;
+                    const int y = bank_of[jy][x];
                     pl[len] = (unsigned char)x; pj[len] = (unsigned char)jy; pb[len] = (unsigned char)y; pc[len] = (unsigned char)bb;
                     ++len;
                     vb = y;
@@ -406,7 +409,7 @@ __host__ __device__ inline void colour_slice(const uint16_t* lx, int W, unsigned
             const int j = lowest_bit(o);
             o &= o - 1ull;
             if (!lane_free[l]) break;
-            const int bk = lx[j * 32 + l] & 31;
+            const int bk = bank_of[j][l];
             int best = -1, best_inc = 1 << 30;
             for (unsigned long long f = lane_free[l]; f; f &= f - 1ull) {
                 const int c = lowest_bit(f);
@@ -414,6 +417,7 @@ __host__ __device__ inline void colour_slice(const uint16_t* lx, int W, unsigned
                 if (inc < best_inc) {
                     best_inc = inc;
                     best = c;
+                    if (inc == 0) break;  // the lowest colour that costs nothing
                 }
             }
             lane_at[l][best] = (unsigned char)j;
@@ -449,7 +453,8 @@ __global__ void __launch_bounds__(kColourThreads) sell_bank_colour(const int* __
                                                                    const uint16_t* __restrict__ lidx,
                                                                    unsigned char* __restrict__ step)
 {
-    __shared__ ColourWork wk[kColourThreads];
+    extern __shared__ __align__(16) unsigned char c_smem[];
+    ColourWork* wk = reinterpret_cast<ColourWork*>(c_smem);
     const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (sl >= nslices) return;
     const int base = sptr[sl];
@@ -626,8 +631,10 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, const std:
         cudaMemcpyAsync(c_in, g->scol, sizeof(int) * ne, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(v_in, g->sval, sizeof(float) * ne, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(l_in, g->xc_lidx, sizeof(uint16_t) * ne, cudaMemcpyDeviceToDevice, s);
-        sell_bank_colour<<<(unsigned)((ns + kColourThreads - 1) / kColourThreads), kColourThreads, 0, s>>>(
-            g->sptr, ns, l_in, stp);
+        cudaFuncSetAttribute(sell_bank_colour, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(ColourWork) * kColourThreads));
+        sell_bank_colour<<<(unsigned)((ns + kColourThreads - 1) / kColourThreads), kColourThreads,
+                           sizeof(ColourWork) * kColourThreads, s>>>(g->sptr, ns, l_in, stp);
         sell_apply_steps<<<(unsigned)((ns + 7) / 8), 256, 0, s>>>(g->sptr, ns, stp, c_in, v_in, l_in, g->scol,
                                                                    g->sval, g->xc_lidx);
         gs_count(ctx, 2);
