@@ -201,6 +201,29 @@ def test_build_graph_with_given_sigma_and_duplicates(gs, ctx):
     assert_close(to_np(A), ex["A"], 1e-6, 0, "A")
 
 
+def test_point_graph_order_gives_compact_blocks(gs, ctx):
+    # a graph built from points is ordered by recursive coordinate bisection into the persistent
+    # loop's blocks; the same graph given as CSR gets the breadth-first order.  The bisection
+    # leaves each block fewer distinct neighbour columns, and both orders give the same operator.
+    X, Z = W.tanh_manifold(30_000, 10, 50, seed=2)
+    g = gs.gs_build_graph(ctx, to_dev(X), 15)
+    rowptr, col, A, _ = gs.gs_graph_export_csr(ctx, g)
+    g2 = gs.gs_graph_from_csr(ctx, rowptr, col, A)
+    lay, lay2 = gs.gs_graph_layout(g), gs.gs_graph_layout(g2)
+    assert lay["blocks"] == lay2["blocks"]
+    assert lay["sum_block_distinct"] < 0.9 * lay2["sum_block_distinct"]
+    a = W.softmax_bump(Z, np.zeros(Z.shape[1]))
+    b = W.softmax_bump(Z, np.full(Z.shape[1], 0.5))
+    out = []
+    for graph in (g, g2):
+        u, v, d, _ = gs.gs_sinkhorn(ctx, graph, to_dev(a), to_dev(b), 5.0, 30, 100)
+        gs.gs_sync(ctx)
+        out.append((to_np(u), to_np(d)[0]))
+    assert out[0][1] == pytest.approx(out[1][1], rel=1e-5)
+    m = out[1][0] > 0
+    np.testing.assert_allclose(out[0][0][m], out[1][0][m], rtol=1e-3)
+
+
 # ---------------------------------------------------------------------------------- Sinkhorn
 @pytest.fixture(scope="module")
 def sphere_graph(gs, ctx):
