@@ -347,6 +347,7 @@ def run_ours(args, rank, world, local_rank):
             extras[key] = hbm_case(gs, ctx, dev, stream, peak, peak_kind, case)
         extras["batched_vs_plain"] = batched_case(gs, ctx, dev, stream)
         extras["adjoint_vs_plain"] = adjoint_case(gs, ctx, dev, stream)
+        extras["barycentric_distance"] = families_case(gs, ctx, dev, stream)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     Xh = torch.from_numpy(p.X).pin_memory()
@@ -490,6 +491,39 @@ def batched_case(gs, ctx, dev, stream, count=64, iters=200):
             "sequential_ms": ms_s, "speedup": ms_s / ms_b,
             "batched_problem_iters_per_s": count * iters / (ms_b / 1e3),
             "max_rel_diff_W2": rel}
+
+
+def families_case(gs, ctx, dev, stream, bary_iters=100, sink_iters=200):
+    """Barycentric distance (Definition 4.3) and expected barycenter effect (Definition 4.4) on the
+    200k-point cluster graph: the 32 cluster-union distributions split into two families of 16,
+    uniform weights, t = 10, K = 40; one library call each, timed with CUDA events."""
+    import torch
+    cfg = W.clusters_barycenter()
+    g = gs.gs_build_graph(ctx, torch.from_numpy(cfg["X"]).to(dev), cfg["k"])
+    M = cfg["M"]
+    MT = torch.from_numpy(np.ascontiguousarray(M[:, :16])).to(dev)
+    MC = torch.from_numpy(np.ascontiguousarray(M[:, 16:])).to(dev)
+    alpha = torch.full((16,), 1.0 / 16, dtype=torch.float64, device=dev)
+    Y = torch.from_numpy(cfg["X"]).to(dev)
+    t, K = cfg["t"], cfg["K"]
+    out = {}
+    run = lambda: out.__setitem__("r", gs.gs_barycentric_distance(ctx, g, MT, alpha, MC, alpha, t, K,  # noqa: E731
+                                                                  bary_iters, sink_iters))
+    run()  # warm (workspace)
+    ms = _time(stream, run)
+    dist, muT, muC = out["r"]
+    ms_e = _time(stream, lambda: out.__setitem__("tau", gs.gs_barycenter_effect(ctx, Y, muT, muC)))
+    gs.gs_sync(ctx)
+    d = dist.cpu().numpy()
+    tau = out["tau"].cpu().numpy()
+    n = int(cfg["X"].shape[0])
+    g.close()
+    return {"workload": "clusters-200k-R30, two families of 16 cluster-union distributions", "n": n,
+            "bary_iters": bary_iters, "sink_iters": sink_iters, "K": K, "t": t,
+            "barycentric_distance_ms": ms, "gamma_squared": float(d[0]),
+            "gamma": float(d[1]) if np.isfinite(d[1]) else None,  # W is undefined where W^2 < 0
+            "effect_ms": ms_e, "effect_norm": float(np.linalg.norm(tau)),
+            "filter_orders": 2 * (2 * K * bary_iters) + 2 * K * sink_iters}
 
 
 def adjoint_case(gs, ctx, dev, stream, iters=40, checkpoint=20):

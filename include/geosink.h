@@ -295,6 +295,38 @@ gs_status gs_distance(gs_ctx *ctx, const gs_graph *g, const float *a, const floa
 gs_status gs_barycenter(gs_ctx *ctx, const gs_graph *g, const float *M, int m, const double *alpha,
                         const float *vol, double t, int K, int iters, float *mu, float *v_state);
 
+/* ---------------------------------------------------------------- families of distributions --- */
+
+/* Barycentric distance between two families of distributions (Definition 4.3):
+ *     gamma(T, C) = W_{H_t}(mu*_T, mu*_C),
+ * the Geodesic Sinkhorn distance (Algorithm 1, `sink_iters` iterations, as gs_distance) between
+ * the barycenters of the two families (Sec. 3.3, `bary_iters` iterations each, as gs_barycenter).
+ * Each barycenter is divided by its mass before the distance: the definition compares
+ * distributions, and Algorithm 1 needs marginals of equal mass.
+ *   MT, MC          : [n, mT] and [n, mC] device FP32, column i a member of the family
+ *   alphaT, alphaC  : [mT], [mC] device FP64 weights (>= 0, summing to 1; not checked on device)
+ *   vol             : [n] vertex weights or NULL (barycenters and distance alike)
+ *   muT, muC        : [n] device FP32 outputs, the normalised barycenters (distinct buffers)
+ *   dist            : [2] device FP64 output, (gamma^2, gamma) as gs_distance's (W^2, W)
+ * Requires 1 <= mT, mC <= 1024 (as gs_barycenter), iterations >= 1.  A barycenter without
+ * positive finite mass raises GS_ERR_NONFINITE at the next gs_sync.  Errors: GS_ERR_ARG,
+ * GS_ERR_UNSUPPORTED. */
+gs_status gs_barycentric_distance(gs_ctx *ctx, const gs_graph *g, const float *MT, int mT,
+                                  const double *alphaT, const float *MC, int mC, const double *alphaC,
+                                  const float *vol, double t, int K, int bary_iters, int sink_iters,
+                                  float *muT, float *muC, double *dist);
+
+/* Expected barycenter effect (Definition 4.4): tau = E_{mu*_T}[Y] - E_{mu*_C}[Y], the features'
+ * expectations under the two barycenters, each measure divided by its mass (the closed form of
+ * the definition: two weighted means).
+ *   Y        : [n, d] device FP32 node features, row-major, in the graph's node numbering
+ *   muT, muC : [n] device FP32 measures (e.g. gs_barycentric_distance's outputs)
+ *   out      : [d] device FP64 output
+ * Sums are FP64 in a fixed order.  A measure without positive finite mass raises
+ * GS_ERR_NONFINITE at the next gs_sync.  Requires n >= 1, 1 <= d <= 65535.  Errors: GS_ERR_ARG. */
+gs_status gs_barycenter_effect(gs_ctx *ctx, const float *Y, int64_t n, int d, const float *muT,
+                               const float *muC, double *out);
+
 /* ------------------------------------------------------------------------------ adjoint --- */
 
 /* Reverse mode of Algorithm 1 unrolled over `iters` iterations (not in the paper; it serves

@@ -391,6 +391,31 @@ def barycenter(Ls, b, M, alpha, iters: int, a=None, return_state: bool = False):
     return mu
 
 
+def barycentric_distance(Ls, b, MT, alphaT, MC, alphaC, t: float, bary_iters: int, sink_iters: int,
+                         a=None):
+    """Definition 4.3: gamma(T, C) = W_{H_t}(mu*_T, mu*_C), the Geodesic Sinkhorn distance
+    (Algorithm 1, ``sink_iters`` iterations) between the barycenters of the families T and C
+    (Sec. 3.3, ``bary_iters`` iterations each).  Each barycenter is divided by its mass first: the
+    definition compares distributions, and Algorithm 1 needs two marginals of equal mass.
+    Returns dict(muT, muC, W2, W, status) with the normalised barycenters."""
+    muT = barycenter(Ls, b, MT, alphaT, bary_iters, a=a)
+    muC = barycenter(Ls, b, MC, alphaC, bary_iters, a=a)
+    muT = muT / muT.sum()
+    muC = muC / muC.sum()
+    r = sinkhorn(Ls, b, muT, muC, t, sink_iters, a=a)
+    return dict(muT=muT, muC=muC, W2=r["W2"], W=r["W"], status=r["status"])
+
+
+def barycenter_effect(Y, muT, muC):
+    """Definition 4.4: tau = E_{mu*_T}[Y] - E_{mu*_C}[Y] for node features Y [n, d], each
+    expectation taken under the barycenter divided by its mass (the closed form: two weighted
+    means of the features)."""
+    Y = np.asarray(Y, np.float64)
+    muT = np.asarray(muT, np.float64)
+    muC = np.asarray(muC, np.float64)
+    return (muT @ Y) / muT.sum() - (muC @ Y) / muC.sum()
+
+
 def barycenter_grad(Ls, b, M, alpha, iters: int, mubar, a=None):
     """Reverse mode of ``barycenter`` unrolled over ``iters`` iterations: given the adjoint mubar
     of the returned barycenter, returns (mu, d<mubar, mu>/dalpha)."""

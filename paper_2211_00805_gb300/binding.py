@@ -35,6 +35,8 @@ SIGNATURES = {
     "gs_launch_count": [_P, _P],
     "gs_cheb_coeffs": [_D, _I, _P],
     "gs_sell_step_order": [_P, _I, _P],
+    "gs_barycentric_distance": [_P, _P, _P, _I, _P, _P, _I, _P, _P, _D, _I, _I, _I, _P, _P, _P],
+    "gs_barycenter_effect": [_P, _P, _I64, _I, _P, _P, _P],
     "gs_knn": [_P, _P, _I64, _I, _I, _P, _P],
     "gs_build_graph": [_P, _P, _I64, _I, _I, _F, _P],
     "gs_graph_from_csr": [_P, _I64, _P, _P, _P, _P],
@@ -349,6 +351,39 @@ def gs_barycenter(ctx: Context, g: Graph, M: torch.Tensor, alpha: torch.Tensor, 
     _raise(ctx, _lib.gs_barycenter(ctx.handle, g.handle, _ptr(M), m, _ptr(alpha), _ptr(vol), float(t),
                                    int(K), int(iters), _ptr(mu), _ptr(v_state)))
     return mu
+
+
+def gs_barycentric_distance(ctx: Context, g: Graph, MT: torch.Tensor, alphaT: torch.Tensor,
+                            MC: torch.Tensor, alphaC: torch.Tensor, t: float, K: int, bary_iters: int,
+                            sink_iters: int, vol: torch.Tensor | None = None):
+    """Definition 4.3: returns (dist[2] FP64 = (gamma^2, gamma), muT, muC) as device tensors, the
+    normalised barycenters of the two families included."""
+    n = g.n
+    mT, mC = MT.shape[1], MC.shape[1]
+    _dev(MT, torch.float32, "MT", (n, mT))
+    _dev(MC, torch.float32, "MC", (n, mC))
+    _dev(alphaT, torch.float64, "alphaT", (mT,))
+    _dev(alphaC, torch.float64, "alphaC", (mC,))
+    if vol is not None:
+        _dev(vol, torch.float32, "vol", (n,))
+    muT = torch.empty(n, dtype=torch.float32, device=MT.device)
+    muC = torch.empty(n, dtype=torch.float32, device=MT.device)
+    dist = torch.empty(2, dtype=torch.float64, device=MT.device)
+    _raise(ctx, _lib.gs_barycentric_distance(ctx.handle, g.handle, _ptr(MT), mT, _ptr(alphaT), _ptr(MC), mC,
+                                             _ptr(alphaC), _ptr(vol), float(t), int(K), int(bary_iters),
+                                             int(sink_iters), _ptr(muT), _ptr(muC), _ptr(dist)))
+    return dist, muT, muC
+
+
+def gs_barycenter_effect(ctx: Context, Y: torch.Tensor, muT: torch.Tensor, muC: torch.Tensor):
+    """Definition 4.4: [d] FP64 device tensor E_muT[Y] - E_muC[Y]."""
+    n, d = Y.shape
+    _dev(Y, torch.float32, "Y", (n, d))
+    _dev(muT, torch.float32, "muT", (n,))
+    _dev(muC, torch.float32, "muC", (n,))
+    out = torch.empty(d, dtype=torch.float64, device=Y.device)
+    _raise(ctx, _lib.gs_barycenter_effect(ctx.handle, _ptr(Y), int(n), int(d), _ptr(muT), _ptr(muC), _ptr(out)))
+    return out
 
 
 def gs_sinkhorn_grad(ctx: Context, g: Graph, a: torch.Tensor, b: torch.Tensor, t: float, K: int,

@@ -422,6 +422,40 @@ extern "C" gs_status gs_barycenter(gs_ctx* ctx, const gs_graph* g, const float* 
     return gs_barycenter_impl(ctx, g, M, m, alpha, vol, t, K, iters, mu, v_state);
 }
 
+// ---------------------------------------------------------------------- families of distributions
+extern "C" gs_status gs_barycentric_distance(gs_ctx* ctx, const gs_graph* g, const float* MT, int mT,
+                                             const double* alphaT, const float* MC, int mC,
+                                             const double* alphaC, const float* vol, double t, int K,
+                                             int bary_iters, int sink_iters, float* muT, float* muC,
+                                             double* dist)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(MT) || bad_ptr(alphaT) || bad_ptr(MC) || bad_ptr(alphaC) || bad_ptr(muT) || bad_ptr(muC) ||
+        bad_ptr(dist))
+        return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (muT == muC) return gs_fail(ctx, GS_ERR_ARG, "muT and muC must be distinct buffers");
+    for (int m : {mT, mC}) {
+        if (m < 1 || m > 1024) return gs_fail(ctx, GS_ERR_ARG, "family sizes must be in [1, 1024]");
+        if (!gs_filter_supports(m, true))
+            return gs_fail(ctx, GS_ERR_UNSUPPORTED, "family sizes must be 1..256, or multiples of 4 up to 1024");
+    }
+    if (bary_iters < 1 || sink_iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iterations must be >= 1");
+    return gs_barycentric_distance_impl(ctx, g, MT, mT, alphaT, MC, mC, alphaC, vol, t, K, bary_iters, sink_iters,
+                                        muT, muC, dist);
+}
+
+extern "C" gs_status gs_barycenter_effect(gs_ctx* ctx, const float* Y, int64_t n, int d, const float* muT,
+                                          const float* muC, double* out)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if (bad_ptr(Y) || bad_ptr(muT) || bad_ptr(muC) || bad_ptr(out)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (n < 1 || d < 1 || d > 65535) return gs_fail(ctx, GS_ERR_ARG, "need n >= 1 and 1 <= d <= 65535");
+    return gs_barycenter_effect_impl(ctx, Y, n, d, muT, muC, out);
+}
+
 // ------------------------------------------------------------------------------ adjoint
 extern "C" gs_status gs_sinkhorn_grad(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
                                       const float* vol, double t, int K, int iters, int checkpoint,

@@ -302,6 +302,13 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
 gs_status gs_barycenter_impl(gs_ctx* ctx, const gs_graph* g, const float* M, int m,
                              const double* alpha, const float* vol, double t, int K, int iters,
                              float* mu, float* v_state);
+// Definition 4.3 (muT, muC: [n] caller buffers, normalised barycenters) and Definition 4.4.
+gs_status gs_barycentric_distance_impl(gs_ctx* ctx, const gs_graph* g, const float* MT, int mT,
+                                       const double* alphaT, const float* MC, int mC, const double* alphaC,
+                                       const float* vol, double t, int K, int bary_iters, int sink_iters,
+                                       float* muT, float* muC, double* dist);
+gs_status gs_barycenter_effect_impl(gs_ctx* ctx, const float* Y, int64_t n, int d, const float* muT,
+                                    const float* muC, double* out);
 
 // ------------------------------------------------------------------------ reduce.cu
 // dist[0] = 4t sum vol (a ln u + b ln v), dist[1] = sqrt; flags NONFINITE on bad scalings.

@@ -168,6 +168,22 @@ def manifold_barycenter_grad(n: int = 500_000, latent: int = 6, ambient: int = 4
                 bary_iters=bary_iters, sink_iters=sink_iters, checkpoint=checkpoint)
 
 
+def treatment_families(outlier=None, seed: int = 0, dim: int = 5, per: int = 500):
+    """Synthetic families of the expected-barycenter-effect experiment (Sec. 5): a control family of
+    ten standard Gaussians and a treatment family of nine Gaussians shifted by 5 along the first
+    axis plus one member centred at `outlier` on that axis (None: a tenth shifted member), `per`
+    samples each in R^dim (the paper does not state the dimension).  Every member is the uniform
+    distribution on its own samples.  Returns (X [n, dim] float32, MC [n, 10], MT [n, 10] float32)
+    with n = 20 per, control samples first."""
+    rng = np.random.default_rng(seed)
+    centres = [0.0] * 10 + [5.0] * 9 + [5.0 if outlier is None else float(outlier)]
+    X = np.concatenate([rng.standard_normal((per, dim)) + np.eye(dim)[0] * c for c in centres])
+    M = np.zeros((20 * per, 20), np.float32)
+    for i in range(20):
+        M[i * per:(i + 1) * per, i] = 1.0 / per
+    return X.astype(np.float32), M[:, :10].copy(), M[:, 10:].copy()
+
+
 def ragged_batch(count: int = 512, seed: int = 5, n_min: int = 1_000, n_max: int = 50_000,
                  t: float = 5.0, iters: int = 200):
     """``count`` independent problems with uneven sizes: n log-uniform in [n_min, n_max], ambient

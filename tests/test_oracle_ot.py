@@ -219,3 +219,100 @@ def test_barycenter_grad_matches_finite_differences(bary_setup):
     for i in (0, 77, 150):
         fd = _central_fd(lambda s: J_of(alpha, s), src, i, 1e-4 * src[i])
         assert gsrc[i] == pytest.approx(fd, rel=1e-6, abs=1e-9 * abs(gsrc).max())
+
+
+# --------------------------------------------------------------- families (Definitions 4.3, 4.4)
+def _dense_sinkhorn_w2(H, mu, nu, t, iters):
+    # Algorithm 1 with the exact kernel matrix H = expm(-t L) (not the Chebyshev series)
+    v, w = np.zeros_like(mu), np.ones_like(nu)
+    for _ in range(iters):
+        v = mu / (H @ w)
+        w = nu / (H @ v)
+    return 4.0 * t * float(np.sum(mu * np.log(v) + nu * np.log(w)))
+
+
+def test_barycentric_distance_one_hot_families_match_the_exact_kernel(bary_setup):
+    # alpha = e_j: mu* = H(mu_j / H(1)) (closed form above); gamma is then Algorithm 1 between the
+    # two normalised closed-form barycenters, here run with the dense matrix exponential
+    X, Ls, Ld, M = bary_setup
+    t, K = 2.0, 30
+    H = heat_expm(Ld, t)
+    one = np.ones(len(X))
+    r = oracle.barycentric_distance(Ls, oracle.cheb_coefficients(t, K), M[:, :2], np.array([1.0, 0.0]),
+                                    M[:, 1:], np.array([0.0, 1.0]), t, 6, 300)
+    bT = H @ (M[:, 0] / (H @ one))
+    bC = H @ (M[:, 2] / (H @ one))
+    bT, bC = bT / bT.sum(), bC / bC.sum()
+    np.testing.assert_allclose(r["muT"], bT, rtol=1e-9)
+    np.testing.assert_allclose(r["muC"], bC, rtol=1e-9)
+    assert r["W2"] == pytest.approx(_dense_sinkhorn_w2(H, bT, bC, t, 300), rel=1e-8)
+    assert r["W"] == pytest.approx(math.sqrt(r["W2"]), rel=1e-15)
+
+
+def test_barycentric_distance_symmetric_and_mass_invariant(bary_setup):
+    X, Ls, Ld, M = bary_setup
+    b = oracle.cheb_coefficients(2.0, 30)
+    aT, aC = np.array([0.7, 0.3]), np.array([0.4, 0.6])
+    r = oracle.barycentric_distance(Ls, b, M[:, :2], aT, M[:, 1:], aC, 2.0, 200, 400)
+    r_swapped = oracle.barycentric_distance(Ls, b, M[:, 1:], aC, M[:, :2], aT, 2.0, 200, 400)
+    assert r["W2"] == pytest.approx(r_swapped["W2"], rel=1e-9)
+    # the barycenter scales with its inputs, and gamma compares the normalised barycenters
+    r_scaled = oracle.barycentric_distance(Ls, b, 3.0 * M[:, :2], aT, 0.25 * M[:, 1:], aC, 2.0, 200, 400)
+    assert r_scaled["W2"] == pytest.approx(r["W2"], rel=1e-9)
+    # the pairing of members and weights matters, not their order
+    r_perm = oracle.barycentric_distance(Ls, b, M[:, 1::-1], aT[::-1], M[:, 1:], aC, 2.0, 200, 400)
+    assert r_perm["W2"] == pytest.approx(r["W2"], rel=1e-9)
+
+
+def test_barycenter_effect_closed_forms():
+    rng = np.random.default_rng(8)
+    n, d = 50, 3
+    Y = rng.standard_normal((n, d))
+    # Dirac barycenters: the difference of the two nodes' features
+    eT, eC = np.eye(n)[4] * 2.5, np.eye(n)[17]
+    np.testing.assert_allclose(oracle.barycenter_effect(Y, eT, eC), Y[4] - Y[17], rtol=1e-14)
+    # equal measures: no effect; a shift of all features: no change; a linear map acts linearly
+    muT, muC = rng.random(n), rng.random(n)
+    assert np.abs(oracle.barycenter_effect(Y, muT, 3 * muT)).max() < 1e-14
+    tau = oracle.barycenter_effect(Y, muT, muC)
+    np.testing.assert_allclose(oracle.barycenter_effect(Y + 7.0, muT, muC), tau, atol=1e-12)
+    A = rng.standard_normal((d, 2))
+    np.testing.assert_allclose(oracle.barycenter_effect(Y @ A, muT, muC), tau @ A, rtol=1e-12)
+    # with the arithmetic mean of each family as its barycenter (the total-variation barycenter)
+    # the effect is the difference of the families' mean features (Sec. 4, after Definition 4.4):
+    # nine members centred at 5 and one at -60 against ten at 0 give (9 * 5 - 60) / 10 = -1.5
+    y = np.concatenate([np.full(10, 5.0), [-60.0], np.zeros(10)])[:, None]
+    T = np.zeros((21, 10))
+    T[np.arange(9), np.arange(9)] = 1.0          # nine members, one node at 5 each
+    T[10, 9] = 1.0                               # the outlier at -60
+    C = np.zeros((21, 10))
+    C[11 + np.arange(10), np.arange(10)] = 1.0   # ten members at 0
+    assert oracle.barycenter_effect(y, T.mean(1), C.mean(1))[0] == pytest.approx(-1.5, rel=1e-14)
+
+
+def _table2_rows():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_expected_barycenter_effect.txt")
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            name, m, s, mtv, stv = line.split()
+            rows[name] = (float(m), float(s), float(mtv), float(stv))
+    return rows
+
+
+@pytest.mark.parametrize("outlier,row", [(None, "none"), (0.0, "0")])
+def test_expected_barycenter_effect_reproduces_table2(outlier, row):
+    # Table 2: the effect of the Geodesic Sinkhorn barycenters stays near the true shift of 5, and
+    # the total-variation effect is the difference of empirical means; one seed against the
+    # printed mean within three printed standard deviations
+    mean, std, mean_tv, std_tv = _table2_rows()[row]
+    X, MC, MT = W.treatment_families(outlier, seed=0)
+    Ls, _ = oracle.build_graph(X.astype(np.float64), 10)
+    b = oracle.cheb_coefficients(5.0, 30)
+    muC = oracle.barycenter(Ls, b, MC, np.full(10, 0.1), 50)
+    muT = oracle.barycenter(Ls, b, MT, np.full(10, 0.1), 50)
+    tau = oracle.barycenter_effect(X[:, :1], muT, muC)[0]
+    tau_tv = oracle.barycenter_effect(X[:, :1], MT.mean(1), MC.mean(1))[0]
+    assert abs(tau - mean) < 3 * std
+    assert abs(tau_tv - mean_tv) < 3 * std_tv
