@@ -348,6 +348,7 @@ def run_ours(args, rank, world, local_rank):
         extras["batched_vs_plain"] = batched_case(gs, ctx, dev, stream)
         extras["adjoint_vs_plain"] = adjoint_case(gs, ctx, dev, stream)
         extras["barycentric_distance"] = families_case(gs, ctx, dev, stream)
+        extras["implicit_vs_chebyshev"] = implicit_case(gs, ctx, dev, stream)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     Xh = torch.from_numpy(p.X).pin_memory()
@@ -491,6 +492,30 @@ def batched_case(gs, ctx, dev, stream, count=64, iters=200):
             "sequential_ms": ms_s, "speedup": ms_s / ms_b,
             "batched_problem_iters_per_s": count * iters / (ms_b / 1e3),
             "max_rel_diff_W2": rel}
+
+
+def implicit_case(gs, ctx, dev, stream, t=5.0, K=30, iters=12):
+    """The Euler implicit kernel (I + (t/K) L)^{-K} (K conjugate-gradient solves, Sec. 4) against the
+    Chebyshev filter of the same degree on the 100k-point manifold graph, one column: time of one
+    apply each, and how far each is from a degree-60 Chebyshev apply (error below 1e-12 of the
+    exponential at t = 5)."""
+    import torch
+    p = W.manifold_pair()
+    g = gs.gs_build_graph(ctx, torch.from_numpy(p.X).to(dev), p.k)
+    V = torch.from_numpy(p.a).to(dev)
+    out = {}
+    gs.gs_heat_apply_implicit(ctx, g, t, K, V, iters=iters)  # warm
+    ms_e = _time(stream, lambda: out.__setitem__("e", gs.gs_heat_apply_implicit(ctx, g, t, K, V, iters=iters)))
+    gs.gs_heat_apply(ctx, g, t, K, V)
+    ms_c = _time(stream, lambda: out.__setitem__("c", gs.gs_heat_apply(ctx, g, t, K, V)))
+    ref = gs.gs_heat_apply(ctx, g, t, 60, V).double()
+    gs.gs_sync(ctx)
+    scale = float(ref.abs().max())
+    err = {k: float((out[k].double() - ref).abs().max()) / scale for k in ("e", "c")}
+    g.close()
+    return {"workload": "manifold-100k-R50, B = 1", "t": t, "K": K, "cg_iters_per_step": iters,
+            "implicit_ms": ms_e, "chebyshev_ms": ms_c, "implicit_over_chebyshev": ms_e / ms_c,
+            "implicit_max_rel_err": err["e"], "chebyshev_max_rel_err": err["c"]}
 
 
 def families_case(gs, ctx, dev, stream, bary_iters=100, sink_iters=200):

@@ -295,6 +295,19 @@ gs_status gs_distance(gs_ctx *ctx, const gs_graph *g, const float *a, const floa
 gs_status gs_barycenter(gs_ctx *ctx, const gs_graph *g, const float *M, int m, const double *alpha,
                         const float *vol, double t, int K, int iters, float *mu, float *v_state);
 
+/* Euler implicit heat kernel, the other approximation of H_t that Sec. 4 cites (backward Euler
+ * with K steps, `(Id - (eps/4K) L)^{-K}` in the paper's sign convention for L):
+ *     Y = (I + (t/K) L)^{-K} V,   L = I - D^{-1/2} A D^{-1/2},
+ * each of the K steps a solve of the symmetric positive definite system (I + (t/K) L) x = b by
+ * conjugate gradients from x = 0, all B columns at once, exactly `iters` iterations per step (a
+ * column whose residual falls below tol |b| stops changing).  The condition number is at most
+ * 1 + 2t/K.  For comparison with gs_heat_apply; not used by the Sinkhorn or barycenter calls.
+ *   V, Y : [n, B] device FP32, row-major, caller's node order, no aliasing; 1 <= B <= 256
+ * Scalars stay on the device: the call is asynchronous like the others.
+ * Errors: GS_ERR_ARG. */
+gs_status gs_heat_apply_implicit(gs_ctx *ctx, const gs_graph *g, double t, int K, const float *V, int B,
+                                 float *Y, double tol, int iters);
+
 /* ---------------------------------------------------------------- families of distributions --- */
 
 /* Barycentric distance between two families of distributions (Definition 4.3):

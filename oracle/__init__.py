@@ -240,6 +240,22 @@ def heat_apply(Ls, b, V):
     return Y[:, 0] if squeeze else Y
 
 
+def heat_apply_implicit(Ls, t: float, K: int, V):
+    """The Euler implicit approximation of H_t (Sec. 4, the remark after the proposition on K): K
+    backward Euler steps of the heat equation, (I + (t/K) L)^{-K} V with L = Ls + I, as the dense
+    inverse of I + (t/K) L applied K times (small graphs only)."""
+    rp, col, val = Ls
+    n = len(rp) - 1
+    L = np.eye(n)
+    row = np.repeat(np.arange(n), np.diff(rp))
+    np.add.at(L, (row, np.asarray(col, np.int64)), np.asarray(val, np.float64))
+    Minv = np.linalg.inv(np.eye(n) + (t / K) * L)
+    Y = np.asarray(V, np.float64)
+    for _ in range(K):
+        Y = Minv @ Y
+    return Y
+
+
 def csr_matmul(Ls, X):
     """Ls X for a CSR matrix (used by the tests' dense pins only through this plain loop)."""
     rp, col, val = Ls

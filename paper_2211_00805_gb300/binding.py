@@ -37,6 +37,7 @@ SIGNATURES = {
     "gs_sell_step_order": [_P, _I, _P],
     "gs_barycentric_distance": [_P, _P, _P, _I, _P, _P, _I, _P, _P, _D, _I, _I, _I, _P, _P, _P],
     "gs_barycenter_effect": [_P, _P, _I64, _I, _P, _P, _P],
+    "gs_heat_apply_implicit": [_P, _P, _D, _I, _P, _I, _P, _D, _I],
     "gs_knn": [_P, _P, _I64, _I, _I, _P, _P],
     "gs_build_graph": [_P, _P, _I64, _I, _I, _F, _P],
     "gs_graph_from_csr": [_P, _I64, _P, _P, _P, _P],
@@ -351,6 +352,17 @@ def gs_barycenter(ctx: Context, g: Graph, M: torch.Tensor, alpha: torch.Tensor, 
     _raise(ctx, _lib.gs_barycenter(ctx.handle, g.handle, _ptr(M), m, _ptr(alpha), _ptr(vol), float(t),
                                    int(K), int(iters), _ptr(mu), _ptr(v_state)))
     return mu
+
+
+def gs_heat_apply_implicit(ctx: Context, g: Graph, t: float, K: int, V: torch.Tensor, tol: float = 1e-7,
+                           iters: int = 30, out: torch.Tensor | None = None):
+    """Euler implicit kernel (I + (t/K) L)^{-K} V by K conjugate-gradient solves; V is [n] or [n, B]."""
+    B = 1 if V.dim() == 1 else V.shape[1]
+    _dev(V, torch.float32, "V", (g.n,) if V.dim() == 1 else (g.n, B))
+    Y = torch.empty_like(V) if out is None else out
+    _raise(ctx, _lib.gs_heat_apply_implicit(ctx.handle, g.handle, float(t), int(K), _ptr(V), int(B), _ptr(Y),
+                                            float(tol), int(iters)))
+    return Y
 
 
 def gs_barycentric_distance(ctx: Context, g: Graph, MT: torch.Tensor, alphaT: torch.Tensor,

@@ -422,6 +422,18 @@ extern "C" gs_status gs_barycenter(gs_ctx* ctx, const gs_graph* g, const float* 
     return gs_barycenter_impl(ctx, g, M, m, alpha, vol, t, K, iters, mu, v_state);
 }
 
+extern "C" gs_status gs_heat_apply_implicit(gs_ctx* ctx, const gs_graph* g, double t, int K, const float* V,
+                                            int B, float* Y, double tol, int iters)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(V) || bad_ptr(Y)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (B < 1 || B > 256) return gs_fail(ctx, GS_ERR_ARG, "B must be in [1, 256]");
+    if (K < 1 || iters < 1 || !(tol >= 0.0)) return gs_fail(ctx, GS_ERR_ARG, "need K >= 1, iters >= 1, tol >= 0");
+    return gs_heat_apply_implicit_impl(ctx, g, t, K, V, B, Y, tol, iters);
+}
+
 // ---------------------------------------------------------------------- families of distributions
 extern "C" gs_status gs_barycentric_distance(gs_ctx* ctx, const gs_graph* g, const float* MT, int mT,
                                              const double* alphaT, const float* MC, int mC,

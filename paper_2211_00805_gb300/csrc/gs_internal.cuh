@@ -309,6 +309,9 @@ gs_status gs_barycentric_distance_impl(gs_ctx* ctx, const gs_graph* g, const flo
                                        float* muT, float* muC, double* dist);
 gs_status gs_barycenter_effect_impl(gs_ctx* ctx, const float* Y, int64_t n, int d, const float* muT,
                                     const float* muC, double* out);
+// Euler implicit heat kernel Y = (I + (t/K) L)^{-K} V by K conjugate-gradient solves (implicit.cu).
+gs_status gs_heat_apply_implicit_impl(gs_ctx* ctx, const gs_graph* g, double t, int K, const float* V, int B,
+                                      float* Y, double tol, int iters);
 
 // ------------------------------------------------------------------------ reduce.cu
 // dist[0] = 4t sum vol (a ln u + b ln v), dist[1] = sqrt; flags NONFINITE on bad scalings.

@@ -206,3 +206,23 @@ def test_benchmark_graphs_are_connected():
         n = len(X)
         A = csr_matrix((ex["A"], ex["col"], ex["rowptr"]), shape=(n, n))
         assert connected_components(A, directed=False)[0] == 1
+
+
+# ------------------------------------------------------------- Euler implicit kernel (Sec. 4)
+def test_euler_implicit_kernel_matches_its_spectral_form_and_tends_to_the_exponential():
+    # (I + (t/K) L)^{-K} = U diag((1 + t lambda / K)^{-K}) U^T, and -> exp(-t L) as K grows
+    from tests.oracle_helpers import dense_knn_laplacian, heat_eigh
+    X = W.sphere(300, seed=4).astype(np.float64)
+    Ls, _ = oracle.build_graph(X, 8)
+    Ld, *_ = dense_knn_laplacian(X, 8)
+    lam, U = np.linalg.eigh(Ld)
+    V = np.random.default_rng(2).random((300, 3))
+    t = 2.0
+    errs = []
+    for K in (5, 20, 80):
+        Y = oracle.heat_apply_implicit(Ls, t, K, V)
+        ref = (U * (1.0 + t * lam / K) ** (-K)) @ (U.T @ V)
+        np.testing.assert_allclose(Y, ref, rtol=1e-9, atol=1e-12)
+        errs.append(np.abs(Y - heat_eigh(Ld, t) @ V).max())
+    # first-order method: the error falls about fourfold per fourfold K
+    assert errs[0] > 3 * errs[1] > 9 * errs[2]
