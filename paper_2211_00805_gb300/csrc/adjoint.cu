@@ -3,11 +3,12 @@
 //
 // The filter is its own adjoint: p_K(L, t) is a polynomial in the symmetric matrix L, so every
 // transposed apply in the reverse sweep is the forward fused-order kernel again.  Forward state
-// is kept only at checkpoints; each segment is recomputed from its checkpoint with the filter
-// outputs saved (the tape), then swept backwards.  Reductions over nodes (the distance, the
+// is kept only at checkpoints; each segment is swept backwards from a tape of its filter outputs,
+// which the forward pass writes directly for the last segment and the reverse sweep recomputes
+// from the checkpoint for the others.  Reductions over nodes (the distance, the
 // barycenter weights' gradient) accumulate in FP64.
 //
-// Notation (BASELINE names; the paper's in brackets): a, b [mu, nu] marginals, u, v [v, w]
+// Notation (the library's names; the paper's in brackets): a, b [mu, nu] marginals, u, v [v, w]
 // scalings, vol [a] vertex weights.  Forward iteration j:
 //     s_j = H(vol v_{j-1}),  u_j = a / s_j,  r_j = H(vol u_j),  v_j = b / r_j
 // and W^2 = 4t sum vol (a ln u_T + b ln v_T).
@@ -92,10 +93,12 @@ __global__ void __launch_bounds__(256) by_adj_pre(int64_t n, int m, float* __res
                                                   const double* __restrict__ alpha,
                                                   float* __restrict__ X, double* __restrict__ partials)
 {
-    extern __shared__ double colacc[];  // [m]
-    for (int c = threadIdx.x; c < m; c += blockDim.x) colacc[c] = 0.0;
+    extern __shared__ double colacc[];  // [warps][m]: each warp sums its own rows, no atomics
+    const int nw = (int)(blockDim.x >> 5);
+    for (int c = threadIdx.x; c < nw * m; c += blockDim.x) colacc[c] = 0.0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    double* wacc = colacc + (threadIdx.x >> 5) * m;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n;
          row += warps) {
@@ -117,13 +120,17 @@ __global__ void __launch_bounds__(256) by_adj_pre(int64_t n, int m, float* __res
             const float vbc = vb[c];
             float dbar = -vbc * vn / d + Lb * (float)alpha[c] / d;
             float vpb = vbc * muj / d + dbar * rr[c];
-            atomicAdd(&colacc[c], (double)Lb * (double)logf(d));
+            wacc[c] += (double)Lb * (double)logf(d);  // lane c of this warp only
             vb[c] = vpb;
             X[row * m + c] = dbar * vp[c];
         }
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < m; c += blockDim.x) partials[(int64_t)blockIdx.x * m + c] += colacc[c];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += colacc[w * m + c];  // warps in order: repeatable sums
+        partials[(int64_t)blockIdx.x * m + c] += t;
+    }
 }
 
 // r_i = H(vol w_i) and w_i = mu_i / s_i:  Wbar = vol f ; X = Sbar = -Wbar w_i / s_i
@@ -228,17 +235,31 @@ gs_status gs_sinkhorn_grad_impl(gs_ctx* ctx, const gs_graph* g, const float* a, 
         return gs_filter_enqueue(ctx, g, c.data(), K, 1, in, true, A, nullptr, y, e, nullptr, nullptr);
     };
 
-    // forward with checkpoints of v_{j0}, j0 = 0, ck, 2ck, ...
+    // forward with checkpoints of v_{j0}, j0 = 0, ck, 2ck, ...; the last segment's states go
+    // straight to the tape, so the reverse sweep does not recompute that segment
+    float* ts = tape;                       // s_j
+    float* tu = tape + (size_t)ck * n;      // u_j
+    float* tr = tape + (size_t)2 * ck * n;  // r_j
+    float* tv = tape + (size_t)3 * ck * n;  // v_j
+    const int j0_last = (nseg - 1) * ck;
     scale_fill<<<nb(n, 256), 256, 0, s>>>(n, 1, nullptr, nullptr, cks);  // v_0 = 1
     scale_fill<<<nb(n, 256), 256, 0, s>>>(n, 1, vol, nullptr, x);
     gs_count(ctx, 2);
     for (int j = 1; j <= iters && st == GS_OK; ++j) {
-        st = half(a, u, nullptr);
-        if (st == GS_OK) st = half(b, v, nullptr);
+        if (j > j0_last) {
+            const size_t l = (size_t)(j - 1 - j0_last);
+            st = half(a, tu + l * n, ts + l * n);
+            if (st == GS_OK) st = half(b, tv + l * n, tr + l * n);
+        } else {
+            st = half(a, u, nullptr);
+            if (st == GS_OK) st = half(b, v, nullptr);
+        }
         if (st == GS_OK && j % ck == 0 && j < iters)
             cudaMemcpyAsync(cks + (size_t)(j / ck) * n, v, vec, cudaMemcpyDeviceToDevice, s);
     }
     if (st != GS_OK) return st;
+    u = tu + (size_t)(iters - 1 - j0_last) * n;  // the last iteration's scalings
+    v = tv + (size_t)(iters - 1 - j0_last) * n;
     if ((st = gs_distance_enqueue(ctx, n, a, b, vol, u, v, t, partials, dist)) != GS_OK) return st;
     sk_out_adj<<<nb(n, 256), 256, 0, s>>>(n, 4.0 * t, a, b, vol, u, v, ubar, vbar, grad_a, grad_b);
     gs_count(ctx, 1);
@@ -247,15 +268,13 @@ gs_status gs_sinkhorn_grad_impl(gs_ctx* ctx, const gs_graph* g, const float* a, 
     for (int seg = nseg - 1; seg >= 0 && st == GS_OK; --seg) {
         const int j0 = seg * ck;
         const int len = (iters - j0) < ck ? (iters - j0) : ck;
-        float* ts = tape;                       // s_j
-        float* tu = tape + (size_t)ck * n;      // u_j
-        float* tr = tape + (size_t)2 * ck * n;  // r_j
-        float* tv = tape + (size_t)3 * ck * n;  // v_j
-        scale_fill<<<nb(n, 256), 256, 0, s>>>(n, 1, vol, cks + (size_t)seg * n, x);
-        gs_count(ctx, 1);
-        for (int l = 0; l < len && st == GS_OK; ++l) {
-            st = half(a, tu + (size_t)l * n, ts + (size_t)l * n);
-            if (st == GS_OK) st = half(b, tv + (size_t)l * n, tr + (size_t)l * n);
+        if (seg < nseg - 1) {  // recompute the segment from its checkpoint (the last one is on tape)
+            scale_fill<<<nb(n, 256), 256, 0, s>>>(n, 1, vol, cks + (size_t)seg * n, x);
+            gs_count(ctx, 1);
+            for (int l = 0; l < len && st == GS_OK; ++l) {
+                st = half(a, tu + (size_t)l * n, ts + (size_t)l * n);
+                if (st == GS_OK) st = half(b, tv + (size_t)l * n, tr + (size_t)l * n);
+            }
         }
         for (int l = len - 1; l >= 0 && st == GS_OK; --l) {
             const bool last = (seg == nseg - 1) && (l == len - 1);
@@ -354,30 +373,41 @@ gs_status gs_barycenter_grad_impl(gs_ctx* ctx, const gs_graph* g, const float* M
         return r;
     };
 
-    // forward with checkpoints of V
+    // forward with checkpoints of V; the last segment's states go straight to the tape, so the
+    // reverse sweep does not recompute that segment
+    const int j0_last = (nseg - 1) * ck;
     scale_fill<<<nb(nm, 256), 256, 0, s>>>(nm, m, nullptr, nullptr, V);
     scale_fill<<<nb(nm, 256), 256, 0, s>>>(nm, m, vol, nullptr, x);
     gs_count(ctx, 2);
     for (int j = 0; j < iters && st == GS_OK; ++j) {
         if (j % ck == 0) cudaMemcpyAsync(cks + (size_t)(j / ck) * nm, V, blk, cudaMemcpyDeviceToDevice, s);
-        st = iterate(nullptr, nullptr, nullptr, mu_out);
+        if (j >= j0_last) {
+            const size_t l = (size_t)(j - j0_last);
+            st = iterate(tVp + l * nm, tS + l * nm, tR + l * nm, tmu + l * n);
+        } else {
+            st = iterate(nullptr, nullptr, nullptr, mu_out);
+        }
     }
     if (st != GS_OK) return st;
+    cudaMemcpyAsync(mu_out, tmu + (size_t)(iters - 1 - j0_last) * n, vecb, cudaMemcpyDeviceToDevice, s);
 
+    cudaFuncSetAttribute(by_adj_pre, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * 8 * m));
     cudaMemsetAsync(partials, 0, sizeof(double) * (size_t)kColBlocks * m, s);
     cudaMemsetAsync(Vbar, 0, blk, s);
     const unsigned rgrid = (unsigned)std::min<int64_t>(kColBlocks, (n + 7) / 8);
     for (int seg = nseg - 1; seg >= 0 && st == GS_OK; --seg) {
         const int j0 = seg * ck;
         const int len = (iters - j0) < ck ? (iters - j0) : ck;
-        cudaMemcpyAsync(V, cks + (size_t)seg * nm, blk, cudaMemcpyDeviceToDevice, s);
-        scale_fill<<<nb(nm, 256), 256, 0, s>>>(nm, m, vol, V, x);
-        gs_count(ctx, 1);
-        for (int l = 0; l < len && st == GS_OK; ++l)
-            st = iterate(tVp + (size_t)l * nm, tS + (size_t)l * nm, tR + (size_t)l * nm, tmu + (size_t)l * n);
+        if (seg < nseg - 1) {  // recompute the segment from its checkpoint (the last one is on tape)
+            cudaMemcpyAsync(V, cks + (size_t)seg * nm, blk, cudaMemcpyDeviceToDevice, s);
+            scale_fill<<<nb(nm, 256), 256, 0, s>>>(nm, m, vol, V, x);
+            gs_count(ctx, 1);
+            for (int l = 0; l < len && st == GS_OK; ++l)
+                st = iterate(tVp + (size_t)l * nm, tS + (size_t)l * nm, tR + (size_t)l * nm, tmu + (size_t)l * n);
+        }
         for (int l = len - 1; l >= 0 && st == GS_OK; --l) {
             const bool last = (seg == nseg - 1) && (l == len - 1);
-            by_adj_pre<<<rgrid, 256, sizeof(double) * m, s>>>(n, m, Vbar, tVp + (size_t)l * nm,
+            by_adj_pre<<<rgrid, 256, sizeof(double) * 8 * m, s>>>(n, m, Vbar, tVp + (size_t)l * nm,
                                                                tR + (size_t)l * nm, tmu + (size_t)l * n,
                                                                last ? mubar : nullptr, alpha, x, partials);
             gs_count(ctx, 1);

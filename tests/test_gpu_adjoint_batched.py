@@ -94,6 +94,12 @@ def test_barycenter_grad_matches_oracle(gs, ctx):
                                          alpha, it, mubar.astype(np.float64))
     assert_close(to_np(mu), rmu, 1e-4, 1e-6 * rmu.max(), "mu")
     assert_close(to_np(galpha), ralpha, GRTOL, GATOL_REL * np.abs(ralpha).max(), "dalpha")
+    # the checkpoint interval changes what is recomputed, never the values: bit for bit, including
+    # one segment (every state taped by the forward pass) and one iteration per segment
+    for ck in (1, 12):
+        mu2, ga2 = gs.gs_barycenter_grad(ctx, g, to_dev(M), to_dev(alpha, torch.float64), t, K, it,
+                                         to_dev(mubar), checkpoint=ck)
+        assert torch.equal(mu2, mu) and torch.equal(ga2, galpha), f"checkpoint {ck}"
 
 
 def test_autograd_distance_to_barycenter(gs, ctx):
