@@ -349,6 +349,7 @@ def run_ours(args, rank, world, local_rank):
         extras["adjoint_vs_plain"] = adjoint_case(gs, ctx, dev, stream)
         extras["barycentric_distance"] = families_case(gs, ctx, dev, stream)
         extras["implicit_vs_chebyshev"] = implicit_case(gs, ctx, dev, stream)
+        extras["log_domain_sinkhorn"] = logdomain_case(gs, ctx, dev, stream)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     Xh = torch.from_numpy(p.X).pin_memory()
@@ -516,6 +517,50 @@ def implicit_case(gs, ctx, dev, stream, t=5.0, K=30, iters=12):
     return {"workload": "manifold-100k-R50, B = 1", "t": t, "K": K, "cg_iters_per_step": iters,
             "implicit_ms": ms_e, "chebyshev_ms": ms_c, "implicit_over_chebyshev": ms_e / ms_c,
             "implicit_max_rel_err": err["e"], "chebyshev_max_rel_err": err["c"]}
+
+
+def logdomain_case(gs, ctx, dev, stream, iters_manifold=100):
+    """Log-domain Sinkhorn (FP64 potentials, extended-range Chebyshev recurrence): the 2,000-point
+    sphere pair at t = 1, K = 20, 200 iterations, where the FP32 scalings overflow; and the
+    100k-point manifold pair at t = 5, K = 30 against the FP32 loop over the same iterations (its
+    cost over the FP32 loop, and how far the two distances are apart)."""
+    import torch
+    out = {}
+    p = W.sphere_pair()
+    g = gs.gs_build_graph(ctx, torch.from_numpy(p.X).to(dev), p.k)
+    a, b = torch.from_numpy(p.a).to(dev), torch.from_numpy(p.b).to(dev)
+    run = lambda: out.__setitem__("s", gs.gs_sinkhorn_log(ctx, g, a, b, p.t, p.K, p.iters))  # noqa: E731
+    run()
+    ms_s = _time(stream, run)
+    gs.gs_sync(ctx)
+    w2_s = float(out["s"][2][0])
+    g.close()
+    q = W.manifold_pair()
+    g = gs.gs_build_graph(ctx, torch.from_numpy(q.X).to(dev), q.k)
+    a, b = torch.from_numpy(q.a).to(dev), torch.from_numpy(q.b).to(dev)
+    it = iters_manifold
+    run = lambda: out.__setitem__("m", gs.gs_sinkhorn_log(ctx, g, a, b, q.t, q.K, it))  # noqa: E731
+    run()
+    ms_m = _time(stream, run)
+    run32 = lambda: out.__setitem__("f", gs.gs_sinkhorn(ctx, g, a, b, q.t, q.K, it))  # noqa: E731
+    run32()
+    ms_f = _time(stream, run32)
+    gs.gs_sync(ctx)
+    w2_m, w2_f = float(out["m"][2][0]), float(out["f"][2][0])
+    g.close()
+    orders = 2 * q.K * it
+    # one order: CSR values and indices, the gathered mantissa and exponent, the row's previous
+    # vector, accumulator and output (8 bytes each)
+    order_bytes = 8 * g.nnz + 4 * (q.X.shape[0] + 1) + 32 * q.X.shape[0]
+    return {"sphere_2k_t1": {"workload": "sphere-2k, t = 1, K = 20 (FP32 scalings overflow here)",
+                             "iters": p.iters, "ms": ms_s, "iters_per_s": p.iters / (ms_s / 1e3),
+                             "W2": w2_s, "launches": 2 * p.K * p.iters + 2},
+            "manifold_100k_t5": {"workload": "manifold-100k-R50, t = 5, K = 30", "iters": it,
+                                 "log_domain_ms": ms_m, "fp32_loop_ms": ms_f,
+                                 "log_over_fp32": ms_m / ms_f, "W2_log": w2_m, "W2_fp32": w2_f,
+                                 "W2_rel_diff": abs(w2_m - w2_f) / abs(w2_f),
+                                 "order_us": ms_m * 1e3 / orders,
+                                 "order_GBps": order_bytes / (ms_m / 1e3 / orders) / 1e9}}
 
 
 def families_case(gs, ctx, dev, stream, bary_iters=100, sink_iters=200):

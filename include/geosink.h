@@ -279,6 +279,27 @@ gs_status gs_sinkhorn(gs_ctx *ctx, const gs_graph *g, const float *a, const floa
 gs_status gs_distance(gs_ctx *ctx, const gs_graph *g, const float *a, const float *b,
                       const float *vol, double t, int K, double eps, int iters, double *dist);
 
+/* Algorithm 1 in the log domain, for diffusion times small enough that the scalings of gs_sinkhorn
+ * leave the FP32 range (it reports GS_ERR_NONFINITE there).  The same iteration,
+ *     ln u <- ln a - ln p_K(vol * e^{ln v}),   ln v <- ln b - ln p_K(vol * e^{ln u}),   ln v = 0 at
+ * the start, with the potentials held in FP64 and every vector of the Chebyshev recurrence held as
+ * an FP32 mantissa with its own int32 binary exponent (each order's row sums align their terms to
+ * the row's largest exponent by exact powers of two), so no value of the loop over- or underflows.
+ * Result: the scalings of gs_sinkhorn as logarithms, and
+ *     dist[0] = W^2 = 4t sum_i vol_i (a_i ln u_i + b_i ln v_i),   dist[1] = W = sqrt(W^2)
+ * in FP64 (0 ln 0 := 0).  Runs exactly `iters` iterations (no eps stop), 2 K launches each, over
+ * the graph in the caller's node order.
+ *   a, b   : [n] non-negative marginals (device FP32; the caller normalises them)
+ *   vol    : [n] vertex weights or NULL
+ *   log_u, log_v : [n] double outputs (device), distinct buffers; -inf where a_i (b_i) = 0
+ *   dist   : [2] double output (device), may be NULL
+ * A non-positive p_K(vol * u)_i where the marginal is positive (the truncated series can dip below
+ * zero) gives NaN there and GS_ERR_NONFINITE at gs_sync.  Requires t > 0, 1 <= K <= 10000,
+ * iters >= 1.  Errors: GS_ERR_ARG. */
+gs_status gs_sinkhorn_log(gs_ctx *ctx, const gs_graph *g, const float *a, const float *b,
+                          const float *vol, double t, int K, int iters, double *log_u, double *log_v,
+                          double *dist);
+
 /* ---------------------------------------------------------------------------- barycenter --- */
 
 /* Fixed-support Wasserstein barycenter (Sec. 3.3) by iterative Bregman projections with the

@@ -50,6 +50,7 @@ SIGNATURES = {
     "gs_heat_apply_noalloc": [_I64, _I64, _P, _P, _P, _D, _I, _P, _I, _P, _P],
     "gs_sinkhorn": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P],
     "gs_distance": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P],
+    "gs_sinkhorn_log": [_P, _P, _P, _P, _P, _D, _I, _I, _P, _P, _P],
     "gs_barycenter": [_P, _P, _P, _I, _P, _P, _D, _I, _I, _P, _P],
     "gs_sinkhorn_grad": [_P, _P, _P, _P, _P, _D, _I, _I, _I, _P, _P, _P],
     "gs_barycenter_grad": [_P, _P, _P, _I, _P, _P, _D, _I, _I, _I, _P, _P, _P],
@@ -323,6 +324,25 @@ def gs_sinkhorn(ctx: Context, g: Graph, a: torch.Tensor, b: torch.Tensor, t: flo
     _raise(ctx, _lib.gs_sinkhorn(ctx.handle, g.handle, _ptr(a), _ptr(b), _ptr(vol), float(t), int(K),
                                  float(eps), int(iters), _ptr(u), _ptr(v), _ptr(dist), _ptr(iters_done)))
     return u, v, dist, iters_done
+
+
+def gs_sinkhorn_log(ctx: Context, g: Graph, a: torch.Tensor, b: torch.Tensor, t: float, K: int,
+                    iters: int, vol: torch.Tensor | None = None, log_u=None, log_v=None, dist=None):
+    """Algorithm 1 with FP64 potentials; returns (ln u, ln v, dist[2] FP64 = (W^2, W)), device tensors."""
+    n = g.n
+    _dev(a, torch.float32, "a", (n,))
+    _dev(b, torch.float32, "b", (n,))
+    if vol is not None:
+        _dev(vol, torch.float32, "vol", (n,))
+    dev = a.device
+    log_u = (torch.empty(n, dtype=torch.float64, device=dev) if log_u is None
+             else _dev(log_u, torch.float64, "log_u", (n,)))
+    log_v = (torch.empty(n, dtype=torch.float64, device=dev) if log_v is None
+             else _dev(log_v, torch.float64, "log_v", (n,)))
+    dist = torch.empty(2, dtype=torch.float64, device=dev) if dist is None else _dev(dist, torch.float64, "dist", (2,))
+    _raise(ctx, _lib.gs_sinkhorn_log(ctx.handle, g.handle, _ptr(a), _ptr(b), _ptr(vol), float(t), int(K),
+                                     int(iters), _ptr(log_u), _ptr(log_v), _ptr(dist)))
+    return log_u, log_v, dist
 
 
 def gs_distance(ctx: Context, g: Graph, a: torch.Tensor, b: torch.Tensor, t: float, K: int,

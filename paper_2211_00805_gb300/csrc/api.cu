@@ -434,6 +434,20 @@ extern "C" gs_status gs_heat_apply_implicit(gs_ctx* ctx, const gs_graph* g, doub
     return gs_heat_apply_implicit_impl(ctx, g, t, K, V, B, Y, tol, iters);
 }
 
+extern "C" gs_status gs_sinkhorn_log(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
+                                     const float* vol, double t, int K, int iters, double* log_u,
+                                     double* log_v, double* dist)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(a) || bad_ptr(b) || bad_ptr(log_u) || bad_ptr(log_v))
+        return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (log_u == log_v) return gs_fail(ctx, GS_ERR_ARG, "log_u and log_v must be distinct buffers");
+    if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
+    return gs_sinkhorn_log_impl(ctx, g, a, b, vol, t, K, iters, log_u, log_v, dist);
+}
+
 // ---------------------------------------------------------------------- families of distributions
 extern "C" gs_status gs_barycentric_distance(gs_ctx* ctx, const gs_graph* g, const float* MT, int mT,
                                              const double* alphaT, const float* MC, int mC,

@@ -1,0 +1,142 @@
+"""GPU log-domain Sinkhorn (gs_sinkhorn_log: Algorithm 1 with FP64 potentials and the
+extended-range Chebyshev recurrence) against the FP64 oracle's Sinkhorn loop.
+
+Tolerances: the recurrence adds FP32 mantissas (rounding ~6e-8 per operation, K orders of ~k
+terms per half-step); the loop does not expand errors in the potentials, so after 200 iterations
+they stay within ~1e-4 of the oracle's (a numpy model of the same arithmetic: 1.4e-5 on the case
+below).  Bounds: 5e-4 absolute on ln u, ln v; 1e-5 relative on W^2, whose constant-shift error
+cancels between the two equal-mass marginals.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_00805_gb300 import workloads as W
+from tests.gpu_common import oracle_csr_to_dev, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+LOG_ATOL, W2_RTOL = 5e-4, 1e-5
+
+
+@pytest.fixture(scope="module")
+def gs():
+    from paper_2211_00805_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(gs):
+    return gs.Context()
+
+
+@pytest.fixture(scope="module")
+def sphere(gs, ctx):
+    p = W.sphere_pair()
+    g = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    Ls, _ = oracle.build_graph(p.X.astype(np.float64), p.k)
+    return p, g, Ls
+
+
+def _check(gs, ctx, g, Ls, a, b, t, K, iters, vol=None):
+    lu, lv, dist = gs.gs_sinkhorn_log(ctx, g, to_dev(a), to_dev(b), t, K, iters,
+                                      vol=None if vol is None else to_dev(vol))
+    gs.gs_sync(ctx)
+    r = oracle.sinkhorn(Ls, oracle.cheb_coefficients(t, K), a.astype(np.float64), b.astype(np.float64), t,
+                        iters, a=None if vol is None else vol.astype(np.float64))
+    assert r["status"] == oracle.OK
+    lu, lv, d = to_np(lu), to_np(lv), to_np(dist)
+    for got, ref, marg, name in ((lu, r["v"], a, "ln u"), (lv, r["w"], b, "ln v")):
+        zero = marg == 0
+        assert np.all(np.isneginf(got[zero])), name  # no mass: u_i = 0
+        err = np.abs(got[~zero] - np.log(ref[~zero]))
+        assert err.max() < LOG_ATOL, f"{name}: max |error| {err.max():.3g}"
+    assert d[0] == pytest.approx(r["W2"], rel=W2_RTOL)
+    if r["W2"] >= 0:
+        assert d[1] == pytest.approx(r["W"], rel=W2_RTOL)
+    else:  # W^2 = 4t (1 + KL) can be negative: no real square root
+        assert np.isnan(d[1])
+    return lu, lv, d, r
+
+
+def test_log_sinkhorn_small_t_where_fp32_overflows(gs, ctx, sphere):
+    # the 2,000-point sphere pair at t = 1, K = 20, 200 iterations: the scalings reach e^{+-170}
+    p, g, Ls = sphere
+    lu, lv, d, r = _check(gs, ctx, g, Ls, p.a, p.b, 1.0, 20, 200)
+    assert max(np.abs(lu).max(), np.abs(lv).max()) > 150.0  # far outside FP32
+    # the FP32 loop cannot represent this case and says so
+    gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 1.0, 20, 200)
+    with pytest.raises(gs.GeosinkError) as e:
+        gs.gs_sync(ctx)
+    assert e.value.status == gs.GS_ERR_NONFINITE
+
+
+def test_log_sinkhorn_agrees_with_the_fp32_loop_where_both_fit(gs, ctx, sphere):
+    p, g, Ls = sphere
+    lu, lv, d, r = _check(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 200)
+    u, v, dist, _ = gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 200)
+    gs.gs_sync(ctx)
+    u, v = to_np(u).astype(np.float64), to_np(v).astype(np.float64)
+    m = (u > 0) & (np.abs(lu) < 80)
+    np.testing.assert_allclose(np.exp(lu[m]), u[m], rtol=1e-3)
+    m = (v > 0) & (np.abs(lv) < 80)
+    np.testing.assert_allclose(np.exp(lv[m]), v[m], rtol=1e-3)
+    assert d[0] == pytest.approx(to_np(dist)[0], rel=1e-4)
+
+
+def test_log_sinkhorn_vertex_weights_zero_mass_odd_K(gs, ctx, sphere):
+    p, g, Ls = sphere
+    vol = np.random.default_rng(1).uniform(0.5, 1.5, len(p.a)).astype(np.float32)
+    a = np.where(p.X[:, 2] > -0.2, p.a, 0).astype(np.float32)
+    a = (a / np.sum(a * vol)).astype(np.float32)
+    b = (p.b / np.sum(p.b * vol)).astype(np.float32)
+    _check(gs, ctx, g, Ls, a, b, 1.0, 21, 100, vol=vol)
+
+
+@pytest.mark.parametrize("t,K", [(2.0, 1), (3.0, 2), (0.5, 3), (0.5, 12)])
+def test_log_sinkhorn_low_degrees(gs, ctx, sphere, t, K):
+    # p_K reaches K hops only, so pole-to-pole marginals have no plan for K below the graph's
+    # diameter (the FP64 oracle's scalings diverge too); b = a times a random +-30% factor needs
+    # only local moves
+    p, g, Ls = sphere
+    b = p.a * (1 + 0.3 * np.random.default_rng(5).uniform(-1, 1, len(p.a)))
+    b = (b / b.sum()).astype(np.float32)
+    _check(gs, ctx, g, Ls, p.a, b, t, K, 60)
+
+
+def test_log_sinkhorn_tiny_graph_one_block_plus_a_row(gs, ctx):
+    # 33 rows: one full block of 32 lane groups and a ragged tail of one row
+    p = W.sphere_pair(n=33)
+    idx, dist = oracle.knn(p.X.astype(np.float64), 6)
+    rp, col, A = oracle.affinity_graph(idx, dist, oracle.median_sigma(dist))
+    g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
+    A32 = np.asarray(A, np.float32).astype(np.float64)  # the affinities the GPU holds
+    Ls = oracle.shifted(oracle.laplacian(rp, col, A32)[1])
+    _check(gs, ctx, g, Ls, p.a, p.b, 1.0, 20, 50)
+
+
+def test_log_sinkhorn_repeats_bit_for_bit(gs, ctx, sphere):
+    p, g, Ls = sphere
+    a, b = to_dev(p.a), to_dev(p.b)
+    r1 = [to_np(x) for x in gs.gs_sinkhorn_log(ctx, g, a, b, 1.0, 20, 40)]
+    r2 = [to_np(x) for x in gs.gs_sinkhorn_log(ctx, g, a, b, 1.0, 20, 40)]
+    gs.gs_sync(ctx)
+    for x, y in zip(r1, r2):
+        assert np.array_equal(x, y)
+
+
+def test_log_sinkhorn_rejects_bad_arguments(gs, ctx, sphere):
+    p, g, Ls = sphere
+    n = len(p.a)
+    lib = gs.lib()
+    a, b = to_dev(p.a), to_dev(p.b)
+    lu = torch.empty(n, dtype=torch.float64, device="cuda")
+    lv = torch.empty(n, dtype=torch.float64, device="cuda")
+    args = [ctx.handle, g.handle, a.data_ptr(), b.data_ptr(), None, 1.0, 20, 10, lu.data_ptr(), lv.data_ptr(), None]
+    assert lib.gs_sinkhorn_log(*args[:8], lu.data_ptr(), lu.data_ptr(), None) == gs.GS_ERR_ARG
+    assert lib.gs_sinkhorn_log(*args[:7], 0, *args[8:]) == gs.GS_ERR_ARG
+    assert lib.gs_sinkhorn_log(*args[:6], 0, *args[7:]) == gs.GS_ERR_ARG
+    assert lib.gs_sinkhorn_log(*args[:5], -1.0, *args[6:]) == gs.GS_ERR_ARG
+    assert lib.gs_sinkhorn_log(*args[:2], None, *args[3:]) == gs.GS_ERR_ARG
+    gs.gs_sync(ctx)  # the context stays usable

@@ -316,3 +316,31 @@ def test_expected_barycenter_effect_reproduces_table2(outlier, row):
     tau_tv = oracle.barycenter_effect(X[:, :1], MT.mean(1), MC.mean(1))[0]
     assert abs(tau - mean) < 3 * std
     assert abs(tau_tv - mean_tv) < 3 * std_tv
+
+
+def test_sinkhorn_small_t_beyond_fp32_matches_dense_log_sum_exp():
+    # The regime of the log-domain GPU loop: on the 2,000-point sphere pair at t = 1 the scalings
+    # leave the FP32 range (|ln u| > ln FLT_MAX = 88.72) within 30 iterations.  The oracle's FP64
+    # loop must still be exact there: compare it with the textbook log-domain form of the same
+    # iteration on the dense kernel, f <- ln mu - LSE_j(ln H_ij + g_j), g <- ln nu - LSE_i(ln H_ij + f_i),
+    # which never forms a scaling.
+    from scipy.special import logsumexp
+    p = W.sphere_pair()
+    Ls, _ = oracle.build_graph(p.X.astype(np.float64), p.k)
+    mu, nu = p.a.astype(np.float64), p.b.astype(np.float64)
+    t, K, iters = 1.0, 20, 30
+    b = oracle.cheb_coefficients(t, K)
+    r = oracle.sinkhorn(Ls, b, mu, nu, t, iters)
+    assert r["status"] == oracle.OK
+    H = _dense_filter(Ls, b, len(mu))
+    assert H.min() >= 0.0  # the truncated series stays non-negative on this graph
+    with np.errstate(divide="ignore"):
+        lH = np.log(H)
+    f, g = np.zeros(len(mu)), np.zeros(len(mu))
+    for _ in range(iters):
+        f = np.log(mu) - logsumexp(lH + g[None, :], axis=1)
+        g = np.log(nu) - logsumexp(lH.T + f[None, :], axis=1)
+    assert max(np.abs(f).max(), np.abs(g).max()) > 88.73
+    np.testing.assert_allclose(np.log(r["v"]), f, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(np.log(r["w"]), g, rtol=0, atol=1e-10)
+    assert r["W2"] == pytest.approx(4 * t * (mu @ f + nu @ g), rel=1e-12)
