@@ -287,8 +287,9 @@ gs_status gs_distance(gs_ctx *ctx, const gs_graph *g, const float *a, const floa
  * the row's largest exponent by exact powers of two), so no value of the loop over- or underflows.
  * Result: the scalings of gs_sinkhorn as logarithms, and
  *     dist[0] = W^2 = 4t sum_i vol_i (a_i ln u_i + b_i ln v_i),   dist[1] = W = sqrt(W^2)
- * in FP64 (0 ln 0 := 0).  Runs exactly `iters` iterations (no eps stop), 2 K launches each, over
- * the graph in the caller's node order.
+ * in FP64 (0 ln 0 := 0).  Runs exactly `iters` iterations (no eps stop), 2 K launches each (one
+ * iteration captured as a CUDA graph and replayed), in the graph's locality order; all arguments
+ * are in the caller's node order.
  *   a, b   : [n] non-negative marginals (device FP32; the caller normalises them)
  *   vol    : [n] vertex weights or NULL
  *   log_u, log_v : [n] double outputs (device), distinct buffers; -inf where a_i (b_i) = 0

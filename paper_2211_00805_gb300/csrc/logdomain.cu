@@ -5,18 +5,23 @@
 // With the potentials absorbed into the kernel, H (vol * v) becomes a sum whose terms span the same
 // range, and the Chebyshev recurrence of Sec. 3.5 carries them through K orders of signed sums.
 // Every vector of the recurrence is therefore held in an extended-range form: an FP32 mantissa m
-// and an int32 binary exponent e, value m 2^e (m = 0 for zero).  One order over a row takes the
-// largest exponent E of the terms it adds, scales every term by the exact power of two 2^{e - E},
-// adds the mantissas in FP32 and renormalises the sum (frexpf).  The sums carry FP32 rounding only
-// (no exponentials per nonzero); a term more than 2^126 below the row's largest one is dropped.
-// Coefficients c_k are split the same way on the host, so c_K below the FP32 range is no problem.
+// and an int32 binary exponent e, value m 2^e (m = 0 for zero), packed in 8 bytes.  Over a row,
+// each lane keeps its partial sum as s 2^E and raises E when a larger term arrives (the partial
+// is rescaled by an exact power of two); terms are scaled by 2^{e - E} and added in FP32, the
+// lanes' partials are aligned the same way, and the row's sum is renormalised (frexpf).  The sums
+// carry FP32 rounding only (no exponentials per nonzero); a term more than 2^126 below the row's
+// largest one is dropped.  Coefficients c_k are split the same way on the host, so c_K below the
+// FP32 range is no problem.
 //
-// Per Sinkhorn half-step (one application of p_K), K launches over the caller-order CSR of P:
+// Per Sinkhorn half-step (one application of p_K), K launches over the CSR of P in the graph's
+// locality order (marginals, weights and potentials are read and written through the node
+// permutation inside the kernels):
 //   order 0     : x1 = P x0;                y = c0 x0 + c1 x1
 //   order k >= 1: x_{k+1} = 2 P x_k - x_{k-1};  y += c_{k+1} x_{k+1}
 // and the last order ends with the division of Algorithm 1 in the log domain,
 //   ln u_i = ln a_i - ln y_i  (-inf where a_i = 0; NaN and GS_FLAG_NONFINITE where a_i > 0 and
-//   y_i <= 0), and writes the next half-step's input vol_i u_i in the extended form.
+//   y_i <= 0), and writes the next half-step's input vol_i u_i in the extended form.  One
+// iteration's 2K launches are captured once and replayed (the loop is launch-bound on small graphs).
 // Then W^2 = 4t sum_i vol_i (a_i ln u_i + b_i ln v_i) from the potentials, in FP64.
 #include <math.h>
 
@@ -27,81 +32,80 @@
 namespace {
 
 constexpr int kZeroExp = -(1 << 30);  // exponent stored with a zero mantissa
-constexpr int kLanes = 8;             // lanes summing one row
+constexpr int kLanes = 4;             // lanes summing one row
 constexpr int kXrThreads = 256;
 constexpr int kRowsPerBlock = kXrThreads / kLanes;
 constexpr int kRedThreads = 1024;
 constexpr double kLn2 = 0.69314718055994530942;
 
-// m 2^d for d <= 1: an exact power of two for d >= -126; the term is dropped below that
+// One vector entry, value m 2^e; packed so that a gather is one 8-byte load.
+struct __align__(8) Xr {
+    float m;  // |m| in [0.5, 1), or 0
+    int e;    // kZeroExp when m = 0
+};
+
+// m 2^d for d <= 0: an exact power of two for d >= -126; the term is dropped below that
 __device__ __forceinline__ float scale_pow2(float m, int d)
 {
     return d < -126 ? 0.f : m * __int_as_float((d + 127) << 23);
 }
 
-// s 2^E as a normalised (m, e): m in [0.5, 1) in magnitude, or m = 0
-__device__ __forceinline__ void xr_normalise(float s, int E, float& m, int& e)
+// keep the value s 2^E while raising E to at least e (exact: a power-of-two scaling)
+__device__ __forceinline__ void xr_raise(float& s, int& E, int e)
 {
-    if (s == 0.f || E == kZeroExp) {
-        m = 0.f;
-        e = kZeroExp;
-        return;
+    if (e > E) {
+        s = scale_pow2(s, E - e);
+        E = e;
     }
+}
+
+// s 2^E as a normalised entry
+__device__ __forceinline__ Xr xr_normalise(float s, int E)
+{
+    if (s == 0.f || E == kZeroExp) return Xr{0.f, kZeroExp};
     int ee;
-    m = frexpf(s, &ee);
-    e = E + ee;
+    const float m = frexpf(s, &ee);
+    return Xr{m, E + ee};
 }
 
-// (m1, e1) += (m2, e2)
-__device__ __forceinline__ void xr_add(float& m1, int& e1, float m2, int e2)
+// y + (m, e) for a nonzero m in [0.25, 1)
+__device__ __forceinline__ Xr xr_add(Xr y, float m, int e)
 {
-    if (m2 == 0.f) return;
-    if (m1 == 0.f) {
-        m1 = m2;
-        e1 = e2;
-        return;
-    }
-    const int E = max(e1, e2);
-    xr_normalise(scale_pow2(m1, e1 - E) + scale_pow2(m2, e2 - E), E, m1, e1);
+    if (y.m == 0.f) return xr_normalise(m, e);
+    float s = y.m;
+    int E = y.e;
+    xr_raise(s, E, e);
+    return xr_normalise(s + scale_pow2(m, e - E), E);
 }
 
-// ln|value| parts -> extended form of exp(z) (z = -inf gives zero)
-__device__ __forceinline__ void xr_from_log(double z, float& m, int& e)
+// the extended form of exp(z) (z = -inf gives zero)
+__device__ __forceinline__ Xr xr_from_log(double z)
 {
-    if (z == -INFINITY) {
-        m = 0.f;
-        e = kZeroExp;
-        return;
-    }
+    if (!(z > -INFINITY)) return Xr{0.f, kZeroExp};  // -inf, or NaN (already flagged)
     const double f = floor(z / kLn2);
-    m = (float)(0.5 * exp(z - f * kLn2));  // in [0.5, 1)
-    e = (int)f + 1;
+    return Xr{(float)(0.5 * exp(z - f * kLn2)), (int)f + 1};  // mantissa in [0.5, 1)
 }
 
 struct XrOrder {
     int64_t n;
-    const int* rowptr;
+    const int* rowptr;  // the filter's CSR of P (node order of the graph's locality ordering)
     const int* col;
     const float* pval;
-    const float* xm;  // T_k x, gathered
-    const int* xe;
-    const float* zm;  // T_{k-1} x, own row only; null in order 0
-    const int* ze;
-    float* om;  // T_{k+1} x (not written by the last order)
-    int* oe;
-    float* ym;  // accumulator y, own row only
-    int* ye;
-    float c0m;  // order 0: coefficient of T_0 (mantissa, exponent)
+    const int* perm;  // filter position -> caller's node index, or null
+    const Xr* x;      // T_k x, gathered
+    const Xr* z;      // T_{k-1} x, own row only; null in order 0
+    Xr* out;          // T_{k+1} x (not written by the last order)
+    Xr* y;            // accumulator, own row only
+    float c0m;        // order 0: coefficient of T_0 (mantissa, exponent)
     int c0e;
     float cm;  // coefficient of T_{k+1}
     int ce;
-    int twice;  // 0: P x (order 0), 1: 2 P x
-    int last;   // last order: division epilogue instead of storing y and T_{k+1} x
-    const float* marg;  // a (or b) of the division
-    const float* vol;   // vertex weights or null
-    double* logout;     // ln u (or ln v)
-    float* nm;          // next half-step's input vol * u
-    int* ne;
+    float twice;  // 1: P x (order 0), 2: 2 P x
+    int last;     // last order: division epilogue instead of storing y and T_{k+1} x
+    const float* marg;  // a (or b) of the division, caller order
+    const float* vol;   // vertex weights or null, caller order
+    double* logout;     // ln u (or ln v), caller order
+    Xr* next;           // next half-step's input vol * u, filter order
     int* flags;
 };
 
@@ -110,95 +114,74 @@ __global__ void __launch_bounds__(kXrThreads) xr_order(XrOrder p)
     const int64_t row = (int64_t)blockIdx.x * kRowsPerBlock + (threadIdx.x / kLanes);
     const int lane = threadIdx.x & (kLanes - 1);
     if (row >= p.n) return;  // whole lane groups leave together
-    const unsigned gmask = 0xffu << (threadIdx.x & 24);
+    const unsigned gmask = ((1u << kLanes) - 1u) << (threadIdx.x & 31 & ~(kLanes - 1));
     const int beg = p.rowptr[row], end = p.rowptr[row + 1];
-    // pass 1: largest exponent of the row's terms
+    // each lane: s 2^E over its entries, E raised as larger terms arrive
+    float s = 0.f;
     int E = kZeroExp;
     for (int k = beg + lane; k < end; k += kLanes) {
-        const int j = p.col[k];
-        if (p.xm[j] != 0.f) E = max(E, p.xe[j]);
-    }
-    for (int off = kLanes / 2; off > 0; off >>= 1) E = max(E, __shfl_xor_sync(gmask, E, off));
-    float zm = 0.f;
-    int ze = kZeroExp;
-    if (p.zm) {
-        zm = p.zm[row];
-        ze = p.ze[row];
-        if (zm != 0.f) E = max(E, ze);
-    }
-    // pass 2: mantissas aligned to 2^E, summed in FP32 (lane partials, then a fixed butterfly)
-    float s = 0.f;
-    if (E != kZeroExp) {
-        for (int k = beg + lane; k < end; k += kLanes) {
-            const int j = p.col[k];
-            const float m = p.xm[j];
-            if (m != 0.f) s = fmaf(p.pval[k], scale_pow2(m, p.xe[j] - E + p.twice), s);
+        const Xr x = p.x[p.col[k]];
+        if (x.m != 0.f) {
+            xr_raise(s, E, x.e);
+            s = fmaf(p.twice * p.pval[k], scale_pow2(x.m, x.e - E), s);
         }
     }
-    for (int off = kLanes / 2; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off);
-    if (zm != 0.f) s -= scale_pow2(zm, ze - E);
-    float xm1;
-    int xe1;
-    xr_normalise(s, E, xm1, xe1);
+    // lane partials combined by a fixed butterfly (both partners compute the same sum)
+    for (int off = kLanes / 2; off > 0; off >>= 1) {
+        const float so = __shfl_xor_sync(gmask, s, off);
+        const int Eo = __shfl_xor_sync(gmask, E, off);
+        const int Em = max(E, Eo);
+        s = scale_pow2(s, E - Em) + scale_pow2(so, Eo - Em);
+        E = Em;
+    }
     if (lane != 0) return;
-    // accumulator
-    float ym;
-    int ye;
-    if (p.zm) {
-        ym = p.ym[row];
-        ye = p.ye[row];
-    } else {  // order 0: y = c0 x0
-        const float x0 = p.xm[row];
-        ym = 0.f;
-        ye = kZeroExp;
-        if (x0 != 0.f && p.c0m != 0.f) {
-            int ee;
-            ym = frexpf(p.c0m * x0, &ee);
-            ye = p.c0e + p.xe[row] + ee;
+    if (p.z) {
+        const Xr z = p.z[row];
+        if (z.m != 0.f) {
+            xr_raise(s, E, z.e);
+            s -= scale_pow2(z.m, z.e - E);
         }
     }
-    if (xm1 != 0.f) {
-        int ee;
-        const float pm = frexpf(p.cm * xm1, &ee);
-        xr_add(ym, ye, pm, p.ce + xe1 + ee);
+    const Xr xn = xr_normalise(s, E);
+    Xr y{0.f, kZeroExp};
+    if (p.z) {
+        y = p.y[row];
+    } else {  // order 0: y = c0 x0
+        const Xr x0 = p.x[row];
+        if (x0.m != 0.f && p.c0m != 0.f) {
+            int ee;
+            const float m = frexpf(p.c0m * x0.m, &ee);
+            y = Xr{m, p.c0e + x0.e + ee};
+        }
     }
+    if (xn.m != 0.f && p.cm != 0.f) y = xr_add(y, p.cm * xn.m, p.ce + xn.e);
     if (!p.last) {
-        p.om[row] = xm1;
-        p.oe[row] = xe1;
-        p.ym[row] = ym;
-        p.ye[row] = ye;
+        p.out[row] = xn;
+        p.y[row] = y;
         return;
     }
     // division epilogue (Algorithm 1) in the log domain
-    const float a = p.marg[row];
+    const int64_t node = p.perm ? p.perm[row] : row;
+    const float a = p.marg[node];
     double lu;
     if (a == 0.f) {
         lu = -INFINITY;
-    } else if (ym > 0.f) {
-        lu = log((double)a) - (log((double)ym) + (double)ye * kLn2);
+    } else if (y.m > 0.f) {
+        lu = log((double)a) - (log((double)y.m) + (double)y.e * kLn2);
     } else {
         lu = NAN;
         atomicOr(p.flags, GS_FLAG_NONFINITE);
     }
-    p.logout[row] = lu;
-    const double z = lu + (p.vol ? log((double)p.vol[row]) : 0.0);
-    float m;
-    int e;
-    xr_from_log(z == z ? z : -INFINITY, m, e);
-    p.nm[row] = m;
-    p.ne[row] = e;
+    p.logout[node] = lu;
+    p.next[row] = xr_from_log(lu + (p.vol ? log((double)p.vol[node]) : 0.0));
 }
 
-// x0 = vol * 1 (the first half-step's input, v = 1)
-__global__ void xr_init(int64_t n, const float* __restrict__ vol, float* __restrict__ m, int* __restrict__ e)
+// x0 = vol * 1 (the first half-step's input, v = 1), filter order
+__global__ void xr_init(int64_t n, const int* __restrict__ perm, const float* __restrict__ vol, Xr* __restrict__ x)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float mm;
-    int ee;
-    xr_from_log(vol ? log((double)vol[i]) : 0.0, mm, ee);
-    m[i] = mm;
-    e[i] = ee;
+    x[i] = xr_from_log(vol ? log((double)vol[perm ? perm[i] : i]) : 0.0);
 }
 
 // W^2 = 4t sum_i vol_i (a_i ln u_i + b_i ln v_i) (0 ln 0 := 0), one block, fixed summation order
@@ -227,27 +210,51 @@ __global__ void __launch_bounds__(kRedThreads) xr_distance(int64_t n, const floa
     dist[1] = W2 >= 0.0 ? sqrt(W2) : NAN;
 }
 
+// Runs body() once under stream capture on the context's private capture stream (ctx->stream
+// points there meanwhile, and launches are not counted) and instantiates the graph.
+template <class F>
+gs_status capture_iteration(gs_ctx* ctx, F&& body, cudaGraphExec_t* out)
+{
+    if (!ctx->cap) {
+        gs_status st = gs_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking),
+                                     "capture stream");
+        if (st != GS_OK) return st;
+    }
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->cap;
+    ctx->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+    const gs_status st = e == cudaSuccess ? body() : GS_OK;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->cap, &graph) : e;
+    ctx->stream = user;
+    ctx->capturing = false;
+    if (st != GS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    gs_status st2 = gs_cuda_check(ctx, e2, "graph capture");
+    if (st2 != GS_OK) return st2;
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    return gs_cuda_check(ctx, e, "graph instantiate");
+}
+
 }  // namespace
 
 gs_status gs_sinkhorn_log_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b, const float* vol,
                                double t, int K, int iters, double* log_u, double* log_v, double* dist)
 {
     const int64_t n = g->n;
+    const bool reordered = g->perm && g->prowptr;
+    const FilterCsr fc = reordered ? gs_filter_csr(g) : FilterCsr{g->rowptr, g->col, g->pval};
     WsPlan plan;
-    const size_t fb = sizeof(float) * (size_t)n, ib = sizeof(int) * (size_t)n;
-    size_t im[6], ie[6];
-    for (int i = 0; i < 6; ++i) {  // two inputs (ping-pong), three recurrence vectors, accumulator
-        im[i] = plan.add(fb);
-        ie[i] = plan.add(ib);
-    }
+    size_t ix[6];
+    for (int i = 0; i < 6; ++i) ix[i] = plan.add(sizeof(Xr) * (size_t)n);  // two inputs, three vectors, y
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
-    float* M[6];
-    int* E[6];
-    for (int i = 0; i < 6; ++i) {
-        M[i] = ws_at<float>(ctx, plan, im[i]);
-        E[i] = ws_at<int>(ctx, plan, ie[i]);
-    }
+    Xr* X[6];
+    for (int i = 0; i < 6; ++i) X[i] = ws_at<Xr>(ctx, plan, ix[i]);
     std::vector<double> c((size_t)K + 1);
     gs_heat_coefficients(t, K, c.data());
     std::vector<float> cm((size_t)K + 1);
@@ -257,45 +264,50 @@ gs_status gs_sinkhorn_log_impl(gs_ctx* ctx, const gs_graph* g, const float* a, c
         cm[k] = (float)frexp(c[k], &ee);
         ce[k] = ee;
     }
-    cudaStream_t s = ctx->stream;
     const unsigned grid = (unsigned)((n + kRowsPerBlock - 1) / kRowsPerBlock);
-    xr_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, vol, M[0], E[0]);
-    int in = 0;  // the current input is buffer `in`, the next one 1 - in; 2..4 recurrence, 5 y
-    for (int it = 0; it < 2 * iters; ++it) {
-        const bool half_u = (it & 1) == 0;
-        XrOrder p{};
-        p.n = n;
-        p.rowptr = g->rowptr;
-        p.col = g->col;
-        p.pval = g->pval;
-        p.ym = M[5];
-        p.ye = E[5];
-        p.c0m = cm[0];
-        p.c0e = ce[0];
-        p.marg = half_u ? a : b;
-        p.vol = vol;
-        p.logout = half_u ? log_u : log_v;
-        p.nm = M[1 - in];
-        p.ne = E[1 - in];
-        p.flags = ctx->flags;
-        for (int k = 0; k < K; ++k) {
-            // gathers x_k, subtracts x_{k-1}, writes x_{k+1}: x_0 is the input, x_j (j >= 1) is 2 + (j - 1) % 3
-            const int xk = k == 0 ? in : 2 + (k - 1) % 3;
-            const int zk = k == 0 ? -1 : (k == 1 ? in : 2 + (k - 2) % 3);
-            const int ok = 2 + k % 3;
-            p.xm = M[xk];
-            p.xe = E[xk];
-            p.zm = zk < 0 ? nullptr : M[zk];
-            p.ze = zk < 0 ? nullptr : E[zk];
-            p.om = M[ok];
-            p.oe = E[ok];
-            p.cm = cm[k + 1];
-            p.ce = ce[k + 1];
-            p.twice = k == 0 ? 0 : 1;
-            p.last = k == K - 1;
-            xr_order<<<grid, kXrThreads, 0, s>>>(p);
+    // one iteration: two half-steps of K orders; the input starts in buffer 0 and comes back to it
+    auto iteration = [&]() -> gs_status {
+        for (int half = 0; half < 2; ++half) {
+            const int in = half;  // this half-step reads buffer `in`, writes the next input to 1 - in
+            XrOrder p{};
+            p.n = n;
+            p.rowptr = fc.rowptr;
+            p.col = fc.col;
+            p.pval = fc.pval;
+            p.perm = reordered ? g->perm : nullptr;
+            p.y = X[5];
+            p.c0m = cm[0];
+            p.c0e = ce[0];
+            p.marg = half == 0 ? a : b;
+            p.vol = vol;
+            p.logout = half == 0 ? log_u : log_v;
+            p.next = X[1 - in];
+            p.flags = ctx->flags;
+            for (int k = 0; k < K; ++k) {
+                // x_0 is the input; x_j (j >= 1) lives in buffer 2 + (j - 1) % 3
+                p.x = X[k == 0 ? in : 2 + (k - 1) % 3];
+                p.z = k == 0 ? nullptr : X[k == 1 ? in : 2 + (k - 2) % 3];
+                p.out = X[2 + k % 3];
+                p.cm = cm[k + 1];
+                p.ce = ce[k + 1];
+                p.twice = k == 0 ? 1.f : 2.f;
+                p.last = k == K - 1;
+                xr_order<<<grid, kXrThreads, 0, ctx->stream>>>(p);
+            }
         }
-        in = 1 - in;
+        return gs_cuda_check(ctx, cudaGetLastError(), "log-domain Sinkhorn order");
+    };
+    cudaStream_t s = ctx->stream;
+    xr_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, reordered ? g->perm : nullptr, vol, X[0]);
+    if (iters == 1) {
+        if ((st = iteration()) != GS_OK) return st;
+    } else {  // launch-bound on small graphs: replay one captured iteration
+        cudaGraphExec_t exec = nullptr;
+        if ((st = capture_iteration(ctx, iteration, &exec)) != GS_OK) return st;
+        cudaError_t e = cudaSuccess;
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) e = cudaGraphLaunch(exec, s);
+        cudaGraphExecDestroy(exec);  // freed once the launches above have run
+        if ((st = gs_cuda_check(ctx, e, "log-domain Sinkhorn replay")) != GS_OK) return st;
     }
     gs_count(ctx, 1 + 2 * (int64_t)iters * K);
     if (dist) {
