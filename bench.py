@@ -549,9 +549,9 @@ def logdomain_case(gs, ctx, dev, stream, iters_manifold=100):
     w2_m, w2_f = float(out["m"][2][0]), float(out["f"][2][0])
     g.close()
     orders = 2 * q.K * it
-    # one order: CSR values and indices, the gathered mantissa and exponent, the row's previous
-    # vector, accumulator and output (8 bytes each)
-    order_bytes = 8 * g.nnz + 4 * (q.X.shape[0] + 1) + 32 * q.X.shape[0]
+    # one order: CSR values and indices; per row the gathered entry (once), the previous vector,
+    # the accumulator read and written, and the output (8 bytes each)
+    order_bytes = 8 * g.nnz + 4 * (q.X.shape[0] + 1) + 40 * q.X.shape[0]
     return {"sphere_2k_t1": {"workload": "sphere-2k, t = 1, K = 20 (FP32 scalings overflow here)",
                              "iters": p.iters, "ms": ms_s, "iters_per_s": p.iters / (ms_s / 1e3),
                              "W2": w2_s, "launches": 2 * p.K * p.iters + 2},
