@@ -15,6 +15,9 @@ Notation follows the paper (arXiv 2211.00805):
              Algorithm 1 (Sec. 4);
 * barycenter: distributions mu_i, weights alpha_i, scalings v_i, w_i (Sec. 3.3, with the
              iterative-Bregman-projection algorithm of the convolutional-Wasserstein paper it cites).
+* the combinatorial Laplacian D - A itself (Sec. 3.4), as a filter variant:
+             ``combinatorial_shifted`` rescales it by 2 / lam, lam = 2 max D_ii >= lambda_n, and
+             ``heat_apply_combinatorial`` runs the same expansion at time t lam / 2.
 
 Two heavy loops (brute-force kNN and the CSR recurrence) live in ``oracle_core.c``, compiled with
 plain ``gcc -O2 -fopenmp``; everything else is numpy, one step per line of the method.
@@ -169,6 +172,40 @@ def shifted(L):
     rp2 = np.zeros(n + 1, np.int64)
     np.cumsum(np.bincount(row[keep], minlength=n), out=rp2[1:])
     return rp2, np.ascontiguousarray(col[keep]), np.ascontiguousarray(val[keep])
+
+
+def combinatorial_shifted(rowptr, col, A):
+    """The combinatorial Laplacian L = D - A of Sec. 3.4 brought to the spectrum [0, 2] that Sec. 3.5
+    assumes: L' = (2 / lam) L with lam = 2 max_i D_ii, an upper bound on the largest eigenvalue
+    (Gershgorin: every disc of D - A lies in [0, 2 D_ii]).  Since exp(-t L) = exp(-s L') with
+    s = t lam / 2, the expansion of Sec. 3.5 at time s in T_k(L' - Id) approximates the heat kernel
+    of the combinatorial Laplacian.
+
+    Returns ``((rowptr, col, val), lam)``: the shifted operator L' - Id as CSR with its diagonal
+    2 D_ii / lam - 1 stored (columns ascending), and lam.
+    """
+    rowptr = np.asarray(rowptr, np.int64)
+    col = np.asarray(col, np.int32)
+    A = np.asarray(A, np.float64)
+    n = len(rowptr) - 1
+    row = np.repeat(np.arange(n), np.diff(rowptr))
+    deg = np.bincount(row, weights=A, minlength=n)
+    lam = 2.0 * float(deg.max())
+    rows = np.concatenate([row, np.arange(n)])
+    cols = np.concatenate([col.astype(np.int64), np.arange(n)])
+    vals = np.concatenate([-(2.0 / lam) * A, (2.0 / lam) * deg - 1.0])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rp[1:])
+    return (rp, cols.astype(np.int32), vals), lam
+
+
+def heat_apply_combinatorial(rowptr, col, A, t: float, K: int, V):
+    """p_K of exp(-t (D - A)) applied to V: the recurrence of Sec. 3.5 on L' - Id at time t lam / 2
+    (see ``combinatorial_shifted``)."""
+    Ls, lam = combinatorial_shifted(rowptr, col, A)
+    return heat_apply(Ls, cheb_coefficients(t * lam / 2.0, K), V)
 
 
 def build_graph(X, k: int, sigma: float = 0.0):

@@ -226,3 +226,62 @@ def test_euler_implicit_kernel_matches_its_spectral_form_and_tends_to_the_expone
         errs.append(np.abs(Y - heat_eigh(Ld, t) @ V).max())
     # first-order method: the error falls about fourfold per fourfold K
     assert errs[0] > 3 * errs[1] > 9 * errs[2]
+
+
+# ----------------------------------------------- combinatorial Laplacian D - A (Sec. 3.4 / 3.5)
+@pytest.mark.parametrize("t,K", [(0.2, 20), (0.5, 30)])
+def test_combinatorial_filter_matches_dense_expm(t, K):
+    X, Ls, ex = _small_graph()
+    n = len(X)
+    _, A, deg, _ = dense_knn_laplacian(X, 6)
+    Lc = np.diag(deg) - A  # straight from the coordinates
+    V = np.random.default_rng(4).standard_normal((n, 3))
+    Y = oracle.heat_apply_combinatorial(ex["rowptr"], ex["col"], ex["A"], t, K, V)
+    lam = 2.0 * deg.max()
+    # |T_k| <= 1 on the spectrum of L' - Id, so the error is at most the tail at time t lam / 2
+    bound = bessel_tail_bound(t * lam / 2, K) * np.linalg.norm(V, axis=0).max() + 1e-12
+    assert np.max(np.abs(Y - heat_expm(Lc, t) @ V)) <= bound
+
+
+def test_combinatorial_rescaling_bounds_the_spectrum():
+    X, Ls, ex = _small_graph()
+    n = len(X)
+    (rp, col, val), lam = oracle.combinatorial_shifted(ex["rowptr"], ex["col"], ex["A"])
+    M = csr_to_dense(rp, col, val, n)
+    ev = np.linalg.eigvalsh(M)
+    assert ev.min() >= -1 - 1e-12 and ev.max() <= 1 + 1e-12
+    np.testing.assert_allclose(M @ np.ones(n), -np.ones(n), atol=1e-13)  # L 1 = 0
+    _, A, deg, _ = dense_knn_laplacian(X, 6)
+    assert np.linalg.eigvalsh(np.diag(deg) - A).max() <= lam
+    assert lam == pytest.approx(2.0 * deg.max(), rel=1e-13)
+
+
+def test_combinatorial_heat_preserves_constants_and_mass():
+    # exp(-t (D - A)) fixes constants and, being symmetric, the total mass sum_i f_i
+    X, Ls, ex = _small_graph()
+    n = len(X)
+    t, K = 0.5, 30
+    (_, _, _), lam = oracle.combinatorial_shifted(ex["rowptr"], ex["col"], ex["A"])
+    tail = bessel_tail_bound(t * lam / 2, K)
+    y = oracle.heat_apply_combinatorial(ex["rowptr"], ex["col"], ex["A"], t, K, np.ones(n))
+    assert np.max(np.abs(y - 1.0)) <= tail + 1e-13
+    f = np.random.default_rng(6).random(n)
+    g = oracle.heat_apply_combinatorial(ex["rowptr"], ex["col"], ex["A"], t, K, f)
+    assert abs(g.sum() - f.sum()) <= tail * f.sum() + 1e-12
+    assert np.max(np.abs(g - f)) > 1e-3  # and it does diffuse
+
+
+@pytest.mark.parametrize("n,t,K", [(50, 0.5, 30), (64, 1.5, 40)])
+def test_combinatorial_cycle_closed_form(n, t, K):
+    # cycle C_n, unit weights: D - A = 2 I - A has eigenvalues 2 - 2 cos(2 pi m / n) on the Fourier
+    # modes (twice the normalised Laplacian's), so H_t(i, 0) is the Fourier sum below
+    rowptr = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
+    col = np.empty(2 * n, np.int32)
+    for i in range(n):
+        col[2 * i:2 * i + 2] = sorted([(i - 1) % n, (i + 1) % n])
+    e0 = np.zeros(n); e0[0] = 1.0
+    y = oracle.heat_apply_combinatorial(rowptr, col, np.ones(2 * n), t, K, e0)
+    m = np.arange(n)
+    closed = (np.exp(-t * (2 - 2 * np.cos(2 * np.pi * m / n)))[None, :]
+              * np.cos(2 * np.pi * np.outer(m, m) / n)).sum(1) / n
+    assert np.max(np.abs(y - closed)) <= bessel_tail_bound(2 * t, K) + 1e-14
