@@ -181,8 +181,9 @@ gs_status gs_build_graph(gs_ctx *ctx, const float *X, int64_t n, int d, int k, f
 
 /* Build the operator from a caller-supplied symmetric weighted adjacency in CSR form
  * (device rowptr [n+1] int64, col [nnz] int32 ascending per row, w [nnz] FP32 >= 0, no self-
- * loops, every row non-empty).  Degrees and P are formed as in gs_build_graph.  Symmetry is the
- * caller's promise and is not checked.  Errors: GS_ERR_ARG (n < 2, nnz >= 2^31), GS_ERR_OOM. */
+ * loops, every row non-empty).  Degrees and P are formed as in gs_build_graph (Sec. 3.4).
+ * Symmetry is the caller's promise and is not checked.  Errors: GS_ERR_ARG (n < 2,
+ * nnz >= 2^31), GS_ERR_OOM. */
 gs_status gs_graph_from_csr(gs_ctx *ctx, int64_t n, const int64_t *rowptr, const int32_t *col,
                             const float *w, gs_graph **out);
 
@@ -192,15 +193,15 @@ gs_status gs_graph_info(const gs_graph *g, int64_t *n, int64_t *nnz, double *sig
 
 /* Host query of the graph's execution layout (diagnostics; not in the paper).  Writes up to
  * `count` values into `out`, in this order: 0 sliced-ELL slices, 1 sliced-ELL entries (with
- * padding), 2 gather-cache tables built (0/1), 3 partition blocks, 4 rows of the largest block, 5 largest
- * entry count of a block, 6 largest distinct-column count of a block, 7 sum of the blocks'
+ * padding), 2 gather-cache tables built (0/1), 3 partition blocks, 4 rows of the largest block,
+ * 5 largest entry count of a block, 6 largest distinct-column count of a block, 7 sum of the blocks'
  * distinct-column counts, 8 largest dependency-list length.  Errors: GS_ERR_ARG. */
 gs_status gs_graph_layout(const gs_graph *g, int64_t *out, int count);
 
 /* Copy the graph out in CSR form, rows in node order and columns ascending (device arrays:
  * rowptr [n+1] int64, col [nnz] int32, A [nnz] FP32 affinities, P [nnz] FP32 normalised
- * weights).  Any of the output pointers may be NULL.  Used to check edge sets against a
- * reference. */
+ * weights D^{-1/2} A D^{-1/2}, both of Sec. 3.4).  Any of the output pointers may be NULL.  Used
+ * to check edge sets against a reference. */
 gs_status gs_graph_export_csr(gs_ctx *ctx, const gs_graph *g, int64_t *rowptr, int32_t *col,
                               float *A, float *P);
 
@@ -234,8 +235,8 @@ gs_status gs_heat_apply(gs_ctx *ctx, const gs_graph *g, double t, int K, const f
  * that runs while a CUDA graph is being captured, plug-ins whose host application owns every
  * device allocation, loops that must never enter the allocator.  The paper has no counterpart;
  * this is a deployment convenience.
- * It computes the same Y = p_K(L, t) V with the same kernels, but takes the operator as plain
- * CSR device arrays (rowptr [n+1] int32 offsets, col [nnz] int32, pval [nnz] FP32 holding
+ * It computes the same Y = p_K(L, t) V (Sec. 3.5) with the same kernels, but takes the operator
+ * as plain CSR device arrays (rowptr [n+1] int32 offsets, col [nnz] int32, pval [nnz] FP32 holding
  * P = D^{-1/2} A D^{-1/2}, as gs_graph_export_csr returns them once rowptr is narrowed to int32)
  * and needs no gs_ctx or gs_graph.  Its two scratch blocks live in a fixed 8 MiB device array
  * inside the library, present on every GPU that loads it until the process exits, so
@@ -388,14 +389,14 @@ gs_status gs_barycenter_grad(gs_ctx *ctx, const gs_graph *g, const float *M, int
 
 /* ------------------------------------------------------------------------------ batched --- */
 
-/* Many independent Algorithm-1 problems in one persistent launch (not in the paper; it serves
- * workloads with many small distances).  Problem i has graph graphs[i] (any size, any order),
- * marginals a[i], b[i] (device [n_i]), diffusion time t[i] and degree K[i]; all run `iters`
- * iterations with unit vertex weights.  Outputs u[i], v[i] (device [n_i]) and dist[2i], dist[2i+1]
- * (device doubles: W^2, W).  `graphs`, `a`, `b`, `t`, `K`, `u`, `v` are HOST arrays of length
- * nprob.  Each problem runs on one thread-block cluster whose Chebyshev orders are separated by
- * hardware cluster barriers.  Requires 1 <= nprob, every K[i] >= 1, t[i] > 0.
- * Errors: GS_ERR_ARG. */
+/* Many independent Algorithm 1 problems in one persistent launch (the batching is not in the
+ * paper; it serves workloads with many small distances). Problem i has graph graphs[i] (any size,
+ * any order), marginals a[i], b[i] (device [n_i]), diffusion time t[i] and degree K[i]; all run
+ * `iters` iterations with unit vertex weights. Outputs u[i], v[i] (device [n_i]) and dist[2i],
+ * dist[2i+1] (device doubles: W^2, W). `graphs`, `a`, `b`, `t`, `K`, `u`, `v` are HOST arrays of
+ * length nprob. Each problem runs on one thread-block cluster whose Chebyshev orders are separated
+ * by hardware cluster barriers. Requires 1 <= nprob, every K[i] >= 1, t[i] > 0. Errors:
+ * GS_ERR_ARG. */
 gs_status gs_sinkhorn_batched(gs_ctx *ctx, int nprob, const gs_graph *const *graphs,
                               const float *const *a, const float *const *b, const double *t,
                               const int *K, int iters, float *const *u, float *const *v,

@@ -36,6 +36,28 @@ def test_library_exports_every_declared_symbol(built):
     assert not missing, f"declared but not exported: {missing}"
 
 
+# Calls with no operation of the paper behind them: context, options, diagnostics, tuning, layout.
+PLUMBING = {"gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_sync", "gs_reserve",
+            "gs_set_option", "gs_get_option", "gs_launch_count", "gs_sell_step_order", "gs_graph_info",
+            "gs_graph_layout", "gs_autotune", "gs_graph_destroy"}
+
+
+def test_every_entry_point_is_documented_and_compute_calls_cite_their_passage():
+    # the comment block(s) between one declaration and the next document the latter
+    txt = open(os.path.join(ROOT, "include", "geosink.h")).read()
+    decl = re.compile(r"^[a-z][^;(]*?\b(gs_[a-z0-9_]+)\s*\([^;]*\);", re.M | re.S)
+    prev, docs = 0, {}
+    for m in decl.finditer(txt):
+        docs[m.group(1)] = " ".join(re.findall(r"/\*(.*?)\*/", txt[prev:m.start()], flags=re.S))
+        prev = m.end()
+    assert sorted(docs) == header_symbols()
+    cite = re.compile(r"Sec\. \d|Algorithm \d|Definition \d|Table \d|Eq\. \d")
+    for name, doc in docs.items():
+        assert doc.strip(), f"{name}: no comment"
+        if name not in PLUMBING:
+            assert cite.search(doc), f"{name}: cites no passage of the paper"
+
+
 def test_binding_wraps_every_symbol(built):
     from paper_2211_00805_gb300 import binding
     assert sorted(binding.SIGNATURES) == header_symbols()
