@@ -2,6 +2,7 @@
 
     python -m paper_2211_00805_gb300.profile_run --case b1   # 100k-point manifold graph, B = 1, K = 30
     python -m paper_2211_00805_gb300.profile_run --case b32  # 200k-point cluster graph, B = 32, K = 40
+    python -m paper_2211_00805_gb300.profile_run --case b1 --log-sinkhorn 20  # log-domain loop
 
 Builds the case's graph on the GPU, then applies the filter ``--reps`` times through the C ABI and
 prints the mean time per apply (CUDA events) and its algorithmic bandwidth.
@@ -58,6 +59,8 @@ def main():
                     help="with --sinkhorn: ';'-separated loop mode,kernel,smem graph,sync tuples")
     ap.add_argument("--sinkhorn", type=int, default=0,
                     help="also time this many Sinkhorn iterations in both loop modes (B = 1 cases)")
+    ap.add_argument("--log-sinkhorn", type=int, default=0,
+                    help="also time this many iterations of the log-domain loop (gs_sinkhorn_log, B = 1 cases)")
     ap.add_argument("--n", type=int, default=0, help="override the case's point count")
     ap.add_argument("--bps", default="1", help="with --sinkhorn: ','-separated GS_OPT_PERSIST_BLOCKS values "
                     "(one graph built per value; timings interleaved)")
@@ -149,6 +152,21 @@ def main():
         gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
         gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
         gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 1)
+    if args.log_sinkhorn and c["B"] == 1:
+        a = torch.full((c["n"],), 1.0 / c["n"], device=dev)
+        it = args.log_sinkhorn
+        gs.gs_sinkhorn_log(ctx, g, a, a, c["t"], c["K"], it)  # warm (workspace, capture stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.reps):
+            gs.gs_sinkhorn_log(ctx, g, a, a, c["t"], c["K"], it)
+        e1.record()
+        torch.cuda.synchronize()
+        gs.gs_sync(ctx)
+        ms = e0.elapsed_time(e1) / args.reps
+        print(json.dumps({"case": args.case, "log_sinkhorn_iters": it, "ms": ms,
+                          "iters_per_s": it / (ms / 1e3), "order_us": ms * 1e3 / (2 * c["K"] * it)}), flush=True)
 
 if __name__ == "__main__":
     main()
