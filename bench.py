@@ -94,6 +94,31 @@ def ncu_traffic(kernel_tag: str, source: str = "cheb.cu"):
 
 
 # ------------------------------------------------------------------------------------- clocks
+CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def summarise_clocks(text: str):
+    """Median SM clock, the largest max clock and the throttle reasons seen Active, from
+    ``nvidia-smi --format=csv,noheader,nounits`` lines of ClockSampler.FIELDS; None without samples."""
+    sm, smax, reasons = [], [], set()
+    for line in text.strip().splitlines():
+        p = [x.strip() for x in line.split(",")]
+        if len(p) < 8:
+            continue
+        try:
+            sm.append(float(p[0]))
+            smax.append(float(p[1]))
+        except ValueError:
+            continue
+        for nm, val in zip(CLOCK_REASONS, p[4:8]):
+            if val.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -134,25 +159,7 @@ class ClockSampler:
             self.proc.kill()
             self.proc.wait()
         self.reader.join(timeout=5)
-        out = "".join(self.lines)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
-            p = [x.strip() for x in line.split(",")]
-            if len(p) < 8:
-                continue
-            try:
-                sm.append(float(p[0]))
-                smax.append(float(p[1]))
-            except ValueError:
-                continue
-            for nm, val in zip(names, p[4:8]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarise_clocks("".join(self.lines))
 
 
 # ------------------------------------------------------------------------------- CPU oracle
