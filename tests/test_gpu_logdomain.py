@@ -4,8 +4,8 @@ extended-range Chebyshev recurrence) against the FP64 oracle's Sinkhorn loop.
 Tolerances: the recurrence adds FP32 mantissas (rounding ~6e-8 per operation, K orders of ~k
 terms per half-step); the loop does not expand errors in the potentials, so after 200 iterations
 they stay within ~1e-4 of the oracle's (the numpy model of the same arithmetic in
-test_logdomain_model.py: 1.4e-5 on the case below).  Bounds: 5e-4 absolute on ln u, ln v; 1e-5 relative on W^2, whose constant-shift error
-cancels between the two equal-mass marginals.
+test_logdomain_model.py: 1.4e-5 on the case below).  Bounds: 5e-4 absolute on ln u, ln v; 1e-5
+relative on W^2, whose constant-shift error cancels between the two equal-mass marginals.
 """
 import numpy as np
 import pytest
