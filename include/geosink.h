@@ -51,7 +51,7 @@ typedef enum gs_status {
     GS_ERR_NONFINITE = 4,      /* a scaling, filter output or distance became inf/NaN/negative  */
     GS_ERR_NOT_CONVERGED = 5,  /* eps > 0 and the marginal error never fell below eps           */
     GS_ERR_TIMEOUT = 6,        /* a bounded in-kernel wait gave up                              */
-    GS_ERR_UNSUPPORTED = 7     /* shape or state this build does not handle                     */
+    GS_ERR_UNSUPPORTED = 7     /* shape or state this library does not handle                   */
 } gs_status;
 
 typedef struct gs_ctx gs_ctx;

@@ -1,6 +1,6 @@
 """GPU (FP32 CUDA path, through the C ABI) against the FP64 oracle on the same seeded inputs.
 
-Tolerances ("Tolerances"):
+Tolerances:
   * kNN edge sets: exact, except where the oracle's FP64 distances tie within 1e-6 relative;
     sigma: the same FP64 number (both sides rank bitwise-identical FP64 distances).
   * heat filter: |gpu - ref| <= 1e-4 |ref| + 1e-6 max|ref| per column block (FP32 sum of K terms of
