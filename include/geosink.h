@@ -100,7 +100,7 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * recurrence; they differ in summation order only. */
 /* GS_OPT_KNN_TENSOR: how kNN distances are screened before the exact FP64 rerank.  2 (default):
  * squared distances as one augmented 3xTF32 contraction on the fifth-generation tensor cores
- * (tcgen05, operands by TMA multicast within CTA pairs, accumulators in tensor memory) when
+ * (tcgen05, operands staged by TMA in each CTA's shared memory, accumulators in tensor memory) when
  * d <= 62; 1: warp-level TF32 MMA (3xTF32) when d >= 16; 0: FP32 CUDA-core dot products.  A
  * choice the shape or device does not allow falls back to the next lower one; the rerank makes
  * every choice exact. */
@@ -126,9 +126,18 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * reads from another may differ from the exact FP32 ones by one unit in the last place (results
  * agree with the exact form to ~1e-8 relative, not bitwise); 8: exact FP32 value plus a 32-bit
  * stage tag (results bitwise equal to the other loop forms), with twice the exchanged bytes. */
+/* GS_OPT_CHECK_ARGS: device-side argument checks (1, default) or none (0).  gs_sinkhorn, gs_distance,
+ * gs_sinkhorn_log, gs_sinkhorn_grad and gs_sinkhorn_batched check that both marginals are finite
+ * and non-negative and that their masses sum_i vol_i a_i and sum_i vol_i b_i (the two marginals of
+ * Algorithm 1's plan, so they must agree for a plan to exist) differ by at most 1e-6 of the larger;
+ * gs_barycenter, gs_barycenter_grad and gs_barycentric_distance check that the weights alpha are
+ * non-negative and sum to 1 within 1e-6 (Sec. 3.3).  The checks run on the device in the call's
+ * stream (one small launch each) and a failure is raised as GS_ERR_ARG by the next gs_sync; the
+ * computation itself still runs.  Turn them off to evaluate the unrolled iteration at unbalanced
+ * marginals on purpose (e.g. a distance to a barycenter that is not normalised). */
 enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
        GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6, GS_OPT_PERSIST_SYNC = 7,
-       GS_OPT_PERSIST_BLOCKS = 8, GS_OPT_TAG_WORD = 9 };
+       GS_OPT_PERSIST_BLOCKS = 8, GS_OPT_TAG_WORD = 9, GS_OPT_CHECK_ARGS = 10 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
 
 /* Host query of an option.  For GS_OPT_LOOP, GS_OPT_B1_KERNEL and GS_OPT_PERSIST_SYNC left on
@@ -231,25 +240,29 @@ gs_status gs_graph_destroy(gs_graph *g);
 gs_status gs_heat_apply(gs_ctx *ctx, const gs_graph *g, double t, int K, const float *V, int B,
                         float *Y);
 
-/* Allocation-free variant of gs_heat_apply for callers that cannot allocate device memory: code
- * that runs while a CUDA graph is being captured, plug-ins whose host application owns every
- * device allocation, loops that must never enter the allocator.  The paper has no counterpart;
- * this is a deployment convenience.
+/* Allocation-free variant of gs_heat_apply for callers that cannot allocate device memory:
+ * plug-ins whose host application owns every device allocation (the library may not take memory
+ * from under it), and real-time loops that must never enter the allocator, where cudaMalloc can
+ * block or fail under memory pressure.  The paper has no counterpart; this is a deployment
+ * convenience.
  * It computes the same Y = p_K(L, t) V (Sec. 3.5) with the same kernels, but takes the operator
  * as plain CSR device arrays (rowptr [n+1] int32 offsets, col [nnz] int32, pval [nnz] FP32 holding
  * P = D^{-1/2} A D^{-1/2}, as gs_graph_export_csr returns them once rowptr is narrowed to int32)
- * and needs no gs_ctx or gs_graph.  Its two scratch blocks live in a fixed 8 MiB device array
- * inside the library, present on every GPU that loads it until the process exits, so
- * n * B <= 1,048,576 (2^20) is required (GS_ERR_UNSUPPORTED otherwise).  No cudaMalloc, cudaFree
- * or other device allocation happens in this call.
+ * and needs no gs_ctx or gs_graph.  The CSR is trusted, not checked: rowptr must start at 0, be
+ * non-decreasing and end at nnz, and every col entry must lie in [0, n); anything else reads out
+ * of bounds.  Its two scratch blocks live in a fixed 8 MiB device array inside the library,
+ * present on every GPU that loads it until the process exits, so n * B <= 1,048,576 (2^20) is
+ * required (GS_ERR_UNSUPPORTED otherwise).  No cudaMalloc, cudaFree or other device allocation
+ * happens in this call.
  *   - Works on the calling thread's current device; `stream` is a cudaStream_t as void*.
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress);
  *     make that first call before any stream capture.
  *   - Every call shares the one scratch array: calls that overlap on the GPU (other streams,
  *     other threads) race and corrupt each other; serialise them.  Nothing in the scratch must
  *     start at zero, so stale contents from an earlier call do no harm.
- * Same limits on t, K and B as gs_heat_apply.  Returns GS_ERR_ARG / GS_ERR_UNSUPPORTED /
- * GS_ERR_CUDA (no message: there is no context). */
+ * Same limits on t, K and B as gs_heat_apply, with both V and Y on a 16-byte boundary for
+ * B > 256.  Returns GS_ERR_ARG / GS_ERR_UNSUPPORTED / GS_ERR_CUDA (no message: there is no
+ * context). */
 gs_status gs_heat_apply_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
                                 const float *pval, double t, int K, const float *V, int B,
                                 float *Y, void *stream);
@@ -261,7 +274,8 @@ gs_status gs_heat_apply_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr, c
  *     dist[0] = W^2 = 4t sum_i vol_i (a_i ln u_i + b_i ln v_i)      (Algorithm 1's return value)
  *     dist[1] = W   = sqrt(W^2)                                     (Definition 4.1)
  * accumulated in FP64 (0 ln 0 := 0; a_i = 0 gives u_i = 0).
- *   a, b   : [n] non-negative marginals (the caller normalises them; not checked on device)
+ *   a, b   : [n] non-negative marginals of equal mass sum(vol a) = sum(vol b) (checked on the device,
+ *            see GS_OPT_CHECK_ARGS)
  *   vol    : [n] vertex weights, NULL = all ones
  *   eps    : > 0 -> stop at the first iteration j, j a multiple of 10, whose marginal error
  *            sum_i |u_i (p_K(vol * v))_i - a_i| is below eps (GS_ERR_NOT_CONVERGED at gs_sync if
@@ -291,7 +305,7 @@ gs_status gs_distance(gs_ctx *ctx, const gs_graph *g, const float *a, const floa
  * in FP64 (0 ln 0 := 0).  Runs exactly `iters` iterations (no eps stop), 2 K launches each (one
  * iteration captured as a CUDA graph and replayed), in the graph's locality order; all arguments
  * are in the caller's node order.
- *   a, b   : [n] non-negative marginals (device FP32; the caller normalises them)
+ *   a, b   : [n] non-negative marginals of equal mass (device FP32; checked as in gs_sinkhorn)
  *   vol    : [n] vertex weights or NULL
  *   log_u, log_v : [n] double outputs (device), distinct buffers; -inf where a_i (b_i) = 0
  *   dist   : [2] double output (device), may be NULL
@@ -310,7 +324,8 @@ gs_status gs_sinkhorn_log(gs_ctx *ctx, const gs_graph *g, const float *a, const 
  * distributions move through the filter as one [n, m] block; the geometric mean is a log-sum
  * accumulated in FP64 inside the last Chebyshev order.
  *   M      : [n, m] input distributions (column i is mu_i)
- *   alpha  : [m] double weights (device), >= 0, summing to 1 (not checked on device)
+ *   alpha  : [m] double weights (device), >= 0, summing to 1 (checked on the device, see
+ *            GS_OPT_CHECK_ARGS)
  *   vol    : [n] vertex weights or NULL
  *   mu     : [n] output barycenter
  *   v_state: [n, m] output scalings v_i after the last iteration, may be NULL
@@ -340,7 +355,7 @@ gs_status gs_heat_apply_implicit(gs_ctx *ctx, const gs_graph *g, double t, int K
  * Each barycenter is divided by its mass before the distance: the definition compares
  * distributions, and Algorithm 1 needs marginals of equal mass.
  *   MT, MC          : [n, mT] and [n, mC] device FP32, column i a member of the family
- *   alphaT, alphaC  : [mT], [mC] device FP64 weights (>= 0, summing to 1; not checked on device)
+ *   alphaT, alphaC  : [mT], [mC] device FP64 weights (>= 0, summing to 1; checked on the device)
  *   vol             : [n] vertex weights or NULL (barycenters and distance alike)
  *   muT, muC        : [n] device FP32 outputs, the normalised barycenters (distinct buffers)
  *   dist            : [2] device FP64 output, (gamma^2, gamma) as gs_distance's (W^2, W)
@@ -373,7 +388,7 @@ gs_status gs_barycenter_effect(gs_ctx *ctx, const float *Y, int64_t n, int d, co
  *     dist[0..1] (device doubles) = W^2, W            (as gs_sinkhorn)
  *     grad_a, grad_b [n] (device)  = dW^2/da, dW^2/db  (of the unrolled map, a and b independent;
  *                                                       entries with zero mass use 0 ln 0 := 0)
- * Requires checkpoint >= 1.  Errors: GS_ERR_ARG. */
+ * Marginals are checked as in gs_sinkhorn.  Requires checkpoint >= 1.  Errors: GS_ERR_ARG. */
 gs_status gs_sinkhorn_grad(gs_ctx *ctx, const gs_graph *g, const float *a, const float *b,
                            const float *vol, double t, int K, int iters, int checkpoint,
                            double *dist, float *grad_a, float *grad_b);
@@ -391,7 +406,7 @@ gs_status gs_barycenter_grad(gs_ctx *ctx, const gs_graph *g, const float *M, int
 
 /* Many independent Algorithm 1 problems in one persistent launch (the batching is not in the
  * paper; it serves workloads with many small distances). Problem i has graph graphs[i] (any size,
- * any order), marginals a[i], b[i] (device [n_i]), diffusion time t[i] and degree K[i]; all run
+ * any order), marginals a[i], b[i] (device [n_i]; checked as in gs_sinkhorn), diffusion time t[i] and degree K[i]; all run
  * `iters` iterations with unit vertex weights. Outputs u[i], v[i] (device [n_i]) and dist[2i],
  * dist[2i+1] (device doubles: W^2, W). `graphs`, `a`, `b`, `t`, `K`, `u`, `v` are HOST arrays of
  * length nprob. Each problem runs on one thread-block cluster whose Chebyshev orders are separated

@@ -67,8 +67,6 @@ def _core():
         p = ctypes.c_void_p
         lib.or_knn_rows.argtypes = [p, i64, i32, i32, p, i64, p, p]
         lib.or_knn_rows.restype = i32
-        lib.or_csr_mm.argtypes = [i64, p, p, p, i32, p, p]
-        lib.or_csr_mm.restype = i32
         lib.or_cheb_filter.argtypes = [i64, p, p, p, i32, p, i32, p, p]
         lib.or_cheb_filter.restype = i32
         lib.or_num_threads.argtypes = []
@@ -291,17 +289,6 @@ def heat_apply_implicit(Ls, t: float, K: int, V):
     for _ in range(K):
         Y = Minv @ Y
     return Y
-
-
-def csr_matmul(Ls, X):
-    """Ls X for a CSR matrix (used by the tests' dense pins only through this plain loop)."""
-    rp, col, val = Ls
-    X2 = np.ascontiguousarray(np.asarray(X, np.float64).reshape(len(rp) - 1, -1))
-    Y = np.empty_like(X2)
-    _core().or_csr_mm(len(rp) - 1, _ptr(np.ascontiguousarray(rp, np.int64)),
-                      _ptr(np.ascontiguousarray(col, np.int32)),
-                      _ptr(np.ascontiguousarray(val, np.float64)), X2.shape[1], _ptr(X2), _ptr(Y))
-    return Y.reshape(np.shape(X))
 
 
 # --------------------------------------------------------------------------------------------

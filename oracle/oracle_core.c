@@ -100,14 +100,6 @@ static void csr_mm(int64_t n, const int64_t *rowptr, const int32_t *col, const d
     }
 }
 
-int or_csr_mm(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val, int B,
-              const double *X, double *Y)
-{
-    if (n < 1 || B < 1) return -1;
-    csr_mm(n, rowptr, col, val, B, X, Y);
-    return 0;
-}
-
 /*
  * Chebyshev heat filter (Sec. 3.5): Y = p_K(L, t) V = (b_0 / 2) V + sum_{k=1..K} b_k T_k(Ls) V,
  * with Ls = L - Id the shifted Laplacian given in CSR form and the coefficients b[0..K] as the

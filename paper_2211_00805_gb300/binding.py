@@ -176,6 +176,7 @@ GS_OPT_PERSIST_SMEM_GRAPH = 6
 GS_OPT_PERSIST_SYNC = 7
 GS_OPT_PERSIST_BLOCKS = 8
 GS_OPT_TAG_WORD = 9
+GS_OPT_CHECK_ARGS = 10
 
 
 def gs_set_option(ctx: Context, option: int, value: int):
@@ -288,7 +289,8 @@ def gs_heat_apply_noalloc(rowptr32: torch.Tensor, col: torch.Tensor, pval: torch
                           K: int, V: torch.Tensor, out: torch.Tensor | None = None,
                           stream: torch.cuda.Stream | None = None):
     """Allocation-free heat filter on caller-held CSR arrays (int32 rowptr); the output buffer
-    is allocated here by torch only when ``out`` is None."""
+    is allocated here by torch only when ``out`` is None.  The library works on the current
+    device, so the call runs with V's device current; every array must live on that device."""
     n = rowptr32.numel() - 1
     _dev(rowptr32, torch.int32, "rowptr32")
     _dev(col, torch.int32, "col")
@@ -296,11 +298,17 @@ def gs_heat_apply_noalloc(rowptr32: torch.Tensor, col: torch.Tensor, pval: torch
     squeeze = V.dim() == 1
     V2 = V.reshape(V.shape[0], -1)
     _dev(V2, torch.float32, "V")
+    if V2.shape[0] != n:
+        raise ValueError("V must have n = rowptr32.numel() - 1 rows")
     Y = torch.empty_like(V2) if out is None else _dev(out, torch.float32, "Y").view(V2.shape)
-    stream = torch.cuda.current_stream(V.device) if stream is None else stream
-    st = _lib.gs_heat_apply_noalloc(n, col.numel(), _ptr(rowptr32), _ptr(col), _ptr(pval), float(t),
-                                    int(K), _ptr(V2), V2.shape[1], _ptr(Y),
-                                    ctypes.c_void_p(stream.cuda_stream))
+    for name, x in (("rowptr32", rowptr32), ("col", col), ("pval", pval), ("Y", Y)):
+        if x.device != V.device:
+            raise ValueError(f"{name} is on {x.device}, V on {V.device}")
+    with torch.cuda.device(V.device):
+        stream = torch.cuda.current_stream(V.device) if stream is None else stream
+        st = _lib.gs_heat_apply_noalloc(n, col.numel(), _ptr(rowptr32), _ptr(col), _ptr(pval), float(t),
+                                        int(K), _ptr(V2), V2.shape[1], _ptr(Y),
+                                        ctypes.c_void_p(stream.cuda_stream))
     if st != GS_OK:
         raise GeosinkError(st, "gs_heat_apply_noalloc")
     return Y.view(V.shape) if squeeze else Y

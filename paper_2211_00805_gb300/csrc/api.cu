@@ -137,6 +137,11 @@ extern "C" gs_status gs_sync(gs_ctx* ctx)
         return st;
     cudaMemset(ctx->flags, 0, sizeof(int));
     if (f & GS_FLAG_TIMEOUT) return gs_fail(ctx, GS_ERR_TIMEOUT, "a bounded in-kernel wait gave up");
+    if (f & GS_FLAG_ARG)
+        return gs_fail(ctx, GS_ERR_ARG,
+                       "device argument check: a marginal with a negative or non-finite entry, marginals whose "
+                       "masses sum(vol a), sum(vol b) differ by more than 1e-6 relative, or barycenter weights "
+                       "that are negative or do not sum to 1 (GS_OPT_CHECK_ARGS 0 skips these checks)");
     if (f & GS_FLAG_NONFINITE)
         return gs_fail(ctx, GS_ERR_NONFINITE, "non-finite or non-positive value in a scaling or filter output");
     if (f & GS_FLAG_NOT_CONVERGED)
@@ -157,6 +162,10 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
     if (!ctx) return GS_ERR_ARG;
     if (option == GS_OPT_LOOP && (value >= 0 && value <= 2)) {
         ctx->loop_mode = value;
+        return GS_OK;
+    }
+    if (option == GS_OPT_CHECK_ARGS && (value == 0 || value == 1)) {
+        ctx->check_args = value;
         return GS_OK;
     }
     if (option == GS_OPT_BARRIER_SELFTEST && (value == 0 || value == 1)) {
@@ -212,6 +221,7 @@ extern "C" gs_status gs_get_option(const gs_ctx* ctx, int option, int* value)
         case GS_OPT_PERSIST_SYNC: *value = gs_persist_sync_choice(ctx, nullptr); return GS_OK;
         case GS_OPT_PERSIST_BLOCKS: *value = ctx->persist_bps; return GS_OK;
         case GS_OPT_TAG_WORD: *value = ctx->tag_word; return GS_OK;
+        case GS_OPT_CHECK_ARGS: *value = ctx->check_args; return GS_OK;
         default: return GS_ERR_ARG;
     }
 }
@@ -390,6 +400,8 @@ extern "C" gs_status gs_sinkhorn(gs_ctx* ctx, const gs_graph* g, const float* a,
         return gs_fail(ctx, GS_ERR_ARG, "null pointer");
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
     if (!(eps == eps)) return gs_fail(ctx, GS_ERR_ARG, "eps is NaN");
+    const gs_marginals mg{a, b, vol, g->n};
+    if ((st = gs_check_marginals(ctx, &mg, 1, nullptr)) != GS_OK) return st;
     return gs_sinkhorn_impl(ctx, g, a, b, vol, t, K, eps, iters, u, v, dist, iters_done);
 }
 
@@ -402,6 +414,8 @@ extern "C" gs_status gs_distance(gs_ctx* ctx, const gs_graph* g, const float* a,
     if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
     if (bad_ptr(a) || bad_ptr(b) || bad_ptr(dist)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
+    const gs_marginals mg{a, b, vol, g->n};
+    if ((st = gs_check_marginals(ctx, &mg, 1, nullptr)) != GS_OK) return st;
     // the scalings stay in the workspace
     return gs_sinkhorn_impl(ctx, g, a, b, vol, t, K, eps, iters, nullptr, nullptr, dist, nullptr);
 }
@@ -419,6 +433,7 @@ extern "C" gs_status gs_barycenter(gs_ctx* ctx, const gs_graph* g, const float* 
     if (!gs_filter_supports(m, true))
         return gs_fail(ctx, GS_ERR_UNSUPPORTED, "m must be 1..256, or a multiple of 4 up to 1024");
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
+    if ((st = gs_check_weights(ctx, alpha, m)) != GS_OK) return st;
     return gs_barycenter_impl(ctx, g, M, m, alpha, vol, t, K, iters, mu, v_state);
 }
 
@@ -445,6 +460,8 @@ extern "C" gs_status gs_sinkhorn_log(gs_ctx* ctx, const gs_graph* g, const float
         return gs_fail(ctx, GS_ERR_ARG, "null pointer");
     if (log_u == log_v) return gs_fail(ctx, GS_ERR_ARG, "log_u and log_v must be distinct buffers");
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
+    const gs_marginals mg{a, b, vol, g->n};
+    if ((st = gs_check_marginals(ctx, &mg, 1, nullptr)) != GS_OK) return st;
     return gs_sinkhorn_log_impl(ctx, g, a, b, vol, t, K, iters, log_u, log_v, dist);
 }
 
@@ -468,6 +485,8 @@ extern "C" gs_status gs_barycentric_distance(gs_ctx* ctx, const gs_graph* g, con
             return gs_fail(ctx, GS_ERR_UNSUPPORTED, "family sizes must be 1..256, or multiples of 4 up to 1024");
     }
     if (bary_iters < 1 || sink_iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iterations must be >= 1");
+    if ((st = gs_check_weights(ctx, alphaT, mT)) != GS_OK || (st = gs_check_weights(ctx, alphaC, mC)) != GS_OK)
+        return st;
     return gs_barycentric_distance_impl(ctx, g, MT, mT, alphaT, MC, mC, alphaC, vol, t, K, bary_iters, sink_iters,
                                         muT, muC, dist);
 }
@@ -493,6 +512,8 @@ extern "C" gs_status gs_sinkhorn_grad(gs_ctx* ctx, const gs_graph* g, const floa
     if (bad_ptr(a) || bad_ptr(b) || bad_ptr(dist) || bad_ptr(grad_a) || bad_ptr(grad_b))
         return gs_fail(ctx, GS_ERR_ARG, "null pointer");
     if (iters < 1 || checkpoint < 1) return gs_fail(ctx, GS_ERR_ARG, "iters and checkpoint must be >= 1");
+    const gs_marginals mg{a, b, vol, g->n};
+    if ((st = gs_check_marginals(ctx, &mg, 1, nullptr)) != GS_OK) return st;
     return gs_sinkhorn_grad_impl(ctx, g, a, b, vol, t, K, iters, checkpoint, dist, grad_a, grad_b);
 }
 
@@ -510,6 +531,7 @@ extern "C" gs_status gs_barycenter_grad(gs_ctx* ctx, const gs_graph* g, const fl
     if (!gs_filter_supports(m, true))
         return gs_fail(ctx, GS_ERR_UNSUPPORTED, "m must be 1..256, or a multiple of 4 up to 1024");
     if (iters < 1 || checkpoint < 1) return gs_fail(ctx, GS_ERR_ARG, "iters and checkpoint must be >= 1");
+    if ((st = gs_check_weights(ctx, alpha, m)) != GS_OK) return st;
     return gs_barycenter_grad_impl(ctx, g, M, m, alpha, vol, t, K, iters, checkpoint, mubar, mu, grad_alpha);
 }
 

@@ -289,7 +289,8 @@ gs_status gs_sinkhorn_batched_impl(gs_ctx* ctx, int nprob, const gs_graph* const
     WsPlan plan;
     const size_t iar = plan.add(sizeof(float) * (size_t)arena), ico = plan.add(sizeof(float) * (size_t)ncoef),
                  ipr = plan.add(sizeof(BatchProblem) * (size_t)nprob), iq = plan.add(sizeof(int) * 4),
-                 ids = plan.add(sizeof(double) * 2 * (size_t)nprob);
+                 ids = plan.add(sizeof(double) * 2 * (size_t)nprob),
+                 imc = plan.add(sizeof(gs_marginals) * (size_t)nprob);
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
     float* ar = ws_at<float>(ctx, plan, iar);
@@ -335,6 +336,13 @@ gs_status gs_sinkhorn_batched_impl(gs_ctx* ctx, int nprob, const gs_graph* const
         coff += K[i] + 1;
     }
     cudaStream_t s = ctx->stream;
+    {
+        // Algorithm 1's argument checks for every problem, one block each (unit vertex weights)
+        std::vector<gs_marginals> mg((size_t)nprob);
+        for (int i = 0; i < nprob; ++i) mg[(size_t)i] = gs_marginals{a[i], b[i], nullptr, graphs[i]->n};
+        if ((st = gs_check_marginals(ctx, mg.data(), nprob, ws_at<gs_marginals>(ctx, plan, imc))) != GS_OK)
+            return st;
+    }
     cudaMemcpyAsync(dprobs, hp.data(), sizeof(BatchProblem) * (size_t)nprob, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(co, hc.data(), sizeof(float) * (size_t)ncoef, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(queue, 0, sizeof(int), s);

@@ -992,8 +992,11 @@ gs_status gs_filter_enqueue(gs_ctx* ctx, const gs_graph* g, const double* c, int
                             float* x, bool x_writable, float* bufA, float* bufB, float* y,
                             const Epilogue& epi_in, const int* done_flag, float** scratch_out)
 {
+    // float4 rows need every block the kernels read or write as float4 on a 16-byte boundary: the
+    // gathered and recurrence blocks, the running sum and the stored output
     const bool aligned = ((uintptr_t)x % 16) == 0 && ((uintptr_t)bufA % 16) == 0 &&
-                         (bufB == nullptr || ((uintptr_t)bufB % 16) == 0);
+                         (bufB == nullptr || ((uintptr_t)bufB % 16) == 0) && ((uintptr_t)y % 16) == 0 &&
+                         (epi_in.out == nullptr || ((uintptr_t)epi_in.out % 16) == 0);
     if (!gs_filter_supports(B, aligned))
         return gs_fail(ctx, GS_ERR_UNSUPPORTED, "B > 256 needs 16-byte aligned blocks with B % 4 == 0");
     const FilterPlan pl = gs_filter_plan(ctx, g, B, aligned);

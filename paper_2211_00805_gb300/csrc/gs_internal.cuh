@@ -38,6 +38,7 @@ enum : int {
     GS_FLAG_NONFINITE = 1,
     GS_FLAG_NOT_CONVERGED = 2,
     GS_FLAG_TIMEOUT = 4,
+    GS_FLAG_ARG = 8,        // an input failed a device-side argument check (raised as GS_ERR_ARG)
 };
 
 // A captured CUDA graph of one or more Sinkhorn iterations, replayed instead of re-launching
@@ -74,6 +75,7 @@ struct gs_ctx {
     int tag_word = 4;              // tagged-value exchange word: 4 (value with a parity bit) or 8 (exact)
     int persist_bps = 1;           // gather-cache partition of graphs built from now on: blocks per
                                    // SM (1: 1024 threads each, 2: 512 threads each)
+    int check_args = 1;            // device-side checks of marginals and barycenter weights (1 on)
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::string err;
@@ -323,3 +325,19 @@ gs_status gs_distance_enqueue(gs_ctx* ctx, int64_t n, const float* a, const floa
                               const float* vol, const float* u, const float* v, double t,
                               double* partials, double* dist);
 int gs_reduce_blocks();
+
+// Device-side argument checks (raised as GS_ERR_ARG at the next gs_sync; skipped while the
+// context's check option is off).  Marginals: every entry finite and >= 0, and the masses
+// sum vol a and sum vol b equal within GS_MASS_RTOL of the larger.  Barycenter weights: alpha >= 0
+// and |sum alpha - 1| <= GS_WEIGHT_TOL.
+constexpr double GS_MASS_RTOL = 1e-6;
+constexpr double GS_WEIGHT_TOL = 1e-6;
+struct gs_marginals {
+    const float* a;
+    const float* b;
+    const float* vol;   // null = unit weights
+    int64_t n;
+};
+// count problems; probs_dev (device, count entries) is needed only for count > 1
+gs_status gs_check_marginals(gs_ctx* ctx, const gs_marginals* probs, int count, gs_marginals* probs_dev);
+gs_status gs_check_weights(gs_ctx* ctx, const double* alpha, int m);

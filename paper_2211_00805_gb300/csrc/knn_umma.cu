@@ -9,11 +9,11 @@
 // accumulated in FP32 in tensor memory.  The screen keeps, per query, the 32 smallest screened
 // distances (ties to the lower index); the FP64 rerank in knn.cu then fixes the exact k-list.
 //
-// One CTA owns 128 queries (the MMA's M) and streams all candidates in tiles of 128 (its N); CTAs
-// run in clusters of two that read each candidate tile from L2 once and multicast it to both:
-//   warp 0    TMA producer: the query operands once, its share of every candidate tile's boxes
-//             into two shared stages of both CTAs (a stage is refilled once both CTAs' MMAs
-//             have released it);
+// One CTA owns 128 queries (the MMA's M) and streams all candidates in tiles of 128 (its N).  All
+// CTAs sweep the candidate tiles in the same order, so the CTAs resident at one time read the same
+// tile and it is served from L2 after its first fetch:
+//   warp 0    TMA producer: the query operands once, then every candidate tile's boxes into two
+//             shared stages (a stage is refilled once the MMAs have released it);
 //   warp 1    TMEM owner and MMA issuer (one thread): per tile 3 x ceil((d+2)/8) MMAs of
 //             128 x 128 x 8 into one of four TMEM accumulators, then commits to the stage's
 //             "empty" barrier and the accumulator's "full" barrier;
@@ -89,26 +89,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// The same box into the shared memory of every CTA in `mask` (same offset, same barrier offset).
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
-                                               uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;\n" ::"r"(su32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
@@ -140,15 +120,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
                  : "memory");
-}
-// Arrive on the barrier at the same offset in every CTA of `mask` once this thread's MMAs complete.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n" ::"r"(
-            su32(bar)),
-        "h"(mask)
-        : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
@@ -251,7 +222,7 @@ struct UmmaLayout {
     static constexpr int ALLOC = BYTES + 1024;                   // slack for 1024-byte alignment
 };
 
-template <int KB, int C>
+template <int KB>
 __global__ void __launch_bounds__(UTHREADS, 1)
     knn_screen_umma(const __grid_constant__ CUtensorMap tq_hi, const __grid_constant__ CUtensorMap tq_lo,
                     const __grid_constant__ CUtensorMap tc_hi, const __grid_constant__ CUtensorMap tc_lo,
@@ -284,13 +255,12 @@ __global__ void __launch_bounds__(UTHREADS, 1)
         mbar_init(drain, 1);
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(full + i, 1);
-            mbar_init(empty + i, C);  // one MMA commit from every CTA of the cluster
+            mbar_init(empty + i, 1);  // one MMA commit
         }
         for (int i = 0; i < NACC; ++i) {
             mbar_init(accf + i, 1);
             mbar_init(acce + i, 4 * 32);
         }
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)),
@@ -300,11 +270,8 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (C > 1) cluster_sync();  // every CTA's barriers exist before any multicast lands in it
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t crank = C > 1 ? cluster_rank() : 0u;
-    constexpr uint16_t cmask = (uint16_t)((1u << C) - 1u);
 
     if (warp == 0) {
         // ---------------------------------------------------------------- TMA producer
@@ -322,19 +289,18 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(full + s, 2 * KB * BOX);  // all boxes land here, whoever issues them
+                mbar_expect_tx(full + s, 2 * KB * BOX);
                 unsigned char* st = sm + L::B + s * 2 * KB * BOX;
                 const int y = tile_of(t) * UN;
                 for (int bx = 0; bx < 2 * KB; ++bx) {  // box bx: operand bx / KB (hi, lo), block bx % KB
                     const CUtensorMap* map = bx < KB ? &tc_hi : &tc_lo;
                     const int kb = bx % KB;
-                    if (C == 1) tma_load_2d(st + bx * BOX, map, kb * UKB, y, full + s);
-                    else if (bx % C == (int)crank) tma_load_2d_mc(st + bx * BOX, map, kb * UKB, y, full + s, cmask);
+                    tma_load_2d(st + bx * BOX, map, kb * UKB, y, full + s);
                 }
                 issued = t + 1;
             }
-            // every copy into this CTA has landed and every CTA's MMA has released the last
-            // stages (their commits arrive here) before the CTA may exit
+            // every copy into this CTA has landed and the MMAs have released the last stages
+            // before the CTA may exit
             for (int t = (issued > STAGES ? issued - STAGES : 0); t < issued; ++t) {
                 if (!mbar_wait(full + t % STAGES, (t / STAGES) & 1)) ok = false;
                 if (!mbar_wait(empty + t % STAGES, (t / STAGES) & 1)) ok = false;
@@ -368,8 +334,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                     umma_tf32(d_tmem, ah, bl, idesc, 1u);
                     umma_tf32(d_tmem, ah, bh, idesc, 1u);
                 }
-                if (C == 1) umma_commit(empty + s);
-                else umma_commit_mc(empty + s, cmask);
+                umma_commit(empty + s);
                 umma_commit(accf + b);
             }
             // all MMAs issued by this thread have completed before tensor memory is freed
@@ -446,7 +411,6 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (C > 1) cluster_sync();  // no CTA leaves while a peer may still signal or fill it
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(TMEM_COLS)
@@ -519,67 +483,25 @@ bool make_map(CUtensorMap* m, const float* base, int64_t n, int w, int rows)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KB, int C>
-bool launch_umma_c(gs_ctx* ctx, const CUtensorMap* maps, int64_t n, int ksteps, int* cand)
+template <int KB>
+gs_status launch_umma(gs_ctx* ctx, const CUtensorMap* maps, int64_t n, int ksteps, int* cand)
 {
     using L = UmmaLayout<KB>;
     static int ready = 0;  // 1 usable, -1 not
     if (!ready) {
-        ready = -1;
-        if (cudaFuncSetAttribute(knn_screen_umma<KB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC) ==
-            cudaSuccess) {
-            ready = 1;
-            if (C > 1) {
-                cudaLaunchConfig_t cfg = {};
-                cudaLaunchAttribute at[1];
-                at[0].id = cudaLaunchAttributeClusterDimension;
-                at[0].val.clusterDim.x = C;
-                at[0].val.clusterDim.y = 1;
-                at[0].val.clusterDim.z = 1;
-                cfg.gridDim = dim3(C);
-                cfg.blockDim = dim3(UTHREADS);
-                cfg.dynamicSmemBytes = L::ALLOC;
-                cfg.attrs = at;
-                cfg.numAttrs = 1;
-                int clusters = 0;
-                if (cudaOccupancyMaxActiveClusters(&clusters, knn_screen_umma<KB, C>, &cfg) != cudaSuccess ||
-                    clusters < 1)
-                    ready = -1;
-            }
-        }
+        ready = cudaFuncSetAttribute(knn_screen_umma<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC) ==
+                        cudaSuccess
+                    ? 1
+                    : -1;
         cudaGetLastError();
     }
-    if (ready < 0) return false;
-    const int64_t blocks = (n + UM - 1) / UM;
-    const unsigned grid = (unsigned)((blocks + C - 1) / C * C);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = C;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(UTHREADS);
-    cfg.dynamicSmemBytes = L::ALLOC;
-    cfg.stream = ctx->stream;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, knn_screen_umma<KB, C>, maps[0], maps[1], maps[2], maps[3], (int)n, ksteps, cand,
-                           ctx->flags) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
+    if (ready < 0) return GS_ERR_UNSUPPORTED;
+    const unsigned grid = (unsigned)((n + UM - 1) / UM);
+    knn_screen_umma<KB><<<grid, UTHREADS, L::ALLOC, ctx->stream>>>(maps[0], maps[1], maps[2], maps[3], (int)n,
+                                                                   ksteps, cand, ctx->flags);
+    if (cudaGetLastError() != cudaSuccess) return GS_ERR_UNSUPPORTED;
     gs_count(ctx, 1);
-    return true;
-}
-
-// Pairs of CTAs share every candidate tile (one TMA read from L2, multicast to both), else single.
-template <int KB>
-gs_status launch_umma(gs_ctx* ctx, const CUtensorMap* maps, int64_t n, int ksteps, int* cand)
-{
-    if (launch_umma_c<KB, 2>(ctx, maps, n, ksteps, cand)) return GS_OK;
-    if (launch_umma_c<KB, 1>(ctx, maps, n, ksteps, cand)) return GS_OK;
-    return GS_ERR_UNSUPPORTED;
+    return GS_OK;
 }
 
 }  // namespace

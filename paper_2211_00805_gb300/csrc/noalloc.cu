@@ -1,8 +1,8 @@
 // Allocation-free heat filter for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running while a CUDA graph is being captured
-// in relaxed or global mode, plug-ins whose host application owns every device allocation, and
-// real-time loops that must never touch the allocator.  gs_heat_apply_noalloc serves them: it
+// Some callers cannot call cudaMalloc at all: plug-ins whose host application owns every device
+// allocation (the library may not take memory from under it), and real-time loops that must never
+// enter the allocator, whose calls can block or fail under memory pressure.  gs_heat_apply_noalloc serves them: it
 // takes the graph as plain CSR device arrays instead of a library-owned handle and keeps the
 // Chebyshev recurrence's two scratch blocks in a fixed array compiled into this file, so it
 // allocates no device memory and needs no gs_ctx.
@@ -63,7 +63,7 @@ extern "C" gs_status gs_heat_apply_noalloc(int64_t n, int64_t nnz, const int32_t
     if (n < 2 || nnz < 0 || nnz >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31)) return GS_ERR_ARG;
     if (!(t > 0.0) || !isfinite(t) || K < 1 || K > 10000 || B < 1) return GS_ERR_ARG;
     if (n * (int64_t)B > kNoAllocBlockFloats) return GS_ERR_UNSUPPORTED;   // n * B above 2^20
-    if (!gs_filter_supports(B, ((uintptr_t)V % 16) == 0)) return GS_ERR_UNSUPPORTED;
+    if (!gs_filter_supports(B, ((uintptr_t)V % 16) == 0 && ((uintptr_t)Y % 16) == 0)) return GS_ERR_UNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();

@@ -77,3 +77,99 @@ gs_status gs_distance_enqueue(gs_ctx* ctx, int64_t n, const float* a, const floa
     gs_count(ctx, 2);
     return gs_cuda_check(ctx, cudaGetLastError(), "distance reduction");
 }
+
+// ---------------------------------------------------------------------- argument checks
+// Algorithm 1 transports a onto b: a plan with marginals vol * a and vol * b exists only when both
+// are non-negative and carry the same mass, sum_i vol_i a_i = sum_i vol_i b_i (the vertex weights
+// multiply both marginals of the plan).  One block per problem sums both masses in FP64 and flags
+// a negative or non-finite entry, or masses further apart than rtol times the larger one.
+namespace {
+
+constexpr int kCheckThreads = 1024;
+
+__device__ void check_one(const gs_marginals& p, double rtol, int* flags)
+{
+    double ma = 0.0, mb = 0.0;
+    int bad = 0;
+    for (int64_t i = threadIdx.x; i < p.n; i += blockDim.x) {
+        const float ai = p.a[i], bi = p.b[i];
+        if (!(ai >= 0.f) || !(bi >= 0.f) || isinf(ai) || isinf(bi)) bad = 1;
+        const double w = p.vol ? (double)p.vol[i] : 1.0;
+        ma += w * (double)ai;
+        mb += w * (double)bi;
+    }
+    __shared__ double ra[kCheckThreads / 32], rb[kCheckThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) {
+        ma += __shfl_xor_sync(0xffffffffu, ma, off);
+        mb += __shfl_xor_sync(0xffffffffu, mb, off);
+    }
+    bad = __syncthreads_or(bad);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        ra[w] = ma;
+        rb[w] = mb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ma = mb = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) {
+            ma += ra[j];
+            mb += rb[j];
+        }
+        const double top = fmax(fabs(ma), fabs(mb));
+        if (bad || !(fabs(ma - mb) <= rtol * top)) atomicOr(flags, GS_FLAG_ARG);
+    }
+}
+
+__global__ void __launch_bounds__(kCheckThreads) check_marginals(const gs_marginals p, double rtol, int* flags)
+{
+    check_one(p, rtol, flags);
+}
+
+__global__ void __launch_bounds__(kCheckThreads) check_marginals_many(const gs_marginals* __restrict__ ps,
+                                                                      double rtol, int* flags)
+{
+    check_one(ps[blockIdx.x], rtol, flags);
+}
+
+// Barycenter weights (Sec. 3.3): alpha_i >= 0 and sum_i alpha_i = 1 within tol.
+__global__ void __launch_bounds__(32) check_weights(const double* __restrict__ alpha, int m, double tol, int* flags)
+{
+    double s = 0.0;
+    int bad = 0;
+    for (int i = threadIdx.x; i < m; i += 32) {
+        const double ai = alpha[i];
+        if (!(ai >= 0.0) || isinf(ai)) bad = 1;
+        s += ai;
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    bad = __any_sync(0xffffffffu, bad);
+    if (threadIdx.x == 0 && (bad || !(fabs(s - 1.0) <= tol))) atomicOr(flags, GS_FLAG_ARG);
+}
+
+}  // namespace
+
+gs_status gs_check_marginals(gs_ctx* ctx, const gs_marginals* probs, int count, gs_marginals* probs_dev)
+{
+    if (!ctx->check_args || count < 1) return GS_OK;
+    if (count == 1 || probs_dev == nullptr) {
+        for (int i = 0; i < count; ++i)
+            check_marginals<<<1, kCheckThreads, 0, ctx->stream>>>(probs[i], GS_MASS_RTOL, ctx->flags);
+        gs_count(ctx, count);
+    } else {
+        cudaMemcpyAsync(probs_dev, probs, sizeof(gs_marginals) * (size_t)count, cudaMemcpyHostToDevice,
+                        ctx->stream);
+        check_marginals_many<<<(unsigned)count, kCheckThreads, 0, ctx->stream>>>(probs_dev, GS_MASS_RTOL,
+                                                                                 ctx->flags);
+        gs_count(ctx, 1);
+    }
+    return gs_cuda_check(ctx, cudaGetLastError(), "marginal check");
+}
+
+gs_status gs_check_weights(gs_ctx* ctx, const double* alpha, int m)
+{
+    if (!ctx->check_args) return GS_OK;
+    check_weights<<<1, 32, 0, ctx->stream>>>(alpha, m, GS_WEIGHT_TOL, ctx->flags);
+    gs_count(ctx, 1);
+    return gs_cuda_check(ctx, cudaGetLastError(), "weight check");
+}

@@ -15,7 +15,7 @@ import torch
 
 import oracle
 from paper_2211_00805_gb300 import workloads as W
-from tests.gpu_common import assert_close, oracle_csr_to_dev, report, to_dev, to_np
+from tests.gpu_common import assert_close, knn_lists_match, oracle_csr_to_dev, report, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -139,40 +139,21 @@ def test_heat_apply_ragged_small_graphs(gs, ctx):
 
 
 # ------------------------------------------------------------------------------------- graph
-def _edge_sets_match(gidx, gdist64_or_None, ref_idx, ref_dist):
-    """Exact neighbour lists, allowing swaps only between entries whose FP64 distances tie
-    within 1e-6 relative."""
-    mism = np.nonzero(np.any(gidx != ref_idx, axis=1))[0]
-    for q in mism:
-        a, b = gidx[q], ref_idx[q]
-        # the sets may differ only by neighbours at (near-)tied distance with the k-th one
-        dk = ref_dist[q, -1]
-        for j in set(a.tolist()) ^ set(b.tolist()):
-            pos = np.nonzero(b == j)[0]
-            dj = ref_dist[q, pos[0]] if len(pos) else None
-            assert dj is None or abs(dj - dk) <= 1e-6 * dk, f"row {q}: neighbour {j} differs"
-        # within the set, order may swap only between ties
-        common = [j for j in a if j in set(b.tolist())]
-        assert len(common) >= len(a) - 2
-    return len(mism)
-
-
 def test_knn_sphere_exact(gs, ctx):
     p = W.sphere_pair()
     idx, dist = gs.gs_knn(ctx, to_dev(p.X), p.k)
     ri, rd = oracle.knn(p.X.astype(np.float64), p.k)
-    gi = to_np(idx)
-    n_mism = _edge_sets_match(gi, None, ri, rd)
-    assert n_mism == 0
+    assert knn_lists_match(to_np(idx), to_np(dist), ri, rd, p.X) == 0
     np.testing.assert_allclose(to_np(dist), rd, rtol=1e-7)
 
 
 def test_knn_manifold_sampled_rows(gs, ctx):
     X, Z = W.tanh_manifold(20_000, 10, 50, seed=2)
-    idx, _ = gs.gs_knn(ctx, to_dev(X), 15)
+    idx, dist = gs.gs_knn(ctx, to_dev(X), 15)
     rows = np.random.default_rng(0).choice(len(X), 300, replace=False)
     ri, rd = oracle.knn(X.astype(np.float64), 15, rows=rows)
-    _edge_sets_match(to_np(idx)[rows], None, ri, rd)
+    # the rerank uses the oracle's FP64 operation order, so even near-ties come out the same
+    assert knn_lists_match(to_np(idx)[rows], to_np(dist)[rows], ri, rd, X, rows=rows) == 0
 
 
 def test_build_graph_matches_oracle(gs, ctx):
@@ -511,7 +492,7 @@ def test_knn_tensor_core_and_cuda_core_screens_exact(gs, ctx, tensor):
     finally:
         gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, saved)
     ri, rd = oracle.knn(X.astype(np.float64), 12)
-    assert _edge_sets_match(to_np(idx), None, ri, rd) == 0
+    assert knn_lists_match(to_np(idx), to_np(dist), ri, rd, X) == 0
     np.testing.assert_allclose(to_np(dist), rd, rtol=1e-7)
 
 
@@ -529,7 +510,7 @@ def test_knn_tcgen05_screen_shapes_exact(gs, ctx, n, d, k):
     finally:
         gs.gs_set_option(ctx, gs.GS_OPT_KNN_TENSOR, saved)
     ri, rd = oracle.knn(X.astype(np.float64), k)
-    assert _edge_sets_match(to_np(idx), None, ri, rd) == 0
+    assert knn_lists_match(to_np(idx), to_np(dist), ri, rd, X) == 0
     np.testing.assert_allclose(to_np(dist), rd, rtol=1e-7)
 
 
