@@ -240,6 +240,18 @@ gs_status gs_graph_destroy(gs_graph *g);
 gs_status gs_heat_apply(gs_ctx *ctx, const gs_graph *g, double t, int K, const float *V, int B,
                         float *Y);
 
+/* Heat filter of the combinatorial Laplacian L = D - A (Sec. 3.4) with the expansion of Sec. 3.5:
+ *     Y = p_K(L', s) V ~ exp(-t (D - A)) V,   L' = (2 / lam)(D - A),   s = t lam / 2,
+ * where lam = 2 max_i D_ii bounds the largest eigenvalue of D - A (Gershgorin), so the spectrum of
+ * L' lies in [0, 2] as Sec. 3.5 assumes, and exp(-t L) = exp(-s L').  The recurrence runs on
+ * M = Id - L' (its diagonal 1 - D_ii / max_j D_jj stored with the off-diagonal A_ij / max_j D_jj)
+ * with the coefficients c_k(s) of gs_cheb_coeffs.  The first call on a graph builds M (device
+ * memory of nnz + n entries kept with the graph; waits for the stream once); later calls are
+ * asynchronous.  lam (host double, may be NULL) receives lam.  V, Y: [n, B] as gs_heat_apply, same
+ * limits.  Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED, GS_ERR_OOM. */
+gs_status gs_heat_apply_combinatorial(gs_ctx *ctx, gs_graph *g, double t, int K, const float *V, int B,
+                                      float *Y, double *lam);
+
 /* Allocation-free variant of gs_heat_apply for callers that cannot allocate device memory:
  * plug-ins whose host application owns every device allocation (the library may not take memory
  * from under it), and real-time loops that must never enter the allocator, where cudaMalloc can

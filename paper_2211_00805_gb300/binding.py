@@ -47,6 +47,7 @@ SIGNATURES = {
     "gs_autotune": [_P, _P, _I, _I, _P],
     "gs_graph_destroy": [_P],
     "gs_heat_apply": [_P, _P, _D, _I, _P, _I, _P],
+    "gs_heat_apply_combinatorial": [_P, _P, _D, _I, _P, _I, _P, _P],
     "gs_heat_apply_noalloc": [_I64, _I64, _P, _P, _P, _D, _I, _P, _I, _P, _P],
     "gs_sinkhorn": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P],
     "gs_distance": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P],
@@ -283,6 +284,22 @@ def gs_heat_apply(ctx: Context, g: Graph, t: float, K: int, V: torch.Tensor, out
     Y = torch.empty_like(V2) if out is None else _dev(out, torch.float32, "Y").view(V2.shape)
     _raise(ctx, _lib.gs_heat_apply(ctx.handle, g.handle, float(t), int(K), _ptr(V2), V2.shape[1], _ptr(Y)))
     return Y.view(V.shape) if squeeze else Y
+
+
+def gs_heat_apply_combinatorial(ctx: Context, g: Graph, t: float, K: int, V: torch.Tensor,
+                                out: torch.Tensor | None = None):
+    """exp(-t (D - A)) V by the Chebyshev filter on the rescaled combinatorial Laplacian; returns
+    (Y, lam) with lam = 2 max_i D_ii, the bound the operator was rescaled by."""
+    squeeze = V.dim() == 1
+    V2 = V.reshape(V.shape[0], -1)
+    _dev(V2, torch.float32, "V")
+    if V2.shape[0] != g.n:
+        raise ValueError("V must have n rows")
+    Y = torch.empty_like(V2) if out is None else _dev(out, torch.float32, "Y").view(V2.shape)
+    lam = ctypes.c_double()
+    _raise(ctx, _lib.gs_heat_apply_combinatorial(ctx.handle, g.handle, float(t), int(K), _ptr(V2), V2.shape[1],
+                                                 _ptr(Y), ctypes.byref(lam)))
+    return (Y.view(V.shape) if squeeze else Y), float(lam.value)
 
 
 def gs_heat_apply_noalloc(rowptr32: torch.Tensor, col: torch.Tensor, pval: torch.Tensor, t: float,

@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgeosink.so")
 SOURCES = ["api.cu", "coeffs.cu", "graph.cu", "cheb.cu", "reduce.cu", "knn.cu", "noalloc.cu",
            "order.cu", "adjoint.cu", "batched.cu", "persist.cu", "autotune.cu",
-           "xcache.cu", "knn_umma.cu", "family.cu", "implicit.cu", "logdomain.cu"]
+           "xcache.cu", "knn_umma.cu", "family.cu", "implicit.cu", "logdomain.cu", "combinatorial.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

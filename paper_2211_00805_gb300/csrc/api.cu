@@ -196,7 +196,7 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->b1_kernel = value;
         return GS_OK;
     }
-    if (option == GS_OPT_BLK_KERNEL && (value == 0 || (value >= 2 && value <= 5))) {
+    if (option == GS_OPT_BLK_KERNEL && (value == 0 || (value >= 2 && value <= 5) || value == 8 || value == 9)) {
         ctx->blk_kernel = value;
         return GS_OK;
     }
@@ -343,11 +343,46 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g)
     cudaFree(g->xc_deps);
     cudaFree(g->xc_ndeps);
     cudaFree(g->xc_rows);
+    cudaFree(g->mrowptr);
+    cudaFree(g->mcol);
+    cudaFree(g->mval);
     delete g;
     return GS_OK;
 }
 
 // ------------------------------------------------------------------------- heat filter
+// Y = sum_k c_k T_k(op) V on the operator of graph g (P, or a view with M in its place): V into the
+// filter's node order, the fused orders, Y back.
+static gs_status heat_apply_coeffs(gs_ctx* ctx, const gs_graph* g, const double* c, int K, const float* V,
+                                   int B, float* Y)
+{
+    gs_status st;
+    const size_t blk = sizeof(float) * (size_t)g->n * (size_t)B;
+    Epilogue e;
+    e.kind = EPI_STORE;
+    if (!g->perm) {
+        WsPlan plan;
+        const size_t iA = plan.add(blk), iB = plan.add(blk);
+        if ((st = gs_ws_ensure(ctx, plan.total)) != GS_OK) return st;
+        e.out = Y;
+        return gs_filter_enqueue(ctx, g, c, K, B, const_cast<float*>(V), false, ws_at<float>(ctx, plan, iA),
+                                 ws_at<float>(ctx, plan, iB), Y, e, nullptr, nullptr);
+    }
+    // reordered graph: V into the filter's node order, apply, Y back
+    WsPlan plan;
+    const size_t iA = plan.add(blk), iV = plan.add(blk), iY = plan.add(blk);
+    if ((st = gs_ws_ensure(ctx, plan.total)) != GS_OK) return st;
+    float* Vp = ws_at<float>(ctx, plan, iV);
+    float* Yp = ws_at<float>(ctx, plan, iY);
+    gs_permute_rows(ctx, g->n, B, g->perm, V, Vp, true);
+    e.out = Yp;
+    if ((st = gs_filter_enqueue(ctx, g, c, K, B, Vp, true, ws_at<float>(ctx, plan, iA), nullptr, Yp, e, nullptr,
+                                nullptr)) != GS_OK)
+        return st;
+    gs_permute_rows(ctx, g->n, B, g->perm, Yp, Y, false);
+    return gs_cuda_check(ctx, cudaGetLastError(), "heat apply");
+}
+
 extern "C" gs_status gs_heat_apply(gs_ctx* ctx, const gs_graph* g, double t, int K, const float* V,
                                    int B, float* Y)
 {
@@ -361,31 +396,30 @@ extern "C" gs_status gs_heat_apply(gs_ctx* ctx, const gs_graph* g, double t, int
                        "B must be 1..256, or a multiple of 4 up to 1024 with V 16-byte aligned");
     std::vector<double> c((size_t)K + 1);
     gs_heat_coefficients(t, K, c.data());
-    const size_t blk = sizeof(float) * (size_t)g->n * (size_t)B;
-    Epilogue e;
-    e.kind = EPI_STORE;
-    if (!g->perm) {
-        WsPlan plan;
-        const size_t iA = plan.add(blk), iB = plan.add(blk);
-        if ((st = gs_ws_ensure(ctx, plan.total)) != GS_OK) return st;
-        e.out = Y;
-        return gs_filter_enqueue(ctx, g, c.data(), K, B, const_cast<float*>(V), false,
-                                 ws_at<float>(ctx, plan, iA), ws_at<float>(ctx, plan, iB), Y, e,
-                                 nullptr, nullptr);
-    }
-    // reordered graph: V into the filter's node order, apply, Y back
-    WsPlan plan;
-    const size_t iA = plan.add(blk), iV = plan.add(blk), iY = plan.add(blk);
-    if ((st = gs_ws_ensure(ctx, plan.total)) != GS_OK) return st;
-    float* Vp = ws_at<float>(ctx, plan, iV);
-    float* Yp = ws_at<float>(ctx, plan, iY);
-    gs_permute_rows(ctx, g->n, B, g->perm, V, Vp, true);
-    e.out = Yp;
-    if ((st = gs_filter_enqueue(ctx, g, c.data(), K, B, Vp, true, ws_at<float>(ctx, plan, iA), nullptr,
-                                Yp, e, nullptr, nullptr)) != GS_OK)
-        return st;
-    gs_permute_rows(ctx, g->n, B, g->perm, Yp, Y, false);
-    return gs_cuda_check(ctx, cudaGetLastError(), "heat apply");
+    return heat_apply_coeffs(ctx, g, c.data(), K, V, B, Y);
+}
+
+extern "C" gs_status gs_heat_apply_combinatorial(gs_ctx* ctx, gs_graph* g, double t, int K, const float* V,
+                                                 int B, float* Y, double* lam)
+{
+    gs_status st = enter(ctx);
+    if (st != GS_OK) return st;
+    if ((st = check_graph(ctx, g)) != GS_OK || (st = check_filter(ctx, t, K)) != GS_OK) return st;
+    if (bad_ptr(V) || bad_ptr(Y)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
+    if (V == Y) return gs_fail(ctx, GS_ERR_ARG, "V and Y must not alias");
+    if (!gs_filter_supports(B, ((uintptr_t)V % 16) == 0))
+        return gs_fail(ctx, GS_ERR_UNSUPPORTED,
+                       "B must be 1..256, or a multiple of 4 up to 1024 with V 16-byte aligned");
+    if ((st = gs_graph_build_combinatorial(ctx, g)) != GS_OK) return st;
+    if (lam) *lam = g->comb_lam;
+    // exp(-t (D - A)) = exp(-s L') with L' = (2 / lam)(D - A) and s = t lam / 2
+    const double s = t * g->comb_lam / 2.0;
+    if (!(s > 0.0) || !isfinite(s)) return gs_fail(ctx, GS_ERR_ARG, "t * lam / 2 must be positive and finite");
+    std::vector<double> c((size_t)K + 1);
+    gs_heat_coefficients(s, K, c.data());
+    gs_graph view;
+    gs_combinatorial_view(g, &view);
+    return heat_apply_coeffs(ctx, &view, c.data(), K, V, B, Y);
 }
 
 // ----------------------------------------------------------------------------- Sinkhorn

@@ -38,6 +38,9 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
     if (B == 1)
         cands = {GS_KERNEL_RANGED, GS_KERNEL_SM_RANGE, GS_KERNEL_SPLIT, GS_KERNEL_SELL,
                  GS_KERNEL_VECTOR, GS_KERNEL_ASYNC};
+    else if (B == 32 || B == 64 || B == 128)
+        cands = {GS_KERNEL_VECTOR, GS_KERNEL_STAGED, GS_KERNEL_ASYNC, GS_KERNEL_RANGED, GS_KERNEL_GROUP_WARP,
+                 GS_KERNEL_GROUP_VEC4};
     else if (B % 4 == 0 && B <= 128) cands = {GS_KERNEL_VECTOR, GS_KERNEL_STAGED, GS_KERNEL_ASYNC, GS_KERNEL_RANGED};
     else cands = {GS_KERNEL_VECTOR, GS_KERNEL_RANGED};
     int* knob = (B == 1) ? &ctx->b1_kernel : &ctx->blk_kernel;

@@ -466,6 +466,202 @@ __global__ void __launch_bounds__(256) order_blk_ranged(const OrderArgs p, int l
     }
 }
 
+// B = L * V columns, L lanes per row (8, 16 or 32), V consecutive floats per lane (1, 2 or 4).
+// The row's column indices and values are fetched L at a time, one entry per lane in a single
+// coalesced load, and handed to the group by shuffles, so the gathers of a round never wait on
+// an index load (four float4 or eight narrower gathers in flight per lane); the row-local loads
+// (T_{k-2}, y) go out before the first round.  Entries are summed in CSR order (the same order as order_blk).
+// The first split_blocks blocks take the long rows, one warp per row: its 32 / L groups each sum
+// one contiguous segment of the entries and the segments are added in order.
+template <int V>
+__device__ __forceinline__ void vload(const float* src, float (&v)[V])
+{
+    if constexpr (V == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (V == 2) {
+        const float2 q = __ldg(reinterpret_cast<const float2*>(src));
+        v[0] = q.x; v[1] = q.y;
+    } else {
+        v[0] = __ldg(src);
+    }
+}
+template <int V>
+__device__ __forceinline__ void vload_stream(const float* src, float (&v)[V])
+{
+    if constexpr (V == 4) {
+        const float4 q = __ldcs(reinterpret_cast<const float4*>(src));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (V == 2) {
+        const float2 q = __ldcs(reinterpret_cast<const float2*>(src));
+        v[0] = q.x; v[1] = q.y;
+    } else {
+        v[0] = __ldcs(src);
+    }
+}
+template <int V>
+__device__ __forceinline__ void vstore_stream(float* dst, const float (&v)[V])
+{
+    if constexpr (V == 4) __stcs(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
+    else if constexpr (V == 2) __stcs(reinterpret_cast<float2*>(dst), make_float2(v[0], v[1]));
+    else __stcs(dst, v[0]);
+}
+
+template <int L, int V>
+__global__ void __launch_bounds__(256, 4) order_grp(const OrderArgs p, int split_blocks)
+{
+    if (p.done != nullptr && *p.done) return;
+    constexpr int G = 32 / L;  // row groups per warp
+    constexpr int U = V == 4 ? 4 : 8;  // gathers in flight per lane (64 or 32 bytes)
+    const int wl = threadIdx.x & 31;
+    const int lane = wl & (L - 1);
+    const int gi = wl / L;
+    const unsigned gmask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (gi * L));
+    const bool split = (int)blockIdx.x < split_blocks;
+    int64_t row;
+    bool active;
+    if (split) {
+        const int64_t h = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+        active = h < p.nheavy;
+        row = active ? __ldg(p.heavy + h) : 0;
+    } else {
+        row = ((int64_t)(blockIdx.x - split_blocks) * blockDim.x + threadIdx.x) / L;
+        active = row < p.n;
+    }
+    int beg = 0, end = 0;
+    if (active) {
+        beg = __ldg(p.rowptr + row);
+        end = __ldg(p.rowptr + row + 1);
+        if (!split && p.heavy_len > 0 && end - beg > p.heavy_len) active = false;
+    }
+    if (!active) beg = end = 0;
+    if (split && G > 1) {
+        const int seg = (end - beg + G - 1) / G;
+        const int sb = min(beg + gi * seg, end);
+        end = min(sb + seg, end);
+        beg = sb;
+    }
+    constexpr int B = L * V;
+    const int64_t base = row * (int64_t)B + lane * V;
+    // row-local loads first (the finishing group's lanes only)
+    const bool finisher = active && (!split || gi == 0);
+    float pv[V], yv0[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) pv[v] = yv0[v] = 0.f;
+    if (finisher) {
+        if (p.first) {
+            vload_stream<V>(p.cur + base, yv0);
+        } else {
+            vload_stream<V>(p.prev + base, pv);
+            vload_stream<V>(p.y + base, yv0);
+        }
+    }
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    for (int e0 = beg; e0 < end; e0 += L) {
+        const int cnt = min(L, end - e0);
+        int cj = 0;
+        float wj = 0.f;
+        if (lane < cnt) {
+            cj = __ldg(p.col + e0 + lane);
+            wj = __ldg(p.pval + e0 + lane);
+        }
+        for (int j = 0; j < cnt; j += U) {
+            float x[U][V], w[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int jj = j + u;
+                const int c = __shfl_sync(gmask, cj, jj & (L - 1), L);
+                w[u] = __shfl_sync(gmask, wj, jj & (L - 1), L);
+                if (jj < cnt) {
+                    vload<V>(p.cur + (int64_t)c * B + lane * V, x[u]);
+                } else {
+                    w[u] = 0.f;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) x[u][v] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j + u < cnt) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] = fmaf(w[u], x[u][v], acc[v]);
+                }
+            }
+        }
+    }
+    if (split && G > 1) {
+        // the segments' partial sums, added in segment order (every group gets its column's total)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            float t = __shfl_sync(0xffffffffu, acc[v], lane);
+#pragma unroll
+            for (int gsrc = 1; gsrc < G; ++gsrc) t += __shfl_sync(0xffffffffu, acc[v], lane + gsrc * L);
+            acc[v] = t;
+        }
+    }
+    if (split && gi != 0) return;  // the first group finishes a long row (no shuffles below cross groups)
+    float tk[V], f[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        tk[v] = p.first ? acc[v] : fmaf(2.f, acc[v], -pv[v]);
+        f[v] = p.first ? fmaf(p.ck, tk[v], p.c0 * yv0[v]) : fmaf(p.ck, tk[v], yv0[v]);
+    }
+    if (!p.last) {
+        if (active) {
+            vstore_stream<V>(p.next + base, tk);
+            vstore_stream<V>(p.y + base, f);
+        }
+        return;
+    }
+    const Epilogue& e = p.epi;
+    const float vol = (active && e.vol) ? e.vol[row] : 1.f;
+    if (e.kind == EPI_STORE || e.kind == EPI_DIVIDE) {
+        if (!active) return;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (e.kind == EPI_STORE) {
+                e.out[base + v] = f[v];
+            } else {
+                const float r = safe_div(e.num[base + v], f[v], p.flags);
+                if (e.fsave) e.fsave[base + v] = f[v];
+                if (e.out) e.out[base + v] = r;
+                if (e.xnext) e.xnext[base + v] = vol * r;
+            }
+        }
+        return;
+    }
+    // EPI_BARY_V: d_i = v_i * f_i; mu = exp(sum_i alpha_i ln d_i); v_i <- v_i mu / d_i
+    const unsigned fmask = split ? ((L == 32) ? 0xffffffffu : ((1u << L) - 1u)) : gmask;
+    double lsum = 0.0;
+    float d[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        d[v] = 0.f;
+        if (!active) continue;
+        if (e.fsave) e.fsave[base + v] = f[v];
+        d[v] = e.V[base + v] * f[v];
+        const double al = e.alpha[lane * V + v];
+        if (al != 0.0) lsum += al * (double)logf(d[v]);
+    }
+    for (int off = L >> 1; off > 0; off >>= 1) lsum += __shfl_xor_sync(fmask, lsum, off, L);
+    const float mu = (float)exp(lsum);
+    if (!active) return;
+    if (lane == 0) {
+        e.mu[row] = mu;
+        if (!(mu >= 0.f) || isinf(mu)) flag(p.flags, GS_FLAG_NONFINITE);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const float vnum = e.V[base + v] * mu;
+        const float vn = (vnum == 0.f) ? 0.f : vnum / d[v];
+        if (e.dsave) e.dsave[base + v] = d[v];
+        e.V[base + v] = vn;
+        if (e.xnext) e.xnext[base + v] = vol * vn;
+    }
+}
+
 // Shared tail of the float4 row-group kernels: recurrence update and the epilogues.  Every
 // thread of the block calls it (the barycenter epilogue reduces across the row's lanes).
 template <int LPR>
@@ -851,6 +1047,38 @@ void launch_blk_async(gs_ctx* ctx, const gs_graph* g, const OrderArgs& a)
     order_blk_async<LPR><<<grid, 256, smem, ctx->stream>>>(a);
 }
 
+// The lane-group kernels for B = L * V: one warp per row (L = 32, V = B / 32) or float4 lanes
+// (V = 4, L = B / 4); long rows to split warps in front.  False when B has no such shape.
+bool launch_grp(gs_ctx* ctx, const gs_graph* g, int B, bool warp_rows, const OrderArgs& a)
+{
+    int L = 0, V = 0;
+    if (warp_rows && (B == 32 || B == 64 || B == 128)) {
+        L = 32;
+        V = B / 32;
+    } else if (!warp_rows && (B == 32 || B == 64 || B == 128)) {
+        L = B / 4;
+        V = 4;
+    }
+    if (!L) return false;
+    OrderArgs sa = a;
+    int split_blocks = 0;
+    if (g->heavy != nullptr && g->nheavy > 0) {
+        sa.heavy = g->heavy;
+        sa.nheavy = g->nheavy;
+        sa.heavy_len = GS_HEAVY_ROW;
+        split_blocks = (int)((g->nheavy + 7) / 8);
+    }
+    const unsigned grid = nblocks(g->n * L, 256) + (unsigned)split_blocks;
+    cudaStream_t s = ctx->stream;
+    if (L == 32 && V == 1) order_grp<32, 1><<<grid, 256, 0, s>>>(sa, split_blocks);
+    else if (L == 32 && V == 2) order_grp<32, 2><<<grid, 256, 0, s>>>(sa, split_blocks);
+    else if (L == 32 && V == 4) order_grp<32, 4><<<grid, 256, 0, s>>>(sa, split_blocks);
+    else if (L == 8) order_grp<8, 4><<<grid, 256, 0, s>>>(sa, split_blocks);
+    else if (L == 16) order_grp<16, 4><<<grid, 256, 0, s>>>(sa, split_blocks);
+    else return false;
+    return true;
+}
+
 void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const OrderArgs& a)
 {
     gs_count(ctx, 1);
@@ -922,6 +1150,9 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
                 default: break;
             }
         }
+    }
+    if (pl.B > 1 && (blk_mode == GS_KERNEL_GROUP_WARP || blk_mode == GS_KERNEL_GROUP_VEC4) && vec == 4) {
+        if (launch_grp(ctx, g, pl.B, blk_mode == GS_KERNEL_GROUP_WARP, a)) return;
     }
     const bool one = pl.B <= lpr * vec;
     const int lg = ilog2(lpr);

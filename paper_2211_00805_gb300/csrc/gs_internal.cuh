@@ -30,6 +30,8 @@ enum : int {
     GS_KERNEL_RANGED = 5,   // each block walks a contiguous row range (sliced ELL / lane groups)
     GS_KERNEL_SPLIT = 6,    // B == 1: sliced ELL with each row split across GS_SPLIT_T threads
     GS_KERNEL_SM_RANGE = 7, // B == 1: one 1024-thread block per SM, one contiguous row range each
+    GS_KERNEL_GROUP_WARP = 8,  // B in {32, 64, 128}: one warp per row, indices loaded by the lanes
+    GS_KERNEL_GROUP_VEC4 = 9,  // B in {32, 64, 128}: B / 4 float4 lanes per row, indices loaded by the lanes
 };
 constexpr int GS_SPLIT_T = 4;
 
@@ -136,6 +138,12 @@ struct gs_graph {
     int* xc_ndeps = nullptr;  // other blocks owning one of its distinct columns
     int xc_max_deps = 0;
     std::vector<int> xc_ucnt_host;
+    // the combinatorial operator M = I - (2 / lam)(D - A), lam = 2 max_i D_ii, in the locality order
+    // with its diagonal (combinatorial.cu); built on the first combinatorial apply
+    int* mrowptr = nullptr;
+    int* mcol = nullptr;
+    float* mval = nullptr;
+    double comb_lam = 0.0;
 };
 
 // The CSR the filter kernels read: the reordered one when present.
@@ -318,6 +326,11 @@ gs_status gs_sinkhorn_log_impl(gs_ctx* ctx, const gs_graph* g, const float* a, c
 // Euler implicit heat kernel Y = (I + (t/K) L)^{-K} V by K conjugate-gradient solves (implicit.cu).
 gs_status gs_heat_apply_implicit_impl(gs_ctx* ctx, const gs_graph* g, double t, int K, const float* V, int B,
                                       float* Y, double tol, int iters);
+
+// ------------------------------------------------------------------ combinatorial.cu
+// Build g's combinatorial operator (once; waits for the stream) and view g with it in place of P.
+gs_status gs_graph_build_combinatorial(gs_ctx* ctx, gs_graph* g);
+void gs_combinatorial_view(const gs_graph* g, gs_graph* view);
 
 // ------------------------------------------------------------------------ reduce.cu
 // dist[0] = 4t sum vol (a ln u + b ln v), dist[1] = sqrt; flags NONFINITE on bad scalings.

@@ -109,7 +109,7 @@ def main():
     V = torch.rand((c["n"], c["B"]), generator=torch.Generator().manual_seed(0)).to(dev)
     Y = torch.empty_like(V)
     option = gs.GS_OPT_B1_KERNEL if c["B"] == 1 else gs.GS_OPT_BLK_KERNEL
-    variants = ([0, 1, 2, 3, 5, 6, 7] if c["B"] == 1 else [0, 2, 3, 4, 5]) if args.sweep else [args.variant]
+    variants = ([0, 1, 2, 3, 5, 6, 7] if c["B"] == 1 else [0, 2, 3, 4, 5, 8, 9]) if args.sweep else [args.variant]
     byts = algorithmic_bytes(c["n"], g.nnz, c["K"], c["B"])
     for var in variants:
         gs.gs_set_option(ctx, option, var)

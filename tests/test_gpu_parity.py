@@ -407,7 +407,9 @@ def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sp
 
 @pytest.mark.parametrize("B,option,variant", [(1, 3, 1), (1, 3, 2), (1, 3, 3), (1, 3, 5), (1, 3, 6), (1, 3, 7), (32, 4, 2),
                                               (32, 4, 3), (32, 4, 4), (32, 4, 5), (64, 4, 3),
-                                              (8, 4, 3), (128, 4, 3), (12, 4, 5), (3, 4, 5)])
+                                              (8, 4, 3), (128, 4, 3), (12, 4, 5), (3, 4, 5),
+                                              (32, 4, 8), (32, 4, 9), (64, 4, 8), (64, 4, 9),
+                                              (128, 4, 8), (128, 4, 9), (12, 4, 8), (96, 4, 9)])
 def test_kernel_variants_match_oracle(gs, ctx, B, option, variant):
     # every order-kernel variant (sliced ELL, lane-split CSR, chunked async gathers, staged lists)
     X, rp, col, A = _random_graph(2500, 4, 9, seed=31 + B)
@@ -445,26 +447,31 @@ def _hub_graph(n, seed):
     return G.indptr.astype(np.int64), G.indices.astype(np.int32), G.data.astype(np.float64)
 
 
-@pytest.mark.parametrize("B", [2, 3, 8, 12, 32, 64, 128, 200])
-def test_long_rows_split_across_a_warp_match_oracle(gs, ctx, B):
+@pytest.mark.parametrize("B,variant", [(2, 0), (3, 0), (8, 0), (12, 0), (32, 0), (64, 0), (128, 0), (200, 0),
+                                       (32, 8), (32, 9), (64, 8), (64, 9), (128, 8), (128, 9)])
+def test_long_rows_split_across_a_warp_match_oracle(gs, ctx, B, variant):
     # rows longer than the split threshold are summed by a whole warp in segments
     rp, col, A = _hub_graph(3000, 71)
     assert np.diff(rp).max() >= 400
     g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
     Ls, _ = _oracle_graph_fp32(rp, col, A)
     V = np.random.default_rng(B).random((3000, B)).astype(np.float32)
-    for t, K in [(5.0, 30), (2.0, 1), (3.0, 2)]:
-        Y = to_np(gs.gs_heat_apply(ctx, g, t, K, to_dev(V)))
-        ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(t, K), V.astype(np.float64))
-        assert_close(Y, ref, HEAT_RTOL, HEAT_ATOL_REL * np.abs(ref).max(), f"B={B} K={K}")
-    Y1 = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
-    Y2 = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
-    assert np.array_equal(Y1, Y2)  # the segment order is fixed: repeatable bit for bit
-    gs.gs_sync(ctx)
+    gs.gs_set_option(ctx, gs.GS_OPT_BLK_KERNEL, variant)
+    try:
+        for t, K in [(5.0, 30), (2.0, 1), (3.0, 2)]:
+            Y = to_np(gs.gs_heat_apply(ctx, g, t, K, to_dev(V)))
+            ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(t, K), V.astype(np.float64))
+            assert_close(Y, ref, HEAT_RTOL, HEAT_ATOL_REL * np.abs(ref).max(), f"B={B} v={variant} K={K}")
+        Y1 = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
+        Y2 = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
+        assert np.array_equal(Y1, Y2)  # the segment order is fixed: repeatable bit for bit
+        gs.gs_sync(ctx)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_BLK_KERNEL, 0)
 
 
-@pytest.mark.parametrize("m", [1, 32])
-def test_barycenter_on_hub_graph_matches_oracle(gs, ctx, m):
+@pytest.mark.parametrize("m,variant", [(1, 0), (32, 0), (32, 8), (32, 9), (64, 8), (64, 9)])
+def test_barycenter_on_hub_graph_matches_oracle(gs, ctx, m, variant):
     # the barycenter epilogue (geometric mean across the row's lanes) on split rows
     rp, col, A = _hub_graph(3000, 72)
     g = gs.gs_graph_from_csr(ctx, *oracle_csr_to_dev(rp, col, A))
@@ -474,10 +481,14 @@ def test_barycenter_on_hub_graph_matches_oracle(gs, ctx, m):
     M = (M / M.sum(0)).astype(np.float32)
     alpha = rng.dirichlet(np.ones(m))
     t, K, iters = 5.0, 20, 10
-    mu = to_np(gs.gs_barycenter(ctx, g, to_dev(M), to_dev(alpha, torch.float64), t, K, iters))
-    gs.gs_sync(ctx)
+    gs.gs_set_option(ctx, gs.GS_OPT_BLK_KERNEL, variant)
+    try:
+        mu = to_np(gs.gs_barycenter(ctx, g, to_dev(M), to_dev(alpha, torch.float64), t, K, iters))
+        gs.gs_sync(ctx)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_BLK_KERNEL, 0)
     ref = oracle.barycenter(Ls, oracle.cheb_coefficients(t, K), M.astype(np.float64), alpha, iters)
-    assert_close(mu, ref, 1e-4, 1e-6 * ref.max(), f"mu m={m}")
+    assert_close(mu, ref, 1e-4, 1e-6 * ref.max(), f"mu m={m} v={variant}")
 
 
 @pytest.mark.parametrize("tensor", [2, 1, 0])

@@ -31,10 +31,11 @@ def _close(a, b, what=""):
 
 def _oracle_operator(n, d, k, seed):
     """Oracle kNN graph of seeded points; returns the oracle's Ls and the CSR of P the GPU gets
-    (P = -Ls off the diagonal, from the FP32-rounded affinities)."""
+    (P = -Ls, from the FP32-rounded affinities)."""
     X = np.random.default_rng(seed).standard_normal((n, d))
     idx, dist = oracle.knn(X, k)
-    rp, col, A = oracle.affinity_graph(idx, dist, oracle.median_sigma(dist))
+    # sigma = the largest kNN distance: no affinity of an outlying point underflows in FP32
+    rp, col, A = oracle.affinity_graph(idx, dist, float(dist.max()))
     A32 = A.astype(np.float32).astype(np.float64)
     _, L = oracle.laplacian(rp, col, A32)
     Ls = oracle.shifted(L)
