@@ -204,6 +204,63 @@ def oracle_sample(cfg=WORKLOAD, small_n=10_000, knn_rows=2400, iters_small=150):
             "kind": "oracle", "sample": sample, "est_step_s": total}
 
 
+def oracle_sample_cfg3(small_n=20_000, knn_rows=1200, iters_small=2, iters=300):
+    """The FP64 oracle on a bounded sample of the barycenter workload (200k cluster points in R^30,
+    k = 10, 32 distributions, K = 40, t = 10, 300 iterations), scaled: kNN on ``knn_rows`` query rows
+    of the full cloud (x n / rows), graph assembly and ``iters_small`` barycenter iterations of the
+    same generator at ``small_n`` points, scaled by n and by the edge count."""
+    import oracle
+    cfg = W.clusters_barycenter()
+    n = cfg["X"].shape[0]
+    X64 = cfg["X"].astype(np.float64)
+    rows = np.random.default_rng(0).choice(n, knn_rows, replace=False)
+    t0 = time.perf_counter()
+    oracle.knn(X64, cfg["k"], rows=rows)
+    t_knn = (time.perf_counter() - t0) * n / knn_rows
+    cs = W.clusters_barycenter(n=small_n)
+    t0 = time.perf_counter()
+    Ls, ex = oracle.build_graph(cs["X"].astype(np.float64), cs["k"])
+    t_graph = (time.perf_counter() - t0) * n / small_n  # includes the small kNN: an overestimate
+    b = oracle.cheb_coefficients(cs["t"], cs["K"])
+    t0 = time.perf_counter()
+    oracle.barycenter(Ls, b, cs["M"].astype(np.float64), cs["alpha"], iters_small)
+    t_it = (time.perf_counter() - t0) / iters_small
+    nnz_full_est = len(ex["col"]) * n / small_n
+    t_iters = t_it * nnz_full_est / len(ex["col"]) * iters
+    total = t_knn + t_graph + t_iters
+    return {"value": iters / t_iters, "unit": "barycenter iters/s (graph build excluded)",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"kNN on {knn_rows} of {n} query rows; graph + {iters_small} barycenter iterations "
+                       f"of the same generator at n={small_n}, scaled by nnz to n={n}; est. "
+                       f"{t_iters:.0f} s for {iters} iterations, {total:.0f} s with the graph build")}
+
+
+def oracle_sample_cfg5(small_n=10_000, iters_small=4, iters=200):
+    """The FP64 oracle on a bounded sample of the differentiation workload (500k manifold points in
+    R^40, 64 inputs, K = 40, t = 8, 200 + 200 iterations): forward (barycenter + distance) and
+    forward + reverse (``barycenter_distance_grad``) at ``iters_small`` iterations each on
+    ``small_n`` points of the same generator, per iteration, scaled by the edge count to the full
+    size and 200 iterations."""
+    import oracle
+    c = W.manifold_barycenter_grad(n=small_n, bary_iters=iters_small, sink_iters=iters_small)
+    Ls, ex = oracle.build_graph(c["X"].astype(np.float64), c["k"])
+    b = oracle.cheb_coefficients(c["t"], c["K"])
+    M, src = c["M"].astype(np.float64), c["src"].astype(np.float64)
+    t0 = time.perf_counter()
+    mu = oracle.barycenter(Ls, b, M, c["alpha"], iters_small)
+    oracle.sinkhorn(Ls, b, src, mu, c["t"], iters_small)
+    t_f = (time.perf_counter() - t0) / iters_small
+    t0 = time.perf_counter()
+    oracle.barycenter_distance_grad(Ls, b, src, M, c["alpha"], c["t"], iters_small, iters_small)
+    t_g = (time.perf_counter() - t0) / iters_small
+    scale = 500_000 / small_n  # edge count grows with n (k fixed)
+    return {"value": 1.0 / (t_g * scale * iters), "unit": "gradient evaluations/s (200 + 200 iterations)",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "forward_s_est": t_f * scale * iters, "forward_plus_reverse_s_est": t_g * scale * iters,
+            "sample": (f"{iters_small} iterations of each loop at n={small_n} of the same generator "
+                       f"(nnz={len(ex['col'])}), scaled by n to 500,000 and to {iters} iterations")}
+
+
 def max_over_ranks(value: float, world: int, device=None) -> float:
     """Largest value across ranks (each rank times its own replica; the job takes the slowest)."""
     if world <= 1:
@@ -352,11 +409,15 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_extras:
         for key, case in HBM_CASES.items():
             extras[key] = hbm_case(gs, ctx, dev, stream, peak, peak_kind, case)
-        extras["batched_vs_plain"] = batched_case(gs, ctx, dev, stream)
-        extras["adjoint_vs_plain"] = adjoint_case(gs, ctx, dev, stream)
+        extras["barycenter_cfg3"] = barycenter_case(gs, ctx, dev, stream, peak, peak_kind)
+        extras["batched_cfg4"] = batched_case(gs, ctx, dev, stream)
+        extras["adjoint_cfg5"] = adjoint_case(gs, ctx, dev, stream)
         extras["barycentric_distance"] = families_case(gs, ctx, dev, stream)
         extras["implicit_vs_chebyshev"] = implicit_case(gs, ctx, dev, stream)
         extras["log_domain_sinkhorn"] = logdomain_case(gs, ctx, dev, stream)
+        extras["combinatorial_filter"] = combinatorial_case(gs, ctx, dev, stream)
+        extras["matmul_peaks"] = matmul_peaks(dev, stream)
+        extras["knn_screen"] = knn_case(gs, ctx, dev, stream, X, cfg, extras["matmul_peaks"])
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     Xh = torch.from_numpy(p.X).pin_memory()
@@ -396,6 +457,9 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample()
         cpu.pop("est_step_s", None)
+        if not args.no_extras:
+            extras["cpu_baselines"] = {"barycenter_cfg3": oracle_sample_cfg3(),
+                                       "adjoint_cfg5": oracle_sample_cfg5()}
 
     if rank == 0:
         line = {
@@ -471,35 +535,44 @@ def _time(stream, fn):
     return e0.elapsed_time(e1)
 
 
-def batched_case(gs, ctx, dev, stream, count=64, iters=200):
-    """Ragged batch (n log-uniform in [1e3, 5e4], d 3..20, k in {8,10,15}, K in {16,24,32}, t = 5,
-    Dirichlet marginals on 10 % supports): one persistent batched launch against `count`
-    sequential single-problem calls on the same graphs."""
+def batched_case(gs, ctx, dev, stream, count=512, iters=200):
+    """The batching workload: `count` ragged problems (n log-uniform in [1e3, 5e4], d 3..20, k in
+    {8,10,15}, K in {16,24,32}, t = 5, Dirichlet marginals on 10 % supports, `iters` iterations) in
+    one batched call (one persistent launch, replayed from a captured CUDA graph from the second
+    call on) against `count` sequential single-problem calls on the same graphs; W^2 agreement."""
     import torch
     probs = W.ragged_batch(count=count, iters=iters)
     graphs = [gs.gs_build_graph(ctx, torch.from_numpy(p.X).to(dev), p.k) for p in probs]
     a = [torch.from_numpy(p.a).to(dev) for p in probs]
     b = [torch.from_numpy(p.b).to(dev) for p in probs]
     ts, Ks = [p.t for p in probs], [p.K for p in probs]
-    out = {}
-    gs.gs_sinkhorn_batched(ctx, graphs, a, b, ts, Ks, iters)  # warm (workspace, queue)
-    ms_b = _time(stream, lambda: out.__setitem__("b", gs.gs_sinkhorn_batched(ctx, graphs, a, b, ts, Ks, iters)))
+    us = [torch.empty(g.n, dtype=torch.float32, device=dev) for g in graphs]
+    vs = [torch.empty(g.n, dtype=torch.float32, device=dev) for g in graphs]
+    dist = torch.empty((count, 2), dtype=torch.float64, device=dev)
+    run_b = lambda: gs.gs_sinkhorn_batched(ctx, graphs, a, b, ts, Ks, iters, us, vs, dist)  # noqa: E731
+    run_b()  # warm (workspace, queue, graph capture)
+    run_b()
+    l0 = gs.gs_launch_count(ctx)
+    ms_b = _time(stream, run_b)
+    launches_b = gs.gs_launch_count(ctx) - l0
+    db = dist[:, 0].cpu().numpy().copy()
     for i, g in enumerate(graphs):  # warm the per-problem graphs
         gs.gs_sinkhorn(ctx, g, a[i], b[i], ts[i], Ks[i], iters)
     seq = []
     ms_s = _time(stream, lambda: seq.extend(gs.gs_sinkhorn(ctx, g, a[i], b[i], ts[i], Ks[i], iters)[2]
                                             for i, g in enumerate(graphs)))
     gs.gs_sync(ctx)
-    db = out["b"][2].cpu().numpy()[:, 0]
     ds = np.array([float(d[0]) for d in seq])
     rel = float(np.max(np.abs(db - ds) / np.maximum(np.abs(ds), 1e-30)))
     nodes = sum(g.n for g in graphs)
+    nnz = sum(g.nnz for g in graphs)
     for g in graphs:
         g.close()
-    return {"problems": count, "iters": iters, "total_nodes": nodes, "batched_ms": ms_b,
-            "sequential_ms": ms_s, "speedup": ms_s / ms_b,
-            "batched_problem_iters_per_s": count * iters / (ms_b / 1e3),
-            "max_rel_diff_W2": rel}
+    return {"workload": f"{count} ragged problems, n log-uniform in [1e3, 5e4], K in {{16, 24, 32}}, t = 5",
+            "problems": count, "iters": iters, "total_nodes": nodes, "total_nnz": nnz,
+            "batched_ms": ms_b, "batched_launches_per_call": launches_b, "sequential_ms": ms_s,
+            "speedup": ms_s / ms_b, "batched_problem_iters_per_s": count * iters / (ms_b / 1e3),
+            "max_rel_diff_W2": rel, "rtol_1e-4_met": rel <= 1e-4}
 
 
 def implicit_case(gs, ctx, dev, stream, t=5.0, K=30, iters=12):
@@ -603,9 +676,11 @@ def families_case(gs, ctx, dev, stream, bary_iters=100, sink_iters=200):
             "filter_orders": 2 * (2 * K * bary_iters) + 2 * K * sink_iters}
 
 
-def adjoint_case(gs, ctx, dev, stream, iters=40, checkpoint=20):
-    """Gradient of W^2(src, barycenter(M, alpha)) on the 500k-point manifold with 64 inputs
-    (K = 40, t = 8): forward only vs forward + reverse sweep, `iters` iterations per loop."""
+def adjoint_case(gs, ctx, dev, stream, iters=200, checkpoint=20):
+    """The differentiation workload: gradient of J = W^2(src, barycenter(M, alpha)) on the
+    500k-point manifold with 64 inputs (K = 40, t = 8), `iters` iterations in each loop, checkpoints
+    every `checkpoint`: forward only (barycenter + distance) vs forward + reverse sweep (dJ/dsrc and
+    dJ/dalpha)."""
     import torch
     cfg = W.manifold_barycenter_grad(bary_iters=iters, sink_iters=iters, checkpoint=checkpoint)
     g = gs.gs_build_graph(ctx, torch.from_numpy(cfg["X"]).to(dev), cfg["k"])
@@ -623,7 +698,7 @@ def adjoint_case(gs, ctx, dev, stream, iters=40, checkpoint=20):
         mu = gs.gs_barycenter(ctx, g, M, alpha, t, K, iters)
         d, ga, gmu = gs.gs_sinkhorn_grad(ctx, g, src, mu, t, K, iters, checkpoint=checkpoint)
         _, galpha = gs.gs_barycenter_grad(ctx, g, M, alpha, t, K, iters, gmu, checkpoint=checkpoint)
-        res["g"] = (ga, galpha)
+        res["g"] = (d, ga, galpha)
 
     # the objective is the distance to the barycenter as the iteration leaves it, whose mass is not
     # exactly the source's: the equal-mass argument check is off for this leg
@@ -634,10 +709,109 @@ def adjoint_case(gs, ctx, dev, stream, iters=40, checkpoint=20):
     ms_g = _time(stream, gradient)
     gs.gs_sync(ctx)
     gs.gs_set_option(ctx, gs.GS_OPT_CHECK_ARGS, 1)
+    w2_f = float(res["d"][0])
+    w2_g = float(res["g"][0][0])
     n = g.n
     g.close()
-    return {"n": n, "m": int(M.shape[1]), "K": K, "iters": iters, "checkpoint": checkpoint,
-            "forward_ms": ms_f, "forward_plus_backward_ms": ms_g, "backward_over_forward": ms_g / ms_f - 1.0}
+    return {"workload": "manifold-500k-R40, 64 inputs, K = 40, t = 8", "n": n, "m": int(M.shape[1]), "K": K,
+            "iters": iters, "checkpoint": checkpoint, "forward_ms": ms_f, "forward_plus_backward_ms": ms_g,
+            "backward_over_forward": ms_g / ms_f - 1.0, "J_forward": w2_f, "J_gradient_pass": w2_g,
+            "J_rel_diff": abs(w2_f - w2_g) / abs(w2_f)}
+
+
+def barycenter_case(gs, ctx, dev, stream, peak, peak_kind, iters=300):
+    """The barycenter workload: 32 cluster-union distributions on the 200k-point cluster graph in
+    R^30 (k = 10, K = 40, t = 10), uniform weights, `iters` barycenter iterations in one call:
+    iterations per second and the counted bytes per Chebyshev order of the two [n, 32] applies."""
+    import torch
+    cfg = W.clusters_barycenter(iters=iters)
+    g = gs.gs_build_graph(ctx, torch.from_numpy(cfg["X"]).to(dev), cfg["k"])
+    M = torch.from_numpy(cfg["M"]).to(dev)
+    alpha = torch.tensor(cfg["alpha"], dtype=torch.float64, device=dev)
+    mu = torch.empty(g.n, dtype=torch.float32, device=dev)
+    t, K, m = cfg["t"], cfg["K"], int(M.shape[1])
+    run = lambda: gs.gs_barycenter(ctx, g, M, alpha, t, K, iters, mu=mu)  # noqa: E731
+    gs.gs_barycenter(ctx, g, M, alpha, t, K, 2, mu=mu)  # warm
+    ms = _time(stream, run)
+    gs.gs_sync(ctx)
+    n, nnz = g.n, g.nnz
+    g.close()
+    # one iteration: w = M / H(vol v) (last order: gather, T, y, M, and the next input vol w) and
+    # d = v H(vol w) with the geometric mean (gather, T, y, v read, v and the next input written,
+    # and the [n] barycenter)
+    per_iter = apply_bytes(n, nnz, K, m, 5) + apply_bytes(n, nnz, K, m, 6) + 4 * n
+    orders = 2 * K * iters
+    ach = per_iter * iters / (ms / 1e3) / 1e9
+    return {"workload": "clusters-200k-R30, 32 cluster-union distributions, K = 40, t = 10", "n": n, "nnz": nnz,
+            "B": m, "K": K, "iters": iters, "ms": ms, "iters_per_s": iters / (ms / 1e3),
+            "order_us": ms * 1e3 / orders, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": f"{peak_kind} hbm_gbs", "bytes_per_iter": per_iter,
+            "mass": float(mu.double().sum())}
+
+
+def combinatorial_case(gs, ctx, dev, stream, K=60):
+    """The combinatorial-Laplacian filter exp(-t (D - A)) (rescaled by lam = 2 max degree) against
+    the normalised-Laplacian filter on the 100k-point manifold graph, one column, the same degree K;
+    t chosen so that the expansion's time s = t lam / 2 equals 5 (the normalised filter's t)."""
+    import torch
+    p = W.manifold_pair()
+    g = gs.gs_build_graph(ctx, torch.from_numpy(p.X).to(dev), p.k)
+    V = torch.from_numpy(p.a).to(dev)
+    _, lam = gs.gs_heat_apply_combinatorial(ctx, g, 1.0, K, V)  # builds the operator, returns lam
+    tc = 2.0 * 5.0 / lam
+    out = {}
+    ms_c = _time(stream, lambda: out.__setitem__("c", gs.gs_heat_apply_combinatorial(ctx, g, tc, K, V)[0]))
+    gs.gs_heat_apply(ctx, g, 5.0, K, V)
+    ms_n = _time(stream, lambda: out.__setitem__("n", gs.gs_heat_apply(ctx, g, 5.0, K, V)))
+    gs.gs_sync(ctx)
+    mass_in, mass_out = float(V.double().sum()), float(out["c"].double().sum())
+    nnz = g.nnz
+    g.close()
+    return {"workload": "manifold-100k-R50, B = 1", "K": K, "lam": lam, "t": tc, "s": tc * lam / 2,
+            "combinatorial_ms": ms_c, "normalised_ms": ms_n, "order_us": ms_c * 1e3 / K,
+            "mass_rel_change": abs(mass_out - mass_in) / mass_in, "nnz_with_diagonal": nnz + p.X.shape[0]}
+
+
+def matmul_peaks(dev, stream, N=8192, reps=10):
+    """Dense-contraction roofs on this GPU: torch (cuBLAS) FP32 matmul with TF32 tensor cores and
+    with plain FP32 (CUDA-core FMA), best of `reps` CUDA-event timings, 2 N^3 flops each."""
+    import torch
+    a = torch.randn(N, N, device=dev)
+    b = torch.randn(N, N, device=dev)
+    out = {}
+    saved = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, tf32 in (("tf32_tflops", True), ("fp32_fma_tflops", False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            for _ in range(3):
+                torch.matmul(a, b)
+            best = 1e30
+            for _ in range(reps):
+                best = min(best, _time(stream, lambda: torch.matmul(a, b)))
+            out[name] = 2.0 * N ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = saved
+    out["how"] = f"torch.matmul float32 {N}^3, best of {reps}, CUDA events (allow_tf32 on / off)"
+    return out
+
+
+def knn_case(gs, ctx, dev, stream, X, cfg, peaks, reps=3):
+    """The kNN graph's distance screen on the headline workload (n = 100k in R^50, k = 15): time of
+    the whole gs_knn call (screen, FP64 rerank, ordering of the lists) and the 3xTF32 tensor-core
+    flops of the screen (3 MMAs of 128 x 128 x 8 per 8 augmented features, all padded query x
+    candidate tiles), as a lower bound on the screen's TF32 rate and its fraction of the measured
+    TF32 matmul peak."""
+    n, d = X.shape
+    gs.gs_knn(ctx, X, cfg["k"])
+    ms = min(_time(stream, lambda: gs.gs_knn(ctx, X, cfg["k"])) for _ in range(reps))
+    gs.gs_sync(ctx)
+    npad = -(-n // 128) * 128
+    kaug = -(-(d + 2) // 8) * 8
+    flops = 3 * 2.0 * npad * npad * kaug
+    tf = flops / (ms / 1e3) / 1e12
+    return {"n": n, "d": d, "knn_ms": ms, "screen_tf32_flops": flops, "tflops_lower_bound": tf,
+            "tf32_peak_tflops": peaks.get("tf32_tflops"),
+            "frac_of_tf32_peak_lower_bound": tf / peaks["tf32_tflops"] if peaks.get("tf32_tflops") else None}
 
 
 def main():

@@ -15,6 +15,8 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -268,36 +270,138 @@ __global__ void __launch_bounds__(kThreads, 1) batched_sinkhorn(const BatchProbl
     }
 }
 
+// Distances from the kernel's sorted problem order back to the caller's order.
+__global__ void scatter_dist(int nprob, const int* __restrict__ order, const double* __restrict__ dsorted,
+                             double* __restrict__ dist)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nprob) return;
+    dist[2 * order[q]] = dsorted[2 * q];
+    dist[2 * order[q] + 1] = dsorted[2 * q + 1];
+}
+
+// The launches of one batched call: argument checks, queue reset, the persistent kernel, the
+// distance scatter.  Every table they read is on the device already.
+gs_status enqueue_batch(gs_ctx* ctx, const BatchCacheEntry& en, int nprob, int iters, int* queue,
+                        double* dsorted, double* dist)
+{
+    cudaStream_t s = ctx->stream;
+    const auto* probs = reinterpret_cast<const BatchProblem*>(static_cast<char*>(en.tables) + en.off_probs);
+    const auto* mg = reinterpret_cast<gs_marginals*>(static_cast<char*>(en.tables) + en.off_checks);
+    const int* order = reinterpret_cast<const int*>(static_cast<char*>(en.tables) + en.off_order);
+    gs_status st = gs_check_marginals_dev(ctx, mg, nprob);
+    if (st != GS_OK) return st;
+    cudaMemsetAsync(queue, 0, sizeof(int), s);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(kClusterCtas * en.clusters);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, batched_sinkhorn, probs, nprob, iters, queue, dsorted, ctx->flags);
+    gs_count(ctx, 1);
+    if ((st = gs_cuda_check(ctx, e, "batched Sinkhorn launch")) != GS_OK) return st;
+    if (dist) {
+        scatter_dist<<<(unsigned)((nprob + 255) / 256), 256, 0, s>>>(nprob, order, dsorted, dist);
+        gs_count(ctx, 1);
+    }
+    return gs_cuda_check(ctx, cudaGetLastError(), "batched Sinkhorn");
+}
+
 }  // namespace
 
+void gs_batch_cache_clear(gs_ctx* ctx)
+{
+    for (auto& en : ctx->bcache) {
+        if (en.exec) cudaGraphExecDestroy(en.exec);
+        if (en.tables) cudaFree(en.tables);
+    }
+    ctx->bcache.clear();
+}
+
+// A batched call's problem tables (descriptors with their workspace arena pointers, coefficients,
+// check descriptors, the problem order) are built once per distinct set of arguments and kept on
+// the device with a CUDA graph of the call's launches, captured on the context's private stream;
+// a repeated call only replays that graph.  The tables point into the workspace, so growing it
+// drops these entries (gs_ws_ensure clears the caches).
 gs_status gs_sinkhorn_batched_impl(gs_ctx* ctx, int nprob, const gs_graph* const* graphs,
                                    const float* const* a, const float* const* b, const double* t,
                                    const int* K, int iters, float* const* u, float* const* v,
                                    double* dist)
 {
+    int64_t arena = 0;
+    for (int i = 0; i < nprob; ++i) arena += 5 * ((graphs[i]->n + 63) / 64 * 64);
+    WsPlan plan;
+    const size_t iar = plan.add(sizeof(float) * (size_t)arena), iq = plan.add(sizeof(int) * 4),
+                 ids = plan.add(sizeof(double) * 2 * (size_t)nprob);
+    gs_status st = gs_ws_ensure(ctx, plan.total);
+    if (st != GS_OK) return st;
+    float* ar = ws_at<float>(ctx, plan, iar);
+    int* queue = ws_at<int>(ctx, plan, iq);
+    double* dsorted = ws_at<double>(ctx, plan, ids);  // distances in the sorted problem order
+
+    // everything a descriptor holds, so that equal keys mean identical tables
+    std::vector<uintptr_t> key;
+    key.reserve(16 * (size_t)nprob + 8);
+    key.push_back((uintptr_t)nprob);
+    key.push_back((uintptr_t)iters);
+    key.push_back((uintptr_t)ctx->ws);
+    key.push_back((uintptr_t)dist);
+    key.push_back((uintptr_t)ctx->check_args);
+    for (int i = 0; i < nprob; ++i) {
+        const gs_graph* g = graphs[i];
+        uint64_t tb;
+        memcpy(&tb, &t[i], sizeof tb);
+        for (uintptr_t x : {(uintptr_t)g->n, (uintptr_t)g->nnz, (uintptr_t)g->rowptr, (uintptr_t)g->col,
+                            (uintptr_t)g->pval, (uintptr_t)g->perm, (uintptr_t)g->prowptr, (uintptr_t)g->pcol,
+                            (uintptr_t)g->ppval, (uintptr_t)g->sptr, (uintptr_t)g->scol, (uintptr_t)g->sval,
+                            (uintptr_t)a[i], (uintptr_t)b[i], (uintptr_t)u[i], (uintptr_t)v[i],
+                            (uintptr_t)tb, (uintptr_t)K[i]})
+            key.push_back(x);
+    }
+    BatchCacheEntry* hit = nullptr;
+    for (auto& en : ctx->bcache)
+        if (en.key == key) hit = &en;
+
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->stream, &cap);
+    if (hit) {
+        if (cap != cudaStreamCaptureStatusNone || !hit->exec)  // inside a caller's capture: the launches
+            return enqueue_batch(ctx, *hit, nprob, iters, queue, dsorted, dist);
+        gs_count(ctx, hit->nodes);
+        return gs_cuda_check(ctx, cudaGraphLaunch(hit->exec, ctx->stream), "batched Sinkhorn graph launch");
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return gs_fail(ctx, GS_ERR_UNSUPPORTED,
+                       "a new batched problem set must be run once before stream capture (its tables are "
+                       "uploaded then)");
+
     // order problems by work (nnz * K), largest first, for the dynamic queue
     std::vector<int> order((size_t)nprob);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
         return (double)graphs[i]->nnz * K[i] > (double)graphs[j]->nnz * K[j];
     });
-    int64_t arena = 0, ncoef = 0;
-    for (int i = 0; i < nprob; ++i) {
-        arena += 5 * ((graphs[i]->n + 63) / 64 * 64);
-        ncoef += K[i] + 1;
+    int64_t ncoef = 0;
+    for (int i = 0; i < nprob; ++i) ncoef += K[i] + 1;
+    BatchCacheEntry en;
+    en.key = key;
+    WsPlan tp;
+    const size_t tpr = tp.add(sizeof(BatchProblem) * (size_t)nprob), tco = tp.add(sizeof(float) * (size_t)ncoef),
+                 tmc = tp.add(sizeof(gs_marginals) * (size_t)nprob), tor = tp.add(sizeof(int) * (size_t)nprob);
+    if (cudaMalloc(&en.tables, tp.total) != cudaSuccess) {
+        cudaGetLastError();
+        return gs_fail(ctx, GS_ERR_OOM, "batched problem tables");
     }
-    WsPlan plan;
-    const size_t iar = plan.add(sizeof(float) * (size_t)arena), ico = plan.add(sizeof(float) * (size_t)ncoef),
-                 ipr = plan.add(sizeof(BatchProblem) * (size_t)nprob), iq = plan.add(sizeof(int) * 4),
-                 ids = plan.add(sizeof(double) * 2 * (size_t)nprob),
-                 imc = plan.add(sizeof(gs_marginals) * (size_t)nprob);
-    gs_status st = gs_ws_ensure(ctx, plan.total);
-    if (st != GS_OK) return st;
-    float* ar = ws_at<float>(ctx, plan, iar);
-    float* co = ws_at<float>(ctx, plan, ico);
-    BatchProblem* dprobs = ws_at<BatchProblem>(ctx, plan, ipr);
-    int* queue = ws_at<int>(ctx, plan, iq);
-    double* dsorted = ws_at<double>(ctx, plan, ids);  // distances in the sorted problem order
+    en.off_probs = tp.offs[tpr];
+    en.off_checks = tp.offs[tmc];
+    en.off_order = tp.offs[tor];
+    float* co = reinterpret_cast<float*>(static_cast<char*>(en.tables) + tp.offs[tco]);
 
     std::vector<BatchProblem> hp((size_t)nprob);
     std::vector<float> hc((size_t)ncoef);
@@ -335,44 +439,85 @@ gs_status gs_sinkhorn_batched_impl(gs_ctx* ctx, int nprob, const gs_graph* const
         p.coef = co + coff;
         coff += K[i] + 1;
     }
+    // Algorithm 1's argument checks for every problem (unit vertex weights)
+    std::vector<gs_marginals> mg((size_t)nprob);
+    for (int i = 0; i < nprob; ++i) mg[(size_t)i] = gs_marginals{a[i], b[i], nullptr, graphs[i]->n};
     cudaStream_t s = ctx->stream;
-    {
-        // Algorithm 1's argument checks for every problem, one block each (unit vertex weights)
-        std::vector<gs_marginals> mg((size_t)nprob);
-        for (int i = 0; i < nprob; ++i) mg[(size_t)i] = gs_marginals{a[i], b[i], nullptr, graphs[i]->n};
-        if ((st = gs_check_marginals(ctx, mg.data(), nprob, ws_at<gs_marginals>(ctx, plan, imc))) != GS_OK)
-            return st;
+    char* tb = static_cast<char*>(en.tables);
+    cudaError_t e = cudaMemcpyAsync(tb + tp.offs[tpr], hp.data(), sizeof(BatchProblem) * (size_t)nprob,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(co, hc.data(), sizeof(float) * (size_t)ncoef, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb + tp.offs[tmc], mg.data(), sizeof(gs_marginals) * (size_t)nprob,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb + tp.offs[tor], order.data(), sizeof(int) * (size_t)nprob, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables go out of scope below
+    if (e != cudaSuccess) {
+        cudaFree(en.tables);
+        return gs_cuda_check(ctx, e, "batched problem tables upload");
     }
-    cudaMemcpyAsync(dprobs, hp.data(), sizeof(BatchProblem) * (size_t)nprob, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(co, hc.data(), sizeof(float) * (size_t)ncoef, cudaMemcpyHostToDevice, s);
-    cudaMemsetAsync(queue, 0, sizeof(int), s);
 
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kClusterCtas;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kThreads);
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int clusters = 0;
-    cfg.gridDim = dim3(kClusterCtas * 64);
-    if (cudaOccupancyMaxActiveClusters(&clusters, (void*)batched_sinkhorn, &cfg) != cudaSuccess || clusters < 1) {
+    {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kClusterCtas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(kThreads);
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        cfg.gridDim = dim3(kClusterCtas * 64);
+        if (cudaOccupancyMaxActiveClusters(&clusters, (void*)batched_sinkhorn, &cfg) != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            clusters = ctx->num_sms / kClusterCtas;
+        }
+        en.clusters = std::max(1, std::min(clusters, nprob));
+    }
+
+    // capture the call's launches once on the private stream; replay it now and on every repeat
+    if (!ctx->cap && cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        clusters = ctx->num_sms / kClusterCtas;
+        ctx->cap = nullptr;
     }
-    clusters = std::max(1, std::min(clusters, nprob));
-    cfg.gridDim = dim3(kClusterCtas * clusters);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, batched_sinkhorn, (const BatchProblem*)dprobs, nprob, iters,
-                                       queue, dsorted, ctx->flags);
-    gs_count(ctx, 1);
-    if ((st = gs_cuda_check(ctx, e, "batched Sinkhorn launch")) != GS_OK) return st;
-    if (dist) {
-        for (int q = 0; q < nprob; ++q)
-            cudaMemcpyAsync(dist + 2 * order[q], dsorted + 2 * q, 2 * sizeof(double),
-                            cudaMemcpyDeviceToDevice, s);
+    if (ctx->cap) {
+        cudaStream_t user = ctx->stream;
+        const int64_t l0 = ctx->launches;
+        ctx->stream = ctx->cap;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+        st = GS_OK;
+        if (e == cudaSuccess) st = enqueue_batch(ctx, en, nprob, iters, queue, dsorted, dist);
+        const cudaError_t e2 = (e == cudaSuccess) ? cudaStreamEndCapture(ctx->cap, &graph) : e;
+        ctx->stream = user;
+        en.nodes = (int)(ctx->launches - l0);
+        ctx->launches = l0;
+        if (st == GS_OK && e2 == cudaSuccess && graph &&
+            cudaGraphInstantiate(&en.exec, graph, 0) == cudaSuccess) {
+            // captured
+        } else {
+            en.exec = nullptr;
+            cudaGetLastError();
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (st != GS_OK) {
+            cudaFree(en.tables);
+            return st;
+        }
     }
-    return gs_cuda_check(ctx, cudaGetLastError(), "batched Sinkhorn");
+    if (ctx->bcache.size() >= 4) {
+        auto& old = ctx->bcache.front();
+        if (old.exec) cudaGraphExecDestroy(old.exec);
+        if (old.tables) cudaFree(old.tables);
+        ctx->bcache.erase(ctx->bcache.begin());
+    }
+    ctx->bcache.push_back(en);
+    const BatchCacheEntry& stored = ctx->bcache.back();
+    if (!stored.exec) return enqueue_batch(ctx, stored, nprob, iters, queue, dsorted, dist);
+    gs_count(ctx, stored.nodes);
+    return gs_cuda_check(ctx, cudaGraphLaunch(stored.exec, ctx->stream), "batched Sinkhorn graph launch");
 }

@@ -1335,6 +1335,7 @@ void gs_graph_cache_clear(gs_ctx* ctx)
         if (en.execR) cudaGraphExecDestroy(en.execR);
     }
     ctx->gcache.clear();
+    gs_batch_cache_clear(ctx);  // batched tables point into the workspace too
 }
 
 // ----------------------------------------------------------------------------- Sinkhorn

@@ -52,6 +52,16 @@ struct GraphCacheEntry {
     int R = 0;
 };
 
+// A batched Sinkhorn call's device tables and the CUDA graph of its launches (batched.cu).
+struct BatchCacheEntry {
+    std::vector<uintptr_t> key;
+    void* tables = nullptr;          // device: descriptors, coefficients, check descriptors, order
+    size_t off_probs = 0, off_checks = 0, off_order = 0;
+    int clusters = 1;
+    cudaGraphExec_t exec = nullptr;
+    int nodes = 0;                   // kernels in the graph (for the launch counter)
+};
+
 struct gs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -80,6 +90,7 @@ struct gs_ctx {
     int check_args = 1;            // device-side checks of marginals and barycenter weights (1 on)
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
+    std::vector<BatchCacheEntry> bcache;
     std::string err;
 };
 
@@ -88,6 +99,7 @@ static inline void gs_count(gs_ctx* ctx, int64_t k)
     if (!ctx->capturing) ctx->launches += k;
 }
 void gs_graph_cache_clear(gs_ctx* ctx);
+void gs_batch_cache_clear(gs_ctx* ctx);
 
 struct gs_graph {
     int device = 0;
@@ -354,3 +366,5 @@ struct gs_marginals {
 // count problems; probs_dev (device, count entries) is needed only for count > 1
 gs_status gs_check_marginals(gs_ctx* ctx, const gs_marginals* probs, int count, gs_marginals* probs_dev);
 gs_status gs_check_weights(gs_ctx* ctx, const double* alpha, int m);
+// the same checks over `count` descriptors already on the device (one block each)
+gs_status gs_check_marginals_dev(gs_ctx* ctx, const gs_marginals* probs_dev, int count);

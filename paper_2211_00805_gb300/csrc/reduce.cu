@@ -166,6 +166,14 @@ gs_status gs_check_marginals(gs_ctx* ctx, const gs_marginals* probs, int count, 
     return gs_cuda_check(ctx, cudaGetLastError(), "marginal check");
 }
 
+gs_status gs_check_marginals_dev(gs_ctx* ctx, const gs_marginals* probs_dev, int count)
+{
+    if (!ctx->check_args || count < 1) return GS_OK;
+    check_marginals_many<<<(unsigned)count, kCheckThreads, 0, ctx->stream>>>(probs_dev, GS_MASS_RTOL, ctx->flags);
+    gs_count(ctx, 1);
+    return gs_cuda_check(ctx, cudaGetLastError(), "marginal check");
+}
+
 gs_status gs_check_weights(gs_ctx* ctx, const double* alpha, int m)
 {
     if (!ctx->check_args) return GS_OK;

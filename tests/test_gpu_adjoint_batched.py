@@ -142,6 +142,16 @@ def test_batched_matches_single_and_oracle(gs, ctx):
     u, v, dist = gs.gs_sinkhorn_batched(ctx, graphs, a, b, [p.t for p in probs], [p.K for p in probs], 40)
     gs.gs_sync(ctx)
     d = to_np(dist)
+    # the same call again replays its captured graph (tables kept on the device): same results
+    u2, v2 = [torch.empty_like(x) for x in u], [torch.empty_like(x) for x in v]
+    dist2 = torch.empty_like(dist)
+    for _ in range(2):
+        gs.gs_sinkhorn_batched(ctx, graphs, a, b, [p.t for p in probs], [p.K for p in probs], 40, u2, v2, dist2)
+    l0 = gs.gs_launch_count(ctx)
+    gs.gs_sinkhorn_batched(ctx, graphs, a, b, [p.t for p in probs], [p.K for p in probs], 40, u2, v2, dist2)
+    assert gs.gs_launch_count(ctx) - l0 == 3  # argument checks, the persistent kernel, the scatter
+    gs.gs_sync(ctx)
+    assert torch.equal(dist2, dist) and all(torch.equal(x, y) for x, y in zip(u2, u))
     for i, (p, g) in enumerate(zip(probs, graphs)):
         us, vs, ds, _ = gs.gs_sinkhorn(ctx, g, a[i], b[i], p.t, p.K, 40)
         gs.gs_sync(ctx)
