@@ -135,9 +135,13 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * stream (one small launch each) and a failure is raised as GS_ERR_ARG by the next gs_sync; the
  * computation itself still runs.  Turn them off to evaluate the unrolled iteration at unbalanced
  * marginals on purpose (e.g. a distance to a barycenter that is not normalised). */
+/* GS_OPT_TILE_LANES: with GS_OPT_BLK_KERNEL set to a row-group variant (2 or 5), the lanes that
+ * share a row (1, 2, 4, 8, 16 or 32; fewer lanes walk the row's columns in more passes, at most 8),
+ * i.e. the RHS tile width; with GS_OPT_B1_KERNEL = 6, the threads per row (2, 4 or 8).  0 (default):
+ * the kernel's own mapping.  gs_autotune times these widths itself; this option fixes one. */
 enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
        GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6, GS_OPT_PERSIST_SYNC = 7,
-       GS_OPT_PERSIST_BLOCKS = 8, GS_OPT_TAG_WORD = 9, GS_OPT_CHECK_ARGS = 10 };
+       GS_OPT_PERSIST_BLOCKS = 8, GS_OPT_TAG_WORD = 9, GS_OPT_CHECK_ARGS = 10, GS_OPT_TILE_LANES = 11 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
 
 /* Host query of an option.  For GS_OPT_LOOP, GS_OPT_B1_KERNEL and GS_OPT_PERSIST_SYNC left on
@@ -220,12 +224,28 @@ gs_status gs_graph_export_csr(gs_ctx *ctx, const gs_graph *g, int64_t *rowptr, i
  * short fixed-count Sinkhorn loop as graph replay and as the persistent launch with each
  * GS_OPT_PERSIST_SYNC form, and records the fastest loop mode and synchronisation.
  * *choice (may be NULL) receives the chosen variant (the GS_OPT_*_KERNEL value).
- * Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED. */
+ * For B > 1 it also times each row-group variant at two RHS tile widths (all of a row's columns
+ * per lane-group pass, or half of them in two passes); for B == 1 the row-split kernel with 2, 4
+ * and 8 threads per row.  The decision is also kept by the context per (n, nnz, B, K)
+ * (gs_autotune_choices).  Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED. */
 /* Later calls on the graph use the recorded choices while the context's options are automatic
  * (GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL 0, GS_OPT_LOOP 2, GS_OPT_PERSIST_SYNC 3); the context also
  * keeps the last one-
  * column choices for graphs that were never tuned (e.g. rebuilt graphs of the same workload). */
 gs_status gs_autotune(gs_ctx *ctx, gs_graph *g, int B, int K, int *choice);
+
+/* Host query of the autotuner's decision for graphs of g's size (n, nnz) and B columns, degree K
+ * preferred (the context keeps one record per (n, nnz, B, K) that gs_autotune timed, so graphs
+ * rebuilt for the same workload use it too).  Writes up to `count` ints into `out`:
+ *   0 order-kernel variant (a GS_OPT_*_KERNEL value; 0 none recorded),
+ *   1 lanes per row the calls will use (B > 1: the RHS tile is this many lanes x 4 or 1 floats;
+ *     B == 1: threads per row of the row-split kernel),
+ *   2 columns per pass of a lane group (B > 1), 1 for B == 1,
+ *   3 Sinkhorn loop mode recorded for B == 1 (1 persistent, 2 CUDA-graph replay, 0 not timed),
+ *   4 the persistent loop's block synchronisation recorded for B == 1 (-1 not timed),
+ *   5 1 if a record exists, else 0 (the other entries then describe the defaults).
+ * Not in the paper (it serves throughput).  Errors: GS_ERR_ARG. */
+gs_status gs_autotune_choices(const gs_ctx *ctx, const gs_graph *g, int B, int K, int *out, int count);
 
 /* Free a graph (waits for the device). NULL is accepted. */
 gs_status gs_graph_destroy(gs_graph *g);

@@ -45,6 +45,7 @@ SIGNATURES = {
     "gs_graph_layout": [_P, _P, ctypes.c_int],
     "gs_graph_export_csr": [_P, _P, _P, _P, _P, _P],
     "gs_autotune": [_P, _P, _I, _I, _P],
+    "gs_autotune_choices": [_P, _P, _I, _I, _P, _I],
     "gs_graph_destroy": [_P],
     "gs_heat_apply": [_P, _P, _D, _I, _P, _I, _P],
     "gs_heat_apply_combinatorial": [_P, _P, _D, _I, _P, _I, _P, _P],
@@ -178,6 +179,7 @@ GS_OPT_PERSIST_SYNC = 7
 GS_OPT_PERSIST_BLOCKS = 8
 GS_OPT_TAG_WORD = 9
 GS_OPT_CHECK_ARGS = 10
+GS_OPT_TILE_LANES = 11
 
 
 def gs_set_option(ctx: Context, option: int, value: int):
@@ -253,6 +255,16 @@ def gs_autotune(ctx: Context, g: Graph, B: int, K: int) -> int:
     ch = ctypes.c_int()
     _raise(ctx, _lib.gs_autotune(ctx.handle, g.handle, int(B), int(K), ctypes.byref(ch)))
     return int(ch.value)
+
+
+AUTOTUNE_FIELDS = ("kernel", "lanes", "columns_per_pass", "loop_mode", "persist_sync", "recorded")
+
+
+def gs_autotune_choices(ctx: Context, g: Graph, B: int, K: int) -> dict:
+    """The autotuner's recorded decision for graphs of g's size and B columns (see the header)."""
+    out = (ctypes.c_int * len(AUTOTUNE_FIELDS))()
+    _raise(ctx, _lib.gs_autotune_choices(ctx.handle, g.handle, int(B), int(K), out, len(AUTOTUNE_FIELDS)))
+    return dict(zip(AUTOTUNE_FIELDS, list(out)))
 
 
 GRAPH_LAYOUT_FIELDS = ("slices", "sell_entries", "cache_tables", "blocks", "rows_per_block",

@@ -164,6 +164,11 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->loop_mode = value;
         return GS_OK;
     }
+    if (option == GS_OPT_TILE_LANES && (value == 0 || value == 1 || value == 2 || value == 4 || value == 8 ||
+                                        value == 16 || value == 32)) {
+        ctx->lanes_override = value;
+        return GS_OK;
+    }
     if (option == GS_OPT_CHECK_ARGS && (value == 0 || value == 1)) {
         ctx->check_args = value;
         return GS_OK;
@@ -222,6 +227,7 @@ extern "C" gs_status gs_get_option(const gs_ctx* ctx, int option, int* value)
         case GS_OPT_PERSIST_BLOCKS: *value = ctx->persist_bps; return GS_OK;
         case GS_OPT_TAG_WORD: *value = ctx->tag_word; return GS_OK;
         case GS_OPT_CHECK_ARGS: *value = ctx->check_args; return GS_OK;
+        case GS_OPT_TILE_LANES: *value = ctx->lanes_override; return GS_OK;
         default: return GS_ERR_ARG;
     }
 }
@@ -316,6 +322,31 @@ extern "C" gs_status gs_autotune(gs_ctx* ctx, gs_graph* g, int B, int K, int* ch
     if (!gs_filter_supports(B, true))
         return gs_fail(ctx, GS_ERR_UNSUPPORTED, "B must be 1..256, or a multiple of 4 up to 1024");
     return gs_autotune_impl(ctx, g, B, K, choice);
+}
+
+extern "C" gs_status gs_autotune_choices(const gs_ctx* ctx, const gs_graph* g, int B, int K, int* out, int count)
+{
+    if (!ctx || !g || !out || count < 1 || B < 1) return GS_ERR_ARG;
+    int v[6] = {0, 0, 0, 0, -1, 0};
+    const TuneRecord* r = gs_tune_lookup(ctx, g, B, K);
+    if (r) {
+        v[0] = r->kernel;
+        v[1] = r->lanes;
+        v[3] = r->loop;
+        v[4] = r->sync;
+    }
+    // what a call would run: lanes per row and columns per pass of the chosen mapping
+    const FilterPlan pl = gs_filter_plan(ctx, g, B, true, K);
+    if (B == 1) {
+        v[1] = pl.kernel == GS_KERNEL_SPLIT || pl.kernel == GS_KERNEL_AUTO ? pl.split_t : v[1];
+        v[2] = 1;
+    } else {
+        v[1] = pl.group;
+        v[2] = pl.group * pl.vec;
+    }
+    v[5] = r ? 1 : 0;
+    for (int i = 0; i < count && i < 6; ++i) out[i] = v[i];
+    return GS_OK;
 }
 
 extern "C" gs_status gs_graph_destroy(gs_graph* g)

@@ -34,27 +34,52 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
     std::vector<double> c((size_t)K + 1);
     gs_heat_coefficients(1.0, K, c.data());
 
-    std::vector<int> cands;
-    if (B == 1)
-        cands = {GS_KERNEL_RANGED, GS_KERNEL_SM_RANGE, GS_KERNEL_SPLIT, GS_KERNEL_SELL,
-                 GS_KERNEL_VECTOR, GS_KERNEL_ASYNC};
-    else if (B == 32 || B == 64 || B == 128)
-        cands = {GS_KERNEL_VECTOR, GS_KERNEL_STAGED, GS_KERNEL_ASYNC, GS_KERNEL_RANGED, GS_KERNEL_GROUP_WARP,
-                 GS_KERNEL_GROUP_VEC4};
-    else if (B % 4 == 0 && B <= 128) cands = {GS_KERNEL_VECTOR, GS_KERNEL_STAGED, GS_KERNEL_ASYNC, GS_KERNEL_RANGED};
-    else cands = {GS_KERNEL_VECTOR, GS_KERNEL_RANGED};
+    // candidates: (order variant, lanes) where lanes is the RHS tile width of the row-group
+    // kernels (lanes per row; each lane walks ceil(B / (lanes x vec)) chunks) for B > 1, and the
+    // threads per row of the row-split kernel for B == 1 (0: the variant's own mapping)
+    struct Cand {
+        int kernel, lanes;
+    };
+    std::vector<Cand> cands;
+    if (B == 1) {
+        cands = {{GS_KERNEL_RANGED, 0}, {GS_KERNEL_SM_RANGE, 0}, {GS_KERNEL_SPLIT, 2}, {GS_KERNEL_SPLIT, 4},
+                 {GS_KERNEL_SPLIT, 8}, {GS_KERNEL_SELL, 0},     {GS_KERNEL_VECTOR, 0}, {GS_KERNEL_ASYNC, 0}};
+    } else {
+        const int vec = (B % 4 == 0) ? 4 : 1;  // the workspace blocks below are 16-byte aligned
+        int full = B / vec;
+        if (full > 32) full = 32;
+        int p2 = 1;
+        while (p2 * 2 <= full) p2 *= 2;
+        full = p2;
+        std::vector<int> widths = {full};
+        if (full >= 2 && (B + (full / 2) * vec - 1) / ((full / 2) * vec) <= 8) widths.push_back(full / 2);
+        for (int w : widths) {
+            cands.push_back({GS_KERNEL_VECTOR, w});
+            cands.push_back({GS_KERNEL_RANGED, w});
+        }
+        if (B == 32 || B == 64 || B == 128) {
+            cands.push_back({GS_KERNEL_GROUP_WARP, 0});
+            cands.push_back({GS_KERNEL_GROUP_VEC4, 0});
+        }
+        if (B % 4 == 0 && B <= 128) {
+            cands.push_back({GS_KERNEL_STAGED, 0});
+            cands.push_back({GS_KERNEL_ASYNC, 0});
+        }
+    }
     int* knob = (B == 1) ? &ctx->b1_kernel : &ctx->blk_kernel;
-    const int saved = *knob;
+    const int saved = *knob, saved_lanes = ctx->lanes_override;
     const int saved_tb1 = g->tuned_b1, saved_tblk = g->tuned_blk, saved_tB = g->tuned_blk_B;
+    const int saved_split = g->tuned_split, saved_tlanes = g->tuned_lanes;
     g->tuned_b1 = 0;
     g->tuned_blk = 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = cands[0];
+    Cand best = cands[0];
     float best_ms = 1e30f;
-    for (int v : cands) {
-        *knob = v;
+    for (const Cand& cd : cands) {
+        *knob = cd.kernel;
+        ctx->lanes_override = cd.lanes;
         Epilogue e;
         e.kind = EPI_STORE;
         e.out = Y;
@@ -71,29 +96,49 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best_ms) {
             best_ms = ms;
-            best = v;
+            best = cd;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *knob = saved;
+    ctx->lanes_override = saved_lanes;
     if (st != GS_OK) {
         g->tuned_b1 = saved_tb1;
         g->tuned_blk = saved_tblk;
         g->tuned_blk_B = saved_tB;
+        g->tuned_split = saved_split;
+        g->tuned_lanes = saved_tlanes;
         return st;
     }
     if (B == 1) {
-        ctx->tuned_b1 = best;
-        g->tuned_b1 = best;
+        ctx->tuned_b1 = best.kernel;
+        g->tuned_b1 = best.kernel;
+        g->tuned_split = best.lanes;
         g->tuned_blk = saved_tblk;
         g->tuned_blk_B = saved_tB;
     } else {
         g->tuned_b1 = saved_tb1;
-        g->tuned_blk = best;
+        g->tuned_blk = best.kernel;
+        g->tuned_lanes = best.lanes;
         g->tuned_blk_B = B;
     }
-    if (choice_out) *choice_out = best;
+    TuneRecord rec;
+    rec.n = n;
+    rec.nnz = g->nnz;
+    rec.B = B;
+    rec.K = K;
+    rec.kernel = best.kernel;
+    rec.lanes = best.lanes;
+    for (auto it = ctx->tune_log.begin(); it != ctx->tune_log.end(); ++it)
+        if (it->n == rec.n && it->nnz == rec.nnz && it->B == B && it->K == K) {
+            ctx->tune_log.erase(it);
+            break;
+        }
+    if (ctx->tune_log.size() >= 64) ctx->tune_log.erase(ctx->tune_log.begin());
+    ctx->tune_log.push_back(rec);
+    const int best_kernel = best.kernel;
+    if (choice_out) *choice_out = best_kernel;
     if (B != 1) return GS_OK;
 
     // one column: also time the fixed-count Sinkhorn loop both ways (persistent / graph replay)
@@ -142,6 +187,11 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
     for (int c = 1; c < 3; ++c)
         if (loop_ms[c] < loop_ms[best_s]) best_s = c;
     g->tuned_sync = best_s;
+    for (auto& r : ctx->tune_log)
+        if (r.n == n && r.nnz == g->nnz && r.B == 1 && r.K == K) {
+            r.loop = g->tuned_loop;
+            r.sync = best_s;
+        }
     ctx->tuned_sync = best_s;
     return GS_OK;
 }

@@ -1084,14 +1084,17 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
     gs_count(ctx, 1);
     const int TB = pl.block;
     if (pl.B == 1 && a.epi.kind != EPI_BARY_V) {
-        const int mode = ctx->b1_kernel != GS_KERNEL_AUTO ? ctx->b1_kernel
-                         : (g->tuned_b1 ? g->tuned_b1 : ctx->tuned_b1);
+        const int mode = pl.kernel;
         if (mode == GS_KERNEL_ASYNC) {
             order_b1_async<<<nblocks(g->n, 256), 256, 0, ctx->stream>>>(a);
             return;
         }
         if ((mode == GS_KERNEL_AUTO || mode == GS_KERNEL_SPLIT) && a.sptr != nullptr) {
-            order_sell_split<GS_SPLIT_T><<<nblocks(g->n, 8 * (32 / GS_SPLIT_T)), 256, 0, ctx->stream>>>(a);
+            switch (pl.split_t) {
+                case 2: order_sell_split<2><<<nblocks(g->n, 8 * 16), 256, 0, ctx->stream>>>(a); break;
+                case 8: order_sell_split<8><<<nblocks(g->n, 8 * 4), 256, 0, ctx->stream>>>(a); break;
+                default: order_sell_split<4><<<nblocks(g->n, 8 * 8), 256, 0, ctx->stream>>>(a); break;
+            }
             return;
         }
         if (mode == GS_KERNEL_SM_RANGE && a.sptr != nullptr) {
@@ -1125,9 +1128,7 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
     const int vec = pl.vec;
     const int lpr = pl.B == 1 ? 1 : pl.group;
     const unsigned grid = nblocks(g->n * lpr, TB);
-    const int blk_mode = ctx->blk_kernel != GS_KERNEL_AUTO
-                             ? ctx->blk_kernel
-                             : (g->tuned_blk_B == pl.B ? g->tuned_blk : GS_KERNEL_AUTO);
+    const int blk_mode = pl.kernel;
     if (vec == 4 && pl.B == 4 * lpr && lpr >= 2) {  // one float4 chunk per lane
         const int mode = blk_mode;
         if (mode == GS_KERNEL_ASYNC) {
@@ -1154,21 +1155,27 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
     if (pl.B > 1 && (blk_mode == GS_KERNEL_GROUP_WARP || blk_mode == GS_KERNEL_GROUP_VEC4) && vec == 4) {
         if (launch_grp(ctx, g, pl.B, blk_mode == GS_KERNEL_GROUP_WARP, a)) return;
     }
-    const bool one = pl.B <= lpr * vec;
+    // chunks of lpr * vec columns each lane group walks (the RHS tile width is lpr * vec)
+    const int chunks = (pl.B + lpr * vec - 1) / (lpr * vec);
     const int lg = ilog2(lpr);
     if (pl.B > 1 && blk_mode == GS_KERNEL_RANGED) {
         static const int occ41 = resident_blocks_per_sm(order_blk_ranged<4, 1>);
+        static const int occ42 = resident_blocks_per_sm(order_blk_ranged<4, 2>);
         static const int occ48 = resident_blocks_per_sm(order_blk_ranged<4, 8>);
         static const int occ11 = resident_blocks_per_sm(order_blk_ranged<1, 1>);
+        static const int occ12 = resident_blocks_per_sm(order_blk_ranged<1, 2>);
         static const int occ18 = resident_blocks_per_sm(order_blk_ranged<1, 8>);
-        const int occ = vec == 4 ? (one ? occ41 : occ48) : (one ? occ11 : occ18);
+        const int occ = vec == 4 ? (chunks == 1 ? occ41 : (chunks == 2 ? occ42 : occ48))
+                                 : (chunks == 1 ? occ11 : (chunks == 2 ? occ12 : occ18));
         const int64_t rpb = ranged_rows(ctx, g->n, TB / lpr, occ);
         const unsigned rgrid = nblocks(g->n, (int)rpb);
         if (vec == 4) {
-            if (one) order_blk_ranged<4, 1><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
+            if (chunks == 1) order_blk_ranged<4, 1><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
+            else if (chunks == 2) order_blk_ranged<4, 2><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
             else order_blk_ranged<4, 8><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
         } else {
-            if (one) order_blk_ranged<1, 1><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
+            if (chunks == 1) order_blk_ranged<1, 1><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
+            else if (chunks == 2) order_blk_ranged<1, 2><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
             else order_blk_ranged<1, 8><<<rgrid, TB, 0, ctx->stream>>>(a, lg, rpb);
         }
         return;
@@ -1184,29 +1191,62 @@ void launch_order(gs_ctx* ctx, const gs_graph* g, const FilterPlan& pl, const Or
     }
     const unsigned sgrid = grid + (unsigned)split_blocks;
     if (vec == 4) {
-        if (one) order_blk<4, 1><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
+        if (chunks == 1) order_blk<4, 1><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
+        else if (chunks == 2) order_blk<4, 2><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
         else order_blk<4, 8><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
     } else {
-        if (one) order_blk<1, 1><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
+        if (chunks == 1) order_blk<1, 1><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
+        else if (chunks == 2) order_blk<1, 2><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
         else order_blk<1, 8><<<sgrid, TB, 0, ctx->stream>>>(sa, lg, split_blocks);
     }
 }
 
 }  // namespace
 
-FilterPlan gs_filter_plan(const gs_ctx*, const gs_graph* g, int B, bool aligned)
+FilterPlan gs_filter_plan(const gs_ctx* ctx, const gs_graph* g, int B, bool aligned, int K)
 {
     FilterPlan p;
     p.B = B;
     p.block = 256;
     p.vec = (B % 4 == 0 && aligned) ? 4 : 1;
+    const TuneRecord* r = gs_tune_lookup(ctx, g, B, K);
     if (B == 1) {
         const float m = g->mean_row;
         p.group = m <= 6.f ? 4 : (m <= 14.f ? 8 : (m <= 28.f ? 16 : 32));
+        // variant: the context option, else this graph's tuning, else the record for its size,
+        // else the context's last one-column choice
+        int split = 0;
+        if (ctx->b1_kernel != GS_KERNEL_AUTO) {
+            p.kernel = ctx->b1_kernel;
+            split = ctx->lanes_override;
+        } else if (g->tuned_b1) {
+            p.kernel = g->tuned_b1;
+            split = g->tuned_split;
+        } else if (r) {
+            p.kernel = r->kernel;
+            split = r->lanes;
+        } else {
+            p.kernel = ctx->tuned_b1;
+        }
+        p.split_t = (split == 2 || split == 4 || split == 8) ? split : GS_SPLIT_T;
     } else {
         int lanes = B / p.vec;
         if (lanes > 32) lanes = 32;
         p.group = 1 << ilog2(lanes);
+        int tl = 0;
+        if (ctx->blk_kernel != GS_KERNEL_AUTO) {
+            p.kernel = ctx->blk_kernel;
+            tl = ctx->lanes_override;
+        } else if (g->tuned_blk_B == B) {
+            p.kernel = g->tuned_blk;
+            tl = g->tuned_lanes;
+        } else if (r) {
+            p.kernel = r->kernel;
+            tl = r->lanes;
+        }
+        // a tuned RHS tile width: fewer lanes per row, each walking more chunks (at most 8)
+        if (tl > 0 && tl < p.group && (tl & (tl - 1)) == 0 && (B + tl * p.vec - 1) / (tl * p.vec) <= 8)
+            p.group = tl;
     }
     return p;
 }
@@ -1230,7 +1270,7 @@ gs_status gs_filter_enqueue(gs_ctx* ctx, const gs_graph* g, const double* c, int
                          (epi_in.out == nullptr || ((uintptr_t)epi_in.out % 16) == 0);
     if (!gs_filter_supports(B, aligned))
         return gs_fail(ctx, GS_ERR_UNSUPPORTED, "B > 256 needs 16-byte aligned blocks with B % 4 == 0");
-    const FilterPlan pl = gs_filter_plan(ctx, g, B, aligned);
+    const FilterPlan pl = gs_filter_plan(ctx, g, B, aligned, K);
     OrderArgs a;
     const FilterCsr csr = gs_filter_csr(g);
     a.n = g->n;
@@ -1414,7 +1454,8 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
     };
 
     bool looped = false;
-    const int tl = g->tuned_loop ? g->tuned_loop : ctx->tuned_loop;
+    const TuneRecord* rec = g->tuned_loop ? nullptr : gs_tune_lookup(ctx, g, 1, K);
+    const int tl = g->tuned_loop ? g->tuned_loop : (rec && rec->loop ? rec->loop : ctx->tuned_loop);
     const int loop = ctx->loop_mode != 2 ? ctx->loop_mode : (tl == 2 ? 1 : 0);
     if (!use_eps && loop == 0) {
         // Fixed iteration count, persistent mode: the whole loop as one cooperative launch.
@@ -1440,8 +1481,8 @@ gs_status gs_sinkhorn_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const
                                       (uintptr_t)n,         (uintptr_t)K,      (uintptr_t)a,
                                       (uintptr_t)b,         (uintptr_t)vol,    (uintptr_t)u,
                                       (uintptr_t)v,         (uintptr_t)ctx->ws, (uintptr_t)R,
-                                      (uintptr_t)ctx->b1_kernel, (uintptr_t)g->tuned_b1,
-                                      (uintptr_t)ctx->tuned_b1};
+                                      (uintptr_t)gs_filter_plan(ctx, g, 1, true, K).kernel,
+                                      (uintptr_t)gs_filter_plan(ctx, g, 1, true, K).split_t};
         uint64_t tb;
         memcpy(&tb, &t, sizeof(tb));
         key.push_back((uintptr_t)tb);

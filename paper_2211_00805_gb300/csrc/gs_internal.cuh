@@ -52,6 +52,18 @@ struct GraphCacheEntry {
     int R = 0;
 };
 
+// One gs_autotune decision, kept by the context for every graph of the same size (rebuilt graphs
+// of a workload find it too).
+struct TuneRecord {
+    int64_t n = 0, nnz = 0;
+    int B = 0, K = 0;
+    int kernel = 0;    // GS_KERNEL_* order variant
+    int lanes = 0;     // B > 1: lanes per row (columns per pass = lanes x floats per lane);
+                       // B == 1: threads per row of the row-split kernel; 0 = the kernel's default
+    int loop = 0;      // B == 1: 1 persistent loop, 2 CUDA-graph replay (0 not timed)
+    int sync = -1;     // B == 1: the persistent loop's block synchronisation (-1 not timed)
+};
+
 // A batched Sinkhorn call's device tables and the CUDA graph of its launches (batched.cu).
 struct BatchCacheEntry {
     std::vector<uintptr_t> key;
@@ -88,6 +100,8 @@ struct gs_ctx {
     int persist_bps = 1;           // gather-cache partition of graphs built from now on: blocks per
                                    // SM (1: 1024 threads each, 2: 512 threads each)
     int check_args = 1;            // device-side checks of marginals and barycenter weights (1 on)
+    int lanes_override = 0;        // autotuner trials: lanes per row (B > 1) / threads per row (B == 1)
+    std::vector<TuneRecord> tune_log;  // gs_autotune decisions by (n, nnz, B, K)
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)
     std::vector<GraphCacheEntry> gcache;
     std::vector<BatchCacheEntry> bcache;
@@ -134,6 +148,8 @@ struct gs_graph {
     int tuned_blk_B = 0;
     int tuned_loop = 0;            // Sinkhorn loop: 0 not tuned, 1 persistent, 2 CUDA-graph replay
     int tuned_sync = -1;           // persistent loop's block synchronisation (0..2), -1 not tuned
+    int tuned_lanes = 0;           // lanes per row of tuned_blk (0: the kernel's default)
+    int tuned_split = 0;           // threads per row of the one-column row-split kernel (0: default)
     std::vector<int> sptr_host;    // host copy of the slice offsets (sizes the persistent kernel's
                                    // shared-memory graph slices)
     // per-block gather cache of the persistent loop (xcache.cu): for the partition into xc_blocks
@@ -216,10 +232,25 @@ std::vector<int> gs_equal_slice_rows(int64_t n, int blocks);
 // rows per block of the persistent loop's partition (one block per SM, whole slices)
 // Block synchronisation of the persistent loop: the option if set, else the autotuned choice for
 // the graph, else the context's last one, else tagged values (the fastest on the graphs measured).
+// The context's autotuner record for a graph of g's size and B columns (degree K preferred).
+static inline const TuneRecord* gs_tune_lookup(const gs_ctx* ctx, const gs_graph* g, int B, int K)
+{
+    const TuneRecord* any = nullptr;
+    for (auto it = ctx->tune_log.rbegin(); it != ctx->tune_log.rend(); ++it) {
+        if (it->n != g->n || it->nnz != g->nnz || it->B != B) continue;
+        if (it->K == K) return &*it;
+        if (!any) any = &*it;
+    }
+    return any;
+}
 static inline int gs_persist_sync_choice(const gs_ctx* ctx, const gs_graph* g)
 {
     if (ctx->persist_sync != 3) return ctx->persist_sync;
     if (g && g->tuned_sync >= 0) return g->tuned_sync;
+    if (g) {
+        const TuneRecord* r = gs_tune_lookup(ctx, g, 1, 0);
+        if (r && r->sync >= 0) return r->sync;
+    }
     if (ctx->tuned_sync >= 0) return ctx->tuned_sync;
     return 2;
 }
@@ -287,10 +318,12 @@ struct FilterPlan {
     int vec = 1;                   // floats per lane access (4 needs B % 4 == 0 and 16 B alignment)
     int group = 8;                 // lanes per row (B == 1: split nonzeros; B > 1: split columns)
     int block = 256;
+    int kernel = 0;                // GS_KERNEL_* variant: the context option, else the autotuned one
+    int split_t = 4;               // B == 1 row-split kernel: threads per row (2, 4 or 8)
 };
 
 // aligned: every block the kernels gather from starts on a 16-byte boundary
-FilterPlan gs_filter_plan(const gs_ctx* ctx, const gs_graph* g, int B, bool aligned);
+FilterPlan gs_filter_plan(const gs_ctx* ctx, const gs_graph* g, int B, bool aligned, int K);
 int gs_err_partials_count();
 
 // Enqueue the K fused Chebyshev orders of p_K applied to x ([n, B]).

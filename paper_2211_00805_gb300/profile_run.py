@@ -55,6 +55,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0,
                     help="order-kernel variant (gs_set_option GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL)")
     ap.add_argument("--sweep", action="store_true", help="time every variant of the case")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run gs_autotune on the case's graph and time the tuned filter (choices printed)")
     ap.add_argument("--configs", default="0,0,2,2;0,0,2,1;0,0,2,0;0,0,1,0;1,6,1,0",
                     help="with --sinkhorn: ';'-separated loop mode,kernel,smem graph,sync tuples")
     ap.add_argument("--sinkhorn", type=int, default=0,
@@ -118,6 +120,14 @@ def main():
                           "K": c["K"], "apply_ms": ms, "order_us": ms * 1e3 / c["K"],
                           "GBps": byts / (ms / 1e3) / 1e9, "bytes_per_order": byts / c["K"]}), flush=True)
     gs.gs_set_option(ctx, option, args.variant)
+    if args.autotune:
+        gs.gs_set_option(ctx, option, 0)
+        choice = gs.gs_autotune(ctx, g, c["B"], c["K"])
+        ms = time_apply(ctx, g, c, V, Y, args.reps)
+        print(json.dumps({"case": args.case, "autotuned": gs.gs_autotune_choices(ctx, g, c["B"], c["K"]),
+                          "choice": choice, "apply_ms": ms, "order_us": ms * 1e3 / c["K"],
+                          "GBps": byts / (ms / 1e3) / 1e9}), flush=True)
+        gs.gs_set_option(ctx, option, args.variant)
     if args.sinkhorn and c["B"] == 1:
         # loop modes x one-column kernel variants, interleaved three times, medians reported
         a = torch.full((c["n"],), 1.0 / c["n"], device=dev)

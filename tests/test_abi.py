@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(built):
 # Calls with no operation of the paper behind them: context, options, diagnostics, tuning, layout.
 PLUMBING = {"gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_sync", "gs_reserve",
             "gs_set_option", "gs_get_option", "gs_launch_count", "gs_sell_step_order", "gs_graph_info",
-            "gs_graph_layout", "gs_autotune", "gs_graph_destroy"}
+            "gs_graph_layout", "gs_autotune", "gs_autotune_choices", "gs_graph_destroy"}
 
 
 def test_every_entry_point_is_documented_and_compute_calls_cite_their_passage():

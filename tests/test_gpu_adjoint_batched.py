@@ -151,7 +151,8 @@ def test_batched_matches_single_and_oracle(gs, ctx):
     gs.gs_sinkhorn_batched(ctx, graphs, a, b, [p.t for p in probs], [p.K for p in probs], 40, u2, v2, dist2)
     assert gs.gs_launch_count(ctx) - l0 == 3  # argument checks, the persistent kernel, the scatter
     gs.gs_sync(ctx)
-    assert torch.equal(dist2, dist) and all(torch.equal(x, y) for x, y in zip(u2, u))
+    assert torch.allclose(dist2, dist, rtol=0, atol=0, equal_nan=True)  # W is NaN where W^2 < 0
+    assert all(torch.equal(x, y) for x, y in zip(u2, u))
     for i, (p, g) in enumerate(zip(probs, graphs)):
         us, vs, ds, _ = gs.gs_sinkhorn(ctx, g, a[i], b[i], p.t, p.K, 40)
         gs.gs_sync(ctx)
@@ -191,12 +192,93 @@ def test_batched_single_order_filter(gs, ctx):
 
 
 def test_autotune_choice_is_used_and_exact(gs, ctx, sphere):
+    # the autotuner picks an order variant and, for B > 1, the RHS tile width (lanes per row) and,
+    # for B = 1, the row-split width; the record serves a rebuilt graph of the same points too
     p, g, Ls = sphere
-    for B in (1, 32):
+    g2 = gs.gs_build_graph(ctx, to_dev(p.X), p.k)  # same size: untuned, finds the record
+    for B in (1, 32, 64):
         choice = gs.gs_autotune(ctx, g, B, 30)
-        assert choice in (1, 2, 3, 4, 5, 6, 7)
+        assert choice in (1, 2, 3, 4, 5, 6, 7, 8, 9)
+        ch = gs.gs_autotune_choices(ctx, g, B, 30)
+        assert ch["recorded"] == 1 and ch["kernel"] == choice
+        if B == 1:
+            assert ch["loop_mode"] in (1, 2) and ch["persist_sync"] in (0, 1, 2)
+        else:
+            assert ch["lanes"] in (1, 2, 4, 8, 16, 32) and ch["columns_per_pass"] in (4 * ch["lanes"], ch["lanes"])
+        assert gs.gs_autotune_choices(ctx, g2, B, 30) == ch
         V = np.random.default_rng(B).random((g.n, B)).astype(np.float32)
-        Y = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
-        ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(5.0, 30), V.astype(np.float64))
-        assert_close(Y, ref, 1e-4, 1e-6 * np.abs(ref).max(), f"autotuned B={B}")
+        for graph in (g, g2):
+            Y = to_np(gs.gs_heat_apply(ctx, graph, 5.0, 30, to_dev(V)))
+            ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(5.0, 30), V.astype(np.float64))
+            assert_close(Y, ref, 1e-4, 1e-6 * np.abs(ref).max(), f"autotuned B={B}")
     gs.gs_sync(ctx)
+
+
+@pytest.mark.parametrize("B,lanes", [(32, 4), (64, 8), (64, 16), (12, 1), (128, 16)])
+def test_rhs_tile_widths_match_oracle(gs, ctx, sphere, B, lanes):
+    # every RHS tile width the autotuner may pick (lanes per row, each lane walking several
+    # chunks), through a record for the graph's size: results equal the oracle's
+    p, g, Ls = sphere
+    V = np.random.default_rng(B + lanes).random((g.n, B)).astype(np.float32)
+    gs.gs_autotune(ctx, g, B, 30)
+    Y0 = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
+    ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(5.0, 30), V.astype(np.float64))
+    assert_close(Y0, ref, 1e-4, 1e-6 * np.abs(ref).max(), f"tuned B={B}")
+    gs.gs_set_option(ctx, gs.GS_OPT_BLK_KERNEL, 2)
+    try:
+        gs.gs_set_option(ctx, gs.GS_OPT_TILE_LANES, lanes)
+        Y = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_TILE_LANES, 0)
+        gs.gs_set_option(ctx, gs.GS_OPT_BLK_KERNEL, 0)
+    assert_close(Y, ref, 1e-4, 1e-6 * np.abs(ref).max(), f"B={B} lanes={lanes}")
+    gs.gs_sync(ctx)
+
+
+def test_differentiation_workload_vs_oracle_finite_differences(gs, ctx):
+    # The differentiation workload's objective J(a, alpha) = W^2(a, barycenter(M, alpha)) with its
+    # recipe (6-d latent tanh manifold in R^40, k = 10, K = 40, t = 8, 64 inputs, checkpoints every
+    # 20) at a size the FP64 oracle can difference: n = 800 points and 100 iterations per loop
+    # instead of 500k and 200.  GPU gradient through the autograd adjoint against central
+    # differences of the oracle's forward map on 50 random coordinates: 25 of a (step 1e-4 a_i)
+    # and 25 of alpha (step 1e-4); perturbed inputs are not renormalised.
+    from paper_2211_00805_gb300.autograd import geodesic_barycenter, geodesic_sinkhorn_distance
+    its = 100
+    cfg = W.manifold_barycenter_grad(n=800, bary_iters=its, sink_iters=its, checkpoint=20)
+    X, M, src = cfg["X"], cfg["M"], cfg["src"]
+    t, K = cfg["t"], cfg["K"]
+    g = gs.gs_build_graph(ctx, to_dev(X), cfg["k"])
+    Ls, _ = oracle.build_graph(X.astype(np.float64), cfg["k"])
+    bk = oracle.cheb_coefficients(t, K)
+    alpha = torch.tensor(cfg["alpha"], dtype=torch.float64, device="cuda", requires_grad=True)
+    a = to_dev(src).requires_grad_(True)
+    gs.gs_set_option(ctx, gs.GS_OPT_CHECK_ARGS, 0)  # the barycenter's mass is not exactly a's
+    try:
+        mu = geodesic_barycenter(ctx, g, to_dev(M), alpha, t, K, its, checkpoint=20)
+        J = geodesic_sinkhorn_distance(ctx, g, a, mu, t, K, its, checkpoint=20)
+        J.backward()
+        gs.gs_sync(ctx)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_CHECK_ARGS, 1)
+    ga, gal = to_np(a.grad).astype(np.float64), to_np(alpha.grad)
+    M64, a64, al64 = M.astype(np.float64), src.astype(np.float64), np.asarray(cfg["alpha"], np.float64)
+    mu0 = oracle.barycenter(Ls, bk, M64, al64, its)
+    J0 = oracle.sinkhorn(Ls, bk, a64, mu0, t, its)["W2"]
+    assert float(J.detach()) == pytest.approx(J0, rel=1e-4)
+    rng = np.random.default_rng(7)
+    for i in rng.choice(len(a64), 25, replace=False):
+        h = 1e-4 * a64[i]
+        ap, am = a64.copy(), a64.copy()
+        ap[i] += h
+        am[i] -= h
+        fd = (oracle.sinkhorn(Ls, bk, ap, mu0, t, its)["W2"] - oracle.sinkhorn(Ls, bk, am, mu0, t, its)["W2"]) / (2 * h)
+        assert ga[i] == pytest.approx(fd, rel=GRTOL, abs=GATOL_REL * np.abs(ga).max()), f"dJ/da[{i}]"
+    for j in rng.choice(len(al64), 25, replace=False):
+        h = 1e-4
+        Jpm = []
+        for sgn in (1.0, -1.0):
+            alj = al64.copy()
+            alj[j] += sgn * h
+            Jpm.append(oracle.sinkhorn(Ls, bk, a64, oracle.barycenter(Ls, bk, M64, alj, its), t, its)["W2"])
+        fd = (Jpm[0] - Jpm[1]) / (2 * h)
+        assert gal[j] == pytest.approx(fd, rel=GRTOL, abs=GATOL_REL * np.abs(gal).max()), f"dJ/dalpha[{j}]"
