@@ -272,28 +272,79 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def static_config(world: int, nnz=None):
+    """The workload description both arms print (no timings in it)."""
+    cfg = WORKLOAD
+    out = {"workload": cfg["name"], "n": cfg["n"], "d": cfg["ambient"], "k": cfg["k"], "K": cfg["K"],
+           "t": cfg["t"], "iters": cfg["iters"], "parallelism": "replicas" if world > 1 else "single GPU",
+           "l2": "256 MB buffer written between timed steps (GPU arm)"}
+    if nnz is not None:
+        out["nnz"] = int(nnz)
+    return out
+
+
+def reference_shares(n: int, iters: int, S: int):
+    """Split one step into S shares: consecutive query-row ranges covering 0..n-1 once, and
+    iteration counts summing to `iters`."""
+    rows = [np.arange(i * n // S, (i + 1) * n // S) for i in range(S)]
+    its = [iters // S + (1 if i < iters % S else 0) for i in range(S)]
+    return rows, its
+
+
 def run_reference(args, rank, world):
+    """The FP64 oracle, as it stands, on the headline workload.  The full step (kNN over all n
+    query rows, graph assembly, 500 Sinkhorn iterations, distance) is split into `steps` equal
+    shares of real work: step i runs the kNN of its n / steps query rows and iters / steps Sinkhorn
+    iterations on the full 100k-point oracle graph (built once before the timed region), plus the
+    graph assembly's measured time / steps.  The timed shares add up to one whole step, so the
+    value is iterations per second of the full workload without extrapolation from a smaller one."""
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_sample()
-    vals, cb = [], None
+    import oracle
+    cfg = WORKLOAD
+    p = W.manifold_pair(n=cfg["n"], latent=cfg["latent"], ambient=cfg["ambient"], seed=cfg["seed"],
+                        k=cfg["k"], K=cfg["K"], t=cfg["t"], iters=cfg["iters"])
+    X64 = p.X.astype(np.float64)
+    n = cfg["n"]
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        cb = oracle_sample()
-        vals.append(cb["est_step_s"])
+    idx, dist = oracle.knn(X64, cfg["k"])
+    t_knn_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s = oracle.median_sigma(dist)
+    rp, col, A = oracle.affinity_graph(idx, dist, s)
+    deg, L = oracle.laplacian(rp, col, A)
+    Ls = oracle.shifted(L)
+    t_assembly = time.perf_counter() - t0
+    b = oracle.cheb_coefficients(cfg["t"], cfg["K"])
+    a64, b64 = p.a.astype(np.float64), p.b.astype(np.float64)
+    S = max(1, args.steps)
+    rows, its = reference_shares(n, cfg["iters"], S)
+
+    def share(i):
+        oracle.knn(X64, cfg["k"], rows=rows[i])
+        if its[i]:
+            oracle.sinkhorn(Ls, b, a64, b64, cfg["t"], its[i])
+
+    for w in range(args.warmup):
+        share(w % S)
+    t0 = time.perf_counter()
+    for i in range(S):
+        share(i)
     wall = time.perf_counter() - t0
-    step_s = statistics.mean(vals)
-    value = WORKLOAD["iters"] / step_s
-    cb = dict(cb, value=value)
-    cb.pop("est_step_s", None)
+    step_s = wall + t_assembly  # one whole step: every share once, plus the graph assembly
+    value = cfg["iters"] / step_s
+    sample = (f"the full step split into {S} shares of real work: kNN of n/{S} query rows and "
+              f"{cfg['iters']}/{S} Sinkhorn iterations per share on the full n={n} oracle graph "
+              f"(nnz={len(col)}); graph assembly timed once ({t_assembly:.2f} s) and added; the oracle's "
+              f"full kNN outside the timed region took {t_knn_setup:.1f} s")
+    cb = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle", "sample": sample}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3 / S,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD["name"], **{k: v for k, v in WORKLOAD.items() if k != "name"}},
-            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                                         "d2h_bytes_per_step": 0},
-            "wall_s": wall}
+            "data": "synthetic (seeded tanh-manifold generator; no dataset)",
+            "config": static_config(world, len(col)), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall, "whole_step_s": step_s}
     print(json.dumps(line), flush=True)
 
 
@@ -467,11 +518,8 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded tanh-manifold generator; no dataset)",
-            "config": {"workload": cfg["name"], "n": n, "d": cfg["ambient"], "k": cfg["k"],
-                       "nnz": nnz, "K": K, "t": cfg["t"], "iters": cfg["iters"],
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "256 MB buffer written between timed steps",
-                       "graph_build_ms": statistics.mean(graph_ms),
+            "config": static_config(world, nnz),
+            "timing": {"graph_build_ms": statistics.mean(graph_ms),
                        "sinkhorn_ms": statistics.mean(sink_ms),
                        "sinkhorn_only_iters_per_s": cfg["iters"] / sink_s,
                        "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],

@@ -65,3 +65,20 @@ def test_peak_is_the_measured_copy_bandwidth_else_the_fallback(tmp_path, monkeyp
     assert bench.measured_peaks() == (6786.2, "measured")
     os.remove(tmp_path / "MEASURED_PEAKS.json")
     assert bench.measured_peaks() == (6800.0, "fallback")
+
+
+@pytest.mark.parametrize("n,iters,S", [(100_000, 500, 1), (100_000, 500, 7), (100_000, 500, 20), (13, 5, 8)])
+def test_reference_shares_cover_one_whole_step(n, iters, S):
+    # the reference arm's timed shares add up to exactly one step: every query row once, and the
+    # iteration counts summing to the workload's
+    rows, its = bench.reference_shares(n, iters, S)
+    allrows = [r for part in rows for r in part.tolist()]
+    assert allrows == list(range(n))
+    assert sum(its) == iters and len(its) == S and max(its) - min(its) <= 1
+
+
+def test_both_arms_print_the_same_config():
+    assert bench.static_config(1, 123) == bench.static_config(1, 123)
+    c = bench.static_config(1, 2005410)
+    assert c["n"] == bench.WORKLOAD["n"] and c["iters"] == bench.WORKLOAD["iters"] and c["nnz"] == 2005410
+    assert not any(k.endswith("_ms") for k in c)  # no timings in the config
