@@ -93,6 +93,8 @@ extern "C" gs_status gs_create(gs_ctx** out, int device, void* stream)
     if (st == GS_OK) st = gs_cuda_check(ctx, cudaMalloc(&ctx->flags, 4 * sizeof(int)), "flags");
     if (st == GS_OK) st = gs_cuda_check(ctx, cudaMemset(ctx->flags, 0, 4 * sizeof(int)), "flags");
     if (st == GS_OK)
+        st = gs_cuda_check(ctx, cudaMalloc(&ctx->check_part, 2 * sizeof(double) * GS_CHECK_BLOCKS), "check scratch");
+    if (st == GS_OK)
         st = gs_cuda_check(ctx, cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device),
                            "SM count");
     if (st != GS_OK) {
@@ -112,6 +114,7 @@ extern "C" gs_status gs_destroy(gs_ctx* ctx)
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->flags) cudaFree(ctx->flags);
+    if (ctx->check_part) cudaFree(ctx->check_part);
     delete ctx;
     return GS_OK;
 }

@@ -78,7 +78,9 @@ struct gs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;    // private stream used only to capture graphs
-    int* flags = nullptr;          // device: status bits (GS_FLAG_*)
+    int* flags = nullptr;          // device: [0] status bits (GS_FLAG_*), [1] scratch word, [2] the
+                                   // argument check's arrival counter (zero between calls)
+    double* check_part = nullptr;  // device: the argument check's partial masses [2 x GS_CHECK_BLOCKS]
     void* ws = nullptr;            // device workspace
     size_t ws_bytes = 0;
     int num_sms = 0;
@@ -389,6 +391,7 @@ int gs_reduce_blocks();
 // sum vol a and sum vol b equal within GS_MASS_RTOL of the larger.  Barycenter weights: alpha >= 0
 // and |sum alpha - 1| <= GS_WEIGHT_TOL.
 constexpr double GS_MASS_RTOL = 1e-6;
+constexpr int GS_CHECK_BLOCKS = 128;  // blocks of the single-problem mass check
 constexpr double GS_WEIGHT_TOL = 1e-6;
 struct gs_marginals {
     const float* a;

@@ -121,9 +121,60 @@ __device__ void check_one(const gs_marginals& p, double rtol, int* flags)
     }
 }
 
-__global__ void __launch_bounds__(kCheckThreads) check_marginals(const gs_marginals p, double rtol, int* flags)
+// One problem over many blocks: each block sums a fixed stride of the entries, the last block to
+// finish adds the blocks' partial masses in block order (so the sums do not depend on timing)
+// and resets the arrival counter for the next call.
+constexpr int kPartThreads = 256;
+__global__ void __launch_bounds__(kPartThreads) check_marginals_part(const gs_marginals p, double rtol,
+                                                                     double* __restrict__ part,
+                                                                     unsigned* __restrict__ counter, int* flags)
 {
-    check_one(p, rtol, flags);
+    double ma = 0.0, mb = 0.0;
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float ai = p.a[i], bi = p.b[i];
+        if (!(ai >= 0.f) || !(bi >= 0.f) || isinf(ai) || isinf(bi)) bad = 1;
+        const double w = p.vol ? (double)p.vol[i] : 1.0;
+        ma += w * (double)ai;
+        mb += w * (double)bi;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        ma += __shfl_xor_sync(0xffffffffu, ma, off);
+        mb += __shfl_xor_sync(0xffffffffu, mb, off);
+    }
+    __shared__ double ra[kPartThreads / 32], rb[kPartThreads / 32];
+    __shared__ bool s_last;
+    bad = __syncthreads_or(bad);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        ra[w] = ma;
+        rb[w] = mb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ma = mb = 0.0;
+        for (int j = 0; j < kPartThreads / 32; ++j) {
+            ma += ra[j];
+            mb += rb[j];
+        }
+        part[2 * blockIdx.x] = ma;
+        part[2 * blockIdx.x + 1] = mb;
+        if (bad) atomicOr(flags, GS_FLAG_ARG);
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        double ta = 0.0, tb = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            ta += __ldcg(part + 2 * b);
+            tb += __ldcg(part + 2 * b + 1);
+        }
+        const double top = fmax(fabs(ta), fabs(tb));
+        if (!(fabs(ta - tb) <= rtol * top)) atomicOr(flags, GS_FLAG_ARG);
+        *counter = 0u;
+    }
 }
 
 __global__ void __launch_bounds__(kCheckThreads) check_marginals_many(const gs_marginals* __restrict__ ps,
@@ -153,8 +204,13 @@ gs_status gs_check_marginals(gs_ctx* ctx, const gs_marginals* probs, int count, 
 {
     if (!ctx->check_args || count < 1) return GS_OK;
     if (count == 1 || probs_dev == nullptr) {
-        for (int i = 0; i < count; ++i)
-            check_marginals<<<1, kCheckThreads, 0, ctx->stream>>>(probs[i], GS_MASS_RTOL, ctx->flags);
+        for (int i = 0; i < count; ++i) {
+            int64_t blocks = (probs[i].n + kPartThreads - 1) / kPartThreads;
+            if (blocks > GS_CHECK_BLOCKS) blocks = GS_CHECK_BLOCKS;
+            if (blocks < 1) blocks = 1;
+            check_marginals_part<<<(unsigned)blocks, kPartThreads, 0, ctx->stream>>>(
+                probs[i], GS_MASS_RTOL, ctx->check_part, reinterpret_cast<unsigned*>(ctx->flags + 2), ctx->flags);
+        }
         gs_count(ctx, count);
     } else {
         cudaMemcpyAsync(probs_dev, probs, sizeof(gs_marginals) * (size_t)count, cudaMemcpyHostToDevice,
