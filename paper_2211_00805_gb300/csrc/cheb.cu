@@ -302,18 +302,18 @@ __device__ __forceinline__ void order_blk_row(const OrderArgs& p, int lpr_log2, 
         if (!active || c0 >= B) continue;
         float* acc = f[ch];
         int e = beg;
-        for (; e + 4 <= end; e += 4) {
-            int j[4];
-            float w[4], x[4][VEC];
+        for (; e + 2 <= end; e += 2) {
+            int j[2];
+            float w[2], x[2][VEC];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 2; ++u) {
                 j[u] = __ldg(p.col + e + u);
                 w[u] = __ldg(p.pval + e + u);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) VecT<VEC>::load(p.cur + (int64_t)j[u] * B + c0, x[u]);
+            for (int u = 0; u < 2; ++u) VecT<VEC>::load(p.cur + (int64_t)j[u] * B + c0, x[u]);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 2; ++u)
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) acc[v] = fmaf(w[u], x[u][v], acc[v]);
         }
