@@ -117,13 +117,34 @@ __global__ void __launch_bounds__(kXrThreads) xr_order(XrOrder p)
     const unsigned gmask = ((1u << kLanes) - 1u) << (threadIdx.x & 31 & ~(kLanes - 1));
     const int beg = p.rowptr[row], end = p.rowptr[row + 1];
     // each lane: s 2^E over its entries, E raised as larger terms arrive
+    // (the lane's entries in CSR order; four gathers are issued before the first is summed)
     float s = 0.f;
     int E = kZeroExp;
-    for (int k = beg + lane; k < end; k += kLanes) {
-        const Xr x = p.x[p.col[k]];
+    int k = beg + lane;
+    for (; k + 3 * kLanes < end; k += 4 * kLanes) {
+        int c[4];
+        float w[4];
+        Xr x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = __ldg(p.col + k + u * kLanes);
+            w[u] = __ldg(p.pval + k + u * kLanes);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = p.x[c[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (x[u].m != 0.f) {
+                xr_raise(s, E, x[u].e);
+                s = fmaf(p.twice * w[u], scale_pow2(x[u].m, x[u].e - E), s);
+            }
+        }
+    }
+    for (; k < end; k += kLanes) {
+        const Xr x = p.x[__ldg(p.col + k)];
         if (x.m != 0.f) {
             xr_raise(s, E, x.e);
-            s = fmaf(p.twice * p.pval[k], scale_pow2(x.m, x.e - E), s);
+            s = fmaf(p.twice * __ldg(p.pval + k), scale_pow2(x.m, x.e - E), s);
         }
     }
     // lane partials combined by a fixed butterfly (both partners compute the same sum)

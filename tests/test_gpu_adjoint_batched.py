@@ -1,9 +1,12 @@
 """GPU reverse mode (gs_sinkhorn_grad / gs_barycenter_grad, the autograd wrappers) and the batched
 persistent solver (gs_sinkhorn_batched) against the FP64 oracle and the single-problem path.
 
-Gradient tolerance: |gpu - ref| <= 2e-3 |ref| + 2e-4 max|ref|.  The reverse sweep is 2 * iters
+Gradient tolerance: |gpu - ref| <= 2e-4 |ref| + 1e-4 max|ref|.  The reverse sweep is 2 * iters
 FP32 filter applies deep, each adding ~K eps_32 relative error to values whose sizes span the
-whole vector, so entries far below the maximum carry an absolute floor.
+whole vector, so entries far below the maximum carry an absolute floor.  Measured against the
+oracle's reverse mode on the 1,500-point sphere pair (30 and 200 iterations): the largest error of
+dW^2/da is 9.4e-5 of max|ref| (5.6e-5 at 200 iterations), of dW^2/db 4.7e-5; of the barycenter's
+weight gradient 1.7e-6.
 """
 import numpy as np
 import pytest
@@ -15,7 +18,7 @@ from tests.gpu_common import assert_close, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
-GRTOL, GATOL_REL = 2e-3, 2e-4
+GRTOL, GATOL_REL = 2e-4, 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -80,7 +83,7 @@ def test_sinkhorn_grad_vs_oracle_finite_differences(gs, ctx, sphere):
         am[i] -= h
         fd = (oracle.sinkhorn(Ls, bk, ap, b64, t, it)["W2"]
               - oracle.sinkhorn(Ls, bk, am, b64, t, it)["W2"]) / (2 * h)
-        assert ga[i] == pytest.approx(fd, rel=2e-3, abs=GATOL_REL * np.abs(ga).max())
+        assert ga[i] == pytest.approx(fd, rel=GRTOL, abs=GATOL_REL * np.abs(ga).max())
 
 
 def test_barycenter_grad_matches_oracle(gs, ctx):
