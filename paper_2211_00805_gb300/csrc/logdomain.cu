@@ -23,10 +23,23 @@
 //   y_i <= 0), and writes the next half-step's input vol_i u_i in the extended form.  One
 // iteration's 2K launches are captured once and replayed (the loop is launch-bound on small graphs).
 // Then W^2 = 4t sum_i vol_i (a_i ln u_i + b_i ln v_i) from the potentials, in FP64.
+//
+// Persistent form (default where the graph carries the persistent loop's gather-cache tables):
+// the whole fixed-count loop in one cooperative launch over that partition, one 1024-thread block
+// per SM, like the FP32 loop.  Each block keeps its slice of P and the distinct-column list in
+// shared memory and its rows' recurrence entries (T_k, T_{k-1}, y, the half-step input) in
+// registers; every order it stages its distinct neighbour entries into a shared-memory cache and
+// sums each row from there in the extended-range arithmetic above (one thread per row, the row's
+// entries in the sliced-ELL order).  Entries other blocks need are exchanged as 8-byte words
+// (FP32 mantissa whose last bit carries the stage parity, int32 exponent) in three rotating
+// slots; a reader re-reads a word until its parity is the wanted one (bounded wait, then
+// GS_FLAG_TIMEOUT).  The owner keeps the exact mantissa, so the exchanged entries differ from the
+// per-order kernels' by at most one unit in the last place.
 #include <math.h>
 
 #include <vector>
 
+#include "cache_slices.cuh"
 #include "gs_internal.cuh"
 
 namespace {
@@ -231,6 +244,273 @@ __global__ void __launch_bounds__(kRedThreads) xr_distance(int64_t n, const floa
     dist[1] = W2 >= 0.0 ? sqrt(W2) : NAN;
 }
 
+// ------------------------------------------------------------------------- persistent loop
+constexpr int kLoopThreads = 1024;
+constexpr long long kLoopBudget = 4000000000ll;  // clock cycles a wait may take (~2 s)
+
+struct XrLoopArgs {
+    int n;
+    const int* sptr;  // sliced ELL of P (locality order) and the gather-cache tables
+    const float* sval;
+    const uint16_t* xc_lidx;
+    const int* xc_ucol;
+    const int* xc_ucnt;
+    const int* xc_rows;
+    int xc_max_e, xc_max_u;
+    const int* perm;    // filter position -> caller's node (null: identity)
+    const float* a;     // caller order
+    const float* b;
+    const float* vol;
+    double* log_u;      // caller order
+    double* log_v;
+    const float* cm;    // [K + 1] coefficient mantissas / exponents
+    const int* ce;
+    int K, iters;
+    unsigned long long* words;  // [3][n] exchange words
+    int* flags;
+};
+
+__device__ __forceinline__ unsigned long long xr_pack(Xr v, unsigned parity)
+{
+    return ((unsigned long long)(unsigned)v.e << 32) | (unsigned long long)((__float_as_uint(v.m) & ~1u) | parity);
+}
+__device__ __forceinline__ Xr xr_unpack(unsigned long long w)
+{
+    const float m = __uint_as_float((unsigned)w & ~1u);
+    return m == 0.f ? Xr{0.f, kZeroExp} : Xr{m, (int)(w >> 32)};
+}
+__device__ __forceinline__ unsigned long long xr_ld(const unsigned long long* a)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void xr_st(unsigned long long* a, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;\n" ::"l"(a), "l"(v) : "memory");
+}
+
+// Algorithm 1's division in the log domain for one row: ln u = ln a - ln y (FP64); returns the
+// next half-step's input vol * u in the extended form.
+__device__ __forceinline__ Xr xr_divide(float a, Xr y, double lvol, double* logout, int* flags)
+{
+    double lu;
+    if (a == 0.f) {
+        lu = -INFINITY;
+    } else if (y.m > 0.f) {
+        lu = log((double)a) - (log((double)y.m) + (double)y.e * kLn2);
+    } else {
+        lu = NAN;
+        atomicOr(flags, GS_FLAG_NONFINITE);
+    }
+    *logout = lu;
+    return xr_from_log(lu + lvol);
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(kLoopThreads) xr_loop(const XrLoopArgs p)
+{
+    __shared__ int s_ok;
+    __shared__ __align__(8) unsigned long long s_mbar;
+    extern __shared__ __align__(128) unsigned char x_smem[];
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    const int r0 = __ldg(p.xc_rows + blockIdx.x), r1 = __ldg(p.xc_rows + blockIdx.x + 1);
+    const int emax = (p.xc_max_e + 31) / 32 * 32, umax = (p.xc_max_u + 31) / 32 * 32;
+    float* sval_s = reinterpret_cast<float*>(x_smem);
+    uint16_t* lidx_s = reinterpret_cast<uint16_t*>(x_smem + (size_t)emax * 4);
+    int* ucol_s = reinterpret_cast<int*>(x_smem + (size_t)emax * 6);
+    Xr* xc = reinterpret_cast<Xr*>(x_smem + (size_t)emax * 6 + (size_t)umax * 4);
+    int e0 = 0, ucnt = 0;
+    bool timed_out = false;
+    if (!gs_load_cache_tables(p.sptr, p.sval, p.xc_lidx, p.xc_ucol, p.xc_ucnt, (int)blockIdx.x, r0, r1, kLoopBudget,
+                              sval_s, lidx_s, ucol_s, &e0, &ucnt, &s_mbar, &timed_out))
+        s_ok = 0;
+    if (timed_out) atomicOr(p.flags, GS_FLAG_TIMEOUT);
+    __syncthreads();
+    if (!s_ok || r0 >= r1) return;
+    const size_t n = (size_t)p.n;
+
+    int off[RPT], width[RPT], node[RPT];
+    float av[RPT], bv[RPT];
+    double lvol[RPT];
+    Xr x0[RPT], xk[RPT], xkm1[RPT], y[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int row = r0 + (int)threadIdx.x + j * kLoopThreads;
+        off[j] = width[j] = node[j] = 0;
+        av[j] = bv[j] = 0.f;
+        lvol[j] = 0.0;
+        x0[j] = xk[j] = xkm1[j] = y[j] = Xr{0.f, kZeroExp};
+        if (row < r1) {
+            const int sl = row / 32;
+            const int beg = __ldg(p.sptr + sl);
+            width[j] = (__ldg(p.sptr + sl + 1) - beg) / 32;
+            off[j] = beg - e0 + row % 32;
+            node[j] = p.perm ? __ldg(p.perm + row) : row;
+            av[j] = __ldg(p.a + node[j]);
+            bv[j] = __ldg(p.b + node[j]);
+            lvol[j] = p.vol ? log((double)__ldg(p.vol + node[j])) : 0.0;
+            x0[j] = xr_from_log(lvol[j]);  // vol * (v = 1)
+            xr_st(p.words + row, xr_pack(x0[j], 0u));  // stage 0 in slot 0
+        }
+    }
+    unsigned stage = 0;
+    int rslot = 0, wslot = 1;
+    const int K = p.K;
+    for (int it = 0; it < p.iters; ++it) {
+        for (int h = 0; h < 2; ++h) {
+            for (int k = 0; k < K; ++k) {
+                ++stage;
+                const unsigned long long* src = p.words + (size_t)rslot * n;
+                unsigned long long* dst = p.words + (size_t)wslot * n;
+                const unsigned want = (stage - 1u) & 1u;
+                for (int i0 = threadIdx.x; i0 < ucnt; i0 += 8 * kLoopThreads) {
+                    unsigned long long w[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + u * kLoopThreads;
+                        w[u] = i < ucnt ? xr_ld(src + ucol_s[i]) : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + u * kLoopThreads;
+                        if (i >= ucnt) break;
+                        if (((unsigned)w[u] & 1u) != want) {
+                            const long long t0 = clock64();
+                            do {
+                                w[u] = xr_ld(src + ucol_s[i]);
+                                if (clock64() - t0 > kLoopBudget) {
+                                    atomicOr(p.flags, GS_FLAG_TIMEOUT);
+                                    s_ok = 0;
+                                    break;
+                                }
+                            } while (((unsigned)w[u] & 1u) != want);
+                        }
+                        xc[i] = xr_unpack(w[u]);
+                    }
+                }
+                __syncthreads();
+                if (!s_ok) return;
+                const float twice = k == 0 ? 1.f : 2.f;
+                const float cm = p.cm[k + 1];
+                const int ce = p.ce[k + 1];
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const int row = r0 + (int)threadIdx.x + j * kLoopThreads;
+                    if (row >= r1) continue;
+                    // the row's sum s 2^E over its stored entries (padding entries have weight 0)
+                    float s = 0.f;
+                    int E = kZeroExp;
+                    const float* vp = sval_s + off[j];
+                    const uint16_t* lp = lidx_s + off[j];
+                    for (int q = 0; q < width[j]; ++q) {
+                        const float v = vp[q * 32];
+                        if (v == 0.f) continue;
+                        const Xr x = xc[lp[q * 32]];
+                        if (x.m != 0.f) {
+                            xr_raise(s, E, x.e);
+                            s = fmaf(twice * v, scale_pow2(x.m, x.e - E), s);
+                        }
+                    }
+                    if (k > 0 && xkm1[j].m != 0.f) {  // T_{k+1} = 2 P T_k - T_{k-1}
+                        xr_raise(s, E, xkm1[j].e);
+                        s -= scale_pow2(xkm1[j].m, xkm1[j].e - E);
+                    }
+                    const Xr xn = xr_normalise(s, E);
+                    if (k == 0) {  // y = c0 x0
+                        y[j] = Xr{0.f, kZeroExp};
+                        if (x0[j].m != 0.f && p.cm[0] != 0.f) {
+                            int ee;
+                            const float m = frexpf(p.cm[0] * x0[j].m, &ee);
+                            y[j] = Xr{m, p.ce[0] + x0[j].e + ee};
+                        }
+                    }
+                    if (xn.m != 0.f && cm != 0.f) y[j] = xr_add(y[j], cm * xn.m, ce + xn.e);
+                    Xr pub;
+                    if (k < K - 1) {
+                        xkm1[j] = k == 0 ? x0[j] : xk[j];
+                        xk[j] = xn;
+                        pub = xn;
+                    } else {
+                        x0[j] = xr_divide(h == 0 ? av[j] : bv[j], y[j], lvol[j],
+                                          (h == 0 ? p.log_u : p.log_v) + node[j], p.flags);
+                        xk[j] = x0[j];
+                        pub = x0[j];
+                    }
+                    xr_st(dst + row, xr_pack(pub, stage & 1u));
+                }
+                __syncthreads();  // xc is refilled by the next order
+                rslot = wslot;
+                wslot = wslot == 2 ? 0 : wslot + 1;
+            }
+        }
+    }
+}
+
+// The whole loop as one cooperative launch; GS_ERR_UNSUPPORTED (nothing enqueued) when the
+// graph has no gather-cache partition of one block per SM, its tables do not fit in shared
+// memory, or the device cannot co-schedule the grid.
+gs_status xr_loop_launch(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b, const float* vol,
+                         const float* cmd, const int* ced, int K, int iters, double* log_u, double* log_v,
+                         unsigned long long* words)
+{
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    if (!coop || !g->xc_ok || !g->sptr || ctx->num_sms < 1 || g->xc_blocks != ctx->num_sms || g->n >= (1ll << 31))
+        return GS_ERR_UNSUPPORTED;
+    const int rpt = (g->xc_rpb + kLoopThreads - 1) / kLoopThreads;
+    const size_t emax = (size_t)(g->xc_max_e + 31) / 32 * 32, umax = (size_t)(g->xc_max_u + 31) / 32 * 32;
+    const size_t smem = emax * 6 + umax * 12;
+    if (rpt < 1 || rpt > 2 || smem > 200 * 1024) return GS_ERR_UNSUPPORTED;
+    void (*kern)(XrLoopArgs) = rpt == 1 ? xr_loop<1> : xr_loop<2>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_UNSUPPORTED;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return GS_ERR_UNSUPPORTED;
+    }
+    XrLoopArgs p;
+    p.n = (int)g->n;
+    p.sptr = g->sptr;
+    p.sval = g->sval;
+    p.xc_lidx = g->xc_lidx;
+    p.xc_ucol = g->xc_ucol;
+    p.xc_ucnt = g->xc_ucnt;
+    p.xc_rows = g->xc_rows;
+    p.xc_max_e = g->xc_max_e;
+    p.xc_max_u = g->xc_max_u;
+    p.perm = g->perm;
+    p.a = a;
+    p.b = b;
+    p.vol = vol;
+    p.log_u = log_u;
+    p.log_v = log_v;
+    p.cm = cmd;
+    p.ce = ced;
+    p.K = K;
+    p.iters = iters;
+    p.words = words;
+    p.flags = ctx->flags;
+    // slot k must not start with stage k's parity: slots 0 and 2 odd, slot 1 even
+    const size_t bytes = sizeof(unsigned long long) * (size_t)g->n;
+    cudaMemsetAsync(words, 0x01, bytes, ctx->stream);
+    cudaMemsetAsync(words + g->n, 0x00, bytes, ctx->stream);
+    cudaMemsetAsync(words + 2 * g->n, 0x01, bytes, ctx->stream);
+    void* params[] = {&p};
+    const cudaError_t e = cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)g->xc_blocks), dim3(kLoopThreads),
+                                                      params, smem, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_UNSUPPORTED;
+    }
+    gs_count(ctx, 1);
+    return GS_OK;
+}
+
 // Runs body() once under stream capture on the context's private capture stream (ctx->stream
 // points there meanwhile, and launches are not counted) and instantiates the graph.
 template <class F>
@@ -319,6 +599,29 @@ gs_status gs_sinkhorn_log_impl(gs_ctx* ctx, const gs_graph* g, const float* a, c
         return gs_cuda_check(ctx, cudaGetLastError(), "log-domain Sinkhorn order");
     };
     cudaStream_t s = ctx->stream;
+    if (ctx->loop_mode != 1 && reordered) {
+        // the whole loop in one persistent launch (GS_OPT_LOOP 1 keeps the per-order launches)
+        WsPlan lp;
+        const size_t icm = lp.add(sizeof(float) * (size_t)(K + 1)), ice = lp.add(sizeof(int) * (size_t)(K + 1)),
+                     iw = lp.add(sizeof(unsigned long long) * 3 * (size_t)n);
+        if ((st = gs_ws_ensure(ctx, plan.total + lp.total + 256)) != GS_OK) return st;
+        for (int i = 0; i < 6; ++i) X[i] = ws_at<Xr>(ctx, plan, ix[i]);
+        char* base = static_cast<char*>(ctx->ws) + ((plan.total + 255) & ~(size_t)255);
+        float* cmd = reinterpret_cast<float*>(base + lp.offs[icm]);
+        int* ced = reinterpret_cast<int*>(base + lp.offs[ice]);
+        unsigned long long* words = reinterpret_cast<unsigned long long*>(base + lp.offs[iw]);
+        cudaMemcpyAsync(cmd, cm.data(), sizeof(float) * (size_t)(K + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(ced, ce.data(), sizeof(int) * (size_t)(K + 1), cudaMemcpyHostToDevice, s);
+        st = xr_loop_launch(ctx, g, a, b, vol, cmd, ced, K, iters, log_u, log_v, words);
+        if (st == GS_OK) {
+            if (dist) {
+                xr_distance<<<1, kRedThreads, 0, s>>>(n, a, b, vol, log_u, log_v, t, dist, ctx->flags);
+                gs_count(ctx, 1);
+            }
+            return gs_cuda_check(ctx, cudaGetLastError(), "log-domain Sinkhorn");
+        }
+        if (st != GS_ERR_UNSUPPORTED) return st;
+    }
     xr_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, reordered ? g->perm : nullptr, vol, X[0]);
     if (iters == 1) {
         if ((st = iteration()) != GS_OK) return st;

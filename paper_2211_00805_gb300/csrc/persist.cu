@@ -17,6 +17,7 @@
 
 #include <algorithm>
 
+#include "cache_slices.cuh"
 #include "gs_internal.cuh"
 #include "sell_row.cuh"
 
@@ -264,15 +265,9 @@ __device__ __forceinline__ void rows_any(const PersistArgs& p, int r0, int r1, i
     else rows_order<G>(p, r0, r1, mode, ck, c0, cur, prev, next, num, out, xnext);
 }
 
-// Bulk (TMA) copy of `bytes` from global to this CTA's shared memory, completing on `mbar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* mbar)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
-        "l"(src), "r"(bytes), "r"(m)
-        : "memory");
+    gs_bulk_g2s(dst, src, bytes, mbar);
 }
 
 // Mode 2: values, local column indices and the distinct-column list of this block into shared
@@ -281,45 +276,11 @@ __device__ bool load_cached_slices(const PersistArgs& p, int r0, int r1, float* 
                                    uint16_t* lidx_s, int* ucol_s, int* e0_out, int* ucnt_out,
                                    unsigned long long* mbar)
 {
-    const int s0 = r0 / GS_SELL_C;
-    const int s1 = (r1 + GS_SELL_C - 1) / GS_SELL_C;
-    const int e0 = __ldg(p.sptr + s0);
-    const int e1 = (r1 > r0) ? __ldg(p.sptr + s1) : e0;
-    const int uc = (r1 > r0) ? __ldg(p.xc_ucnt + blockIdx.x) : 0;
-    *e0_out = e0;
-    *ucnt_out = uc;
-    const unsigned E = (unsigned)(e1 - e0);
-    if (E == 0) return true;
-    const unsigned bv = E * 4u, bl = E * 2u;            // E is a multiple of 32: both multiples of 16
-    const unsigned bu = ((unsigned)uc * 4u + 15u) & ~15u;  // <= E * 4 (the list lives in [e0, e1))
-    const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(m) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(m), "r"(bv + bl + bu)
-                     : "memory");
-        bulk_g2s(sval_s, p.sval + e0, bv, mbar);
-        bulk_g2s(lidx_s, p.xc_lidx + e0, bl, mbar);
-        if (bu) bulk_g2s(ucol_s, p.xc_ucol + e0, bu, mbar);
-    }
-    const long long t0 = clock64();
-    unsigned done = 0;
-    while (!done) {
-        asm volatile(
-            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\n"
-            " selp.u32 %0, 1, 0, P;\n}\n"
-            : "=r"(done)
-            : "r"(m)
-            : "memory");
-        if (!done && clock64() - t0 > p.budget) {
-            atomicOr(p.flags, GS_FLAG_TIMEOUT);
-            return false;
-        }
-    }
-    return true;
+    bool timed_out = false;
+    const bool ok = gs_load_cache_tables(p.sptr, p.sval, p.xc_lidx, p.xc_ucol, p.xc_ucnt, (int)blockIdx.x, r0, r1,
+                                         p.budget, sval_s, lidx_s, ucol_s, e0_out, ucnt_out, mbar, &timed_out);
+    if (timed_out) atomicOr(p.flags, GS_FLAG_TIMEOUT);
+    return ok;
 }
 
 // Load this block's sliced-ELL entries into shared memory with two bulk copies tracked by one

@@ -31,6 +31,15 @@ def ctx(gs):
     return gs.Context()
 
 
+@pytest.fixture(params=[2, 1], ids=["persistent", "per-order"])
+def mode(request, gs, ctx):
+    # GS_OPT_LOOP 2: the whole loop as one persistent launch where the graph allows it;
+    # 1: one launch per Chebyshev order, replayed as a CUDA graph
+    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, request.param)
+    yield request.param
+    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
+
+
 @pytest.fixture(scope="module")
 def sphere(gs, ctx):
     p = W.sphere_pair()
@@ -60,7 +69,7 @@ def _check(gs, ctx, g, Ls, a, b, t, K, iters, vol=None):
     return lu, lv, d, r
 
 
-def test_log_sinkhorn_small_t_where_fp32_overflows(gs, ctx, sphere):
+def test_log_sinkhorn_small_t_where_fp32_overflows(gs, ctx, mode, sphere):
     # the 2,000-point sphere pair at t = 1, K = 20, 200 iterations: the scalings reach e^{+-170}
     p, g, Ls = sphere
     lu, lv, d, r = _check(gs, ctx, g, Ls, p.a, p.b, 1.0, 20, 200)
@@ -72,7 +81,7 @@ def test_log_sinkhorn_small_t_where_fp32_overflows(gs, ctx, sphere):
     assert e.value.status == gs.GS_ERR_NONFINITE
 
 
-def test_log_sinkhorn_agrees_with_the_fp32_loop_where_both_fit(gs, ctx, sphere):
+def test_log_sinkhorn_agrees_with_the_fp32_loop_where_both_fit(gs, ctx, mode, sphere):
     p, g, Ls = sphere
     lu, lv, d, r = _check(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 200)
     u, v, dist, _ = gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 200)
@@ -85,7 +94,7 @@ def test_log_sinkhorn_agrees_with_the_fp32_loop_where_both_fit(gs, ctx, sphere):
     assert d[0] == pytest.approx(to_np(dist)[0], rel=1e-4)
 
 
-def test_log_sinkhorn_vertex_weights_zero_mass_odd_K(gs, ctx, sphere):
+def test_log_sinkhorn_vertex_weights_zero_mass_odd_K(gs, ctx, mode, sphere):
     p, g, Ls = sphere
     vol = np.random.default_rng(1).uniform(0.5, 1.5, len(p.a)).astype(np.float32)
     a = np.where(p.X[:, 2] > -0.2, p.a, 0).astype(np.float32)
@@ -95,7 +104,7 @@ def test_log_sinkhorn_vertex_weights_zero_mass_odd_K(gs, ctx, sphere):
 
 
 @pytest.mark.parametrize("t,K", [(2.0, 1), (3.0, 2), (0.5, 3), (0.5, 12)])
-def test_log_sinkhorn_low_degrees(gs, ctx, sphere, t, K):
+def test_log_sinkhorn_low_degrees(gs, ctx, mode, sphere, t, K):
     # p_K reaches K hops only, so pole-to-pole marginals have no plan for K below the graph's
     # diameter (the FP64 oracle's scalings diverge too); b = a times a random +-30% factor needs
     # only local moves
@@ -105,7 +114,7 @@ def test_log_sinkhorn_low_degrees(gs, ctx, sphere, t, K):
     _check(gs, ctx, g, Ls, p.a, b, t, K, 60)
 
 
-def test_log_sinkhorn_tiny_graph_one_block_plus_a_row(gs, ctx):
+def test_log_sinkhorn_tiny_graph_one_block_plus_a_row(gs, ctx, mode):
     # 33 rows: one full block of 32 lane groups and a ragged tail of one row
     p = W.sphere_pair(n=33)
     idx, dist = oracle.knn(p.X.astype(np.float64), 6)
@@ -116,7 +125,7 @@ def test_log_sinkhorn_tiny_graph_one_block_plus_a_row(gs, ctx):
     _check(gs, ctx, g, Ls, p.a, p.b, 1.0, 20, 50)
 
 
-def test_log_sinkhorn_repeats_bit_for_bit(gs, ctx, sphere):
+def test_log_sinkhorn_repeats_bit_for_bit(gs, ctx, mode, sphere):
     p, g, Ls = sphere
     a, b = to_dev(p.a), to_dev(p.b)
     r1 = [to_np(x) for x in gs.gs_sinkhorn_log(ctx, g, a, b, 1.0, 20, 40)]
@@ -124,6 +133,25 @@ def test_log_sinkhorn_repeats_bit_for_bit(gs, ctx, sphere):
     gs.gs_sync(ctx)
     for x, y in zip(r1, r2):
         assert np.array_equal(x, y)
+
+
+def test_log_sinkhorn_persistent_and_per_order_forms_agree(gs, ctx, sphere):
+    # the persistent loop sums each row by one thread in the sliced-ELL entry order and exchanges
+    # mantissas with a parity bit in their last place; the per-order launches sum by four lanes:
+    # the same iteration to FP32 rounding
+    p, g, Ls = sphere
+    a, b = to_dev(p.a), to_dev(p.b)
+    out = {}
+    for m in (2, 1):
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP, m)
+        out[m] = [to_np(x) for x in gs.gs_sinkhorn_log(ctx, g, a, b, 1.0, 20, 100)]
+    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
+    gs.gs_sync(ctx)
+    for x, y in zip(out[2][:2], out[1][:2]):
+        fin = np.isfinite(y)
+        assert np.array_equal(np.isfinite(x), fin)
+        assert np.abs(x[fin] - y[fin]).max() < 2e-4
+    assert out[2][2][0] == pytest.approx(out[1][2][0], rel=1e-6)
 
 
 def test_log_sinkhorn_rejects_bad_arguments(gs, ctx, sphere):
