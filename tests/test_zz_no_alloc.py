@@ -132,3 +132,18 @@ def test_noalloc_rejects_oversized_blocks():
     with pytest.raises(gs.GeosinkError) as e:
         gs.gs_heat_apply_noalloc(rowptr32, col, pval, 1.0, 5, V)
     assert e.value.status == gs.GS_ERR_UNSUPPORTED
+
+
+def test_noalloc_wide_blocks_need_aligned_blocks():
+    # B > 256 columns are read as float4 only: V and Y must start on 16-byte boundaries
+    from paper_2211_00805_gb300 import binding as gs
+    n, B = 1000, 260
+    Ls, (rp, col, pval) = _oracle_operator(n, 3, 8, seed=9)
+    V = np.random.default_rng(4).random((n, B)).astype(np.float32)
+    Y = to_np(gs.gs_heat_apply_noalloc(rp, col, pval, 2.0, 15, to_dev(V)))
+    ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(2.0, 15), V.astype(np.float64))
+    _close(Y, ref, "B = 260")
+    Yoff = torch.empty(n * B + 1, dtype=torch.float32, device="cuda")[1:].view(n, B)
+    with pytest.raises(gs.GeosinkError) as e:
+        gs.gs_heat_apply_noalloc(rp, col, pval, 2.0, 15, to_dev(V), out=Yoff)
+    assert e.value.status == gs.GS_ERR_UNSUPPORTED
