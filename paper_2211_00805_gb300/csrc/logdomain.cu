@@ -30,7 +30,8 @@
 // shared memory and its rows' recurrence entries (T_k, T_{k-1}, y, the half-step input) in
 // registers; every order it stages its distinct neighbour entries into a shared-memory cache and
 // sums each row from there in the extended-range arithmetic above (one thread per row, the row's
-// entries in the sliced-ELL order).  Entries other blocks need are exchanged as 8-byte words
+// entries in the sliced-ELL order, aligned to the row's largest exponent found in a first pass).
+// Entries other blocks need are exchanged as 8-byte words
 // (FP32 mantissa whose last bit carries the stage parity, int32 exponent) in three rotating
 // slots; a reader re-reads a word until its parity is the wanted one (bounded wait, then
 // GS_FLAG_TIMEOUT).  The owner keeps the exact mantissa, so the exchanged entries differ from the
@@ -399,24 +400,23 @@ __global__ void __launch_bounds__(kLoopThreads) xr_loop(const XrLoopArgs p)
                 for (int j = 0; j < RPT; ++j) {
                     const int row = r0 + (int)threadIdx.x + j * kLoopThreads;
                     if (row >= r1) continue;
-                    // the row's sum s 2^E over its stored entries (padding entries have weight 0)
-                    float s = 0.f;
-                    int E = kZeroExp;
+                    // the row's sum s 2^E over its stored entries (padding entries have weight 0):
+                    // first the largest exponent E of the row's terms, then the terms aligned to it
                     const float* vp = sval_s + off[j];
                     const uint16_t* lp = lidx_s + off[j];
+                    int E = (k > 0 && xkm1[j].m != 0.f) ? xkm1[j].e : kZeroExp;
+                    for (int q = 0; q < width[j]; ++q) {
+                        const Xr x = xc[lp[q * 32]];
+                        if (vp[q * 32] != 0.f && x.m != 0.f) E = max(E, x.e);
+                    }
+                    float s = 0.f;
                     for (int q = 0; q < width[j]; ++q) {
                         const float v = vp[q * 32];
-                        if (v == 0.f) continue;
                         const Xr x = xc[lp[q * 32]];
-                        if (x.m != 0.f) {
-                            xr_raise(s, E, x.e);
-                            s = fmaf(twice * v, scale_pow2(x.m, x.e - E), s);
-                        }
+                        if (v != 0.f && x.m != 0.f) s = fmaf(twice * v, scale_pow2(x.m, x.e - E), s);
                     }
-                    if (k > 0 && xkm1[j].m != 0.f) {  // T_{k+1} = 2 P T_k - T_{k-1}
-                        xr_raise(s, E, xkm1[j].e);
+                    if (k > 0 && xkm1[j].m != 0.f)  // T_{k+1} = 2 P T_k - T_{k-1}
                         s -= scale_pow2(xkm1[j].m, xkm1[j].e - E);
-                    }
                     const Xr xn = xr_normalise(s, E);
                     if (k == 0) {  // y = c0 x0
                         y[j] = Xr{0.f, kZeroExp};
