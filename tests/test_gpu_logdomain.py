@@ -154,6 +154,33 @@ def test_log_sinkhorn_persistent_and_per_order_forms_agree(gs, ctx, sphere):
     assert out[2][2][0] == pytest.approx(out[1][2][0], rel=1e-6)
 
 
+def test_log_sinkhorn_two_rows_per_thread_at_scale(gs, ctx):
+    # 160k points: more rows per partition block than threads (two rows per thread in the
+    # persistent form); against the per-order form and the FP32 loop (t = 5, where both fit)
+    # (a broad bump and a local tilt of it: K = 30 hops cover the transport on this large sphere)
+    p = W.sphere_pair(n=160_000, t=5.0, K=30)
+    g = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    assert gs.gs_graph_layout(g)["rows_per_block"] > 1024
+    a0 = W.vmf_bump(p.X, np.array([0.0, 0.0, 1.0]), 1.0)
+    b0 = a0 * (1.0 + 0.3 * np.tanh(p.X[:, 0]))
+    a, b = to_dev(a0), to_dev((b0 / b0.sum()).astype(np.float32))
+    out = {}
+    for m in (2, 1):
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP, m)
+        out[m] = [to_np(x) for x in gs.gs_sinkhorn_log(ctx, g, a, b, 5.0, 30, 30)]
+    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
+    u, v, dist, _ = gs.gs_sinkhorn(ctx, g, a, b, 5.0, 30, 30)
+    gs.gs_sync(ctx)
+    for x, y in zip(out[2][:2], out[1][:2]):
+        fin = np.isfinite(y)
+        assert np.array_equal(np.isfinite(x), fin)
+        assert np.abs(x[fin] - y[fin]).max() < 2e-4
+    lu, uu = out[2][0], to_np(u).astype(np.float64)
+    msk = (uu > 0) & (np.abs(lu) < 80)
+    np.testing.assert_allclose(np.exp(lu[msk]), uu[msk], rtol=1e-3)
+    assert out[2][2][0] == pytest.approx(float(to_np(dist)[0]), rel=1e-4)
+
+
 def test_log_sinkhorn_rejects_bad_arguments(gs, ctx, sphere):
     p, g, Ls = sphere
     n = len(p.a)
