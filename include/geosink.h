@@ -87,10 +87,11 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * per-order launches; 2 (default) the mode gs_autotune measured faster on the graph, else 0.
  * All compute the same thing.  Errors: GS_ERR_ARG. */
 /* GS_OPT_BARRIER_SELFTEST = 1 makes the next persistent launch wait at its first grid barrier for
- * one block more than the grid has (with neighbour-flag sync: for a stage no block will publish,
- * including its own): every block's bounded wait runs out (~10 ms), the launch ends
- * and gs_sync reports GS_ERR_TIMEOUT, leaving the context usable.  It exercises failure handling
- * without faulting the GPU; the option resets itself after that launch. */
+ * one block more than the grid has (with neighbour-flag sync, tagged values, or the persistent
+ * log-domain loop of gs_sinkhorn_log: for a stage no block will publish, including its own):
+ * every block's bounded wait runs out (~10 ms), the launch ends and gs_sync reports
+ * GS_ERR_TIMEOUT, leaving the context usable.  It exercises failure handling without faulting the
+ * GPU; the option resets itself after that launch. */
 /* GS_OPT_B1_KERNEL / GS_OPT_BLK_KERNEL pick the Chebyshev order kernel for one column / several
  * columns: 0 automatic, 1 sliced ELL (one column), 2 lane-split CSR, 3 chunked CSR with
  * asynchronous gathers into shared memory, 4 staged neighbour lists (several columns), 5 the

@@ -248,6 +248,9 @@ __global__ void __launch_bounds__(kRedThreads) xr_distance(int64_t n, const floa
 // ------------------------------------------------------------------------- persistent loop
 constexpr int kLoopThreads = 1024;
 constexpr long long kLoopBudget = 4000000000ll;  // clock cycles a wait may take (~2 s)
+// Self-test (GS_OPT_BARRIER_SELFTEST): every staging wait looks for a parity no word carries, so
+// each runs out after this much shorter budget and the launch ends with GS_FLAG_TIMEOUT.
+constexpr long long kLoopSelfTestBudget = 20000000ll;
 
 struct XrLoopArgs {
     int n;
@@ -269,6 +272,8 @@ struct XrLoopArgs {
     int K, iters;
     unsigned long long* words;  // [3][n] exchange words
     int* flags;
+    long long budget;   // clock cycles a wait may take
+    int selftest;       // wait for a parity no word carries (bounded-wait self-test)
 };
 
 __device__ __forceinline__ unsigned long long xr_pack(Xr v, unsigned parity)
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(kLoopThreads) xr_loop(const XrLoopArgs p)
                 ++stage;
                 const unsigned long long* src = p.words + (size_t)rslot * n;
                 unsigned long long* dst = p.words + (size_t)wslot * n;
-                const unsigned want = (stage - 1u) & 1u;
+                const unsigned want = p.selftest ? 2u : ((stage - 1u) & 1u);
                 for (int i0 = threadIdx.x; i0 < ucnt; i0 += 8 * kLoopThreads) {
                     unsigned long long w[8];
 #pragma unroll
@@ -381,7 +386,7 @@ __global__ void __launch_bounds__(kLoopThreads) xr_loop(const XrLoopArgs p)
                             const long long t0 = clock64();
                             do {
                                 w[u] = xr_ld(src + ucol_s[i]);
-                                if (clock64() - t0 > kLoopBudget) {
+                                if (clock64() - t0 > p.budget) {
                                     atomicOr(p.flags, GS_FLAG_TIMEOUT);
                                     s_ok = 0;
                                     break;
@@ -495,6 +500,8 @@ gs_status xr_loop_launch(gs_ctx* ctx, const gs_graph* g, const float* a, const f
     p.iters = iters;
     p.words = words;
     p.flags = ctx->flags;
+    p.budget = ctx->barrier_selftest ? kLoopSelfTestBudget : kLoopBudget;
+    p.selftest = ctx->barrier_selftest;
     // slot k must not start with stage k's parity: slots 0 and 2 odd, slot 1 even
     const size_t bytes = sizeof(unsigned long long) * (size_t)g->n;
     cudaMemsetAsync(words, 0x01, bytes, ctx->stream);
@@ -507,6 +514,7 @@ gs_status xr_loop_launch(gs_ctx* ctx, const gs_graph* g, const float* a, const f
         cudaGetLastError();
         return GS_ERR_UNSUPPORTED;
     }
+    ctx->barrier_selftest = 0;  // the self-test applies to one launch
     gs_count(ctx, 1);
     return GS_OK;
 }

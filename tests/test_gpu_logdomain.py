@@ -181,6 +181,19 @@ def test_log_sinkhorn_two_rows_per_thread_at_scale(gs, ctx):
     assert out[2][2][0] == pytest.approx(float(to_np(dist)[0]), rel=1e-4)
 
 
+def test_log_sinkhorn_bounded_wait_timeout_is_reported_and_context_survives(gs, ctx, sphere):
+    # the self-test makes every staging wait of the persistent log-domain loop look for a parity no
+    # exchanged word carries: the waits run out, gs_sync reports the timeout, the next call works
+    p, g, Ls = sphere
+    gs.gs_set_option(ctx, gs.GS_OPT_BARRIER_SELFTEST, 1)
+    gs.gs_sinkhorn_log(ctx, g, to_dev(p.a), to_dev(p.b), 5.0, 30, 5)
+    with pytest.raises(gs.GeosinkError) as e:
+        gs.gs_sync(ctx)
+    assert e.value.status == gs.GS_ERR_TIMEOUT
+    assert gs.gs_get_option(ctx, gs.GS_OPT_BARRIER_SELFTEST) == 0
+    _check(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 40)
+
+
 def test_log_sinkhorn_rejects_bad_arguments(gs, ctx, sphere):
     p, g, Ls = sphere
     n = len(p.a)
