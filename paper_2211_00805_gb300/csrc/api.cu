@@ -469,7 +469,7 @@ extern "C" gs_status gs_sinkhorn(gs_ctx* ctx, const gs_graph* g, const float* a,
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
     if (!(eps == eps)) return gs_fail(ctx, GS_ERR_ARG, "eps is NaN");
     const gs_marginals mg{a, b, vol, g->n};
-    if ((st = gs_check_marginals(ctx, &mg, 1, nullptr)) != GS_OK) return st;
+    if ((st = gs_check_marginals(ctx, mg)) != GS_OK) return st;
     return gs_sinkhorn_impl(ctx, g, a, b, vol, t, K, eps, iters, u, v, dist, iters_done);
 }
 
@@ -483,7 +483,7 @@ extern "C" gs_status gs_distance(gs_ctx* ctx, const gs_graph* g, const float* a,
     if (bad_ptr(a) || bad_ptr(b) || bad_ptr(dist)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
     const gs_marginals mg{a, b, vol, g->n};
-    if ((st = gs_check_marginals(ctx, &mg, 1, nullptr)) != GS_OK) return st;
+    if ((st = gs_check_marginals(ctx, mg)) != GS_OK) return st;
     // the scalings stay in the workspace
     return gs_sinkhorn_impl(ctx, g, a, b, vol, t, K, eps, iters, nullptr, nullptr, dist, nullptr);
 }
@@ -529,7 +529,7 @@ extern "C" gs_status gs_sinkhorn_log(gs_ctx* ctx, const gs_graph* g, const float
     if (log_u == log_v) return gs_fail(ctx, GS_ERR_ARG, "log_u and log_v must be distinct buffers");
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
     const gs_marginals mg{a, b, vol, g->n};
-    if ((st = gs_check_marginals(ctx, &mg, 1, nullptr)) != GS_OK) return st;
+    if ((st = gs_check_marginals(ctx, mg)) != GS_OK) return st;
     return gs_sinkhorn_log_impl(ctx, g, a, b, vol, t, K, iters, log_u, log_v, dist);
 }
 
@@ -581,7 +581,7 @@ extern "C" gs_status gs_sinkhorn_grad(gs_ctx* ctx, const gs_graph* g, const floa
         return gs_fail(ctx, GS_ERR_ARG, "null pointer");
     if (iters < 1 || checkpoint < 1) return gs_fail(ctx, GS_ERR_ARG, "iters and checkpoint must be >= 1");
     const gs_marginals mg{a, b, vol, g->n};
-    if ((st = gs_check_marginals(ctx, &mg, 1, nullptr)) != GS_OK) return st;
+    if ((st = gs_check_marginals(ctx, mg)) != GS_OK) return st;
     return gs_sinkhorn_grad_impl(ctx, g, a, b, vol, t, K, iters, checkpoint, dist, grad_a, grad_b);
 }
 

@@ -399,8 +399,8 @@ struct gs_marginals {
     const float* vol;   // null = unit weights
     int64_t n;
 };
-// count problems; probs_dev (device, count entries) is needed only for count > 1
-gs_status gs_check_marginals(gs_ctx* ctx, const gs_marginals* probs, int count, gs_marginals* probs_dev);
+// one problem (blocks over its entries, fixed-order final sum)
+gs_status gs_check_marginals(gs_ctx* ctx, const gs_marginals& m);
 gs_status gs_check_weights(gs_ctx* ctx, const double* alpha, int m);
 // the same checks over `count` descriptors already on the device (one block each)
 gs_status gs_check_marginals_dev(gs_ctx* ctx, const gs_marginals* probs_dev, int count);

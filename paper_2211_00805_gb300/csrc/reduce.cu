@@ -1,6 +1,7 @@
 // Distance reduction of Algorithm 1's return statement and Definition 4.1:
 //     W^2 = 4t sum_i vol_i (a_i ln u_i + b_i ln v_i),   W = sqrt(W^2),
-// accumulated in FP64 with a fixed two-pass tree (deterministic), 0 ln 0 := 0.
+// accumulated in FP64 with a fixed two-pass tree (deterministic), 0 ln 0 := 0; and the device-side
+// argument checks of the marginals and barycenter weights.
 #include <math.h>
 
 #include "gs_internal.cuh"
@@ -81,8 +82,9 @@ gs_status gs_distance_enqueue(gs_ctx* ctx, int64_t n, const float* a, const floa
 // ---------------------------------------------------------------------- argument checks
 // Algorithm 1 transports a onto b: a plan with marginals vol * a and vol * b exists only when both
 // are non-negative and carry the same mass, sum_i vol_i a_i = sum_i vol_i b_i (the vertex weights
-// multiply both marginals of the plan).  One block per problem sums both masses in FP64 and flags
-// a negative or non-finite entry, or masses further apart than rtol times the larger one.
+// multiply both marginals of the plan).  The masses are summed in FP64 (one problem over many
+// blocks, or many problems at one block each) and a negative or non-finite entry, or masses further
+// apart than rtol times the larger one, raise GS_FLAG_ARG.
 namespace {
 
 constexpr int kCheckThreads = 1024;
@@ -200,25 +202,15 @@ __global__ void __launch_bounds__(32) check_weights(const double* __restrict__ a
 
 }  // namespace
 
-gs_status gs_check_marginals(gs_ctx* ctx, const gs_marginals* probs, int count, gs_marginals* probs_dev)
+gs_status gs_check_marginals(gs_ctx* ctx, const gs_marginals& m)
 {
-    if (!ctx->check_args || count < 1) return GS_OK;
-    if (count == 1 || probs_dev == nullptr) {
-        for (int i = 0; i < count; ++i) {
-            int64_t blocks = (probs[i].n + kPartThreads - 1) / kPartThreads;
-            if (blocks > GS_CHECK_BLOCKS) blocks = GS_CHECK_BLOCKS;
-            if (blocks < 1) blocks = 1;
-            check_marginals_part<<<(unsigned)blocks, kPartThreads, 0, ctx->stream>>>(
-                probs[i], GS_MASS_RTOL, ctx->check_part, reinterpret_cast<unsigned*>(ctx->flags + 2), ctx->flags);
-        }
-        gs_count(ctx, count);
-    } else {
-        cudaMemcpyAsync(probs_dev, probs, sizeof(gs_marginals) * (size_t)count, cudaMemcpyHostToDevice,
-                        ctx->stream);
-        check_marginals_many<<<(unsigned)count, kCheckThreads, 0, ctx->stream>>>(probs_dev, GS_MASS_RTOL,
-                                                                                 ctx->flags);
-        gs_count(ctx, 1);
-    }
+    if (!ctx->check_args) return GS_OK;
+    int64_t blocks = (m.n + kPartThreads - 1) / kPartThreads;
+    if (blocks > GS_CHECK_BLOCKS) blocks = GS_CHECK_BLOCKS;
+    if (blocks < 1) blocks = 1;
+    check_marginals_part<<<(unsigned)blocks, kPartThreads, 0, ctx->stream>>>(
+        m, GS_MASS_RTOL, ctx->check_part, reinterpret_cast<unsigned*>(ctx->flags + 2), ctx->flags);
+    gs_count(ctx, 1);
     return gs_cuda_check(ctx, cudaGetLastError(), "marginal check");
 }
 
