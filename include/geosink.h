@@ -112,13 +112,13 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * global memory.  Each mode falls back to the next lower one when its tables do not fit in 200 KB
  * of shared memory.  Same arithmetic in every mode. */
 /* GS_OPT_PERSIST_SYNC: how the blocks of the persistent loop wait for one another between
- * Chebyshev orders when the gather-cache tables are in use (mode 2 above).  1 (default): each
- * block waits only for the blocks owning rows it reads (per-block ready counters) and keeps its own
- * rows' recurrence values in registers; 2: the same, with the readiness carried by the exchanged
- * values themselves (64-bit value + stage words in three rotating slots, no counters or fences);
- * 0: a barrier over the whole grid; 3 (default): the one gs_autotune measured fastest on the
- * graph (else on the context's last tuned graph, else 2).  Same arithmetic in all of them.  All
- * honour GS_OPT_BARRIER_SELFTEST. */
+ * Chebyshev orders when the gather-cache tables are in use (mode 2 above).  1: each block waits
+ * only for the blocks owning rows it reads (per-block ready counters) and keeps its own rows'
+ * recurrence values in registers; 2: the same, with the readiness carried by the exchanged values
+ * themselves (value + stage words in three rotating slots, see GS_OPT_TAG_WORD; no counters or
+ * fences); 0: a barrier over the whole grid; 3 (default): the one gs_autotune measured fastest on
+ * the graph (else on the context's last tuned graph, else 2).  Same arithmetic in all of them.
+ * All honour GS_OPT_BARRIER_SELFTEST. */
 /* GS_OPT_PERSIST_BLOCKS: blocks per SM of the gather-cache partition (1 = one 1024-thread block,
  * default; 2 = two 512-thread blocks, so one block's exchange overlaps the other's sums), for the
  * tagged-value and neighbour-flag forms.  Applies to graphs built after the call. */
@@ -335,19 +335,24 @@ gs_status gs_distance(gs_ctx *ctx, const gs_graph *g, const float *a, const floa
  * the row's largest exponent by exact powers of two), so no value of the loop over- or underflows.
  * Result: the scalings of gs_sinkhorn as logarithms, and
  *     dist[0] = W^2 = 4t sum_i vol_i (a_i ln u_i + b_i ln v_i),   dist[1] = W = sqrt(W^2)
- * in FP64 (0 ln 0 := 0).  Runs exactly `iters` iterations (no eps stop), 2 K launches each (one
- * iteration captured as a CUDA graph and replayed), in the graph's locality order; all arguments
- * are in the caller's node order.
+ * in FP64 (0 ln 0 := 0).  A fixed iteration count runs as one persistent launch (one launch per
+ * Chebyshev order replayed from a CUDA graph with GS_OPT_LOOP 1, or where the graph has no
+ * persistent partition); an eps stop runs one launch per order.  All arguments are in the
+ * caller's node order.
  *   a, b   : [n] non-negative marginals of equal mass (device FP32; checked as in gs_sinkhorn)
  *   vol    : [n] vertex weights or NULL
+ *   eps    : > 0 -> stop at the first iteration j, j a multiple of 10, whose marginal error
+ *            sum_i |u_i (p_K(vol * v))_i - a_i| is below eps (computed in FP64 from the
+ *            potentials; GS_ERR_NOT_CONVERGED at gs_sync if none); <= 0 -> exactly `iters`
  *   log_u, log_v : [n] double outputs (device), distinct buffers; -inf where a_i (b_i) = 0
  *   dist   : [2] double output (device), may be NULL
+ *   iters_done : [1] int32 output (device), may be NULL
  * A non-positive p_K(vol * u)_i where the marginal is positive (the truncated series can dip below
  * zero) gives NaN there and GS_ERR_NONFINITE at gs_sync.  Requires t > 0, 1 <= K <= 10000,
  * iters >= 1.  Errors: GS_ERR_ARG. */
 gs_status gs_sinkhorn_log(gs_ctx *ctx, const gs_graph *g, const float *a, const float *b,
-                          const float *vol, double t, int K, int iters, double *log_u, double *log_v,
-                          double *dist);
+                          const float *vol, double t, int K, double eps, int iters, double *log_u,
+                          double *log_v, double *dist, int32_t *iters_done);
 
 /* ---------------------------------------------------------------------------- barycenter --- */
 

@@ -52,7 +52,7 @@ SIGNATURES = {
     "gs_heat_apply_noalloc": [_I64, _I64, _P, _P, _P, _D, _I, _P, _I, _P, _P],
     "gs_sinkhorn": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P],
     "gs_distance": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P],
-    "gs_sinkhorn_log": [_P, _P, _P, _P, _P, _D, _I, _I, _P, _P, _P],
+    "gs_sinkhorn_log": [_P, _P, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P],
     "gs_barycenter": [_P, _P, _P, _I, _P, _P, _D, _I, _I, _P, _P],
     "gs_sinkhorn_grad": [_P, _P, _P, _P, _P, _D, _I, _I, _I, _P, _P, _P],
     "gs_barycenter_grad": [_P, _P, _P, _I, _P, _P, _D, _I, _I, _I, _P, _P, _P],
@@ -364,8 +364,10 @@ def gs_sinkhorn(ctx: Context, g: Graph, a: torch.Tensor, b: torch.Tensor, t: flo
 
 
 def gs_sinkhorn_log(ctx: Context, g: Graph, a: torch.Tensor, b: torch.Tensor, t: float, K: int,
-                    iters: int, vol: torch.Tensor | None = None, log_u=None, log_v=None, dist=None):
-    """Algorithm 1 with FP64 potentials; returns (ln u, ln v, dist[2] FP64 = (W^2, W)), device tensors."""
+                    iters: int, eps: float = 0.0, vol: torch.Tensor | None = None, log_u=None, log_v=None,
+                    dist=None, iters_done=None):
+    """Algorithm 1 with FP64 potentials; returns (ln u, ln v, dist[2] FP64 = (W^2, W),
+    iters_done[1] int32), device tensors."""
     n = g.n
     _dev(a, torch.float32, "a", (n,))
     _dev(b, torch.float32, "b", (n,))
@@ -377,9 +379,12 @@ def gs_sinkhorn_log(ctx: Context, g: Graph, a: torch.Tensor, b: torch.Tensor, t:
     log_v = (torch.empty(n, dtype=torch.float64, device=dev) if log_v is None
              else _dev(log_v, torch.float64, "log_v", (n,)))
     dist = torch.empty(2, dtype=torch.float64, device=dev) if dist is None else _dev(dist, torch.float64, "dist", (2,))
+    iters_done = (torch.empty(1, dtype=torch.int32, device=dev) if iters_done is None
+                  else _dev(iters_done, torch.int32, "iters_done", (1,)))
     _raise(ctx, _lib.gs_sinkhorn_log(ctx.handle, g.handle, _ptr(a), _ptr(b), _ptr(vol), float(t), int(K),
-                                     int(iters), _ptr(log_u), _ptr(log_v), _ptr(dist)))
-    return log_u, log_v, dist
+                                     float(eps), int(iters), _ptr(log_u), _ptr(log_v), _ptr(dist),
+                                     _ptr(iters_done)))
+    return log_u, log_v, dist, iters_done
 
 
 def gs_distance(ctx: Context, g: Graph, a: torch.Tensor, b: torch.Tensor, t: float, K: int,

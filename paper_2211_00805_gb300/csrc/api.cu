@@ -518,8 +518,8 @@ extern "C" gs_status gs_heat_apply_implicit(gs_ctx* ctx, const gs_graph* g, doub
 }
 
 extern "C" gs_status gs_sinkhorn_log(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b,
-                                     const float* vol, double t, int K, int iters, double* log_u,
-                                     double* log_v, double* dist)
+                                     const float* vol, double t, int K, double eps, int iters, double* log_u,
+                                     double* log_v, double* dist, int32_t* iters_done)
 {
     gs_status st = enter(ctx);
     if (st != GS_OK) return st;
@@ -528,9 +528,10 @@ extern "C" gs_status gs_sinkhorn_log(gs_ctx* ctx, const gs_graph* g, const float
         return gs_fail(ctx, GS_ERR_ARG, "null pointer");
     if (log_u == log_v) return gs_fail(ctx, GS_ERR_ARG, "log_u and log_v must be distinct buffers");
     if (iters < 1) return gs_fail(ctx, GS_ERR_ARG, "iters must be >= 1");
+    if (!(eps == eps)) return gs_fail(ctx, GS_ERR_ARG, "eps is NaN");
     const gs_marginals mg{a, b, vol, g->n};
     if ((st = gs_check_marginals(ctx, mg)) != GS_OK) return st;
-    return gs_sinkhorn_log_impl(ctx, g, a, b, vol, t, K, iters, log_u, log_v, dist);
+    return gs_sinkhorn_log_impl(ctx, g, a, b, vol, t, K, eps, iters, log_u, log_v, dist, iters_done);
 }
 
 // ---------------------------------------------------------------------- families of distributions

@@ -367,9 +367,10 @@ gs_status gs_barycentric_distance_impl(gs_ctx* ctx, const gs_graph* g, const flo
 gs_status gs_barycenter_effect_impl(gs_ctx* ctx, const float* Y, int64_t n, int d, const float* muT,
                                     const float* muC, double* out);
 // Algorithm 1 with FP64 potentials ln u, ln v and an extended-range Chebyshev recurrence
-// (logdomain.cu); caller node order, fixed iteration count.
+// (logdomain.cu); caller node order; eps > 0 stops as gs_sinkhorn does.
 gs_status gs_sinkhorn_log_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b, const float* vol,
-                               double t, int K, int iters, double* log_u, double* log_v, double* dist);
+                               double t, int K, double eps, int iters, double* log_u, double* log_v, double* dist,
+                               int32_t* iters_done);
 // Euler implicit heat kernel Y = (I + (t/K) L)^{-K} V by K conjugate-gradient solves (implicit.cu).
 gs_status gs_heat_apply_implicit_impl(gs_ctx* ctx, const gs_graph* g, double t, int K, const float* V, int B,
                                       float* Y, double tol, int iters);

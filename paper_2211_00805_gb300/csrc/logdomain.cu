@@ -38,10 +38,12 @@
 // per-order kernels' by at most one unit in the last place.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "cache_slices.cuh"
 #include "gs_internal.cuh"
+#include "sell_row.cuh"
 
 namespace {
 
@@ -121,10 +123,14 @@ struct XrOrder {
     double* logout;     // ln u (or ln v), caller order
     Xr* next;           // next half-step's input vol * u, filter order
     int* flags;
+    const int* done;     // eps stop: the loop's early-exit flag, or null
+    double* err;         // eps check (last order): adds sum_i |u_i y_i - a_i|, u the committed scaling
+    const double* lold;  // eps check: the committed ln u, caller order
 };
 
 __global__ void __launch_bounds__(kXrThreads) xr_order(XrOrder p)
 {
+    if (p.done != nullptr && *p.done) return;
     const int64_t row = (int64_t)blockIdx.x * kRowsPerBlock + (threadIdx.x / kLanes);
     const int lane = threadIdx.x & (kLanes - 1);
     if (row >= p.n) return;  // whole lane groups leave together
@@ -209,6 +215,37 @@ __global__ void __launch_bounds__(kXrThreads) xr_order(XrOrder p)
     }
     p.logout[node] = lu;
     p.next[row] = xr_from_log(lu + (p.vol ? log((double)p.vol[node]) : 0.0));
+    if (p.err != nullptr && a != 0.f)  // u_old y - a = a (u_old / u_new - 1), as ln u_new = ln a - ln y
+        atomicAdd(p.err, (double)a * fabs(expm1(p.lold[node] - lu)));
+}
+
+__global__ void xr_eps_init(int* done, int32_t* iters_done, int iters)
+{
+    if (done) *done = 0;
+    if (iters_done) *iters_done = iters;
+}
+
+// After a checked u half-step (new ln u in lalt, error of the committed ln u in *err): stop at
+// iteration j keeping the committed scalings, or commit the new ln u.
+__global__ void xr_eps_check(int64_t n, const double* err, double eps, int* done, int32_t* iters_done, int j,
+                             double* __restrict__ lu, const double* __restrict__ lalt, int commit)
+{
+    if (*done) return;
+    if (*err < eps) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *done = 1;
+            if (iters_done) *iters_done = j;
+        }
+        return;
+    }
+    if (!commit) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        lu[i] = lalt[i];
+}
+
+__global__ void xr_eps_finalize(const int* done, int* flags)
+{
+    if (!*done) atomicOr(flags, GS_FLAG_NOT_CONVERGED);
 }
 
 // x0 = vol * 1 (the first half-step's input, v = 1), filter order
@@ -378,22 +415,32 @@ __global__ void __launch_bounds__(kLoopThreads) xr_loop(const XrLoopArgs p)
                         const int i = i0 + u * kLoopThreads;
                         w[u] = i < ucnt ? xr_ld(src + ucol_s[i]) : 0ull;
                     }
+                    // words not yet carrying the wanted parity are re-read together (one round trip
+                    // per retry round)
+                    unsigned pending = 0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (i0 + u * kLoopThreads < ucnt && ((unsigned)w[u] & 1u) != want) pending |= 1u << u;
+                    if (pending) {
+                        const long long t0 = clock64();
+                        do {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (pending & (1u << u)) w[u] = xr_ld(src + ucol_s[i0 + u * kLoopThreads]);
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if ((pending & (1u << u)) && ((unsigned)w[u] & 1u) == want) pending &= ~(1u << u);
+                            if (pending && clock64() - t0 > p.budget) {
+                                atomicOr(p.flags, GS_FLAG_TIMEOUT);
+                                s_ok = 0;
+                                break;
+                            }
+                        } while (pending);
+                    }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int i = i0 + u * kLoopThreads;
-                        if (i >= ucnt) break;
-                        if (((unsigned)w[u] & 1u) != want) {
-                            const long long t0 = clock64();
-                            do {
-                                w[u] = xr_ld(src + ucol_s[i]);
-                                if (clock64() - t0 > p.budget) {
-                                    atomicOr(p.flags, GS_FLAG_TIMEOUT);
-                                    s_ok = 0;
-                                    break;
-                                }
-                            } while (((unsigned)w[u] & 1u) != want);
-                        }
-                        xc[i] = xr_unpack(w[u]);
+                        if (i < ucnt) xc[i] = xr_unpack(w[u]);
                     }
                 }
                 __syncthreads();
@@ -408,18 +455,19 @@ __global__ void __launch_bounds__(kLoopThreads) xr_loop(const XrLoopArgs p)
                     // the row's sum s 2^E over its stored entries (padding entries have weight 0):
                     // first the largest exponent E of the row's terms, then the terms aligned to it
                     const float* vp = sval_s + off[j];
-                    const uint16_t* lp = lidx_s + off[j];
+                    const int r = (int)threadIdx.x & 31;
+                    const uint16_t* lp = lidx_s + off[j] - r;  // the slice's paired local indices
                     int E = (k > 0 && xkm1[j].m != 0.f) ? xkm1[j].e : kZeroExp;
-                    for (int q = 0; q < width[j]; ++q) {
-                        const Xr x = xc[lp[q * 32]];
+                    gs_cached_lidx_each(lp, r, width[j], [&](int q, unsigned li) {
+                        const Xr x = xc[li];
                         if (vp[q * 32] != 0.f && x.m != 0.f) E = max(E, x.e);
-                    }
+                    });
                     float s = 0.f;
-                    for (int q = 0; q < width[j]; ++q) {
+                    gs_cached_lidx_each(lp, r, width[j], [&](int q, unsigned li) {
                         const float v = vp[q * 32];
-                        const Xr x = xc[lp[q * 32]];
+                        const Xr x = xc[li];
                         if (v != 0.f && x.m != 0.f) s = fmaf(twice * v, scale_pow2(x.m, x.e - E), s);
-                    }
+                    });
                     if (k > 0 && xkm1[j].m != 0.f)  // T_{k+1} = 2 P T_k - T_{k-1}
                         s -= scale_pow2(xkm1[j].m, xkm1[j].e - E);
                     const Xr xn = xr_normalise(s, E);
@@ -552,18 +600,26 @@ gs_status capture_iteration(gs_ctx* ctx, F&& body, cudaGraphExec_t* out)
 }  // namespace
 
 gs_status gs_sinkhorn_log_impl(gs_ctx* ctx, const gs_graph* g, const float* a, const float* b, const float* vol,
-                               double t, int K, int iters, double* log_u, double* log_v, double* dist)
+                               double t, int K, double eps, int iters, double* log_u, double* log_v, double* dist,
+                               int32_t* iters_done)
 {
     const int64_t n = g->n;
     const bool reordered = g->perm && g->prowptr;
     const FilterCsr fc = reordered ? gs_filter_csr(g) : FilterCsr{g->rowptr, g->col, g->pval};
+    const bool use_eps = eps > 0.0;
     WsPlan plan;
     size_t ix[6];
     for (int i = 0; i < 6; ++i) ix[i] = plan.add(sizeof(Xr) * (size_t)n);  // two inputs, three vectors, y
+    // eps stop: the checked half-step's ln u, the error and the early-exit flag
+    const size_t ialt = use_eps ? plan.add(sizeof(double) * (size_t)n) : 0;
+    const size_t ierr = use_eps ? plan.add(sizeof(double) + sizeof(int)) : 0;
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
     Xr* X[6];
     for (int i = 0; i < 6; ++i) X[i] = ws_at<Xr>(ctx, plan, ix[i]);
+    double* lalt = use_eps ? ws_at<double>(ctx, plan, ialt) : nullptr;
+    double* err = use_eps ? ws_at<double>(ctx, plan, ierr) : nullptr;
+    int* done = use_eps ? reinterpret_cast<int*>(err + 1) : nullptr;
     std::vector<double> c((size_t)K + 1);
     gs_heat_coefficients(t, K, c.data());
     std::vector<float> cm((size_t)K + 1);
@@ -574,40 +630,48 @@ gs_status gs_sinkhorn_log_impl(gs_ctx* ctx, const gs_graph* g, const float* a, c
         ce[k] = ee;
     }
     const unsigned grid = (unsigned)((n + kRowsPerBlock - 1) / kRowsPerBlock);
-    // one iteration: two half-steps of K orders; the input starts in buffer 0 and comes back to it
-    auto iteration = [&]() -> gs_status {
-        for (int half = 0; half < 2; ++half) {
-            const int in = half;  // this half-step reads buffer `in`, writes the next input to 1 - in
-            XrOrder p{};
-            p.n = n;
-            p.rowptr = fc.rowptr;
-            p.col = fc.col;
-            p.pval = fc.pval;
-            p.perm = reordered ? g->perm : nullptr;
-            p.y = X[5];
-            p.c0m = cm[0];
-            p.c0e = ce[0];
-            p.marg = half == 0 ? a : b;
-            p.vol = vol;
-            p.logout = half == 0 ? log_u : log_v;
-            p.next = X[1 - in];
-            p.flags = ctx->flags;
-            for (int k = 0; k < K; ++k) {
-                // x_0 is the input; x_j (j >= 1) lives in buffer 2 + (j - 1) % 3
-                p.x = X[k == 0 ? in : 2 + (k - 1) % 3];
-                p.z = k == 0 ? nullptr : X[k == 1 ? in : 2 + (k - 2) % 3];
-                p.out = X[2 + k % 3];
-                p.cm = cm[k + 1];
-                p.ce = ce[k + 1];
-                p.twice = k == 0 ? 1.f : 2.f;
-                p.last = k == K - 1;
-                xr_order<<<grid, kXrThreads, 0, ctx->stream>>>(p);
-            }
+    // one half-step of K orders: half 0 reads buffer 0 and writes the next input to buffer 1, half 1
+    // the other way round; chk: write ln u to lalt and add its marginal error to *err
+    auto half_step = [&](int half, bool chk) -> gs_status {
+        const int in = half;
+        XrOrder p{};
+        p.n = n;
+        p.rowptr = fc.rowptr;
+        p.col = fc.col;
+        p.pval = fc.pval;
+        p.perm = reordered ? g->perm : nullptr;
+        p.y = X[5];
+        p.c0m = cm[0];
+        p.c0e = ce[0];
+        p.marg = half == 0 ? a : b;
+        p.vol = vol;
+        p.logout = chk ? lalt : (half == 0 ? log_u : log_v);
+        p.next = X[1 - in];
+        p.flags = ctx->flags;
+        p.done = done;
+        p.err = chk ? err : nullptr;
+        p.lold = chk ? log_u : nullptr;
+        for (int k = 0; k < K; ++k) {
+            // x_0 is the input; x_j (j >= 1) lives in buffer 2 + (j - 1) % 3
+            p.x = X[k == 0 ? in : 2 + (k - 1) % 3];
+            p.z = k == 0 ? nullptr : X[k == 1 ? in : 2 + (k - 2) % 3];
+            p.out = X[2 + k % 3];
+            p.cm = cm[k + 1];
+            p.ce = ce[k + 1];
+            p.twice = k == 0 ? 1.f : 2.f;
+            p.last = k == K - 1;
+            xr_order<<<grid, kXrThreads, 0, ctx->stream>>>(p);
         }
         return gs_cuda_check(ctx, cudaGetLastError(), "log-domain Sinkhorn order");
     };
+    auto iteration = [&]() -> gs_status {
+        const gs_status s0 = half_step(0, false);
+        return s0 != GS_OK ? s0 : half_step(1, false);
+    };
     cudaStream_t s = ctx->stream;
-    if (ctx->loop_mode != 1 && reordered) {
+    xr_eps_init<<<1, 1, 0, s>>>(done, iters_done, iters);
+    gs_count(ctx, 1);
+    if (!use_eps && ctx->loop_mode != 1 && reordered) {
         // the whole loop in one persistent launch (GS_OPT_LOOP 1 keeps the per-order launches)
         WsPlan lp;
         const size_t icm = lp.add(sizeof(float) * (size_t)(K + 1)), ice = lp.add(sizeof(int) * (size_t)(K + 1)),
@@ -631,7 +695,32 @@ gs_status gs_sinkhorn_log_impl(gs_ctx* ctx, const gs_graph* g, const float* a, c
         if (st != GS_ERR_UNSUPPORTED) return st;
     }
     xr_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, reordered ? g->perm : nullptr, vol, X[0]);
-    if (iters == 1) {
+    if (use_eps) {
+        // the eps stop of gs_sinkhorn: at the start of iteration j (j - 1 a multiple of 10) the u
+        // half-step also measures the marginal error of the committed u; below eps the loop stops
+        // there (later launches return at once), otherwise the new u is committed
+        const unsigned cgrid = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+        for (int j = 1; j <= iters && st == GS_OK; ++j) {
+            if (j > 1 && (j - 1) % 10 == 0) {
+                cudaMemsetAsync(err, 0, sizeof(double), s);
+                st = half_step(0, true);
+                xr_eps_check<<<cgrid, 256, 0, s>>>(n, err, eps, done, iters_done, j - 1, log_u, lalt, 1);
+                gs_count(ctx, 1);
+            } else {
+                st = half_step(0, false);
+            }
+            if (st == GS_OK) st = half_step(1, false);
+        }
+        if (st != GS_OK) return st;
+        if (iters % 10 == 0) {
+            cudaMemsetAsync(err, 0, sizeof(double), s);
+            if ((st = half_step(0, true)) != GS_OK) return st;
+            xr_eps_check<<<1, 32, 0, s>>>(n, err, eps, done, iters_done, iters, log_u, lalt, 0);
+            gs_count(ctx, 1 + K);
+        }
+        xr_eps_finalize<<<1, 1, 0, s>>>(done, ctx->flags);
+        gs_count(ctx, 2 + 2 * (int64_t)iters * K);
+    } else if (iters == 1) {
         if ((st = iteration()) != GS_OK) return st;
     } else {  // launch-bound on small graphs: replay one captured iteration
         cudaGraphExec_t exec = nullptr;
@@ -641,7 +730,7 @@ gs_status gs_sinkhorn_log_impl(gs_ctx* ctx, const gs_graph* g, const float* a, c
         cudaGraphExecDestroy(exec);  // freed once the launches above have run
         if ((st = gs_cuda_check(ctx, e, "log-domain Sinkhorn replay")) != GS_OK) return st;
     }
-    gs_count(ctx, 1 + 2 * (int64_t)iters * K);
+    if (!use_eps) gs_count(ctx, 1 + 2 * (int64_t)iters * K);
     if (dist) {
         xr_distance<<<1, kRedThreads, 0, s>>>(n, a, b, vol, log_u, log_v, t, dist, ctx->flags);
         gs_count(ctx, 1);

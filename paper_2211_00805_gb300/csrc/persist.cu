@@ -227,8 +227,8 @@ __device__ __forceinline__ void rows_order_cached(const PersistArgs& p, int r0, 
         const int sl = row / GS_SELL_C;
         const int beg = __ldg(p.sptr + sl);
         const int width = (__ldg(p.sptr + sl + 1) - beg) / GS_SELL_C;
-        const int off = beg - e0 + row % GS_SELL_C;
-        const float s = gs_sell_dot_cached(lidx_s + off, sval_s + off, width, xc);
+        const int r = row % GS_SELL_C;
+        const float s = gs_sell_dot_cached(lidx_s + (beg - e0), r, sval_s + (beg - e0) + r, width, xc);
         const float tk = first ? s : fmaf(2.f, s, -pv);
         const float acc = fmaf(ck, tk, yv);
         if (mode < 2) {
@@ -513,7 +513,8 @@ __global__ void __launch_bounds__(NT) sinkhorn_neighbour_sync(const PersistArgs 
                 for (int j = 0; j < RPT; ++j) {
                     const int row = r0 + (int)threadIdx.x + j * NT;
                     if (row >= r1) continue;
-                    const float s = gs_sell_dot_cached(lidx_s + off[j], sval_s + off[j], width[j], xc);
+                    const float s = gs_sell_dot_cached(lidx_s + off[j] - (threadIdx.x & (GS_SELL_C - 1)),
+                                                       threadIdx.x & (GS_SELL_C - 1), sval_s + off[j], width[j], xc);
                     float tk, acc;
                     if (k == 1) {
                         tk = s;
@@ -664,9 +665,11 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
                 // stage s - 1 carries tag s (8-byte words) or parity (s - 1) & 1 (4-byte words);
                 // the self-test waits for a tag no word will carry
                 const unsigned want = W4 ? (p.selftest ? 2u : ((stage - 1u) & 1u)) : stage + extra;
-                // issue up to 8 loads per thread before checking any tag
+                // issue up to 8 loads per thread before checking any tag; words not yet carrying
+                // the wanted tag are re-read together, so each retry round costs one round trip
                 for (int i0 = threadIdx.x; i0 < ucnt; i0 += 8 * NT) {
                     unsigned long long w[8];
+                    unsigned pending = 0;
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int i = i0 + u * NT;
@@ -674,22 +677,30 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
                                                        : ld_relaxed_u64(src + ucol_s[i]));
                     }
 #pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (i0 + u * NT < ucnt && tag_of<W4>(w[u]) != want) pending |= 1u << u;
+                    if (pending) {
+                        const long long t0 = clock64();
+                        do {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (pending & (1u << u))
+                                    w[u] = W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i0 + u * NT])
+                                              : ld_relaxed_u64(src + ucol_s[i0 + u * NT]);
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if ((pending & (1u << u)) && tag_of<W4>(w[u]) == want) pending &= ~(1u << u);
+                            if (pending && clock64() - t0 > p.budget) {
+                                atomicOr(p.flags, GS_FLAG_TIMEOUT);
+                                s_ok = 0;
+                                break;
+                            }
+                        } while (pending);
+                    }
+#pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int i = i0 + u * NT;
-                        if (i >= ucnt) break;
-                        if (tag_of<W4>(w[u]) != want) {
-                            const long long t0 = clock64();
-                            do {
-                                w[u] = W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i])
-                                          : ld_relaxed_u64(src + ucol_s[i]);
-                                if (clock64() - t0 > p.budget) {
-                                    atomicOr(p.flags, GS_FLAG_TIMEOUT);
-                                    s_ok = 0;
-                                    break;
-                                }
-                            } while (tag_of<W4>(w[u]) != want);
-                        }
-                        xc[i] = __uint_as_float((unsigned)w[u]);
+                        if (i < ucnt) xc[i] = __uint_as_float((unsigned)w[u]);
                     }
                 }
                 __syncthreads();
@@ -699,7 +710,8 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
                 for (int j = 0; j < RPT; ++j) {
                     const int row = r0 + (int)threadIdx.x + j * NT;
                     if (row >= r1) continue;
-                    const float s = gs_sell_dot_cached(lidx_s + off[j], sval_s + off[j], width[j], xc);
+                    const float s = gs_sell_dot_cached(lidx_s + off[j] - (threadIdx.x & (GS_SELL_C - 1)),
+                                                       threadIdx.x & (GS_SELL_C - 1), sval_s + off[j], width[j], xc);
                     float tk, acc;
                     if (k == 1) {
                         tk = s;

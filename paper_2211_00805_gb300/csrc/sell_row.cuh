@@ -45,19 +45,44 @@ __device__ __forceinline__ float gs_sell_dot(const int* cp, const float* vp, int
     return s0 + s1;
 }
 
-// Same loop with the neighbour values taken from a shared-memory cache through 16-bit local
-// indices (the per-block gather cache of the persistent loop); identical summation order.
-__device__ __forceinline__ float gs_sell_dot_cached(const uint16_t* lp, const float* vp, int width,
+// Local column indices of the gather cache (16-bit positions in a block's distinct-column list),
+// stored per slice with two steps of a row in one 32-bit word: steps 2q and 2q + 1 of row r are
+// the low and high halves of word q * GS_SELL_C + r of the slice, so one warp-wide load brings two
+// steps' indices; an odd last step keeps the plain layout, entry (W - 1) * GS_SELL_C + r.
+// slice_lidx must be 4-byte aligned (slices are whole multiples of GS_SELL_C entries).
+
+// Calls f(j, index) for the steps j = 0 .. width - 1 of row r in order, one 32-bit load per pair.
+template <class F>
+__device__ __forceinline__ void gs_cached_lidx_each(const uint16_t* slice_lidx, int r, int width, F&& f)
+{
+    const uint32_t* lp2 = reinterpret_cast<const uint32_t*>(slice_lidx) + r;
+    int j = 0;
+    for (; j + 2 <= width; j += 2) {
+        const unsigned pr = lp2[(j >> 1) * GS_SELL_C];
+        f(j, pr & 0xffffu);
+        f(j + 1, pr >> 16);
+    }
+    if (j < width) f(j, (unsigned)slice_lidx[j * GS_SELL_C + r]);
+}
+
+// Same loop with the neighbour values taken from a shared-memory cache through the paired 16-bit
+// local indices above (the per-block gather cache of the persistent loop); identical summation
+// order.  vp points at row r's first value.
+__device__ __forceinline__ float gs_sell_dot_cached(const uint16_t* slice_lidx, int r, const float* vp, int width,
                                                     const float* xc)
 {
+    const uint32_t* lp2 = reinterpret_cast<const uint32_t*>(slice_lidx) + r;
     float s0 = 0.f, s1 = 0.f;
     int j = 0;
     for (; j + 8 <= width; j += 8) {
         float w[8], x[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            w[u] = vp[(j + u) * GS_SELL_C];
-            x[u] = xc[lp[(j + u) * GS_SELL_C]];
+        for (int q = 0; q < 4; ++q) {
+            const unsigned pr = lp2[((j >> 1) + q) * GS_SELL_C];
+            w[2 * q] = vp[(j + 2 * q) * GS_SELL_C];
+            w[2 * q + 1] = vp[(j + 2 * q + 1) * GS_SELL_C];
+            x[2 * q] = xc[pr & 0xffffu];
+            x[2 * q + 1] = xc[pr >> 16];
         }
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
@@ -65,7 +90,12 @@ __device__ __forceinline__ float gs_sell_dot_cached(const uint16_t* lp, const fl
             s1 = fmaf(w[u + 1], x[u + 1], s1);
         }
     }
-    for (; j < width; ++j) s0 = fmaf(vp[j * GS_SELL_C], xc[lp[j * GS_SELL_C]], s0);
+    for (; j + 2 <= width; j += 2) {
+        const unsigned pr = lp2[(j >> 1) * GS_SELL_C];
+        s0 = fmaf(vp[j * GS_SELL_C], xc[pr & 0xffffu], s0);
+        s0 = fmaf(vp[(j + 1) * GS_SELL_C], xc[pr >> 16], s0);
+    }
+    if (j < width) s0 = fmaf(vp[j * GS_SELL_C], xc[slice_lidx[j * GS_SELL_C + r]], s0);
     return s0 + s1;
 }
 

@@ -463,7 +463,10 @@ __global__ void __launch_bounds__(kColourThreads) sell_bank_colour(const int* __
     colour_slice(lidx + base, W, step + base, wk[threadIdx.x]);
 }
 
-// Moves every entry of a slice to its step (from copies of the three arrays).
+// Moves every entry of a slice to its step (from copies of the three arrays; slices too wide for
+// the colouring keep their order) and writes the local indices in the paired layout the cached
+// row sums read: steps 2q and 2q + 1 of row l in the 32-bit word q * 32 + l of the slice, an odd
+// last step at its plain position.
 __global__ void sell_apply_steps(const int* __restrict__ sptr, int64_t nslices, const unsigned char* __restrict__ step,
                                  const int* __restrict__ c_in, const float* __restrict__ v_in,
                                  const uint16_t* __restrict__ l_in, int* __restrict__ scol,
@@ -474,13 +477,15 @@ __global__ void sell_apply_steps(const int* __restrict__ sptr, int64_t nslices, 
     const int l = threadIdx.x & 31;
     const int base = sptr[sl];
     const int W = (sptr[sl + 1] - base) / 32;
-    if (W < 1 || W > kSchedMaxWidth) return;
+    if (W < 1) return;
+    const bool coloured = W <= kSchedMaxWidth;
     for (int j = 0; j < W; ++j) {
         const int e = base + j * 32 + l;
-        const int d = base + step[e] * 32 + l;
+        const int t = coloured ? (int)step[e] : j;
+        const int d = base + t * 32 + l;
         scol[d] = c_in[e];
         sval[d] = v_in[e];
-        lidx[d] = l_in[e];
+        lidx[t < (W & ~1) ? base + (t >> 1) * 64 + 2 * l + (t & 1) : d] = l_in[e];
     }
 }
 

@@ -49,13 +49,14 @@ def sphere(gs, ctx):
 
 
 def _check(gs, ctx, g, Ls, a, b, t, K, iters, vol=None):
-    lu, lv, dist = gs.gs_sinkhorn_log(ctx, g, to_dev(a), to_dev(b), t, K, iters,
-                                      vol=None if vol is None else to_dev(vol))
+    lu, lv, dist, it = gs.gs_sinkhorn_log(ctx, g, to_dev(a), to_dev(b), t, K, iters,
+                                          vol=None if vol is None else to_dev(vol))
     gs.gs_sync(ctx)
     r = oracle.sinkhorn(Ls, oracle.cheb_coefficients(t, K), a.astype(np.float64), b.astype(np.float64), t,
                         iters, a=None if vol is None else vol.astype(np.float64))
     assert r["status"] == oracle.OK
     lu, lv, d = to_np(lu), to_np(lv), to_np(dist)
+    assert int(to_np(it)[0]) == iters
     for got, ref, marg, name in ((lu, r["v"], a, "ln u"), (lv, r["w"], b, "ln v")):
         zero = marg == 0
         assert np.all(np.isneginf(got[zero])), name  # no mass: u_i = 0
@@ -201,10 +202,65 @@ def test_log_sinkhorn_rejects_bad_arguments(gs, ctx, sphere):
     a, b = to_dev(p.a), to_dev(p.b)
     lu = torch.empty(n, dtype=torch.float64, device="cuda")
     lv = torch.empty(n, dtype=torch.float64, device="cuda")
-    args = [ctx.handle, g.handle, a.data_ptr(), b.data_ptr(), None, 1.0, 20, 10, lu.data_ptr(), lv.data_ptr(), None]
-    assert lib.gs_sinkhorn_log(*args[:8], lu.data_ptr(), lu.data_ptr(), None) == gs.GS_ERR_ARG
-    assert lib.gs_sinkhorn_log(*args[:7], 0, *args[8:]) == gs.GS_ERR_ARG
-    assert lib.gs_sinkhorn_log(*args[:6], 0, *args[7:]) == gs.GS_ERR_ARG
-    assert lib.gs_sinkhorn_log(*args[:5], -1.0, *args[6:]) == gs.GS_ERR_ARG
-    assert lib.gs_sinkhorn_log(*args[:2], None, *args[3:]) == gs.GS_ERR_ARG
+    # ctx, g, a, b, vol, t, K, eps, iters, log_u, log_v, dist, iters_done
+    args = [ctx.handle, g.handle, a.data_ptr(), b.data_ptr(), None, 1.0, 20, 0.0, 10, lu.data_ptr(), lv.data_ptr(),
+            None, None]
+    assert lib.gs_sinkhorn_log(*args[:9], lu.data_ptr(), lu.data_ptr(), None, None) == gs.GS_ERR_ARG
+    assert lib.gs_sinkhorn_log(*args[:8], 0, *args[9:]) == gs.GS_ERR_ARG  # iters
+    assert lib.gs_sinkhorn_log(*args[:7], float("nan"), *args[8:]) == gs.GS_ERR_ARG  # eps
+    assert lib.gs_sinkhorn_log(*args[:6], 0, *args[7:]) == gs.GS_ERR_ARG  # K
+    assert lib.gs_sinkhorn_log(*args[:5], -1.0, *args[6:]) == gs.GS_ERR_ARG  # t
+    assert lib.gs_sinkhorn_log(*args[:2], None, *args[3:]) == gs.GS_ERR_ARG  # a
     gs.gs_sync(ctx)  # the context stays usable
+
+
+def _oracle_marginal_errors(Ls, t, K, a, b, upto):
+    """sum_i |u_i p_K(w)_i - a_i| after iterations 10, 20, ..., upto (the eps stop's measure)."""
+    c = oracle.cheb_coefficients(t, K)
+    w = np.ones(len(a))
+    errs = []
+    for j in range(1, upto + 1):
+        u = oracle._div0(a, oracle.heat_apply(Ls, c, w))
+        w = oracle._div0(b, oracle.heat_apply(Ls, c, u))
+        if j % 10 == 0:
+            errs.append(np.abs(u * oracle.heat_apply(Ls, c, w) - a).sum())
+    return errs
+
+
+def test_log_sinkhorn_eps_stop_matches_oracle(gs, ctx, sphere):
+    # t = 1 (FP32 scalings overflow): eps between the oracle's marginal errors after 30 and 40
+    # iterations, so the oracle and the GPU both stop after iteration 40, whether the stop is
+    # found at the start of iteration 41 or by the check after the last iteration
+    p, g, Ls = sphere
+    t, K = 1.0, 20
+    a64, b64 = p.a.astype(np.float64), p.b.astype(np.float64)
+    e30, e40 = _oracle_marginal_errors(Ls, t, K, a64, b64, 40)[2:4]
+    assert e40 < 0.99 * e30  # a clear gap: the GPU's errors are within ~1e-3 of these
+    eps = float(np.sqrt(e30 * e40))
+    r = oracle.sinkhorn(Ls, oracle.cheb_coefficients(t, K), a64, b64, t, 60, eps=eps)
+    assert r["status"] == oracle.OK and r["iters"] == 40
+    a, b = to_dev(p.a), to_dev(p.b)
+    res = {}
+    for iters in (60, 40):
+        lu, lv, dist, it = gs.gs_sinkhorn_log(ctx, g, a, b, t, K, iters, eps=eps)
+        gs.gs_sync(ctx)
+        assert int(to_np(it)[0]) == 40
+        res[iters] = (to_np(lu), to_np(lv), to_np(dist))
+        for got, ref in ((res[iters][0], r["v"]), (res[iters][1], r["w"])):
+            err = np.abs(got - np.log(ref))
+            assert err.max() < LOG_ATOL
+        assert res[iters][2][0] == pytest.approx(r["W2"], rel=W2_RTOL)
+    for x, y in zip(res[60], res[40]):  # the same 40 iterations either way
+        assert np.array_equal(x, y)
+
+
+def test_log_sinkhorn_eps_not_reached_is_reported(gs, ctx, sphere):
+    p, g, Ls = sphere
+    lu, lv, dist, it = gs.gs_sinkhorn_log(ctx, g, to_dev(p.a), to_dev(p.b), 1.0, 20, 20, eps=1e-30)
+    with pytest.raises(gs.GeosinkError) as e:
+        gs.gs_sync(ctx)
+    assert e.value.status == gs.GS_ERR_NOT_CONVERGED
+    assert int(to_np(it)[0]) == 20
+    _, _, _, r = _check(gs, ctx, g, Ls, p.a, p.b, 1.0, 20, 20)  # the oracle's 20 iterations
+    for got, ref in ((to_np(lu), r["v"]), (to_np(lv), r["w"])):
+        assert np.abs(got - np.log(ref)).max() < LOG_ATOL
