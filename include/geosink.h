@@ -116,9 +116,11 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * only for the blocks owning rows it reads (per-block ready counters) and keeps its own rows'
  * recurrence values in registers; 2: the same, with the readiness carried by the exchanged values
  * themselves (value + stage words in three rotating slots, see GS_OPT_TAG_WORD; no counters or
- * fences); 0: a barrier over the whole grid; 3 (default): the one gs_autotune measured fastest on
- * the graph (else on the context's last tuned graph, else 2).  Same arithmetic in all of them.
- * All honour GS_OPT_BARRIER_SELFTEST. */
+ * fences), a thread's words that are not ready yet re-read together; 4: as 2, those words re-read
+ * one at a time (fewer loads in flight: faster where the exchange dominates, e.g. small graphs);
+ * 0: a barrier over the whole grid; 3 (default): the one gs_autotune measured fastest on the graph
+ * (else on the context's last tuned graph, else 2).  Same arithmetic in all of them.  All honour
+ * GS_OPT_BARRIER_SELFTEST. */
 /* GS_OPT_PERSIST_BLOCKS: blocks per SM of the gather-cache partition (1 = one 1024-thread block,
  * default; 2 = two 512-thread blocks, so one block's exchange overlaps the other's sums), for the
  * tagged-value and neighbour-flag forms.  Applies to graphs built after the call. */

@@ -192,7 +192,7 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->persist_bps = value;
         return GS_OK;
     }
-    if (option == GS_OPT_PERSIST_SYNC && (value >= 0 && value <= 3)) {
+    if (option == GS_OPT_PERSIST_SYNC && (value >= 0 && value <= 4)) {
         ctx->persist_sync = value;
         return GS_OK;
     }
@@ -226,7 +226,7 @@ extern "C" gs_status gs_get_option(const gs_ctx* ctx, int option, int* value)
         case GS_OPT_BLK_KERNEL: *value = ctx->blk_kernel; return GS_OK;
         case GS_OPT_KNN_TENSOR: *value = ctx->knn_tensor_cores; return GS_OK;
         case GS_OPT_PERSIST_SMEM_GRAPH: *value = ctx->persist_smem_graph; return GS_OK;
-        case GS_OPT_PERSIST_SYNC: *value = gs_persist_sync_choice(ctx, nullptr); return GS_OK;
+        case GS_OPT_PERSIST_SYNC: *value = gs_persist_sync_setting(ctx, nullptr); return GS_OK;
         case GS_OPT_PERSIST_BLOCKS: *value = ctx->persist_bps; return GS_OK;
         case GS_OPT_TAG_WORD: *value = ctx->tag_word; return GS_OK;
         case GS_OPT_CHECK_ARGS: *value = ctx->check_args; return GS_OK;

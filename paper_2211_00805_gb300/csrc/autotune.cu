@@ -151,16 +151,17 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
     gs_count(ctx, 1);
     const int saved_loop = ctx->loop_mode, saved_sync = ctx->persist_sync;
     // candidates: the persistent loop with each block synchronisation (grid barrier, neighbour
-    // flags, tagged values), then graph replay
-    float loop_ms[4] = {0.f, 0.f, 0.f, 0.f};
+    // flags, tagged values re-read in groups, tagged values re-read one at a time), then graph replay
+    constexpr int kSyncs[5] = {0, 1, 2, 4, -1};
+    float loop_ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     int saved_flags = 0;  // the synthetic loop's status must not reach the caller's next gs_sync
     cudaStreamSynchronize(ctx->stream);
     cudaMemcpy(&saved_flags, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int c = 0; c < 4 && st == GS_OK; ++c) {
-        ctx->loop_mode = c < 3 ? 0 : 1;
-        ctx->persist_sync = c < 3 ? c : saved_sync;
+    for (int c = 0; c < 5 && st == GS_OK; ++c) {
+        ctx->loop_mode = kSyncs[c] >= 0 ? 0 : 1;
+        ctx->persist_sync = kSyncs[c] >= 0 ? kSyncs[c] : saved_sync;
         for (int rep = 0; rep < 2 && st == GS_OK; ++rep) {  // first run warms (graph capture)
             cudaEventRecord(e0, ctx->stream);
             st = gs_sinkhorn_impl(ctx, g, ab, ab + n, nullptr, 1.0, K, 0.0, 10, nullptr, nullptr,
@@ -179,13 +180,14 @@ gs_status gs_autotune_impl(gs_ctx* ctx, gs_graph* g, int B, int K, int* choice_o
     cudaMemcpy(ctx->flags, &saved_flags, sizeof(int), cudaMemcpyHostToDevice);
     if (st != GS_OK) return st;
     int best_c = 0;
-    for (int c = 1; c < 4; ++c)
+    for (int c = 1; c < 5; ++c)
         if (loop_ms[c] < loop_ms[best_c]) best_c = c;
-    g->tuned_loop = best_c < 3 ? 1 : 2;
+    g->tuned_loop = kSyncs[best_c] >= 0 ? 1 : 2;
     ctx->tuned_loop = g->tuned_loop;
-    int best_s = 0;
-    for (int c = 1; c < 3; ++c)
-        if (loop_ms[c] < loop_ms[best_s]) best_s = c;
+    int best_p = 0;
+    for (int c = 1; c < 4; ++c)
+        if (loop_ms[c] < loop_ms[best_p]) best_p = c;
+    const int best_s = kSyncs[best_p];
     g->tuned_sync = best_s;
     for (auto& r : ctx->tune_log)
         if (r.n == n && r.nnz == g->nnz && r.B == 1 && r.K == K) {

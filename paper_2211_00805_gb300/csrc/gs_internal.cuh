@@ -95,9 +95,10 @@ struct gs_ctx {
     int tuned_loop = 0;            // last gs_autotune loop choice (1 persistent, 2 graph replay)
     int persist_smem_graph = 2;    // persistent loop: 0 graph from global memory, 1 graph slices in
                                    // shared memory, 2 slices plus the per-block gather cache
-    int persist_sync = 3;          // persistent loop with the gather cache: 2 tagged values,
-                                   // 1 neighbour flags, 0 grid barrier, 3 the autotuned choice
-    int tuned_sync = -1;           // last gs_autotune choice of the above (0..2), -1 none
+    int persist_sync = 3;          // persistent loop with the gather cache: 2 tagged values re-read
+                                   // in groups, 4 one at a time, 1 neighbour flags, 0 grid barrier,
+                                   // 3 the autotuned choice
+    int tuned_sync = -1;           // last gs_autotune choice of the above (0, 1, 2, 4), -1 none
     int tag_word = 4;              // tagged-value exchange word: 4 (value with a parity bit) or 8 (exact)
     int persist_bps = 1;           // gather-cache partition of graphs built from now on: blocks per
                                    // SM (1: 1024 threads each, 2: 512 threads each)
@@ -149,7 +150,7 @@ struct gs_graph {
     int tuned_blk = 0;
     int tuned_blk_B = 0;
     int tuned_loop = 0;            // Sinkhorn loop: 0 not tuned, 1 persistent, 2 CUDA-graph replay
-    int tuned_sync = -1;           // persistent loop's block synchronisation (0..2), -1 not tuned
+    int tuned_sync = -1;           // persistent loop's block synchronisation (0, 1, 2, 4), -1 not tuned
     int tuned_lanes = 0;           // lanes per row of tuned_blk (0: the kernel's default)
     int tuned_split = 0;           // threads per row of the one-column row-split kernel (0: default)
     std::vector<int> sptr_host;    // host copy of the slice offsets (sizes the persistent kernel's
@@ -245,7 +246,19 @@ static inline const TuneRecord* gs_tune_lookup(const gs_ctx* ctx, const gs_graph
     }
     return any;
 }
-static inline int gs_persist_sync_choice(const gs_ctx* ctx, const gs_graph* g)
+// Tagged-word staging for a graph without its own autotune record: grouped re-reads pay where a
+// block's sums are long enough that most words are ready when its staging starts (672 rows per
+// block: 2.29 against 2.36 us per order on the 100k manifold), one-at-a-time re-reads where the
+// exchange dominates (480 rows: 1.87 against 1.92 us; 160 rows: 1.36 against 1.58 us).
+constexpr int kGroupedStagingRows = 576;
+static inline int gs_tagged_form(const gs_graph* g)
+{
+    return (g && g->xc_rpb > 0 && g->xc_rpb < kGroupedStagingRows) ? 4 : 2;
+}
+// The block synchronisation as chosen (option, else the graph's autotune record, else the
+// context's last choice if it was not a tagged form, else the tagged form above): 0 grid
+// barrier, 1 neighbour flags, 2 tagged words re-read in groups, 4 tagged words re-read one at a time.
+static inline int gs_persist_sync_setting(const gs_ctx* ctx, const gs_graph* g)
 {
     if (ctx->persist_sync != 3) return ctx->persist_sync;
     if (g && g->tuned_sync >= 0) return g->tuned_sync;
@@ -253,8 +266,15 @@ static inline int gs_persist_sync_choice(const gs_ctx* ctx, const gs_graph* g)
         const TuneRecord* r = gs_tune_lookup(ctx, g, 1, 0);
         if (r && r->sync >= 0) return r->sync;
     }
-    if (ctx->tuned_sync >= 0) return ctx->tuned_sync;
-    return 2;
+    if (ctx->tuned_sync == 0 || ctx->tuned_sync == 1) return ctx->tuned_sync;
+    if (!g && ctx->tuned_sync >= 0) return ctx->tuned_sync;
+    return gs_tagged_form(g);
+}
+// The synchronisation family: both tagged-word forms report 2 (they need the same exchange buffer).
+static inline int gs_persist_sync_choice(const gs_ctx* ctx, const gs_graph* g)
+{
+    const int s = gs_persist_sync_setting(ctx, g);
+    return s == 4 ? 2 : s;
 }
 // Words of the persistent loop's synchronisation buffer: barrier counter and generation, then one
 // 128-byte line per block (up to two blocks per SM) for its ready counter.

@@ -350,7 +350,7 @@ __device__ __forceinline__ Xr xr_divide(float a, Xr y, double lvol, double* logo
     return xr_from_log(lu + lvol);
 }
 
-template <int RPT>
+template <int RPT, bool GROUP>
 __global__ void __launch_bounds__(kLoopThreads) xr_loop(const XrLoopArgs p)
 {
     __shared__ int s_ok;
@@ -415,32 +415,52 @@ __global__ void __launch_bounds__(kLoopThreads) xr_loop(const XrLoopArgs p)
                         const int i = i0 + u * kLoopThreads;
                         w[u] = i < ucnt ? xr_ld(src + ucol_s[i]) : 0ull;
                     }
-                    // words not yet carrying the wanted parity are re-read together (one round trip
-                    // per retry round)
-                    unsigned pending = 0;
+                    // words not yet carrying the wanted parity are re-read together (GROUP: one
+                    // round trip per retry round) or one at a time, as in the FP32 loop
+                    if (GROUP) {
+                        unsigned pending = 0;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (i0 + u * kLoopThreads < ucnt && ((unsigned)w[u] & 1u) != want) pending |= 1u << u;
-                    if (pending) {
-                        const long long t0 = clock64();
-                        do {
+                        for (int u = 0; u < 8; ++u)
+                            if (i0 + u * kLoopThreads < ucnt && ((unsigned)w[u] & 1u) != want) pending |= 1u << u;
+                        if (pending) {
+                            const long long t0 = clock64();
+                            do {
 #pragma unroll
-                            for (int u = 0; u < 8; ++u)
-                                if (pending & (1u << u)) w[u] = xr_ld(src + ucol_s[i0 + u * kLoopThreads]);
+                                for (int u = 0; u < 8; ++u)
+                                    if (pending & (1u << u)) w[u] = xr_ld(src + ucol_s[i0 + u * kLoopThreads]);
 #pragma unroll
-                            for (int u = 0; u < 8; ++u)
-                                if ((pending & (1u << u)) && ((unsigned)w[u] & 1u) == want) pending &= ~(1u << u);
-                            if (pending && clock64() - t0 > p.budget) {
-                                atomicOr(p.flags, GS_FLAG_TIMEOUT);
-                                s_ok = 0;
-                                break;
+                                for (int u = 0; u < 8; ++u)
+                                    if ((pending & (1u << u)) && ((unsigned)w[u] & 1u) == want) pending &= ~(1u << u);
+                                if (pending && clock64() - t0 > p.budget) {
+                                    atomicOr(p.flags, GS_FLAG_TIMEOUT);
+                                    s_ok = 0;
+                                    break;
+                                }
+                            } while (pending);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = i0 + u * kLoopThreads;
+                            if (i < ucnt) xc[i] = xr_unpack(w[u]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = i0 + u * kLoopThreads;
+                            if (i >= ucnt) break;
+                            if (((unsigned)w[u] & 1u) != want) {
+                                const long long t0 = clock64();
+                                do {
+                                    w[u] = xr_ld(src + ucol_s[i]);
+                                    if (clock64() - t0 > p.budget) {
+                                        atomicOr(p.flags, GS_FLAG_TIMEOUT);
+                                        s_ok = 0;
+                                        break;
+                                    }
+                                } while (((unsigned)w[u] & 1u) != want);
                             }
-                        } while (pending);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int i = i0 + u * kLoopThreads;
-                        if (i < ucnt) xc[i] = xr_unpack(w[u]);
+                            xc[i] = xr_unpack(w[u]);
+                        }
                     }
                 }
                 __syncthreads();
@@ -516,7 +536,11 @@ gs_status xr_loop_launch(gs_ctx* ctx, const gs_graph* g, const float* a, const f
     const size_t emax = (size_t)(g->xc_max_e + 31) / 32 * 32, umax = (size_t)(g->xc_max_u + 31) / 32 * 32;
     const size_t smem = emax * 6 + umax * 12;
     if (rpt < 1 || rpt > 2 || smem > 200 * 1024) return GS_ERR_UNSUPPORTED;
-    void (*kern)(XrLoopArgs) = rpt == 1 ? xr_loop<1> : xr_loop<2>;
+    // staging re-reads as the FP32 loop takes them on this graph (grouped where blocks are large)
+    const int form = gs_persist_sync_setting(ctx, g);
+    const bool group = form == 2 || (form != 4 && gs_tagged_form(g) == 2);
+    void (*kern)(XrLoopArgs) = rpt == 1 ? (group ? xr_loop<1, true> : xr_loop<1, false>)
+                                        : (group ? xr_loop<2, true> : xr_loop<2, false>);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return GS_ERR_UNSUPPORTED;

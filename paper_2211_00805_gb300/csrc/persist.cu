@@ -602,7 +602,7 @@ __device__ __forceinline__ unsigned tag_of(unsigned long long w)
     return W4 ? (unsigned)(w & 1ull) : (unsigned)(w >> 32);
 }
 
-template <int RPT, int NT, bool W4>
+template <int RPT, int NT, bool W4, bool GROUP>
 __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
 {
     __shared__ int s_ok;
@@ -666,41 +666,65 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
                 // the self-test waits for a tag no word will carry
                 const unsigned want = W4 ? (p.selftest ? 2u : ((stage - 1u) & 1u)) : stage + extra;
                 // issue up to 8 loads per thread before checking any tag; words not yet carrying
-                // the wanted tag are re-read together, so each retry round costs one round trip
+                // the wanted tag are then re-read together (GROUP: each retry round costs one round
+                // trip) or one at a time in list order, each stored as soon as it is ready (fewer
+                // loads in flight while the owners have not published: the faster form where the
+                // exchange dominates the order)
                 for (int i0 = threadIdx.x; i0 < ucnt; i0 += 8 * NT) {
                     unsigned long long w[8];
-                    unsigned pending = 0;
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int i = i0 + u * NT;
                         w[u] = i >= ucnt ? 0ull : (W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i])
                                                        : ld_relaxed_u64(src + ucol_s[i]));
                     }
+                    if (GROUP) {
+                        unsigned pending = 0;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (i0 + u * NT < ucnt && tag_of<W4>(w[u]) != want) pending |= 1u << u;
-                    if (pending) {
-                        const long long t0 = clock64();
-                        do {
+                        for (int u = 0; u < 8; ++u)
+                            if (i0 + u * NT < ucnt && tag_of<W4>(w[u]) != want) pending |= 1u << u;
+                        if (pending) {
+                            const long long t0 = clock64();
+                            do {
 #pragma unroll
-                            for (int u = 0; u < 8; ++u)
-                                if (pending & (1u << u))
-                                    w[u] = W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i0 + u * NT])
-                                              : ld_relaxed_u64(src + ucol_s[i0 + u * NT]);
+                                for (int u = 0; u < 8; ++u)
+                                    if (pending & (1u << u))
+                                        w[u] = W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i0 + u * NT])
+                                                  : ld_relaxed_u64(src + ucol_s[i0 + u * NT]);
 #pragma unroll
-                            for (int u = 0; u < 8; ++u)
-                                if ((pending & (1u << u)) && tag_of<W4>(w[u]) == want) pending &= ~(1u << u);
-                            if (pending && clock64() - t0 > p.budget) {
-                                atomicOr(p.flags, GS_FLAG_TIMEOUT);
-                                s_ok = 0;
-                                break;
+                                for (int u = 0; u < 8; ++u)
+                                    if ((pending & (1u << u)) && tag_of<W4>(w[u]) == want) pending &= ~(1u << u);
+                                if (pending && clock64() - t0 > p.budget) {
+                                    atomicOr(p.flags, GS_FLAG_TIMEOUT);
+                                    s_ok = 0;
+                                    break;
+                                }
+                            } while (pending);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = i0 + u * NT;
+                            if (i < ucnt) xc[i] = __uint_as_float((unsigned)w[u]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = i0 + u * NT;
+                            if (i >= ucnt) break;
+                            if (tag_of<W4>(w[u]) != want) {
+                                const long long t0 = clock64();
+                                do {
+                                    w[u] = W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i])
+                                              : ld_relaxed_u64(src + ucol_s[i]);
+                                    if (clock64() - t0 > p.budget) {
+                                        atomicOr(p.flags, GS_FLAG_TIMEOUT);
+                                        s_ok = 0;
+                                        break;
+                                    }
+                                } while (tag_of<W4>(w[u]) != want);
                             }
-                        } while (pending);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int i = i0 + u * NT;
-                        if (i < ucnt) xc[i] = __uint_as_float((unsigned)w[u]);
+                            xc[i] = __uint_as_float((unsigned)w[u]);
+                        }
                     }
                 }
                 __syncthreads();
@@ -750,16 +774,19 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
 
 constexpr int kSmemGraphMax = 200 * 1024;  // shared-memory budget for the resident graph slice
 
-template <int NT, bool W4>
+template <int NT, bool W4, bool GROUP>
 void (*tagged_kernel(int rpt))(PersistArgs)
 {
-    return rpt == 1 ? sinkhorn_tagged<1, NT, W4> : (rpt == 2 ? sinkhorn_tagged<2, NT, W4> : sinkhorn_tagged<4, NT, W4>);
+    return rpt == 1 ? sinkhorn_tagged<1, NT, W4, GROUP>
+                    : (rpt == 2 ? sinkhorn_tagged<2, NT, W4, GROUP> : sinkhorn_tagged<4, NT, W4, GROUP>);
 }
 
 template <int NT>
-void (*gather_cache_kernel(bool tagged, bool w4, int rpt))(PersistArgs)
+void (*gather_cache_kernel(bool tagged, bool w4, bool group, int rpt))(PersistArgs)
 {
-    if (tagged) return w4 ? tagged_kernel<NT, true>(rpt) : tagged_kernel<NT, false>(rpt);
+    if (tagged)
+        return w4 ? (group ? tagged_kernel<NT, true, true>(rpt) : tagged_kernel<NT, true, false>(rpt))
+                  : (group ? tagged_kernel<NT, false, true>(rpt) : tagged_kernel<NT, false, false>(rpt));
     return rpt == 1 ? sinkhorn_neighbour_sync<1, NT>
                     : (rpt == 2 ? sinkhorn_neighbour_sync<2, NT> : sinkhorn_neighbour_sync<4, NT>);
 }
@@ -794,8 +821,9 @@ gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
             args.rows_per_block = g->xc_rpb;
             args.smem_graph = 2;
             const bool w4 = ctx->tag_word == 4;
-            void (*kern)(PersistArgs) = bps == 1 ? gather_cache_kernel<kThreads>(tagged, w4, rpt)
-                                                 : gather_cache_kernel<kThreads / 2>(tagged, w4, rpt);
+            const bool group = gs_persist_sync_setting(ctx, g) != 4;
+            void (*kern)(PersistArgs) = bps == 1 ? gather_cache_kernel<kThreads>(tagged, w4, group, rpt)
+                                                 : gather_cache_kernel<kThreads / 2>(tagged, w4, group, rpt);
             if (tagged && !w4)  // 8-byte words: tag 0 is no stage
                 cudaMemsetAsync(args.tagged, 0, sizeof(unsigned long long) * 3 * (size_t)args.n, ctx->stream);
             if (tagged && w4) {  // 4-byte words: slot k must not start with stage k's parity

@@ -324,14 +324,15 @@ def _broad_pair(p):
 @pytest.mark.parametrize("t,K", [(5.0, 30), (0.5, 1), (1.0, 2)])
 def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph, t, K):
     # every persistent form (graph from global memory, slices in shared memory, gather cache with a
-    # grid barrier, neighbour flags or tagged values) and graph replay of the thread-per-row sliced-ELL kernel
+    # grid barrier, neighbour flags or tagged values re-read in groups or one at a time) and graph
+    # replay of the thread-per-row sliced-ELL kernel
     # sum in the same order; K = 1 (the only order is first and last) and K = 2 are the edge cases
     p, g, Ls = sphere_graph
     a, b = (p.a, p.b) if K > 2 else _broad_pair(p)
     out = {}
     gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 1)
     gs.gs_set_option(ctx, gs.GS_OPT_TAG_WORD, 8)  # exact exchange words: bitwise comparable
-    for cfg in ((0, 1, 1), (0, 0, 1), (0, 2, 0), (0, 2, 1), (0, 2, 2), (1, 1, 1)):
+    for cfg in ((0, 1, 1), (0, 0, 1), (0, 2, 0), (0, 2, 1), (0, 2, 2), (0, 2, 4), (1, 1, 1)):
         mode, smem, sync = cfg
         gs.gs_set_option(ctx, gs.GS_OPT_LOOP, mode)
         gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, smem)
@@ -351,7 +352,7 @@ def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph, t, K):
     gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 0)
     gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
     out2 = {}
-    for sync in (2, 1):
+    for sync in (2, 4, 1):
         gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, sync)
         u, v, d, _ = gs.gs_sinkhorn(ctx, g2, to_dev(a), to_dev(b), t, K, 120)
         gs.gs_sync(ctx)
@@ -371,6 +372,7 @@ def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph, t, K):
     ref = out[(0, 1, 1)]
     for i in range(3):
         np.testing.assert_array_equal(out2[2][i], out2[1][i], err_msg="two blocks per SM")
+        np.testing.assert_array_equal(out2[4][i], out2[1][i], err_msg="two blocks per SM, one at a time")
     assert out2[2][2][0] == pytest.approx(ref[2][0], rel=1e-6)
     for got, want in ((out2[2][0], ref[0]), (out2[2][1], ref[1])):
         m = want > 0
@@ -388,7 +390,7 @@ def test_sinkhorn_single_order_filter_matches_oracle(gs, ctx, sphere_graph):
     _check_sinkhorn(gs, ctx, g, Ls, a, b, 0.5, 1, 60)
 
 
-@pytest.mark.parametrize("sync,word", [(0, 4), (1, 4), (2, 4), (2, 8)])
+@pytest.mark.parametrize("sync,word", [(0, 4), (1, 4), (2, 4), (2, 8), (4, 4), (4, 8)])
 def test_persistent_barrier_timeout_is_reported_and_context_survives(gs, ctx, sphere_graph, sync, word):
     # the self-test makes every block wait for an arrival (or a stage) that never comes; the
     # bounded wait runs out, the launch ends, gs_sync reports the timeout, and the next call works
