@@ -259,7 +259,7 @@ extern "C" gs_status gs_knn(gs_ctx* ctx, const float* X, int64_t n, int d, int k
     if (bad_ptr(X) || bad_ptr(idx)) return gs_fail(ctx, GS_ERR_ARG, "null pointer");
     if (n < 2 || n >= ((int64_t)1 << 31) || d < 1 || d > 1024 || k < 1 || k > 24 || k >= n)
         return gs_fail(ctx, GS_ERR_ARG, "need 2 <= n < 2^31, 1 <= d <= 1024, 1 <= k <= 24, k < n");
-    return gs_knn_launch(ctx, X, n, d, k, idx, dist, nullptr);
+    return gs_knn_launch(ctx, X, n, d, k, idx, dist, nullptr, nullptr);
 }
 
 extern "C" gs_status gs_build_graph(gs_ctx* ctx, const float* X, int64_t n, int d, int k,

@@ -136,7 +136,7 @@ gs_status gs_graph_import_csr(gs_ctx* ctx, int64_t n, const int64_t* rowptr, con
         gs_graph_destroy(g);
         return gs_fail(ctx, GS_ERR_ARG, "rowptr not monotone or column index out of range");
     }
-    if ((st = gs_graph_finish(ctx, g)) != GS_OK || (st = gs_graph_reorder(ctx, g, nullptr, 0)) != GS_OK) {
+    if ((st = gs_graph_finish(ctx, g)) != GS_OK || (st = gs_graph_reorder(ctx, g, nullptr, 0, nullptr)) != GS_OK) {
         gs_graph_destroy(g);
         return st;
     }

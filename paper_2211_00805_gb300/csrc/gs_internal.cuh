@@ -226,7 +226,12 @@ gs_status gs_graph_export(gs_ctx* ctx, const gs_graph* g, int64_t* rowptr, int32
 // Node order of the filter: recursive coordinate bisection of the points X [n, d] (device FP32,
 // or null) into the persistent loop's partition, else breadth-first; then the sliced ELL and the
 // gather-cache tables.
-gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d);
+gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d, const int* points_order);
+// Coordinate bisection of the points into the persistent loop's partition (order.cu): *ord
+// (inside buf) receives position -> point, or stays null when the points cannot be bisected
+// (dimension, part sizes); buf holds gs_points_order_bytes(ctx, n, d) bytes (0: not possible).
+size_t gs_points_order_bytes(const gs_ctx* ctx, int64_t n, int d);
+gs_status gs_points_order(gs_ctx* ctx, const float* X, int64_t n, int d, void* buf, size_t bytes, int** ord);
 // Gather-cache tables for `blocks` partition blocks: on the given row ranges (parts, blocks + 1
 // boundaries), else on cost-balanced ranges.
 gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, const std::vector<int>* parts);
@@ -298,14 +303,16 @@ void gs_permute_rows(gs_ctx* ctx, int64_t n, int B, const int* perm, const float
 
 // --------------------------------------------------------------------- knn.cu
 void gs_exclusive_scan(cudaStream_t s, const int* cnt, int64_t n, int64_t* out, int64_t* sums);
+// ord: the points' bisection order (position -> point) for the tensor-memory screen, or null (it
+// is then computed in the workspace when the screen runs and the points can be bisected).
 gs_status gs_knn_launch(gs_ctx* ctx, const float* X, int64_t n, int d, int k, int32_t* idx,
-                        float* dist, double* dist64);
+                        float* dist, double* dist64, const int* ord);
 size_t gs_knn_ws_bytes(const gs_ctx* ctx, int64_t n, int d);
 // --------------------------------------------------------------------- knn_umma.cu
 size_t gs_knn_umma_bytes(int64_t n, int d);
 bool gs_knn_umma_available();
 gs_status gs_knn_screen_umma(gs_ctx* ctx, const float* X, const float* norms, int64_t n, int d,
-                             unsigned char* ws, int* cand);
+                             unsigned char* ws, const int* ord, int* cand);
 gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int k, float sigma,
                               gs_graph** out);
 

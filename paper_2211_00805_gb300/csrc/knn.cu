@@ -697,7 +697,7 @@ __global__ void rowptr_to32(int64_t n1, const int64_t* __restrict__ in, int* __r
 // 2 tensor-memory kernel (tcgen05; d + 2 <= 64), 1 warp-level TF32 MMA (d >= 16), 0 CUDA cores.
 struct KnnPlan {
     WsPlan p;
-    size_t inorm = 0, icand = 0, ihi = 0, ilo = 0, iumma = 0;
+    size_t inorm = 0, icand = 0, ihi = 0, ilo = 0, iumma = 0, iord = 0, ord_bytes = 0;
     int mode = 0;
 };
 
@@ -713,14 +713,18 @@ static KnnPlan knn_plan(const gs_ctx* ctx, int64_t n, int d)
         k.ihi = k.p.add(sizeof(float) * n * dp);
         k.ilo = k.p.add(sizeof(float) * n * dp);
     }
-    if (k.mode == 2) k.iumma = k.p.add(gs_knn_umma_bytes(n, d));
+    if (k.mode == 2) {
+        k.iumma = k.p.add(gs_knn_umma_bytes(n, d));
+        k.ord_bytes = gs_points_order_bytes(ctx, n, d);  // the screen's spatial order of the points
+        if (k.ord_bytes) k.iord = k.p.add(k.ord_bytes);
+    }
     return k;
 }
 
 size_t gs_knn_ws_bytes(const gs_ctx* ctx, int64_t n, int d) { return knn_plan(ctx, n, d).p.total; }
 
 gs_status gs_knn_launch(gs_ctx* ctx, const float* X, int64_t n, int d, int k, int32_t* idx,
-                        float* dist, double* dist64)
+                        float* dist, double* dist64, const int* ord)
 {
     const KnnPlan kp = knn_plan(ctx, n, d);
     const int dp = (d + 7) / 8 * 8;
@@ -732,7 +736,12 @@ gs_status gs_knn_launch(gs_ctx* ctx, const float* X, int64_t n, int d, int k, in
     gs_count(ctx, 1);
     bool screened = false;
     if (kp.mode == 2) {
-        st = gs_knn_screen_umma(ctx, X, norms, n, d, ws_at<unsigned char>(ctx, kp.p, kp.iumma), cand);
+        int* own = nullptr;
+        if (!ord && kp.ord_bytes &&
+            (st = gs_points_order(ctx, X, n, d, ws_at<void>(ctx, kp.p, kp.iord), kp.ord_bytes, &own)) != GS_OK)
+            return st;
+        st = gs_knn_screen_umma(ctx, X, norms, n, d, ws_at<unsigned char>(ctx, kp.p, kp.iumma), ord ? ord : own,
+                                cand);
         if (st == GS_OK) screened = true;
         else if (st != GS_ERR_UNSUPPORTED) return st;
     }
@@ -802,8 +811,24 @@ gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int
     double* sig = ws_at<double>(ctx, plan, i_sig);
     int* bad = ws_at<int>(ctx, plan, i_bad);
 
+    // 0: the points' coordinate bisection into the persistent loop's partition, used by the kNN
+    // screen's sweep and by the node order; in its own allocation (the stages below reuse the
+    // workspace)
+    void* obuf = nullptr;
+    int* ord = nullptr;
+    const size_t obytes = gs_points_order_bytes(ctx, n, d);
+    if (obytes && cudaMalloc(&obuf, obytes) != cudaSuccess) {
+        cudaGetLastError();
+        obuf = nullptr;  // the kNN and the reordering compute their own
+    }
+    struct FreeOnExit {
+        void* p;
+        ~FreeOnExit() { cudaFree(p); }
+    } free_obuf{obuf};
+    if (obuf && (st = gs_points_order(ctx, X, n, d, obuf, obytes, &ord)) != GS_OK) return st;
+
     // 1-2: kNN (front of the workspace holds norms and candidates)
-    if ((st = gs_knn_launch(ctx, X, n, d, k, idx, nullptr, d64)) != GS_OK) return st;
+    if ((st = gs_knn_launch(ctx, X, n, d, k, idx, nullptr, d64, ord)) != GS_OK) return st;
 
     // 3: sigma
     if (sigma > 0.f) {
@@ -867,7 +892,7 @@ gs_status gs_build_graph_impl(gs_ctx* ctx, const float* X, int64_t n, int d, int
         gs_graph_destroy(g);
         return gs_fail(ctx, GS_ERR_ARG, "graph has a node with zero degree");
     }
-    if ((st = gs_graph_reorder(ctx, g, X, d)) != GS_OK) {
+    if ((st = gs_graph_reorder(ctx, g, X, d, ord)) != GS_OK) {
         gs_graph_destroy(g);
         return st;
     }

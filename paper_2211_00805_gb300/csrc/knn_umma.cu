@@ -9,18 +9,23 @@
 // accumulated in FP32 in tensor memory.  The screen keeps, per query, the 32 smallest screened
 // distances (ties to the lower index); the FP64 rerank in knn.cu then fixes the exact k-list.
 //
-// One CTA owns 128 queries (the MMA's M) and streams all candidates in tiles of 128 (its N).  All
-// CTAs sweep the candidate tiles in the same order, so the CTAs resident at one time read the same
-// tile and it is served from L2 after its first fetch:
-//   warp 0    TMA producer: the query operands once, then every candidate tile's boxes into two
-//             shared stages (a stage is refilled once the MMAs have released it);
-//   warp 1    TMEM owner and MMA issuer (one thread): per tile 3 x ceil((d+2)/8) MMAs of
-//             128 x 128 x 8 into one of four TMEM accumulators, then commits to the stage's
-//             "empty" barrier and the accumulator's "full" barrier;
-//   warps 2-5 epilogue: thread = query row = TMEM lane; reads the tile's 128 distances
-//             (tcgen05.ld), tests them against its current threshold in a compact loop, inserts
-//             the rare hits into its top-32 list in shared memory (four groups of eight with
-//             their maxima, so an insertion rescans eight entries), frees the accumulator.
+// One CTA owns 128 queries (the MMA's M) and streams all candidates in tiles of 256 (its N: the
+// widest MMA, which does the most work per instruction).  All CTAs sweep the candidate tiles in
+// the same order, so the CTAs resident at one time read the same tile and it is served from L2
+// after its first fetch:
+//   warp 0    TMA producer: the query operands once, then the candidates unit by unit (one unit =
+//             the hi and lo boxes of one 32-feature K-block of one tile, 64 KB) into two shared
+//             stages, so one unit's copy runs while the MMAs read the other (a stage is refilled
+//             once the MMAs have released it);
+//   warp 1    TMEM owner and MMA issuer (one thread): per unit 3 MMAs of 128 x 256 x 8 for each
+//             of its k-steps (3 x ceil((d+2)/8) per tile) into one of two TMEM accumulators, then
+//             commits to the stage's "empty" barrier and, after a tile's last unit, to the
+//             accumulator's "full" barrier;
+//   warps 2-5 epilogue: thread = query row = TMEM lane; reads the tile's 256 distances
+//             (tcgen05.ld, 128 at a time), tests them against its current threshold in a compact
+//             loop, inserts the rare hits into its top-32 list in shared memory (four groups of
+//             eight with their maxima, so an insertion rescans eight entries), frees the
+//             accumulator.
 // Operands are K-major with the 128-byte swizzle that TMA writes and the MMA descriptors read.
 // Every wait is bounded by a clock budget; a timeout sets GS_FLAG_TIMEOUT and the CTA drains its
 // own copies and MMAs (bounded again) before it frees tensor memory and exits.
@@ -32,13 +37,14 @@
 namespace {
 
 constexpr int UM = 128;                 // queries per CTA (MMA M = TMEM lanes)
-constexpr int UN = 128;                 // candidates per tile (MMA N = accumulator columns)
+constexpr int UN = 256;                 // candidates per tile (MMA N = accumulator columns)
 constexpr int UKB = 32;                 // features per K-block: one 128-byte swizzle row of FP32
 constexpr int UTHREADS = 192;           // 6 warps
 constexpr int BOXA = UM * 128;          // bytes of one query K-block box (128 rows x 128 B)
 constexpr int BOX = UN * 128;           // bytes of one candidate K-block box (128 rows x 128 B)
-constexpr int STAGES = 2;               // candidate tiles in flight in shared memory
-constexpr int NACC = 4;                 // accumulators in tensor memory
+constexpr int STAGES = 2;               // candidate units (one K-block of one tile) in shared memory
+constexpr int NACC = 2;                 // accumulators in tensor memory
+constexpr int UHALF = 128;              // columns the epilogue reads per pass (registers)
 constexpr int LIST = 32;                // screened candidates per query
 constexpr int TMEM_COLS = NACC * UN;    // 512 columns: all of tensor memory
 constexpr long long kBudget = 2000000000ll;  // clock cycles per wait (~1 s)
@@ -151,6 +157,7 @@ struct TopList {
     float gd0, gd1, gd2, gd3;
     int gi0, gi1, gi2, gi3, gp0, gp1, gp2, gp3;
     float thr;  // distance of the worst entry overall
+    int thr_i;  // its index
     int wg;     // its group
 
     __device__ __forceinline__ static bool worse(float da, int ia, float db, int ib)
@@ -170,12 +177,12 @@ struct TopList {
         gi0 = gi1 = gi2 = gi3 = 0x7fffffff;
         gp0 = gp1 = gp2 = gp3 = 0;
         thr = INFINITY;
+        thr_i = 0x7fffffff;
         wg = 0;
     }
 
-    // Replace the worst entry by (dv, iv), rescan its group, find the new worst group.  The
-    // candidates of a query arrive in increasing index order, so a candidate tied with the worst
-    // entry never ranks before it: the strict test dv < thr is the (distance, index) order.
+    // Replace the worst entry by (dv, iv), rescan its group, find the new worst group.  A
+    // candidate enters when it ranks before the worst entry in the (distance, index) order.
     __device__ __forceinline__ void insert(float dv, int iv)
     {
         const int g = wg;
@@ -206,14 +213,15 @@ struct TopList {
         if (worse(gd3, gi3, bd, bi)) { bd = gd3; bi = gi3; w = 3; }
         wg = w;
         thr = bd;
+        thr_i = bi;
     }
 };
 
 template <int KB>
 struct UmmaLayout {
     static constexpr int A = 0;                                  // [hi, lo][KB] query boxes
-    static constexpr int B = A + 2 * KB * BOXA;                  // [stage][hi, lo][KB] boxes
-    static constexpr int LD = B + STAGES * 2 * KB * BOX;         // list distances [32][UM]
+    static constexpr int B = A + 2 * KB * BOXA;                  // [stage][hi, lo] boxes of one K-block
+    static constexpr int LD = B + STAGES * 2 * BOX;              // list distances [32][UM]
     static constexpr int LI = LD + LIST * UM * 4;                // list indices [32][UM]
     static constexpr int NBAR = 2 + 2 * STAGES + 2 * NACC;
     static constexpr int BAR = LI + LIST * UM * 4;               // NBAR mbarriers
@@ -226,7 +234,8 @@ template <int KB>
 __global__ void __launch_bounds__(UTHREADS, 1)
     knn_screen_umma(const __grid_constant__ CUtensorMap tq_hi, const __grid_constant__ CUtensorMap tq_lo,
                     const __grid_constant__ CUtensorMap tc_hi, const __grid_constant__ CUtensorMap tc_lo,
-                    int n, int ksteps, int* __restrict__ cand, int* __restrict__ flags)
+                    int n, int ksteps, const int* __restrict__ ord, int* __restrict__ cand,
+                    int* __restrict__ flags)
 {
     using L = UmmaLayout<KB>;
     extern __shared__ unsigned char um_raw[];
@@ -244,10 +253,14 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q0 = blockIdx.x * UM;
     const int ntiles = (n + UN - 1) / UN;
-    // All CTAs sweep the candidate tiles in the same (increasing) order, so the CTAs running at
-    // the same time read the same tile from L2, and every query sees its candidates in increasing
-    // index order.
-    auto tile_of = [](int t) { return t; };
+    const int nunits = ntiles * KB;
+    // Points in the bisection order (ord: position -> point): each CTA starts its sweep at the tile
+    // holding its own queries, whose neighbours mostly lie in the same part of the bisection, so its
+    // top-32 thresholds fall within the first tiles and later tiles rarely insert.  Points in the
+    // caller's order: all CTAs sweep in the same order.  Either way the CTAs resident at one time
+    // read few distinct tiles, served from L2.
+    const int rot = ord ? (int)(((int64_t)blockIdx.x * UM / UN) % ntiles) : 0;
+    auto tile_of = [rot, ntiles](int t) { const int u = t + rot; return u >= ntiles ? u - ntiles : u; };
 
     if (threadIdx.x == 0) {
         s_ok = 1;
@@ -282,28 +295,27 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                 tma_load_2d(sm + L::A + kb * BOXA, &tq_hi, kb * UKB, q0, full_a);
                 tma_load_2d(sm + L::A + (KB + kb) * BOXA, &tq_lo, kb * UKB, q0, full_a);
             }
+            // unit u = K-block u % KB of tile u / KB: its hi and lo boxes into stage u % STAGES,
+            // so the next unit's copy runs while the MMAs read the other stage
             int issued = 0;
-            for (int t = 0; t < ntiles; ++t) {
-                const int s = t % STAGES;
-                if (t >= STAGES && !mbar_wait(empty + s, ((t / STAGES) - 1) & 1)) {
+            for (int u = 0; u < nunits; ++u) {
+                const int s = u % STAGES;
+                if (u >= STAGES && !mbar_wait(empty + s, ((u / STAGES) - 1) & 1)) {
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(full + s, 2 * KB * BOX);
-                unsigned char* st = sm + L::B + s * 2 * KB * BOX;
-                const int y = tile_of(t) * UN;
-                for (int bx = 0; bx < 2 * KB; ++bx) {  // box bx: operand bx / KB (hi, lo), block bx % KB
-                    const CUtensorMap* map = bx < KB ? &tc_hi : &tc_lo;
-                    const int kb = bx % KB;
-                    tma_load_2d(st + bx * BOX, map, kb * UKB, y, full + s);
-                }
-                issued = t + 1;
+                mbar_expect_tx(full + s, 2 * BOX);
+                unsigned char* st = sm + L::B + s * 2 * BOX;
+                const int y = tile_of(u / KB) * UN, kb = u % KB;
+                tma_load_2d(st, &tc_hi, kb * UKB, y, full + s);
+                tma_load_2d(st + BOX, &tc_lo, kb * UKB, y, full + s);
+                issued = u + 1;
             }
             // every copy into this CTA has landed and the MMAs have released the last stages
             // before the CTA may exit
-            for (int t = (issued > STAGES ? issued - STAGES : 0); t < issued; ++t) {
-                if (!mbar_wait(full + t % STAGES, (t / STAGES) & 1)) ok = false;
-                if (!mbar_wait(empty + t % STAGES, (t / STAGES) & 1)) ok = false;
+            for (int u = (issued > STAGES ? issued - STAGES : 0); u < issued; ++u) {
+                if (!mbar_wait(full + u % STAGES, (u / STAGES) & 1)) ok = false;
+                if (!mbar_wait(empty + u % STAGES, (u / STAGES) & 1)) ok = false;
             }
             if (!mbar_wait(full_a, 0)) ok = false;
             if (!ok) {
@@ -317,17 +329,18 @@ __global__ void __launch_bounds__(UTHREADS, 1)
             constexpr uint32_t idesc = umma_idesc_tf32(UM, UN);
             bool ok = mbar_wait(full_a, 0);
             const uint32_t a_hi = su32(sm + L::A), a_lo = su32(sm + L::A + KB * BOXA);
-            for (int t = 0; ok && t < ntiles; ++t) {
-                const int s = t % STAGES, b = t % NACC;
-                if (!mbar_wait(full + s, (t / STAGES) & 1)) { ok = false; break; }
-                if (t >= NACC && !mbar_wait(acce + b, ((t / NACC) - 1) & 1)) { ok = false; break; }
+            for (int u = 0; ok && u < nunits; ++u) {
+                const int s = u % STAGES, t = u / KB, kb = u % KB, b = t % NACC;
+                if (!mbar_wait(full + s, (u / STAGES) & 1)) { ok = false; break; }
+                if (kb == 0 && t >= NACC && !mbar_wait(acce + b, ((t / NACC) - 1) & 1)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tbase + (uint32_t)(b * UN);
-                const uint32_t b_hi = su32(sm + L::B + s * 2 * KB * BOX);
-                const uint32_t b_lo = b_hi + KB * BOX;
-                for (int ks = 0; ks < ksteps; ++ks) {
-                    const uint32_t offa = (uint32_t)((ks >> 2) * BOXA + (ks & 3) * 32);
-                    const uint32_t offb = (uint32_t)((ks >> 2) * BOX + (ks & 3) * 32);
+                const uint32_t b_hi = su32(sm + L::B + s * 2 * BOX);
+                const uint32_t b_lo = b_hi + BOX;
+                const int ks1 = 4 * kb + 4 < ksteps ? 4 * kb + 4 : ksteps;  // this K-block's k-steps
+                for (int ks = 4 * kb; ks < ks1; ++ks) {
+                    const uint32_t offa = (uint32_t)(kb * BOXA + (ks & 3) * 32);
+                    const uint32_t offb = (uint32_t)((ks & 3) * 32);
                     const uint64_t ah = sw128_desc(a_hi + offa), al = sw128_desc(a_lo + offa);
                     const uint64_t bh = sw128_desc(b_hi + offb), bl = sw128_desc(b_lo + offb);
                     umma_tf32(d_tmem, al, bh, idesc, ks > 0 ? 1u : 0u);
@@ -335,7 +348,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
                     umma_tf32(d_tmem, ah, bh, idesc, 1u);
                 }
                 umma_commit(empty + s);
-                umma_commit(accf + b);
+                if (kb == KB - 1) umma_commit(accf + b);
             }
             // all MMAs issued by this thread have completed before tensor memory is freed
             umma_commit(drain);
@@ -354,6 +367,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
         tl.init(reinterpret_cast<float*>(sm + L::LD), reinterpret_cast<int*>(sm + L::LI), row);
         // rows past n (zero-filled by TMA) score 0 against everything: they test nothing
         if (q >= n) tl.thr = -INFINITY;
+        const int qo = (q < n && ord) ? __ldg(ord + q) : q;  // the query's own index
         bool ok = true;
         for (int t = 0; t < ntiles; ++t) {
             const int b = t % NACC;
@@ -361,41 +375,45 @@ __global__ void __launch_bounds__(UTHREADS, 1)
             if (!__all_sync(0xffffffffu, mbar_wait(accf + b, (t / NACC) & 1))) { ok = false; break; }
             tc_fence_after();
             const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * UN);
-            float v[UN / 32][32];
-            __syncwarp();
+            for (int hb = 0; hb < UN; hb += UHALF) {  // one pass per UHALF columns
+                float v[UHALF / 32][32];
+                __syncwarp();
 #pragma unroll
-            for (int h = 0; h < UN / 32; ++h) tmem_ld32(ta + (uint32_t)(32 * h), v[h]);
-            tmem_wait_ld();
-            // per chunk of 32: the minimum (a depth-5 tree; the chunks' trees are independent, so
-            // they overlap) against the threshold; most chunks have no hit, and the rare hits
-            // are inserted one at a time through a single copy of the insertion code
-            float mn[UN / 32];
+                for (int h = 0; h < UHALF / 32; ++h) tmem_ld32(ta + (uint32_t)(hb + 32 * h), v[h]);
+                tmem_wait_ld();
+                // per chunk of 32: the minimum (a depth-5 tree; the chunks' trees are independent, so
+                // they overlap) against the threshold; most chunks have no hit, and the rare hits
+                // are inserted one at a time through a single copy of the insertion code
+                float mn[UHALF / 32];
 #pragma unroll
-            for (int h = 0; h < UN / 32; ++h) {
-                float m16[16], m8[8], m4[4];
+                for (int h = 0; h < UHALF / 32; ++h) {
+                    float m16[16], m8[8], m4[4];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) m16[j] = fminf(v[h][j], v[h][j + 16]);
+                    for (int j = 0; j < 16; ++j) m16[j] = fminf(v[h][j], v[h][j + 16]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) m8[j] = fminf(m16[j], m16[j + 8]);
+                    for (int j = 0; j < 8; ++j) m8[j] = fminf(m16[j], m16[j + 8]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) m4[j] = fminf(m8[j], m8[j + 4]);
-                mn[h] = fminf(fminf(m4[0], m4[2]), fminf(m4[1], m4[3]));
-            }
+                    for (int j = 0; j < 4; ++j) m4[j] = fminf(m8[j], m8[j + 4]);
+                    mn[h] = fminf(fminf(m4[0], m4[2]), fminf(m4[1], m4[3]));
+                }
 #pragma unroll
-            for (int h = 0; h < UN / 32; ++h) {
-                if (!(mn[h] < tl.thr)) continue;
-                const int cbase = tile_of(t) * UN + 32 * h;
-                uint32_t hits = 0;
+                for (int h = 0; h < UHALF / 32; ++h) {
+                    if (!(mn[h] <= tl.thr)) continue;
+                    const int cbase = tile_of(t) * UN + hb + 32 * h;
+                    uint32_t hits = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) hits |= (v[h][j] < tl.thr) ? (1u << j) : 0u;
-                while (hits) {
-                    const int j = __ffs(hits) - 1;
-                    hits &= hits - 1;
-                    float dv = v[h][0];
+                    for (int j = 0; j < 32; ++j) hits |= (v[h][j] <= tl.thr) ? (1u << j) : 0u;
+                    while (hits) {
+                        const int j = __ffs(hits) - 1;
+                        hits &= hits - 1;
+                        float dv = v[h][0];
 #pragma unroll
-                    for (int jj = 1; jj < 32; ++jj) dv = (jj == j) ? v[h][jj] : dv;
-                    const int ci = cbase + j;
-                    if (dv < tl.thr && ci < n && ci != q) tl.insert(dv, ci);
+                        for (int jj = 1; jj < 32; ++jj) dv = (jj == j) ? v[h][jj] : dv;
+                        const int ci = cbase + j;
+                        if (ci >= n || ci == q || !(dv <= tl.thr)) continue;
+                        const int co = ord ? __ldg(ord + ci) : ci;  // the candidate's own index
+                        if (dv < tl.thr || co < tl.thr_i) tl.insert(dv, co);
+                    }
                 }
             }
             tc_fence_before();
@@ -406,7 +424,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
             s_ok = 0;
         }
         if (q < n) {
-            for (int e = 0; e < LIST; ++e) cand[(int64_t)q * LIST + e] = tl.i[e * UM + row];
+            for (int e = 0; e < LIST; ++e) cand[(int64_t)qo * LIST + e] = tl.i[e * UM + row];
         }
     }
     tc_fence_before();
@@ -418,15 +436,17 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     }
 }
 
-// Augmented 3xTF32 operands: rows [n][32 KB] of q' = (x, 1, |x|^2) and c' = (-2x, |x|^2, 1).
+// Augmented 3xTF32 operands: rows [n][32 KB] of q' = (x, 1, |x|^2) and c' = (-2x, |x|^2, 1), row r
+// holding point ord[r] (or r).
 __global__ void umma_operands(const float* __restrict__ X, const float* __restrict__ norms, int64_t n,
-                              int d, int w, float* __restrict__ qh, float* __restrict__ ql,
-                              float* __restrict__ ch, float* __restrict__ cl)
+                              int d, int w, const int* __restrict__ ord, float* __restrict__ qh,
+                              float* __restrict__ ql, float* __restrict__ ch, float* __restrict__ cl)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * w) return;
-    const int64_t r = e / w;
-    const int j = (int)(e - r * w);
+    const int64_t rr = e / w;
+    const int j = (int)(e - rr * w);
+    const int64_t r = ord ? (int64_t)ord[rr] : rr;
     float qv = 0.f, cv = 0.f;
     if (j < d) {
         const float x = X[r * d + j];
@@ -484,7 +504,7 @@ bool make_map(CUtensorMap* m, const float* base, int64_t n, int w, int rows)
 }
 
 template <int KB>
-gs_status launch_umma(gs_ctx* ctx, const CUtensorMap* maps, int64_t n, int ksteps, int* cand)
+gs_status launch_umma(gs_ctx* ctx, const CUtensorMap* maps, int64_t n, int ksteps, const int* ord, int* cand)
 {
     using L = UmmaLayout<KB>;
     static int ready = 0;  // 1 usable, -1 not
@@ -498,7 +518,7 @@ gs_status launch_umma(gs_ctx* ctx, const CUtensorMap* maps, int64_t n, int kstep
     if (ready < 0) return GS_ERR_UNSUPPORTED;
     const unsigned grid = (unsigned)((n + UM - 1) / UM);
     knn_screen_umma<KB><<<grid, UTHREADS, L::ALLOC, ctx->stream>>>(maps[0], maps[1], maps[2], maps[3], (int)n,
-                                                                   ksteps, cand, ctx->flags);
+                                                                   ksteps, ord, cand, ctx->flags);
     if (cudaGetLastError() != cudaSuccess) return GS_ERR_UNSUPPORTED;
     gs_count(ctx, 1);
     return GS_OK;
@@ -517,10 +537,12 @@ size_t gs_knn_umma_bytes(int64_t n, int d)
 }
 
 // Screen the 32 nearest candidates of every point with the tensor-memory kernel.  `ws` holds
-// gs_knn_umma_bytes(n, d) bytes (256-byte aligned); `norms` are the FP32 squared norms.
+// gs_knn_umma_bytes(n, d) bytes (256-byte aligned); `norms` are the FP32 squared norms; `ord`
+// (position -> point, or null) lays the points out in a spatial order for the sweep; lists and
+// tie-breaking use the points' own indices either way.
 // Returns GS_ERR_UNSUPPORTED (nothing enqueued) when the shape or the driver does not allow it.
 gs_status gs_knn_screen_umma(gs_ctx* ctx, const float* X, const float* norms, int64_t n, int d,
-                             unsigned char* ws, int* cand)
+                             unsigned char* ws, const int* ord, int* cand)
 {
     if (!gs_knn_umma_bytes(n, d) || !tensor_map_encoder()) return GS_ERR_UNSUPPORTED;
     const int kb = d + 2 <= UKB ? 1 : 2;
@@ -534,8 +556,8 @@ gs_status gs_knn_screen_umma(gs_ctx* ctx, const float* X, const float* norms, in
     if (!make_map(&maps[0], qh, n, w, UM) || !make_map(&maps[1], ql, n, w, UM) || !make_map(&maps[2], ch, n, w, UN) ||
         !make_map(&maps[3], cl, n, w, UN))
         return GS_ERR_UNSUPPORTED;
-    umma_operands<<<(unsigned)((n * w + 255) / 256), 256, 0, ctx->stream>>>(X, norms, n, d, w, qh, ql, ch, cl);
+    umma_operands<<<(unsigned)((n * w + 255) / 256), 256, 0, ctx->stream>>>(X, norms, n, d, w, ord, qh, ql, ch, cl);
     gs_count(ctx, 1);
     const int ksteps = (d + 2 + 7) / 8;
-    return kb == 1 ? launch_umma<1>(ctx, maps, n, ksteps, cand) : launch_umma<2>(ctx, maps, n, ksteps, cand);
+    return kb == 1 ? launch_umma<1>(ctx, maps, n, ksteps, ord, cand) : launch_umma<2>(ctx, maps, n, ksteps, ord, cand);
 }

@@ -512,13 +512,12 @@ void gs_permute_rows(gs_ctx* ctx, int64_t n, int B, const int* perm, const float
 }
 
 // Recursive coordinate bisection of the points X [n, d] into the parts [parts[b], parts[b+1]) of
-// the order, then decreasing degree inside each part; writes g->perm.  ord / ord2: n ints of
-// scratch.  Every level is a handful of launches with no host synchronisation.
-static gs_status rcb_order(gs_ctx* ctx, gs_graph* g, const float* X, int d, const std::vector<int>& parts,
-                           int* ord, int* ord2, void* scratch, size_t scratch_bytes)
+// the order: *result (ord or ord2, n ints each) receives position -> point.  Every level is a
+// handful of launches with no host synchronisation.
+static gs_status rcb_points(gs_ctx* ctx, const float* X, int64_t n, int d, const std::vector<int>& parts,
+                            int* ord, int* ord2, void* scratch, size_t scratch_bytes, int** result)
 {
     cudaStream_t s = ctx->stream;
-    const int64_t n = g->n;
     const int P = (int)parts.size() - 1;
     const int max_chunks = (int)((n + kRcbChunk - 1) / kRcbChunk) + P;
     // scratch layout
@@ -538,7 +537,6 @@ static gs_status rcb_order(gs_ctx* ctx, gs_graph* g, const float* X, int d, cons
     int* base = static_cast<int*>(take(sizeof(int) * 3 * (size_t)max_chunks));
     RcbSeg* segs_d = static_cast<RcbSeg*>(take(sizeof(RcbSeg) * (size_t)P));
     RcbChunk* chunks_d = static_cast<RcbChunk*>(take(sizeof(RcbChunk) * (size_t)max_chunks));
-    int* parts_d = static_cast<int*>(take(sizeof(int) * ((size_t)P + 1)));
     if (off > scratch_bytes) return gs_fail(ctx, GS_ERR_OOM, "bisection scratch");
 
     const int S_max = kRcbSampleFloats / d;
@@ -587,13 +585,46 @@ static gs_status rcb_order(gs_ctx* ctx, gs_graph* g, const float* X, int d, cons
         }
         cur.swap(next);
     }
-    int maxpart = 0;
-    for (int b = 0; b < P; ++b) maxpart = std::max(maxpart, parts[(size_t)b + 1] - parts[(size_t)b]);
-    cudaMemcpyAsync(parts_d, parts.data(), sizeof(int) * ((size_t)P + 1), cudaMemcpyHostToDevice, s);
-    cudaFuncSetAttribute(part_degree_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * maxpart));
-    part_degree_sort<<<P, 256, sizeof(int) * std::max(maxpart, 1), s>>>(parts_d, ord, g->rowptr, g->perm);
-    gs_count(ctx, 1);
+    *result = ord;
     return gs_cuda_check(ctx, cudaGetLastError(), "coordinate bisection");
+}
+
+// Scratch bytes of rcb_points for n points of dimension d in P parts.
+static size_t rcb_scratch_bytes(int64_t n, int d, int64_t P)
+{
+    const int64_t chunks = (n + kRcbChunk - 1) / kRcbChunk + P;
+    return (size_t)(2 * n + 4 * P * kRcbBins + 8 * P * (d > 0 ? d : 1) + 16 * P + 20 * chunks + 12 * chunks +
+                    24 * P + 4 * (P + 1) + 16 * 256);
+}
+
+// The persistent loop's partition of n rows when the points can be bisected into it (each part
+// small enough for the in-part degree sort), else empty.
+static std::vector<int> rcb_parts(const gs_ctx* ctx, int64_t n, int d)
+{
+    const int blocks = gs_persist_cache_blocks(ctx);
+    if (d < 1 || d > kRcbMaxDim || blocks < 2 || n < 2) return {};
+    std::vector<int> parts = gs_equal_slice_rows(n, blocks);
+    for (int b = 0; b < blocks; ++b)
+        if (parts[(size_t)b + 1] - parts[(size_t)b] > kRcbMaxPart) return {};
+    return parts;
+}
+
+size_t gs_points_order_bytes(const gs_ctx* ctx, int64_t n, int d)
+{
+    const std::vector<int> parts = rcb_parts(ctx, n, d);
+    if (parts.empty()) return 0;
+    return sizeof(int) * 2 * (size_t)n + 256 + rcb_scratch_bytes(n, d, (int64_t)parts.size() - 1);
+}
+
+gs_status gs_points_order(gs_ctx* ctx, const float* X, int64_t n, int d, void* buf, size_t bytes, int** ord)
+{
+    *ord = nullptr;
+    const std::vector<int> parts = rcb_parts(ctx, n, d);
+    if (parts.empty() || bytes < gs_points_order_bytes(ctx, n, d)) return GS_OK;
+    int* a = static_cast<int*>(buf);
+    int* b = a + n;
+    void* scratch = static_cast<char*>(buf) + ((sizeof(int) * 2 * (size_t)n + 255) & ~(size_t)255);
+    return rcb_points(ctx, X, n, d, parts, a, b, scratch, rcb_scratch_bytes(n, d, (int64_t)parts.size() - 1), ord);
 }
 
 // One breadth-first sweep from `root` (device int), producing perm/iperm over all components.
@@ -637,7 +668,7 @@ static gs_status bfs_sweep(gs_ctx* ctx, const gs_graph* g, const int* root, int*
     return gs_cuda_check(ctx, cudaGetLastError(), "node ordering");
 }
 
-gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d)
+gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d, const int* points_order)
 {
     const int64_t n = g->n, nnz = g->nnz;
     WsPlan plan;
@@ -647,10 +678,8 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d)
                  i_p64 = plan.add(sizeof(int64_t) * (n + 1)), i_hflag = plan.add(sizeof(int) * n),
                  i_h64 = plan.add(sizeof(int64_t) * (n + 1));
     // coordinate bisection scratch (bins, histograms, per-segment statistics, chunk tables)
-    const int64_t P_ = gs_persist_cache_blocks(ctx), chunks_ = (n + kRcbChunk - 1) / kRcbChunk + P_;
-    const size_t rcb_bytes = (X != nullptr) ? (size_t)(2 * n + 4 * P_ * kRcbBins + 8 * P_ * (d > 0 ? d : 1) + 16 * P_ +
-                                                       20 * chunks_ + 12 * chunks_ + 24 * P_ + 4 * (P_ + 1) + 16 * 256)
-                                            : 0;
+    const int64_t P_ = gs_persist_cache_blocks(ctx);
+    const size_t rcb_bytes = (X != nullptr && !points_order) ? rcb_scratch_bytes(n, d, P_) : 0;
     const size_t i_rcb = plan.add(rcb_bytes > 0 ? rcb_bytes : 1);
     gs_status st = gs_ws_ensure(ctx, plan.total);
     if (st != GS_OK) return st;
@@ -676,15 +705,28 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d)
     // points given: recursive coordinate bisection into the persistent loop's partition (when the
     // parts fit the in-part sort); otherwise the breadth-first order
     const int blocks = gs_persist_cache_blocks(ctx);
-    std::vector<int> parts;
-    bool rcb = X != nullptr && d >= 1 && d <= kRcbMaxDim && blocks >= 2 && n >= 2;
+    const std::vector<int> parts = X != nullptr ? rcb_parts(ctx, n, d) : std::vector<int>();
+    const bool rcb = !parts.empty();
     if (rcb) {
-        parts = gs_equal_slice_rows(n, blocks);
-        for (int b = 0; b < blocks && rcb; ++b) rcb = parts[(size_t)b + 1] - parts[(size_t)b] <= kRcbMaxPart;
-    }
-    if (rcb) {
-        if ((st = rcb_order(ctx, g, X, d, parts, owner, cnt, ws_at<void>(ctx, plan, i_rcb), rcb_bytes)) != GS_OK)
-            return st;
+        // the bisection order of the points (given, or computed here), then decreasing degree
+        // inside each part
+        const int* ord = points_order;
+        if (!ord) {
+            int* res = nullptr;
+            if ((st = rcb_points(ctx, X, n, d, parts, owner, cnt, ws_at<void>(ctx, plan, i_rcb), rcb_bytes, &res)) !=
+                GS_OK)
+                return st;
+            ord = res;
+        }
+        const int P = (int)parts.size() - 1;
+        int maxpart = 0;
+        for (int b = 0; b < P; ++b) maxpart = std::max(maxpart, parts[(size_t)b + 1] - parts[(size_t)b]);
+        int* parts_d = reinterpret_cast<int*>(p64);  // free until the permuted CSR below (P + 1 <= n + 1)
+        cudaMemcpyAsync(parts_d, parts.data(), sizeof(int) * ((size_t)P + 1), cudaMemcpyHostToDevice, s);
+        cudaFuncSetAttribute(part_degree_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(int) * maxpart));
+        part_degree_sort<<<P, 256, sizeof(int) * std::max(maxpart, 1), s>>>(parts_d, ord, g->rowptr, g->perm);
+        gs_count(ctx, 1);
         g->levels = 0;
         invert_perm<<<nblk(n, 256), 256, 0, s>>>(n, g->perm, g->iperm);
         gs_count(ctx, 1);
