@@ -156,6 +156,17 @@ def test_knn_manifold_sampled_rows(gs, ctx):
     assert knn_lists_match(to_np(idx)[rows], to_np(dist)[rows], ri, rd, X, rows=rows) == 0
 
 
+def test_knn_screen_in_caller_order_above_the_bisection_limit(gs, ctx):
+    # With more points than the persistent loop's partition can bisect (152 parts of at most 4,096
+    # points on this GPU) the tensor-memory screen sweeps the candidates in the caller's order
+    # instead of the bisection order; lists and ties follow the same (distance, index) order.
+    X, _ = W.tanh_manifold(700_000, 4, 8, seed=9)
+    idx, dist = gs.gs_knn(ctx, to_dev(X), 10)
+    rows = np.random.default_rng(1).choice(len(X), 200, replace=False)
+    ri, rd = oracle.knn(X.astype(np.float64), 10, rows=rows)
+    assert knn_lists_match(to_np(idx)[rows], to_np(dist)[rows], ri, rd, X, rows=rows) == 0
+
+
 def test_build_graph_matches_oracle(gs, ctx):
     p = W.sphere_pair()
     g = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
