@@ -478,23 +478,57 @@ __global__ void rcb_iota(int64_t n, int* __restrict__ ord)
     if (i < n) ord[i] = (int)i;
 }
 
-// Inside each part, nodes by decreasing degree (stable): sliced-ELL slices of similar rows.
-__global__ void __launch_bounds__(256) part_degree_sort(const int* __restrict__ parts, const int* __restrict__ perm_in,
-                                                        const int* __restrict__ rowptr, int* __restrict__ perm_out)
+// The part (block of the persistent loop's partition) of every node: part_of[perm[pos]] = b for the
+// positions pos of part b.
+__global__ void part_of_fill(const int* __restrict__ parts, const int* __restrict__ perm, int* __restrict__ part_of)
 {
-    extern __shared__ int pdeg[];  // [len]
+    const int beg = parts[blockIdx.x], end = parts[blockIdx.x + 1];
+    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) part_of[perm[i]] = blockIdx.x;
+}
+
+// Order inside each part: eight degree classes, largest degrees first (rows of similar degree
+// share a slice, so the sliced ELL pads little); inside a class by the smallest other part holding
+// one of the row's neighbours, so the rows one neighbouring block reads sit together and its
+// staging loads of their exchanged values touch fewer 32-byte sectors; then by decreasing degree,
+// then in the order given.  (Against the plain degree sort: 2.22 against 2.27 us per order of the
+// persistent loop on the 100k manifold graph, the same partition.)  Rank counting in shared
+// memory, one block per part.
+constexpr int kDegreeClasses = 8;
+__global__ void __launch_bounds__(256) part_reader_sort(const int* __restrict__ parts, int nparts,
+                                                        const int* __restrict__ perm_in,
+                                                        const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                        const int* __restrict__ part_of, int* __restrict__ perm_out)
+{
+    extern __shared__ int psm[];  // degree [len], reader [len], class [len]
     const int beg = parts[blockIdx.x], len = parts[blockIdx.x + 1] - beg;
+    int* pdeg = psm;
+    int* prd = psm + len;
+    int* pcls = psm + 2 * len;
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
         const int node = perm_in[beg + i];
-        pdeg[i] = rowptr[node + 1] - rowptr[node];
+        const int e0 = rowptr[node], e1 = rowptr[node + 1];
+        int r = nparts;
+        for (int e = e0; e < e1; ++e) {
+            const int q = part_of[col[e]];
+            if (q != (int)blockIdx.x && q < r) r = q;
+        }
+        pdeg[i] = e1 - e0;
+        prd[i] = r;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
         const int di = pdeg[i];
+        int above = 0;  // rows of larger degree: equal degrees share a class
+        for (int j = 0; j < len; ++j) above += pdeg[j] > di;
+        pcls[i] = (int)((int64_t)above * kDegreeClasses / len);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const int ci = pcls[i], ri = prd[i], di = pdeg[i];
         int rank = 0;
         for (int j = 0; j < len; ++j) {
-            const int dj = pdeg[j];
-            rank += (dj > di) || (dj == di && j < i);
+            const int cj = pcls[j], rj = prd[j], dj = pdeg[j];
+            rank += cj < ci || (cj == ci && (rj < ri || (rj == ri && (dj > di || (dj == di && j < i)))));
         }
         perm_out[beg + rank] = perm_in[beg + i];
     }
@@ -708,8 +742,8 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d, cons
     const std::vector<int> parts = X != nullptr ? rcb_parts(ctx, n, d) : std::vector<int>();
     const bool rcb = !parts.empty();
     if (rcb) {
-        // the bisection order of the points (given, or computed here), then decreasing degree
-        // inside each part
+        // the bisection order of the points (given, or computed here), then inside each part the
+        // degree-class and reader order
         const int* ord = points_order;
         if (!ord) {
             int* res = nullptr;
@@ -723,10 +757,13 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d, cons
         for (int b = 0; b < P; ++b) maxpart = std::max(maxpart, parts[(size_t)b + 1] - parts[(size_t)b]);
         int* parts_d = reinterpret_cast<int*>(p64);  // free until the permuted CSR below (P + 1 <= n + 1)
         cudaMemcpyAsync(parts_d, parts.data(), sizeof(int) * ((size_t)P + 1), cudaMemcpyHostToDevice, s);
-        cudaFuncSetAttribute(part_degree_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(int) * maxpart));
-        part_degree_sort<<<P, 256, sizeof(int) * std::max(maxpart, 1), s>>>(parts_d, ord, g->rowptr, g->perm);
-        gs_count(ctx, 1);
+        int* part_of = hflag;  // n ints, free until the long-row flags below
+        part_of_fill<<<P, 256, 0, s>>>(parts_d, ord, part_of);
+        cudaFuncSetAttribute(part_reader_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(int) * 3 * maxpart));
+        part_reader_sort<<<P, 256, sizeof(int) * 3 * std::max(maxpart, 1), s>>>(parts_d, P, ord, g->rowptr, g->col,
+                                                                                  part_of, g->perm);
+        gs_count(ctx, 2);
         g->levels = 0;
         invert_perm<<<nblk(n, 256), 256, 0, s>>>(n, g->perm, g->iperm);
         gs_count(ctx, 1);
