@@ -36,10 +36,10 @@ WORKLOAD = dict(name="manifold-100k-R50: Geodesic Sinkhorn distance, graph build
                 n=100_000, latent=10, ambient=50, seed=2, k=15, K=30, t=5.0, iters=500)
 HBM_CASES = {
     "spmm_hbm": dict(name="clusters-200k-R30, B=32 heat filter", kind="clusters", n=200_000, dim=30,
-                     m=32, k=10, K=40, t=10.0, seed=3, tag="order_blk_clusters200k_B32"),
+                     m=32, k=10, K=40, t=10.0, seed=3, tag="order_blk_clusters200k_B32", node_order=0),
     "spmm_hbm_b64": dict(name="manifold-500k-R40, B=64 heat filter", kind="manifold", n=500_000,
                          latent=6, ambient=40, m=64, k=10, K=40, t=8.0, seed=4,
-                         tag="order_blk_manifold500k_B64"),
+                         tag="order_blk_manifold500k_B64", node_order=1),
 }
 L2_FLUSH_BYTES = 256 << 20
 
@@ -545,7 +545,7 @@ def hbm_case(gs, ctx, dev, stream, peak, peak_kind, c, reps=5):
     else:
         X, Z = W.tanh_manifold(c["n"], c["latent"], c["ambient"], c["seed"])
         M = np.random.default_rng(c["seed"]).random((c["n"], c["m"])).astype(np.float32)
-    g = gs.gs_build_graph(ctx, torch.from_numpy(X).to(dev), c["k"])
+    g = build_graph(gs, ctx, torch.from_numpy(X).to(dev), c["k"], c["node_order"])
     V = torch.from_numpy(M).to(dev)
     Y = torch.empty_like(V)
     for _ in range(2):
@@ -566,10 +566,22 @@ def hbm_case(gs, ctx, dev, stream, peak, peak_kind, c, reps=5):
            "apply_ms": s * 1e3, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
            "bytes_per_apply": byts, "peak_kind": f"{peak_kind} hbm_gbs",
            "bytes_per_order": byts / c["K"], "order_us": s * 1e6 / c["K"],
+           "node_order": c["node_order"],
            "note": "apply time includes the two [n, B] permutations into and out of the locality order",
            "traffic": ncu_traffic(c["tag"]), "traffic_unit": "DRAM bytes per order launch (ncu)"}
     g.close()
     return out
+
+
+def build_graph(gs, ctx, X, k, node_order=1):
+    """Graph build with the node order inside each bisection part set for this graph only: 1 groups
+    rows by the part that reads them (the default, best for the one-column loop), 0 orders by degree
+    alone (best for the row-group kernel of the many-column filters)."""
+    gs.gs_set_option(ctx, gs.GS_OPT_NODE_ORDER, node_order)
+    try:
+        return gs.gs_build_graph(ctx, X, k)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_NODE_ORDER, 1)
 
 
 def _time(stream, fn):
@@ -700,7 +712,7 @@ def families_case(gs, ctx, dev, stream, bary_iters=100, sink_iters=200):
     uniform weights, t = 10, K = 40; one library call each, timed with CUDA events."""
     import torch
     cfg = W.clusters_barycenter()
-    g = gs.gs_build_graph(ctx, torch.from_numpy(cfg["X"]).to(dev), cfg["k"])
+    g = build_graph(gs, ctx, torch.from_numpy(cfg["X"]).to(dev), cfg["k"], node_order=0)
     M = cfg["M"]
     MT = torch.from_numpy(np.ascontiguousarray(M[:, :16])).to(dev)
     MC = torch.from_numpy(np.ascontiguousarray(M[:, 16:])).to(dev)
@@ -776,7 +788,7 @@ def barycenter_case(gs, ctx, dev, stream, peak, peak_kind, iters=300):
     iterations per second and the counted bytes per Chebyshev order of the two [n, 32] applies."""
     import torch
     cfg = W.clusters_barycenter(iters=iters)
-    g = gs.gs_build_graph(ctx, torch.from_numpy(cfg["X"]).to(dev), cfg["k"])
+    g = build_graph(gs, ctx, torch.from_numpy(cfg["X"]).to(dev), cfg["k"], node_order=0)
     M = torch.from_numpy(cfg["M"]).to(dev)
     alpha = torch.tensor(cfg["alpha"], dtype=torch.float64, device=dev)
     mu = torch.empty(g.n, dtype=torch.float32, device=dev)

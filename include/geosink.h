@@ -142,9 +142,16 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * share a row (1, 2, 4, 8, 16 or 32; fewer lanes walk the row's columns in more passes, at most 8),
  * i.e. the RHS tile width; with GS_OPT_B1_KERNEL = 6, the threads per row (2, 4 or 8).  0 (default):
  * the kernel's own mapping.  gs_autotune times these widths itself; this option fixes one. */
+/* GS_OPT_NODE_ORDER: the order inside each part of the coordinate bisection for graphs built from
+ * points after the call.  1 (default): eight degree classes, inside a class the rows by the
+ * smallest neighbouring part that reads them (fastest for the one-column filter and the Sinkhorn
+ * loop, whose exchanged values a neighbouring block then stages from fewer memory sectors);
+ * 0: decreasing degree only (fastest for the several-column filter and the barycenter, whose row
+ * groups then hold rows of equal length).  Same results either way up to summation order. */
 enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
        GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6, GS_OPT_PERSIST_SYNC = 7,
-       GS_OPT_PERSIST_BLOCKS = 8, GS_OPT_TAG_WORD = 9, GS_OPT_CHECK_ARGS = 10, GS_OPT_TILE_LANES = 11 };
+       GS_OPT_PERSIST_BLOCKS = 8, GS_OPT_TAG_WORD = 9, GS_OPT_CHECK_ARGS = 10, GS_OPT_TILE_LANES = 11,
+       GS_OPT_NODE_ORDER = 12 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
 
 /* Host query of an option.  For GS_OPT_LOOP, GS_OPT_B1_KERNEL and GS_OPT_PERSIST_SYNC left on

@@ -180,6 +180,7 @@ GS_OPT_PERSIST_BLOCKS = 8
 GS_OPT_TAG_WORD = 9
 GS_OPT_CHECK_ARGS = 10
 GS_OPT_TILE_LANES = 11
+GS_OPT_NODE_ORDER = 12
 
 
 def gs_set_option(ctx: Context, option: int, value: int):

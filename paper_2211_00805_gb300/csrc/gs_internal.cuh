@@ -103,6 +103,7 @@ struct gs_ctx {
     int persist_bps = 1;           // gather-cache partition of graphs built from now on: blocks per
                                    // SM (1: 1024 threads each, 2: 512 threads each)
     int check_args = 1;            // device-side checks of marginals and barycenter weights (1 on)
+    int node_order = 1;            // inside each bisection part: 1 degree classes + reader, 0 degree
     int lanes_override = 0;        // autotuner trials: lanes per row (B > 1) / threads per row (B == 1)
     std::vector<TuneRecord> tune_log;  // gs_autotune decisions by (n, nnz, B, K)
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)

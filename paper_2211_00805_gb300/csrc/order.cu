@@ -494,7 +494,8 @@ __global__ void part_of_fill(const int* __restrict__ parts, const int* __restric
 // persistent loop on the 100k manifold graph, the same partition.)  Rank counting in shared
 // memory, one block per part.
 constexpr int kDegreeClasses = 8;
-__global__ void __launch_bounds__(256) part_reader_sort(const int* __restrict__ parts, int nparts,
+// by_reader = 0: decreasing degree only (then in the order given).
+__global__ void __launch_bounds__(256) part_reader_sort(const int* __restrict__ parts, int nparts, int by_reader,
                                                         const int* __restrict__ perm_in,
                                                         const int* __restrict__ rowptr, const int* __restrict__ col,
                                                         const int* __restrict__ part_of, int* __restrict__ perm_out)
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(256) part_reader_sort(const int* __restrict__ 
         const int node = perm_in[beg + i];
         const int e0 = rowptr[node], e1 = rowptr[node + 1];
         int r = nparts;
-        for (int e = e0; e < e1; ++e) {
+        for (int e = by_reader ? e0 : e1; e < e1; ++e) {
             const int q = part_of[col[e]];
             if (q != (int)blockIdx.x && q < r) r = q;
         }
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(256) part_reader_sort(const int* __restrict__ 
         const int di = pdeg[i];
         int above = 0;  // rows of larger degree: equal degrees share a class
         for (int j = 0; j < len; ++j) above += pdeg[j] > di;
-        pcls[i] = (int)((int64_t)above * kDegreeClasses / len);
+        pcls[i] = by_reader ? (int)((int64_t)above * kDegreeClasses / len) : 0;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
@@ -761,8 +762,8 @@ gs_status gs_graph_reorder(gs_ctx* ctx, gs_graph* g, const float* X, int d, cons
         part_of_fill<<<P, 256, 0, s>>>(parts_d, ord, part_of);
         cudaFuncSetAttribute(part_reader_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(int) * 3 * maxpart));
-        part_reader_sort<<<P, 256, sizeof(int) * 3 * std::max(maxpart, 1), s>>>(parts_d, P, ord, g->rowptr, g->col,
-                                                                                  part_of, g->perm);
+        part_reader_sort<<<P, 256, sizeof(int) * 3 * std::max(maxpart, 1), s>>>(parts_d, P, ctx->node_order, ord,
+                                                                                  g->rowptr, g->col, part_of, g->perm);
         gs_count(ctx, 2);
         g->levels = 0;
         invert_perm<<<nblk(n, 256), 256, 0, s>>>(n, g->perm, g->iperm);

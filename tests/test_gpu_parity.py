@@ -394,6 +394,27 @@ def test_persistent_and_graph_loops_agree(gs, ctx, sphere_graph, t, K):
         np.testing.assert_allclose(got[m], want[m], rtol=1e-4)
 
 
+def test_node_order_option_gives_the_oracle_results(gs, ctx, sphere_graph):
+    # GS_OPT_NODE_ORDER 0 (decreasing degree inside each bisection part) and 1 (degree classes, then
+    # the reading block, the default) lay the same graph out differently; both give the oracle's
+    # filter and Sinkhorn results (up to summation order)
+    p, g1, Ls = sphere_graph
+    assert gs.gs_get_option(ctx, gs.GS_OPT_NODE_ORDER) == 1
+    gs.gs_set_option(ctx, gs.GS_OPT_NODE_ORDER, 0)
+    try:
+        g0 = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_NODE_ORDER, 1)
+    V = np.random.default_rng(3).random((len(p.X), 32)).astype(np.float32)
+    ref = oracle.heat_apply(Ls, oracle.cheb_coefficients(5.0, 30), V.astype(np.float64))
+    for g in (g0, g1):
+        Y = to_np(gs.gs_heat_apply(ctx, g, 5.0, 30, to_dev(V)))
+        assert_close(Y, ref, HEAT_RTOL, HEAT_ATOL_REL * np.abs(ref).max(), "node order")
+        _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, 5.0, 30, 60)
+    with pytest.raises(gs.GeosinkError):
+        gs.gs_set_option(ctx, gs.GS_OPT_NODE_ORDER, 2)
+
+
 def test_sinkhorn_single_order_filter_matches_oracle(gs, ctx, sphere_graph):
     # K = 1: H = c_0 I + c_1 P, positive for t = 0.5 (I_0(t) > 2 I_1(t)); persistent default path
     p, g, Ls = sphere_graph
