@@ -417,6 +417,22 @@ void launch_tc_reg(gs_ctx* ctx, const float* hi, const float* lo, const float* n
 
 // One warp per query: FP64 direct-difference squared distances of the 32 candidates, in the
 // definition's order (no fused multiply-add), rank by (distance, index), keep the first k.
+// float -> double by moving the bits (exact, as the conversion is): a normal or zero float only
+// widens its exponent and mantissa fields; subnormal, infinite and NaN inputs take the conversion
+// instruction.  Keeps the 2 x d conversions per candidate off the FP64 pipe, which bounds this
+// kernel.
+__device__ __forceinline__ double widen_exact(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned m = u & 0x7fffffu;
+    if (e == 0xffu || (e == 0u && m != 0u)) return (double)f;
+    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                    (e ? (unsigned long long)(e + 896u) << 52 : 0ull) |
+                                    ((unsigned long long)m << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 __global__ void knn_rerank(const float* __restrict__ X, int n, int d, int k,
                            const int* __restrict__ cand, int32_t* __restrict__ idx,
                            float* __restrict__ dist, double* __restrict__ dist64)
@@ -431,15 +447,18 @@ __global__ void knn_rerank(const float* __restrict__ X, int n, int d, int k,
         const float* xq = X + q * d;
         const float* xc = X + (int64_t)c * d;
         for (int i = 0; i < d; ++i) {
-            const double diff = __dsub_rn((double)xq[i], (double)xc[i]);
+            const double diff = __dsub_rn(widen_exact(xq[i]), widen_exact(xc[i]));
             s = __dadd_rn(s, __dmul_rn(diff, diff));
         }
     }
+    // s is +0, positive or +inf (NaN only from NaN coordinates), so the order of the values is the
+    // order of their bit patterns: the rank is taken with integer compares
+    const unsigned long long key = (unsigned long long)__double_as_longlong(s);
     int rank = 0;
     for (int j = 0; j < 32; ++j) {
-        const double sj = __shfl_sync(FULL, s, j);
+        const unsigned long long kj = __shfl_sync(FULL, key, j);
         const int cj = __shfl_sync(FULL, c, j);
-        rank += (sj < s) || (sj == s && cj < c);
+        rank += (kj < key) || (kj == key && cj < c);
     }
     if (rank < k) {
         const double e = sqrt(s);

@@ -445,22 +445,25 @@ __host__ __device__ inline void colour_slice(const uint16_t* lx, int W, unsigned
         }
 }
 
-// One thread per slice, its working arrays in shared memory (a few KB: in local memory they
-// would not stay in L1).
-constexpr int kColourThreads = 8;
+// One slice per warp, worked by its first lane, its working arrays in shared memory (a few KB:
+// in local memory they would not stay in L1).  Slices sharing a warp would serialise their
+// data-dependent path searches; the kernel's time is the slowest slice's.
+constexpr int kColourSlices = 4;  // per block
 
-__global__ void __launch_bounds__(kColourThreads) sell_bank_colour(const int* __restrict__ sptr, int64_t nslices,
-                                                                   const uint16_t* __restrict__ lidx,
-                                                                   unsigned char* __restrict__ step)
+__global__ void __launch_bounds__(32 * kColourSlices) sell_bank_colour(const int* __restrict__ sptr, int64_t nslices,
+                                                                       const uint16_t* __restrict__ lidx,
+                                                                       unsigned char* __restrict__ step)
 {
     extern __shared__ __align__(16) unsigned char c_smem[];
     ColourWork* wk = reinterpret_cast<ColourWork*>(c_smem);
-    const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((threadIdx.x & 31) != 0) return;
+    const int w = threadIdx.x >> 5;
+    const int64_t sl = (int64_t)blockIdx.x * kColourSlices + w;
     if (sl >= nslices) return;
     const int base = sptr[sl];
     const int W = (sptr[sl + 1] - base) / 32;
     if (W < 1 || W > kSchedMaxWidth) return;
-    colour_slice(lidx + base, W, step + base, wk[threadIdx.x]);
+    colour_slice(lidx + base, W, step + base, wk[w]);
 }
 
 // Moves every entry of a slice to its step (from copies of the three arrays; slices too wide for
@@ -637,9 +640,9 @@ gs_status gs_graph_build_xcache(gs_ctx* ctx, gs_graph* g, int blocks, const std:
         cudaMemcpyAsync(v_in, g->sval, sizeof(float) * ne, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(l_in, g->xc_lidx, sizeof(uint16_t) * ne, cudaMemcpyDeviceToDevice, s);
         cudaFuncSetAttribute(sell_bank_colour, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(ColourWork) * kColourThreads));
-        sell_bank_colour<<<(unsigned)((ns + kColourThreads - 1) / kColourThreads), kColourThreads,
-                           sizeof(ColourWork) * kColourThreads, s>>>(g->sptr, ns, l_in, stp);
+                             (int)(sizeof(ColourWork) * kColourSlices));
+        sell_bank_colour<<<(unsigned)((ns + kColourSlices - 1) / kColourSlices), 32 * kColourSlices,
+                           sizeof(ColourWork) * kColourSlices, s>>>(g->sptr, ns, l_in, stp);
         sell_apply_steps<<<(unsigned)((ns + 7) / 8), 256, 0, s>>>(g->sptr, ns, stp, c_in, v_in, l_in, g->scol,
                                                                    g->sval, g->xc_lidx);
         gs_count(ctx, 2);
