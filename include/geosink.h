@@ -148,10 +148,15 @@ gs_status gs_reserve(gs_ctx *ctx, int64_t bytes);
  * loop, whose exchanged values a neighbouring block then stages from fewer memory sectors);
  * 0: decreasing degree only (fastest for the several-column filter and the barycenter, whose row
  * groups then hold rows of equal length).  Same results either way up to summation order. */
+/* GS_OPT_LOOP_REGS: the persistent loop with tagged 4-byte exchange words, where every block of its
+ * partition has at most 672 rows, runs one row per thread and keeps each row's first 16 operator
+ * entries (values and cache indices) in registers for the whole loop, so that only the neighbour
+ * values are read from shared memory there.  1 (default): on; 0: off (all entries read from shared
+ * memory every order, 1024 threads per block).  Bitwise the same results either way. */
 enum { GS_OPT_LOOP = 1, GS_OPT_BARRIER_SELFTEST = 2, GS_OPT_B1_KERNEL = 3, GS_OPT_BLK_KERNEL = 4,
        GS_OPT_KNN_TENSOR = 5, GS_OPT_PERSIST_SMEM_GRAPH = 6, GS_OPT_PERSIST_SYNC = 7,
        GS_OPT_PERSIST_BLOCKS = 8, GS_OPT_TAG_WORD = 9, GS_OPT_CHECK_ARGS = 10, GS_OPT_TILE_LANES = 11,
-       GS_OPT_NODE_ORDER = 12 };
+       GS_OPT_NODE_ORDER = 12, GS_OPT_LOOP_REGS = 13 };
 gs_status gs_set_option(gs_ctx *ctx, int option, int value);
 
 /* Host query of an option.  For GS_OPT_LOOP, GS_OPT_B1_KERNEL and GS_OPT_PERSIST_SYNC left on

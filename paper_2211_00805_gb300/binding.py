@@ -181,6 +181,7 @@ GS_OPT_TAG_WORD = 9
 GS_OPT_CHECK_ARGS = 10
 GS_OPT_TILE_LANES = 11
 GS_OPT_NODE_ORDER = 12
+GS_OPT_LOOP_REGS = 13
 
 
 def gs_set_option(ctx: Context, option: int, value: int):

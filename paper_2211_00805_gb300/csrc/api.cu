@@ -208,6 +208,10 @@ extern "C" gs_status gs_set_option(gs_ctx* ctx, int option, int value)
         ctx->node_order = value;
         return GS_OK;
     }
+    if (option == GS_OPT_LOOP_REGS && (value == 0 || value == 1)) {
+        ctx->loop_regs = value;
+        return GS_OK;
+    }
     if (option == GS_OPT_BLK_KERNEL && (value == 0 || (value >= 2 && value <= 5) || value == 8 || value == 9)) {
         ctx->blk_kernel = value;
         return GS_OK;
@@ -236,6 +240,7 @@ extern "C" gs_status gs_get_option(const gs_ctx* ctx, int option, int* value)
         case GS_OPT_CHECK_ARGS: *value = ctx->check_args; return GS_OK;
         case GS_OPT_TILE_LANES: *value = ctx->lanes_override; return GS_OK;
         case GS_OPT_NODE_ORDER: *value = ctx->node_order; return GS_OK;
+        case GS_OPT_LOOP_REGS: *value = ctx->loop_regs; return GS_OK;
         default: return GS_ERR_ARG;
     }
 }

@@ -104,6 +104,7 @@ struct gs_ctx {
                                    // SM (1: 1024 threads each, 2: 512 threads each)
     int check_args = 1;            // device-side checks of marginals and barycenter weights (1 on)
     int node_order = 1;            // inside each bisection part: 1 degree classes + reader, 0 degree
+    int loop_regs = 1;             // persistent tagged loop: rows' first steps in registers where blocks fit
     int lanes_override = 0;        // autotuner trials: lanes per row (B > 1) / threads per row (B == 1)
     std::vector<TuneRecord> tune_log;  // gs_autotune decisions by (n, nnz, B, K)
     int64_t launches = 0;          // kernels enqueued (graph replays count their nodes)

@@ -18,6 +18,8 @@
 #include <algorithm>
 
 #include "cache_slices.cuh"
+#include <type_traits>
+
 #include "gs_internal.cuh"
 #include "sell_row.cuh"
 
@@ -602,7 +604,91 @@ __device__ __forceinline__ unsigned tag_of(unsigned long long w)
     return W4 ? (unsigned)(w & 1ull) : (unsigned)(w >> 32);
 }
 
-template <int RPT, int NT, bool W4, bool GROUP>
+// A row's first WR steps of the sliced ELL held in registers for the whole loop (the operator does
+// not change between orders): values wv[t], and local cache indices paired two steps to a word as
+// in the shared-memory table (an odd last step alone in the low half).  Loaded once per launch.
+template <int WR>
+__device__ __forceinline__ void load_row_regs(const uint16_t* slice_lidx, int r, const float* vp, int width,
+                                              float (&wv)[WR], unsigned (&lp)[WR / 2])
+{
+    const uint32_t* lp2 = reinterpret_cast<const uint32_t*>(slice_lidx) + r;
+#pragma unroll
+    for (int q = 0; q < WR / 2; ++q) {
+        const int t = 2 * q;
+        unsigned pr = 0u;
+        if (t + 1 < width) pr = lp2[q * GS_SELL_C];
+        else if (t < width) pr = (unsigned)slice_lidx[t * GS_SELL_C + r];
+        lp[q] = pr;
+        wv[t] = t < width ? vp[t * GS_SELL_C] : 0.f;
+        wv[t + 1] = t + 1 < width ? vp[(t + 1) * GS_SELL_C] : 0.f;
+    }
+}
+
+// The cached row sum of gs_sell_dot_cached (same products, same two accumulators, same order:
+// blocks of eight steps, then pairs, then an odd last step) with steps below WR taken from
+// registers and only the neighbour values read from shared memory there.  Every branch depends
+// on the slice width alone, so it is uniform across the warp.
+template <int WR>
+__device__ __forceinline__ float row_dot_regs(const float (&wv)[WR], const unsigned (&lp)[WR / 2],
+                                              const uint16_t* slice_lidx, int r, const float* vp, int width,
+                                              const float* xc)
+{
+    static_assert(WR % 8 == 0, "register steps come in blocks of eight");
+    const uint32_t* lp2 = reinterpret_cast<const uint32_t*>(slice_lidx) + r;
+    const int full8 = width & ~7;
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int jb = 0; jb < WR; jb += 8) {
+        if (jb < full8) {
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                const unsigned pr = lp[(jb + u) >> 1];
+                s0 = fmaf(wv[jb + u], xc[pr & 0xffffu], s0);
+                s1 = fmaf(wv[jb + u + 1], xc[pr >> 16], s1);
+            }
+        }
+    }
+    int j = WR;
+    for (; j + 8 <= width; j += 8) {
+        float w[8], x[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const unsigned pr = lp2[((j >> 1) + q) * GS_SELL_C];
+            w[2 * q] = vp[(j + 2 * q) * GS_SELL_C];
+            w[2 * q + 1] = vp[(j + 2 * q + 1) * GS_SELL_C];
+            x[2 * q] = xc[pr & 0xffffu];
+            x[2 * q + 1] = xc[pr >> 16];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            s0 = fmaf(w[u], x[u], s0);
+            s1 = fmaf(w[u + 1], x[u + 1], s1);
+        }
+    }
+    if (full8 < WR) {  // the tail (under eight steps) lies in registers: pairs, then an odd step
+#pragma unroll
+        for (int t = 0; t + 2 <= WR; t += 2)
+            if (t >= full8 && t + 2 <= width) {
+                const unsigned pr = lp[t >> 1];
+                s0 = fmaf(wv[t], xc[pr & 0xffffu], s0);
+                s0 = fmaf(wv[t + 1], xc[pr >> 16], s0);
+            }
+#pragma unroll
+        for (int t = 0; t < WR; t += 2)
+            if ((width & 1) && t + 1 == width) s0 = fmaf(wv[t], xc[lp[t >> 1] & 0xffffu], s0);
+    } else {
+        j = full8;
+        for (; j + 2 <= width; j += 2) {
+            const unsigned pr = lp2[(j >> 1) * GS_SELL_C];
+            s0 = fmaf(vp[j * GS_SELL_C], xc[pr & 0xffffu], s0);
+            s0 = fmaf(vp[(j + 1) * GS_SELL_C], xc[pr >> 16], s0);
+        }
+        if (j < width) s0 = fmaf(vp[j * GS_SELL_C], xc[slice_lidx[j * GS_SELL_C + r]], s0);
+    }
+    return s0 + s1;
+}
+
+template <int RPT, int NT, bool W4, bool GROUP, int WR = 0, int UL = 8>
 __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
 {
     __shared__ int s_ok;
@@ -650,6 +736,14 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
             else st_relaxed_u64(p.tagged + row, pack_tagged(xo[j], 1u));
         }
     }
+    static_assert(WR == 0 || RPT == 1, "register-resident rows: one row per thread");
+    using Word = typename std::conditional<W4, unsigned, unsigned long long>::type;  // an exchange word
+    constexpr int WRA = WR > 0 ? WR : 8;
+    float wv[WRA];
+    unsigned lp[WRA / 2];
+    if (WR > 0)
+        load_row_regs<WRA>(lidx_s + off[0] - (threadIdx.x & (GS_SELL_C - 1)), threadIdx.x & (GS_SELL_C - 1),
+                           sval_s + off[0], width[0], wv, lp);
     unsigned stage = 0;
     int rslot = 0, wslot = 1;  // slots of stage - 1 and stage (mod 3) inside the order loop
     const float c0 = p.coef[0];
@@ -665,34 +759,34 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
                 // stage s - 1 carries tag s (8-byte words) or parity (s - 1) & 1 (4-byte words);
                 // the self-test waits for a tag no word will carry
                 const unsigned want = W4 ? (p.selftest ? 2u : ((stage - 1u) & 1u)) : stage + extra;
-                // issue up to 8 loads per thread before checking any tag; words not yet carrying
+                // issue up to UL loads per thread before checking any tag; words not yet carrying
                 // the wanted tag are then re-read together (GROUP: each retry round costs one round
                 // trip) or one at a time in list order, each stored as soon as it is ready (fewer
                 // loads in flight while the owners have not published: the faster form where the
                 // exchange dominates the order)
-                for (int i0 = threadIdx.x; i0 < ucnt; i0 += 8 * NT) {
-                    unsigned long long w[8];
+                for (int i0 = threadIdx.x; i0 < ucnt; i0 += UL * NT) {
+                    Word w[UL];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < UL; ++u) {
                         const int i = i0 + u * NT;
-                        w[u] = i >= ucnt ? 0ull : (W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i])
-                                                       : ld_relaxed_u64(src + ucol_s[i]));
+                        w[u] = i >= ucnt ? Word(0) : (W4 ? (Word)ld_relaxed_u32(src4 + ucol_s[i])
+                                                        : (Word)ld_relaxed_u64(src + ucol_s[i]));
                     }
                     if (GROUP) {
                         unsigned pending = 0;
 #pragma unroll
-                        for (int u = 0; u < 8; ++u)
+                        for (int u = 0; u < UL; ++u)
                             if (i0 + u * NT < ucnt && tag_of<W4>(w[u]) != want) pending |= 1u << u;
                         if (pending) {
                             const long long t0 = clock64();
                             do {
 #pragma unroll
-                                for (int u = 0; u < 8; ++u)
+                                for (int u = 0; u < UL; ++u)
                                     if (pending & (1u << u))
-                                        w[u] = W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i0 + u * NT])
-                                                  : ld_relaxed_u64(src + ucol_s[i0 + u * NT]);
+                                        w[u] = W4 ? (Word)ld_relaxed_u32(src4 + ucol_s[i0 + u * NT])
+                                                  : (Word)ld_relaxed_u64(src + ucol_s[i0 + u * NT]);
 #pragma unroll
-                                for (int u = 0; u < 8; ++u)
+                                for (int u = 0; u < UL; ++u)
                                     if ((pending & (1u << u)) && tag_of<W4>(w[u]) == want) pending &= ~(1u << u);
                                 if (pending && clock64() - t0 > p.budget) {
                                     atomicOr(p.flags, GS_FLAG_TIMEOUT);
@@ -702,20 +796,20 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
                             } while (pending);
                         }
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
+                        for (int u = 0; u < UL; ++u) {
                             const int i = i0 + u * NT;
                             if (i < ucnt) xc[i] = __uint_as_float((unsigned)w[u]);
                         }
                     } else {
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
+                        for (int u = 0; u < UL; ++u) {
                             const int i = i0 + u * NT;
                             if (i >= ucnt) break;
                             if (tag_of<W4>(w[u]) != want) {
                                 const long long t0 = clock64();
                                 do {
-                                    w[u] = W4 ? (unsigned long long)ld_relaxed_u32(src4 + ucol_s[i])
-                                              : ld_relaxed_u64(src + ucol_s[i]);
+                                    w[u] = W4 ? (Word)ld_relaxed_u32(src4 + ucol_s[i])
+                                              : (Word)ld_relaxed_u64(src + ucol_s[i]);
                                     if (clock64() - t0 > p.budget) {
                                         atomicOr(p.flags, GS_FLAG_TIMEOUT);
                                         s_ok = 0;
@@ -734,8 +828,11 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
                 for (int j = 0; j < RPT; ++j) {
                     const int row = r0 + (int)threadIdx.x + j * NT;
                     if (row >= r1) continue;
-                    const float s = gs_sell_dot_cached(lidx_s + off[j] - (threadIdx.x & (GS_SELL_C - 1)),
-                                                       threadIdx.x & (GS_SELL_C - 1), sval_s + off[j], width[j], xc);
+                    const float s =
+                        WR > 0 ? row_dot_regs<WRA>(wv, lp, lidx_s + off[j] - (threadIdx.x & (GS_SELL_C - 1)),
+                                                   threadIdx.x & (GS_SELL_C - 1), sval_s + off[j], width[j], xc)
+                               : gs_sell_dot_cached(lidx_s + off[j] - (threadIdx.x & (GS_SELL_C - 1)),
+                                                    threadIdx.x & (GS_SELL_C - 1), sval_s + off[j], width[j], xc);
                     float tk, acc;
                     if (k == 1) {
                         tk = s;
@@ -773,6 +870,15 @@ __global__ void __launch_bounds__(NT) sinkhorn_tagged(const PersistArgs p)
 }
 
 constexpr int kSmemGraphMax = 200 * 1024;  // shared-memory budget for the resident graph slice
+// Register-resident form of the tagged loop: blocks of up to kRegThreads rows (21 slices), one row
+// per thread.  With 21 warps one SM sub-partition holds six of them, so a thread may hold 80
+// registers; the first kRegSteps steps of its row stay in registers (24 steps spill).  Staging
+// issues kRegLoads loads per thread per round (6,720 distinct columns in one round trip; 5,503 is
+// the largest block of the 100k-point manifold graph, whose second round trip cost more than the
+// registers saved).
+constexpr int kRegThreads = 672;
+constexpr int kRegSteps = 16;
+constexpr int kRegLoads = 10;
 
 template <int NT, bool W4, bool GROUP>
 void (*tagged_kernel(int rpt))(PersistArgs)
@@ -824,6 +930,13 @@ gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
             const bool group = gs_persist_sync_setting(ctx, g) != 4;
             void (*kern)(PersistArgs) = bps == 1 ? gather_cache_kernel<kThreads>(tagged, w4, group, rpt)
                                                  : gather_cache_kernel<kThreads / 2>(tagged, w4, group, rpt);
+            int nt_launch = nt;
+            if (bps == 1 && tagged && w4 && ctx->loop_regs && g->xc_rpb <= kRegThreads) {
+                // one row per thread, each row's first kRegSteps steps in registers
+                kern = group ? sinkhorn_tagged<1, kRegThreads, true, true, kRegSteps, kRegLoads>
+                             : sinkhorn_tagged<1, kRegThreads, true, false, kRegSteps, kRegLoads>;
+                nt_launch = kRegThreads;
+            }
             if (tagged && !w4)  // 8-byte words: tag 0 is no stage
                 cudaMemsetAsync(args.tagged, 0, sizeof(unsigned long long) * 3 * (size_t)args.n, ctx->stream);
             if (tagged && w4) {  // 4-byte words: slot k must not start with stage k's parity
@@ -835,11 +948,11 @@ gs_status launch_persistent(gs_ctx* ctx, const gs_graph* g, PersistArgs& args)
             }
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cache_smem);
             int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, cache_smem) == cudaSuccess &&
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt_launch, cache_smem) == cudaSuccess &&
                 per_sm >= bps) {
                 ctx->barrier_selftest = 0;
                 void* params[] = {&args};
-                const cudaError_t e = cudaLaunchCooperativeKernel((void*)kern, dim3(g->xc_blocks), dim3(nt),
+                const cudaError_t e = cudaLaunchCooperativeKernel((void*)kern, dim3(g->xc_blocks), dim3(nt_launch),
                                                                   params, cache_smem, ctx->stream);
                 if (e == cudaSuccess) {
                     gs_count(ctx, 1);

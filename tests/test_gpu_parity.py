@@ -415,6 +415,43 @@ def test_node_order_option_gives_the_oracle_results(gs, ctx, sphere_graph):
         gs.gs_set_option(ctx, gs.GS_OPT_NODE_ORDER, 2)
 
 
+def test_register_rows_loop_matches_shared_memory_form_and_oracle(gs, ctx):
+    # GS_OPT_LOOP_REGS: the tagged 4-byte loop with each row's first 16 entries in registers sums
+    # in the shared-memory form's order, so both give bitwise the same u, v and distance (both
+    # staging forms); rows here run from under 8 to over 40 entries, odd and even widths, so the
+    # register blocks, the register tail and the shared-memory continuation all take part
+    p = W.manifold_pair(n=6000, iters=80)
+    g = gs.gs_build_graph(ctx, to_dev(p.X), p.k)
+    Ls, ex = oracle.build_graph(p.X.astype(np.float64), p.k)
+    deg = np.diff(ex["rowptr"])
+    assert deg.max() > 32 and deg.min() < 16 and (deg % 2 == 1).any()
+    assert gs.gs_get_option(ctx, gs.GS_OPT_LOOP_REGS) == 1
+    gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 0)
+    gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
+    gs.gs_set_option(ctx, gs.GS_OPT_TAG_WORD, 4)
+    out = {}
+    try:
+        for sync in (2, 4):
+            gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, sync)
+            for regs in (1, 0):
+                gs.gs_set_option(ctx, gs.GS_OPT_LOOP_REGS, regs)
+                u, v, d, _ = gs.gs_sinkhorn(ctx, g, to_dev(p.a), to_dev(p.b), p.t, p.K, p.iters)
+                gs.gs_sync(ctx)
+                out[(sync, regs)] = (to_np(u), to_np(v), to_np(d))
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP_REGS, 1)
+        gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 2)
+        _check_sinkhorn(gs, ctx, g, Ls, p.a, p.b, p.t, p.K, p.iters)
+    finally:
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP_REGS, 1)
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP, 2)
+        gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 3)
+    for sync in (2, 4):
+        for i in range(3):
+            np.testing.assert_array_equal(out[(sync, 1)][i], out[(sync, 0)][i], err_msg=f"sync {sync}")
+    with pytest.raises(gs.GeosinkError):
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP_REGS, 2)
+
+
 def test_sinkhorn_single_order_filter_matches_oracle(gs, ctx, sphere_graph):
     # K = 1: H = c_0 I + c_1 P, positive for t = 0.5 (I_0(t) > 2 I_1(t)); persistent default path
     p, g, Ls = sphere_graph
