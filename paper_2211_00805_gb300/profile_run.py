@@ -66,6 +66,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the case's point count")
     ap.add_argument("--bps", default="1", help="with --sinkhorn: ','-separated GS_OPT_PERSIST_BLOCKS values "
                     "(one graph built per value; timings interleaved)")
+    ap.add_argument("--loop-regs", type=int, default=1,
+                    help="with --sinkhorn: GS_OPT_LOOP_REGS (1: rows' first entries in registers, 0: off)")
     ap.add_argument("--knn-modes", default="2,1,0", help="with --knn: GS_OPT_KNN_TENSOR values to time")
     ap.add_argument("--knn", action="store_true",
                     help="time the kNN graph builder (tensor-core and CUDA-core screens) instead")
@@ -134,6 +136,7 @@ def main():
         configs = [(bps,) + tuple(int(x) for x in c.split(",")) for c in args.configs.split(";")
                    for bps in graphs]
         times = {cfg: [] for cfg in configs}
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP_REGS, args.loop_regs)
         for rnd in range(4):
             for bps, mode, var, sg, sy in configs:
                 g = graphs[bps]
@@ -154,7 +157,7 @@ def main():
         for (bps, mode, var, sg, sy), ts in times.items():
             ms = sorted(ts)[len(ts) // 2]
             print(json.dumps({"case": args.case, "sinkhorn_loop_mode": mode, "b1_variant": var,
-                              "smem_graph": sg, "sync": sy, "bps": bps,
+                              "smem_graph": sg, "sync": sy, "bps": bps, "loop_regs": args.loop_regs,
                               "iters": args.sinkhorn, "ms_median": ms,
                               "iters_per_s": args.sinkhorn / (ms / 1e3),
                               "order_us": ms * 1e3 / (2 * c["K"] * args.sinkhorn)}), flush=True)
@@ -162,6 +165,7 @@ def main():
         gs.gs_set_option(ctx, gs.GS_OPT_B1_KERNEL, 0)
         gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SMEM_GRAPH, 2)
         gs.gs_set_option(ctx, gs.GS_OPT_PERSIST_SYNC, 1)
+        gs.gs_set_option(ctx, gs.GS_OPT_LOOP_REGS, 1)
     if args.log_sinkhorn and c["B"] == 1:
         a = torch.full((c["n"],), 1.0 / c["n"], device=dev)
         it = args.log_sinkhorn
