@@ -42,6 +42,7 @@ HBM_CASES = {
                          tag="order_blk_manifold500k_B64", node_order=1),
 }
 L2_FLUSH_BYTES = 256 << 20
+EXCHANGE_FLOOR_US = 1.446  # µs per Chebyshev order, 100k-point manifold graph (see roofline)
 
 
 def parse():
@@ -445,7 +446,13 @@ def run_ours(args, rank, world, local_rank):
         tr = ncu_traffic("sinkhorn_persistent_manifold100k_500it", "persist.cu")
         name = {0: "sinkhorn_persistent", 1: "sinkhorn_neighbour_sync", 2: "sinkhorn_tagged"}[tuned["persist_sync"]]
         kern = {"kernel": f"{name} (whole 500-iteration loop, one cooperative launch)",
-                "bytes_per_launch": 2 * cfg["iters"] * per_apply, "launch_us": sink_s * 1e6}
+                "bytes_per_launch": 2 * cfg["iters"] * per_apply, "launch_us": sink_s * 1e6,
+                # the loop's own floor: the same launch with each row's sum replaced by one staged
+                # neighbour value (staging, tagged words and both block barriers kept), 500
+                # iterations of this workload timed with CUDA events on a GB300; that copy skips
+                # the arithmetic, so it is not part of the library and not re-timed here
+                "exchange_floor_us_per_order": EXCHANGE_FLOOR_US,
+                "frac_of_exchange_floor": EXCHANGE_FLOOR_US / (sink_s / orders * 1e6)}
     else:
         tr = ncu_traffic("order_b1_manifold100k")
         kern = {"kernel": "fused Chebyshev order kernel (B=1), one launch per order",
