@@ -419,8 +419,8 @@ void launch_tc_reg(gs_ctx* ctx, const float* hi, const float* lo, const float* n
 // definition's order (no fused multiply-add), rank by (distance, index), keep the first k.
 // float -> double by moving the bits (exact, as the conversion is): a normal or zero float only
 // widens its exponent and mantissa fields; subnormal, infinite and NaN inputs take the conversion
-// instruction.  Keeps the 2 x d conversions per candidate off the FP64 pipe, which bounds this
-// kernel.
+// instruction.  The rerank is bound by its double-precision instructions; this and the integer
+// rank compares below took it from 1.94 to 1.56 ms at n = 100k (the two not measured apart).
 __device__ __forceinline__ double widen_exact(float f)
 {
     const unsigned u = __float_as_uint(f);
