@@ -434,34 +434,10 @@ def run_ours(args, rank, world, local_rank):
     total_ms = max_over_ranks(total_ms, world, dev)
     value = cfg["iters"] * args.steps * world / (total_ms / 1e3)
 
-    # roofline of the dominant kernel of the step: the Sinkhorn loop's Chebyshev orders (B = 1),
-    # either one persistent launch per loop (loop mode 0) or one launch per order (mode 1)
-    K = cfg["K"]
-    per_apply = apply_bytes(n, nnz, K, 1, last_streams=6)  # gather, T_{K-2}, y, num, out, xnext
-    orders = 2 * K * cfg["iters"]
+    # roofline of the dominant kernel of the step: the Sinkhorn loop's Chebyshev orders (B = 1)
     sink_s = statistics.mean(sink_ms) / 1e3
-    achieved = 2 * cfg["iters"] * per_apply / sink_s / 1e9
     peak, peak_kind = measured_peaks()
-    if tuned["loop_mode"] == 0:
-        tr = ncu_traffic("sinkhorn_persistent_manifold100k_500it", "persist.cu")
-        name = {0: "sinkhorn_persistent", 1: "sinkhorn_neighbour_sync", 2: "sinkhorn_tagged"}[tuned["persist_sync"]]
-        kern = {"kernel": f"{name} (whole 500-iteration loop, one cooperative launch)",
-                "bytes_per_launch": 2 * cfg["iters"] * per_apply, "launch_us": sink_s * 1e6,
-                # the loop's own floor: the same launch with each row's sum replaced by one staged
-                # neighbour value (staging, tagged words and both block barriers kept), 500
-                # iterations of this workload timed with CUDA events on a GB300; that copy skips
-                # the arithmetic, so it is not part of the library and not re-timed here
-                "exchange_floor_us_per_order": EXCHANGE_FLOOR_US,
-                "frac_of_exchange_floor": EXCHANGE_FLOOR_US / (sink_s / orders * 1e6)}
-    else:
-        tr = ncu_traffic("order_b1_manifold100k")
-        kern = {"kernel": "fused Chebyshev order kernel (B=1), one launch per order",
-                "bytes_per_launch": per_apply / K, "launch_us": sink_s / orders * 1e6}
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": tr, **kern,
-                "order_us": sink_s / orders * 1e6,
-                "peak_kind": f"{peak_kind} hbm_gbs",
-                "note": "working set (~19 MB) is L2-resident; see spmm_hbm for the HBM-bound case"}
+    roofline = loop_roofline(n, nnz, cfg["K"], cfg["iters"], sink_s, tuned, peak, peak_kind)
 
     extras = {}
     if not args.no_extras:
@@ -540,6 +516,35 @@ def run_ours(args, rank, world, local_rank):
         }
         line.update(extras)
         print(json.dumps(line), flush=True)
+
+
+def loop_roofline(n, nnz, K, iters, sink_s, tuned, peak, peak_kind):
+    """The `roofline` object of the Sinkhorn loop (B = 1) run in `sink_s` seconds: one persistent
+    launch per loop (loop mode 0) or one launch per Chebyshev order (mode 1).  `achieved` counts the
+    byte model of every order; the persistent form adds its fraction of the exchange floor."""
+    per_apply = apply_bytes(n, nnz, K, 1, last_streams=6)  # gather, T_{K-2}, y, num, out, xnext
+    orders = 2 * K * iters
+    order_us = sink_s / orders * 1e6
+    achieved = 2 * iters * per_apply / sink_s / 1e9
+    if tuned["loop_mode"] == 0:
+        tr = ncu_traffic("sinkhorn_persistent_manifold100k_500it", "persist.cu")
+        name = {0: "sinkhorn_persistent", 1: "sinkhorn_neighbour_sync", 2: "sinkhorn_tagged"}[tuned["persist_sync"]]
+        kern = {"kernel": f"{name} (whole {iters}-iteration loop, one cooperative launch)",
+                "bytes_per_launch": 2 * iters * per_apply, "launch_us": sink_s * 1e6,
+                # the loop's own floor: the same launch with each row's sum replaced by one staged
+                # neighbour value (staging, tagged words and both block barriers kept), 500
+                # iterations of this workload timed with CUDA events on a GB300; that copy skips
+                # the arithmetic, so it is not part of the library and not re-timed here
+                "exchange_floor_us_per_order": EXCHANGE_FLOOR_US,
+                "frac_of_exchange_floor": EXCHANGE_FLOOR_US / order_us}
+    else:
+        tr = ncu_traffic("order_b1_manifold100k")
+        kern = {"kernel": "fused Chebyshev order kernel (B=1), one launch per order",
+                "bytes_per_launch": per_apply / K, "launch_us": order_us}
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": tr, **kern, "order_us": order_us,
+            "peak_kind": f"{peak_kind} hbm_gbs",
+            "note": "working set (~19 MB) is L2-resident; see spmm_hbm for the HBM-bound case"}
 
 
 def hbm_case(gs, ctx, dev, stream, peak, peak_kind, c, reps=5):

@@ -82,3 +82,24 @@ def test_both_arms_print_the_same_config():
     c = bench.static_config(1, 2005410)
     assert c["n"] == bench.WORKLOAD["n"] and c["iters"] == bench.WORKLOAD["iters"] and c["nnz"] == 2005410
     assert not any(k.endswith("_ms") for k in c)  # no timings in the config
+
+
+def test_loop_roofline_persistent_form_counts_every_order_and_its_floor():
+    # 100k rows, 2,005,410 nonzeros, K = 30, 500 iterations in 61.5 ms: the byte model of the
+    # 30,000 orders over the loop's time, against the peak; the floor fraction from the per-order time
+    n, nnz, K, iters, s = 100_000, 2_005_410, 30, 500, 0.0615
+    r = bench.loop_roofline(n, nnz, K, iters, s, {"loop_mode": 0, "persist_sync": 2}, 6800.3, "measured")
+    per_apply = bench.apply_bytes(n, nnz, K, 1, last_streams=6)
+    assert r["bytes_per_launch"] == 2 * iters * per_apply
+    assert r["achieved"] == pytest.approx(2 * iters * per_apply / s / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6800.3)
+    assert r["order_us"] == pytest.approx(s / (2 * K * iters) * 1e6)
+    assert r["frac_of_exchange_floor"] == pytest.approx(bench.EXCHANGE_FLOOR_US / r["order_us"])
+    assert 0 < r["frac_of_exchange_floor"] < 1  # a loop cannot beat its own exchange
+    assert r["kernel"].startswith("sinkhorn_tagged") and r["unit"] == "GB/s" and r["bound"] == "hbm"
+
+
+def test_loop_roofline_per_order_form_has_no_floor():
+    r = bench.loop_roofline(100_000, 2_005_410, 30, 500, 0.3, {"loop_mode": 1, "persist_sync": 2}, 6800.3, "measured")
+    assert "frac_of_exchange_floor" not in r
+    assert r["launch_us"] == pytest.approx(r["order_us"])
