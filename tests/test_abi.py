@@ -58,6 +58,26 @@ def test_every_entry_point_is_documented_and_compute_calls_cite_their_passage():
             assert cite.search(doc), f"{name}: cites no passage of the paper"
 
 
+def header_constants():
+    """Every `GS_NAME = value` of the header's enums (status codes, option numbers)."""
+    txt = open(os.path.join(ROOT, "include", "geosink.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(GS_[A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+
+
+def test_binding_constants_match_the_header_enums():
+    # a caller reaching the library through the binding must pass the header's option numbers and
+    # read its status codes: every status and option the header defines has the same value there
+    from paper_2211_00805_gb300 import binding
+    consts = header_constants()
+    assert "GS_OK" in consts and "GS_OPT_LOOP_REGS" in consts
+    for name, value in consts.items():
+        if name.startswith(("GS_OPT_", "GS_OK", "GS_ERR_")):
+            assert getattr(binding, name) == value, name
+    assert {v: k for k, v in binding.STATUS.items()} == {k: v for k, v in consts.items()
+                                                         if k == "GS_OK" or k.startswith("GS_ERR_")}
+
+
 def test_binding_wraps_every_symbol(built):
     from paper_2211_00805_gb300 import binding
     assert sorted(binding.SIGNATURES) == header_symbols()
