@@ -163,6 +163,27 @@ def test_barycenter_fixed_point_marginals(bary_setup):
     assert np.max(np.abs(Vs * H(Ws) - mu[:, None])) < 1e-8 * mu.max()
 
 
+def test_barycenter_fixed_point_marginals_with_vertex_weights(bary_setup):
+    # with vertex weights a the inputs are densities of equal weighted mass sum(a mu_i); at
+    # convergence w_i (H(a v_i)) = mu_i and v_i (H(a w_i)) = mu* for every i, with a inside both
+    # filter inputs, and mu* keeps that weighted mass
+    X, Ls, Ld, M = bary_setup
+    t, K = 2.0, 30
+    b = oracle.cheb_coefficients(t, K)
+    a = np.random.default_rng(12).uniform(0.7, 1.3, len(X))
+    Mw = M / (a @ M)
+    alpha = np.array([0.5, 0.3, 0.2])
+    mu, Vs = oracle.barycenter(Ls, b, Mw, alpha, 600, a=a, return_state=True)
+    H = lambda x: oracle.heat_apply(Ls, b, x)  # noqa: E731
+    Ws = Mw / H(a[:, None] * Vs)
+    assert np.max(np.abs(Ws * H(a[:, None] * Vs) - Mw)) < 1e-14 * Mw.max()
+    assert np.max(np.abs(Vs * H(a[:, None] * Ws) - mu[:, None])) < 1e-8 * mu.max()
+    assert a @ mu == pytest.approx(1.0, rel=1e-10)
+    # and the weights matter: the unweighted fixed point of the same columns is another measure
+    mu1 = oracle.barycenter(Ls, b, Mw, alpha, 600)
+    assert np.max(np.abs(mu1 - mu)) > 1e-3 * mu.max()
+
+
 # ------------------------------------------------------------------------------ reverse mode
 def _central_fd(f, x, i, h):
     xp, xm = x.copy(), x.copy()
@@ -217,6 +238,30 @@ def test_barycenter_grad_matches_finite_differences(bary_setup):
         fd = _central_fd(J_of, alpha, i, 1e-5)
         assert galpha[i] == pytest.approx(fd, rel=1e-5)
     for i in (0, 77, 150):
+        fd = _central_fd(lambda s: J_of(alpha, s), src, i, 1e-4 * src[i])
+        assert gsrc[i] == pytest.approx(fd, rel=1e-6, abs=1e-9 * abs(gsrc).max())
+
+
+def test_barycenter_grad_with_vertex_weights_matches_finite_differences(bary_setup):
+    # the same composition with vertex weights a in every filter input (barycenter and Algorithm 1)
+    X, Ls, Ld, M = bary_setup
+    t, K = 2.0, 20
+    b = oracle.cheb_coefficients(t, K)
+    a = np.random.default_rng(13).uniform(0.7, 1.3, len(X))
+    alpha = np.array([0.2, 0.5, 0.3])
+    src = W.vmf_bump(X, np.array([0.0, 1.0, 0.0]), 3.0).astype(np.float64)
+    src /= src.sum()
+    J, gsrc, galpha = oracle.barycenter_distance_grad(Ls, b, src, M, alpha, t, 12, 15, a=a)
+
+    def J_of(al, s=src):
+        mu = oracle.barycenter(Ls, b, M, al, 12, a=a)
+        return oracle.sinkhorn(Ls, b, s, mu, t, 15, a=a)["W2"]
+
+    assert J == pytest.approx(J_of(alpha), rel=1e-13)
+    for i in range(3):  # the central difference's O(h^2) error is 1.4e-5 at h = 1e-5 for alpha_3
+        fd = _central_fd(J_of, alpha, i, 1e-6)
+        assert galpha[i] == pytest.approx(fd, rel=2e-6)
+    for i in (3, 90, 171):
         fd = _central_fd(lambda s: J_of(alpha, s), src, i, 1e-4 * src[i])
         assert gsrc[i] == pytest.approx(fd, rel=1e-6, abs=1e-9 * abs(gsrc).max())
 
