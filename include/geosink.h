@@ -375,7 +375,9 @@ gs_status gs_sinkhorn_log(gs_ctx *ctx, const gs_graph *g, const float *a, const 
  * d_i <- v_i * p_K(vol * w_i); mu <- prod_i d_i^alpha_i; v_i <- v_i * mu / d_i }.  All m
  * distributions move through the filter as one [n, m] block; the geometric mean is a log-sum
  * accumulated in FP64 inside the last Chebyshev order.
- *   M      : [n, m] input distributions (column i is mu_i)
+ *   M      : [n, m] input distributions (column i is mu_i), non-negative, of equal mass
+ *            sum(vol * mu_i) (not checked: with unequal masses the iteration has no fixed point
+ *            and mu depends on `iters`); the barycenter keeps that mass
  *   alpha  : [m] double weights (device), >= 0, summing to 1 (checked on the device, see
  *            GS_OPT_CHECK_ARGS)
  *   vol    : [n] vertex weights or NULL
