@@ -322,6 +322,28 @@ def test_barycenter_matches_oracle(gs, ctx, m):
     assert_close(to_np(V), Vref, 1e-3, 1e-6 * np.abs(Vref).max(), f"v_i m={m}")
 
 
+@pytest.mark.parametrize("m", [3, 32])
+def test_barycenter_with_vertex_weights_matches_oracle(gs, ctx, m):
+    # vertex weights enter both filter inputs of every iteration (vol v_i, vol w_i); the inputs
+    # are densities of equal weighted mass sum(vol mu_i); one-column-per-lane (m = 3) and float4
+    # row-group (m = 32) kernels
+    cfg = W.clusters_barycenter(n=4000, m=m, iters=30)
+    X = cfg["X"]
+    vol = np.random.default_rng(40 + m).uniform(0.7, 1.3, len(X)).astype(np.float32)
+    M = cfg["M"][:, :m].astype(np.float64)
+    M = (M / (vol.astype(np.float64) @ M)).astype(np.float32)
+    alpha = np.random.default_rng(m).dirichlet(np.ones(m))
+    g = gs.gs_build_graph(ctx, to_dev(X), cfg["k"])
+    Ls, ex = oracle.build_graph(X.astype(np.float64), cfg["k"])
+    t, K = 10.0, 40
+    mu = to_np(gs.gs_barycenter(ctx, g, to_dev(M), to_dev(alpha, torch.float64), t, K, cfg["iters"],
+                                vol=to_dev(vol)))
+    gs.gs_sync(ctx)
+    ref = oracle.barycenter(Ls, oracle.cheb_coefficients(t, K), M.astype(np.float64), alpha, cfg["iters"],
+                            a=vol.astype(np.float64))
+    assert_close(mu, ref, 1e-4, 1e-6 * ref.max(), f"mu m={m}, vertex weights")
+
+
 # ------------------------------------------------------------------------- loop modes, faults
 def _broad_pair(p):
     # a broad bump (vMF, kappa = 1) and a mild tilt of it: with the one- and two-hop kernels of
